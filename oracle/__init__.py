@@ -1,0 +1,333 @@
+"""FP64 CPU oracle of the JABBA symbolization path (arXiv 2401.00109).
+
+TEST INFRASTRUCTURE: only the tests, `__graft_entry__.smoke()` and the CPU
+baseline leg of `bench.py` use this package.  The product (the CUDA library and
+its binding in `paper_2401_00109_gb300`) never imports it, and it imports
+nothing from the product.  The arithmetic lives in `jabba_oracle.c` (plain C,
+built without fused multiply-add or fast-math); this module only marshals
+numpy arrays through ctypes.
+
+Functions follow the paper's steps (section in brackets):
+  domains            Alg. 1 Phase I, Sec. 4.1.1
+  compress           Eq. 1, Alg. 1 Phase II, Sec. 4.1.2-4.1.3
+  sigma              Eq. 4 (normalisation by the standard deviations)
+  greedy             Sec. 3.2 greedy aggregation with the Sec. 5 pruning rule
+  local_aggregate    Sec. 5 Stage I, one block per domain
+  merge              Sec. 5 Stage II, merge of the local groups
+  symbolize          Sec. 5 label propagation
+  reconstruct        Sec. 3.3 inverse digitization, quantization, inverse compression
+  mse                Sec. 3.3 reconstruction error
+  reconstruct_grad   gradient of the MSE w.r.t. the dictionary increments
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jabba_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libjabba_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+I64 = C.POINTER(C.c_int64)
+I32 = C.POINTER(C.c_int32)
+U64 = C.POINTER(C.c_uint64)
+F64 = C.POINTER(C.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            sig = {
+                "jo_count_domains": (C.c_int64, [I64, C.c_int64, C.c_int, C.c_int64]),
+                "jo_build_domains": (C.c_int64, [I64, C.c_int64, C.c_int, C.c_int64, I64, I64, I32]),
+                "jo_piece_error": (C.c_double, [F64, C.c_int64, C.c_int64]),
+                "jo_piece_admissible": (C.c_int, [F64, C.c_int64, C.c_int64, C.c_double]),
+                "jo_compress_domain": (C.c_int64, [F64, C.c_int64, C.c_int64, C.c_double, I32, F64]),
+                "jo_compress_all": (None, [F64, I64, I64, C.c_int64, I64, C.c_double, I32, F64, I64, C.c_int]),
+                "jo_sigma": (None, [I32, F64, C.c_int64, F64, F64]),
+                "jo_greedy": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_int, I64, I64]),
+                "jo_local_aggregate": (C.c_int64, [I32, F64, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                                   C.c_double, I32, I64, I64, U64]),
+                "jo_centre": (None, [C.c_int64, C.c_int64, U64, F64, F64]),
+                "jo_merge": (C.c_int64, [I64, I64, U64, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, I32, F64, F64, I64]),
+                "jo_symbolize": (None, [I32, I64, I64, C.c_int64, I32, I32]),
+                "jo_reconstruct_series": (None, [I32, C.c_int64, F64, F64, C.c_double, C.c_int64, C.c_int,
+                                                 I32, F64]),
+                "jo_mse": (C.c_double, [F64, F64, C.c_int64]),
+                "jo_reconstruct_grad_series": (None, [F64, F64, I32, I32, C.c_int64, C.c_int64, C.c_double, F64]),
+                "jo_fx_sum": (C.c_double, [F64, C.c_int64]),
+                "jo_fx_of": (None, [C.c_double, U64]),
+                "jo_fx_round": (C.c_double, [U64]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ---------------------------------------------------------------- domains
+def domains(series_off, mode: int, value: int):
+    off = _c(series_off, np.int64)
+    S = len(off) - 1
+    D = lib().jo_count_domains(_p(off, I64), S, mode, value)
+    b = np.empty(D, np.int64)
+    e = np.empty(D, np.int64)
+    s = np.empty(D, np.int32)
+    lib().jo_build_domains(_p(off, I64), S, mode, value, _p(b, I64), _p(e, I64), _p(s, I32))
+    return b, e, s
+
+
+# ---------------------------------------------------------------- compression
+def piece_error(x, s: int, e: int) -> float:
+    x = _c(x, np.float64)
+    return lib().jo_piece_error(_p(x, F64), s, e)
+
+
+def admissible(x, s: int, e: int, tol: float) -> bool:
+    x = _c(x, np.float64)
+    return bool(lib().jo_piece_admissible(_p(x, F64), s, e, tol))
+
+
+def compress(x, dom_begin, dom_end, tol: float, threads: int = 1):
+    """Pieces of every domain, concatenated in domain order (Sec. 4.1.3).
+    Returns (piece_len int32[N], piece_inc float64[N], dom_piece_off int64[D+1])."""
+    x = _c(x, np.float64)
+    b = _c(dom_begin, np.int64)
+    e = _c(dom_end, np.int64)
+    D = len(b)
+    cap = e - b
+    cap_off = np.zeros(D + 1, np.int64)
+    np.cumsum(cap, out=cap_off[1:])
+    total = int(cap_off[-1])
+    ln = np.empty(max(total, 1), np.int32)
+    inc = np.empty(max(total, 1), np.float64)
+    cnt = np.zeros(max(D, 1), np.int64)
+    lib().jo_compress_all(_p(x, F64), _p(b, I64), _p(e, I64), D, _p(cap_off, I64), tol,
+                          _p(ln, I32), _p(inc, F64), _p(cnt, I64), threads)
+    cnt = cnt[:D]
+    off = np.zeros(D + 1, np.int64)
+    np.cumsum(cnt, out=off[1:])
+    idx = np.concatenate([np.arange(cap_off[d], cap_off[d] + cnt[d]) for d in range(D)]) if D else np.zeros(0, np.int64)
+    return ln[idx].copy(), inc[idx].copy(), off
+
+
+# ---------------------------------------------------------------- digitization
+def sigma(piece_len, piece_inc):
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    sl = C.c_double()
+    si = C.c_double()
+    lib().jo_sigma(_p(ln, I32), _p(inc, F64), len(ln), C.byref(sl), C.byref(si))
+    return sl.value, si.value
+
+
+def greedy(X, Y, alpha: float, prune: bool = True):
+    X = _c(X, np.float64)
+    Y = _c(Y, np.float64)
+    n = len(X)
+    lab = np.empty(max(n, 1), np.int64)
+    st = np.empty(max(n, 1), np.int64)
+    g = lib().jo_greedy(_p(X, F64), _p(Y, F64), n, alpha, int(prune), _p(lab, I64), _p(st, I64))
+    return lab[:n], st[:g]
+
+
+def normalised(piece_len, piece_inc, sigma_len, sigma_inc, scl):
+    """Eq. 4 coordinates, evaluated as the C oracle does."""
+    X = (scl * np.asarray(piece_len, np.float64)) / sigma_len
+    Y = np.asarray(piece_inc, np.float64) / sigma_inc
+    return X, Y
+
+
+def local_aggregate(piece_len, piece_inc, dom_piece_off, sigma_len, sigma_inc, alpha, scl):
+    """Stage I per domain.  Returns (local_label int32[N], dom_group_off int64[D+1],
+    grp_count int64[G], grp_lensum int64[G], grp_incacc uint64[G,4])."""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    off = _c(dom_piece_off, np.int64)
+    D = len(off) - 1
+    N = len(ln)
+    label = np.empty(max(N, 1), np.int32)
+    cnt = np.empty(max(N, 1), np.int64)
+    ls = np.empty(max(N, 1), np.int64)
+    ia = np.zeros((max(N, 1), 4), np.uint64)
+    goff = np.zeros(D + 1, np.int64)
+    L = lib()
+    g = 0
+    for d in range(D):
+        a, b = int(off[d]), int(off[d + 1])
+        n = b - a
+        G = L.jo_local_aggregate(
+            C.cast(ln.ctypes.data + 4 * a, I32), C.cast(inc.ctypes.data + 8 * a, F64), n,
+            sigma_len, sigma_inc, alpha, scl, C.cast(label.ctypes.data + 4 * a, I32),
+            C.cast(cnt.ctypes.data + 8 * g, I64), C.cast(ls.ctypes.data + 8 * g, I64),
+            C.cast(ia.ctypes.data + 32 * g, U64))
+        g += G
+        goff[d + 1] = g
+    return label[:N].copy(), goff, cnt[:g].copy(), ls[:g].copy(), ia[:g].copy()
+
+
+def centre(count: int, lensum: int, incacc):
+    ia = _c(incacc, np.uint64)
+    cl = C.c_double()
+    ci = C.c_double()
+    lib().jo_centre(count, lensum, _p(ia, U64), C.byref(cl), C.byref(ci))
+    return cl.value, ci.value
+
+
+def merge(grp_count, grp_lensum, grp_incacc, sigma_len, sigma_inc, alpha, scl):
+    """Stage II.  Returns (l2g int32[G], dict_len, dict_inc, dict_count)."""
+    cnt = _c(grp_count, np.int64)
+    ls = _c(grp_lensum, np.int64)
+    ia = _c(grp_incacc, np.uint64).reshape(-1, 4)
+    G = len(cnt)
+    l2g = np.empty(max(G, 1), np.int32)
+    dl = np.empty(max(G, 1), np.float64)
+    di = np.empty(max(G, 1), np.float64)
+    dc = np.empty(max(G, 1), np.int64)
+    k = lib().jo_merge(_p(cnt, I64), _p(ls, I64), _p(ia, U64), G, sigma_len, sigma_inc, alpha, scl,
+                       _p(l2g, I32), _p(dl, F64), _p(di, F64), _p(dc, I64))
+    return l2g[:G].copy(), dl[:k].copy(), di[:k].copy(), dc[:k].copy()
+
+
+def symbolize(local_label, dom_piece_off, dom_group_off, l2g):
+    lab = _c(local_label, np.int32)
+    po = _c(dom_piece_off, np.int64)
+    go = _c(dom_group_off, np.int64)
+    m = _c(l2g, np.int32)
+    out = np.empty(max(len(lab), 1), np.int32)
+    lib().jo_symbolize(_p(lab, I32), _p(po, I64), _p(go, I64), len(po) - 1, _p(m, I32), _p(out, I32))
+    return out[:len(lab)].copy()
+
+
+# ---------------------------------------------------------------- inverse symbolization
+def series_piece_offsets(series_off, dom_series, dom_piece_off):
+    """First piece of each series (its domains are consecutive)."""
+    S = len(series_off) - 1
+    dom_series = np.asarray(dom_series, np.int64)
+    first = np.searchsorted(dom_series, np.arange(S + 1), side="left")
+    return np.asarray(dom_piece_off, np.int64)[first]
+
+
+def reconstruct(symbol, series_piece_off, dict_len, dict_inc, x, series_off, round_mode: int = 0):
+    """Returns (qlen int32[N], xhat float64[n])."""
+    sym = _c(symbol, np.int32)
+    spo = _c(series_piece_off, np.int64)
+    dl = _c(dict_len, np.float64)
+    di = _c(dict_inc, np.float64)
+    x = _c(x, np.float64)
+    off = _c(series_off, np.int64)
+    qlen = np.zeros(max(len(sym), 1), np.int32)
+    xhat = np.zeros(max(len(x), 1), np.float64)
+    L = lib()
+    for s in range(len(off) - 1):
+        a, b = int(spo[s]), int(spo[s + 1])
+        n_s = int(off[s + 1] - off[s])
+        if n_s <= 0:
+            continue
+        L.jo_reconstruct_series(C.cast(sym.ctypes.data + 4 * a, I32), b - a, _p(dl, F64), _p(di, F64),
+                                float(x[off[s]]), n_s, round_mode, C.cast(qlen.ctypes.data + 4 * a, I32),
+                                C.cast(xhat.ctypes.data + 8 * int(off[s]), F64))
+    return qlen[:len(sym)].copy(), xhat[:len(x)].copy()
+
+
+def mse(x, xhat) -> float:
+    x = _c(x, np.float64)
+    xh = _c(xhat, np.float64)
+    return lib().jo_mse(_p(x, F64), _p(xh, F64), len(x))
+
+
+def reconstruct_grad(x, xhat, symbol, qlen, series_piece_off, series_off, k: int):
+    """d MSE / d dict_inc (float64[k]) with the quantized lengths held fixed."""
+    x = _c(x, np.float64)
+    xh = _c(xhat, np.float64)
+    sym = _c(symbol, np.int32)
+    ql = _c(qlen, np.int32)
+    spo = _c(series_piece_off, np.int64)
+    off = _c(series_off, np.int64)
+    grad = np.zeros(max(k, 1), np.float64)
+    L = lib()
+    n_total = float(len(x))
+    for s in range(len(off) - 1):
+        a, b = int(spo[s]), int(spo[s + 1])
+        o = int(off[s])
+        n_s = int(off[s + 1]) - o
+        if n_s <= 0:
+            continue
+        L.jo_reconstruct_grad_series(C.cast(x.ctypes.data + 8 * o, F64), C.cast(xh.ctypes.data + 8 * o, F64),
+                                     C.cast(sym.ctypes.data + 4 * a, I32), C.cast(ql.ctypes.data + 4 * a, I32),
+                                     b - a, n_s, n_total, _p(grad, F64))
+    return grad[:k].copy()
+
+
+# ---------------------------------------------------------------- fixed point (tests)
+def fx_sum(values) -> float:
+    v = _c(values, np.float64)
+    return lib().jo_fx_sum(_p(v, F64), len(v))
+
+
+def fx_of(value: float) -> int:
+    limbs = np.zeros(4, np.uint64)
+    lib().jo_fx_of(float(value), _p(limbs, U64))
+    u = sum(int(limbs[i]) << (64 * i) for i in range(4))
+    return u - (1 << 256) if u >> 255 else u
+
+
+def fx_round(limbs) -> float:
+    lm = _c(limbs, np.uint64)
+    return lib().jo_fx_round(_p(lm, U64))
+
+
+def fx_value(limbs) -> int:
+    """Signed integer value (in units of 2^-96) of 4 little-endian limbs."""
+    u = sum(int(limbs[i]) << (64 * i) for i in range(4))
+    return u - (1 << 256) if u >> 255 else u
+
+
+# ---------------------------------------------------------------- whole path
+def pipeline(x, series_off, tol, alpha, scl=1.0, domain_mode=0, domain_value=4, threads=1,
+             with_reconstruct=True, round_mode=0):
+    """The whole forward path on one collection; returns a dict of every stage."""
+    b, e, ds = domains(series_off, domain_mode, domain_value)
+    ln, inc, po = compress(x, b, e, tol, threads)
+    sl, si = sigma(ln, inc)
+    lab, go, gc, gl, gi = local_aggregate(ln, inc, po, sl, si, alpha, scl)
+    l2g, dl, di, dc = merge(gc, gl, gi, sl, si, alpha, scl)
+    sym = symbolize(lab, po, go, l2g)
+    out = dict(dom_begin=b, dom_end=e, dom_series=ds, piece_len=ln, piece_inc=inc, dom_piece_off=po,
+               sigma_len=sl, sigma_inc=si, local_label=lab, dom_group_off=go, grp_count=gc,
+               grp_lensum=gl, grp_incacc=gi, l2g=l2g, dict_len=dl, dict_inc=di, dict_count=dc, symbol=sym)
+    if with_reconstruct:
+        spo = series_piece_offsets(series_off, ds, po)
+        ql, xh = reconstruct(sym, spo, dl, di, x, series_off, round_mode)
+        out.update(series_piece_off=spo, qlen=ql, xhat=xh, mse=mse(x, xh))
+    return out

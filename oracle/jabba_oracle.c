@@ -1,0 +1,502 @@
+/*
+ * jabba_oracle.c -- plain, slow, FP64 CPU oracle of the JABBA symbolization
+ * path (arXiv 2401.00109).  TEST INFRASTRUCTURE ONLY: the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark call it; the product path
+ * never does.  It shares no code with the CUDA library.
+ *
+ * Every function states the passage it follows.  Where the paper is silent or
+ * ambiguous the reading taken is stated beside the code.  Build with
+ *   gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC
+ * so that every floating-point expression is evaluated exactly as written
+ * (IEEE double, round to nearest even, no fused multiply-add).
+ *
+ * Index base: series are 0-based, x[0..n_s-1] (the paper uses both t_1..t_n,
+ * Sec. 3, and t_0..t_n, Table 1).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Exact fixed-point accumulator (order-independent sums of doubles).        */
+/* A value v is represented by the integer floor_toward_zero(v * 2^96) held  */
+/* in 256-bit two's complement (4 little-endian 64-bit limbs).  Sums of such */
+/* integers are exact, so any summation order gives the same total; the     */
+/* total is rounded once to double (round to nearest, ties to even).        */
+/* Range contract: |v| < 2^120 per term (callers guarantee far less).        */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint64_t w[4]; } jo_fx;
+
+static void fx_zero(jo_fx* a) { memset(a, 0, sizeof *a); }
+
+static void fx_add_fx(jo_fx* a, const jo_fx* b) {
+  unsigned __int128 c = 0;
+  for (int i = 0; i < 4; ++i) {
+    c += (unsigned __int128)a->w[i] + b->w[i];
+    a->w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+}
+
+static void fx_neg(jo_fx* a) {
+  unsigned __int128 c = 1;
+  for (int i = 0; i < 4; ++i) {
+    c += (uint64_t)~a->w[i];
+    a->w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+}
+
+/* Exact magnitude |v| * 2^96 truncated toward zero, with the sign of v. */
+static void fx_from_double(jo_fx* out, double v) {
+  fx_zero(out);
+  if (v == 0.0) return;
+  int e;
+  double f = frexp(fabs(v), &e);          /* |v| = f * 2^e, f in [0.5, 1) */
+  uint64_t m = (uint64_t)ldexp(f, 53);    /* exact 53-bit integer          */
+  int sh = e - 53 + 96;                   /* |v| * 2^96 = m * 2^sh         */
+  if (sh <= -64) return;                  /* below resolution: zero        */
+  if (sh < 0) {
+    m >>= -sh;                            /* truncate toward zero          */
+    sh = 0;
+  }
+  int limb = sh / 64, bit = sh % 64;
+  if (limb < 4) out->w[limb] = m << bit;
+  if (bit && limb + 1 < 4) out->w[limb + 1] = m >> (64 - bit);
+  if (v < 0) fx_neg(out);
+}
+
+static void fx_add_double(jo_fx* a, double v) {
+  jo_fx t;
+  fx_from_double(&t, v);
+  fx_add_fx(a, &t);
+}
+
+/* Bit b of the 256-bit magnitude. */
+static int fx_bit(const jo_fx* m, int b) { return (int)((m->w[b / 64] >> (b % 64)) & 1u); }
+
+/* Round the 256-bit integer to double (nearest, ties to even), then scale by
+ * 2^-96 (exact: results here are far from the subnormal range). */
+static double fx_to_double(const jo_fx* a) {
+  jo_fx m = *a;
+  int neg = (int)(m.w[3] >> 63);
+  if (neg) fx_neg(&m);
+  int top = -1;
+  for (int i = 3; i >= 0 && top < 0; --i)
+    if (m.w[i]) top = i * 64 + 63 - __builtin_clzll(m.w[i]);
+  if (top < 0) return 0.0;
+  double r;
+  if (top <= 52) {
+    r = ldexp((double)m.w[0], -96);              /* fewer than 54 bits: exact */
+  } else {
+    int lo = top - 52;                            /* keep bits lo..top         */
+    uint64_t sig = 0;
+    for (int b = top; b >= lo; --b) sig = (sig << 1) | (uint64_t)fx_bit(&m, b);
+    int rb = fx_bit(&m, lo - 1), sticky = 0;
+    for (int b = lo - 2; b >= 0 && !sticky; --b) sticky = fx_bit(&m, b);
+    if (rb && (sticky || (sig & 1u))) sig += 1;   /* 2^53 is still exact       */
+    r = ldexp((double)sig, lo - 96);
+  }
+  return neg ? -r : r;
+}
+
+/* Exposed for the tests: fixed-point round trip of a list of doubles. */
+double jo_fx_sum(const double* v, int64_t n) {
+  jo_fx a;
+  fx_zero(&a);
+  for (int64_t i = 0; i < n; ++i) fx_add_double(&a, v[i]);
+  return fx_to_double(&a);
+}
+
+/* Exposed for the tests: the 4 limbs of the fixed-point image of v. */
+void jo_fx_of(double v, uint64_t* limbs) {
+  jo_fx a;
+  fx_from_double(&a, v);
+  memcpy(limbs, a.w, 32);
+}
+
+/* Exposed for the tests: round 4 limbs to double. */
+double jo_fx_round(const uint64_t* limbs) {
+  jo_fx a;
+  memcpy(a.w, limbs, 32);
+  return fx_to_double(&a);
+}
+
+/* Correctly rounded conversion of an unsigned 128-bit integer. */
+static double u128_to_double(unsigned __int128 v) { return (double)v; }
+
+/* ------------------------------------------------------------------------ */
+/* Phase I: domain construction (Alg. 1 Phase I; Sec. 4.1.1).                */
+/* Domains are consecutive, share endpoints (s_{k+1} = e_k) and never cross  */
+/* a series boundary.  Reading of "split uniformly":                         */
+/*   EQUAL_COUNT M: M_s = min(M, n_s - 1) domains, b_k = floor(k (n_s-1)/M_s)*/
+/*   FIXED_LEN   D: ceil((n_s-1)/D) domains, b_k = min(k D, n_s - 1)        */
+/* (D counts intervals, so a full domain holds D+1 points).  A series with   */
+/* fewer than 2 points has no domain.                                        */
+/* ------------------------------------------------------------------------ */
+static int64_t series_domains(int64_t n_s, int mode, int64_t value) {
+  if (n_s < 2 || value < 1) return 0;
+  int64_t iv = n_s - 1;
+  if (mode == 0) return value < iv ? value : iv;
+  return (iv + value - 1) / value;
+}
+
+int64_t jo_count_domains(const int64_t* series_off, int64_t n_series, int mode, int64_t value) {
+  int64_t d = 0;
+  for (int64_t s = 0; s < n_series; ++s) d += series_domains(series_off[s + 1] - series_off[s], mode, value);
+  return d;
+}
+
+int64_t jo_build_domains(const int64_t* series_off, int64_t n_series, int mode, int64_t value,
+                         int64_t* dom_begin, int64_t* dom_end, int32_t* dom_series) {
+  int64_t d = 0;
+  for (int64_t s = 0; s < n_series; ++s) {
+    int64_t base = series_off[s], n_s = series_off[s + 1] - base;
+    int64_t M = series_domains(n_s, mode, value), iv = n_s - 1;
+    for (int64_t k = 0; k < M; ++k) {
+      int64_t b0, b1;
+      if (mode == 0) {
+        b0 = (int64_t)(((unsigned __int128)k * (uint64_t)iv) / (uint64_t)M);
+        b1 = (int64_t)(((unsigned __int128)(k + 1) * (uint64_t)iv) / (uint64_t)M);
+      } else {
+        b0 = k * value < iv ? k * value : iv;
+        b1 = (k + 1) * value < iv ? (k + 1) * value : iv;
+      }
+      dom_begin[d] = base + b0;
+      dom_end[d] = base + b1;
+      dom_series[d] = (int32_t)s;
+      ++d;
+    }
+  }
+  return d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Phase II: compression of one domain (Sec. 3.1, Eq. 1).                    */
+/* Piece (s, e) is admissible when the squared distance of the interior      */
+/* points from the chord through (s, x_s) and (e, x_e) is at most            */
+/* (e - s - 1) tol^2.  Readings:                                             */
+/*  - greedy: from s, extend e while the next end is admissible, stop at the */
+/*    first inadmissible end ("largest possible i_j" read as the largest     */
+/*    end reached by extension, which keeps the method linear);              */
+/*  - the sum runs over interior points only (the endpoint residuals are     */
+/*    zero in exact arithmetic);                                             */
+/*  - residual r_i = (x_s + (inc * k) / L) - x_i, k = i - s, L = e - s,      */
+/*    inc = x_e - x_s, evaluated in that order, summed in ascending i;       */
+/*  - no slack on "<=".                                                      */
+/* ------------------------------------------------------------------------ */
+double jo_piece_error(const double* x, int64_t s, int64_t e) {
+  int64_t L = e - s;
+  double inc = x[e] - x[s];
+  double err = 0.0;
+  for (int64_t k = 1; k < L; ++k) {
+    double r = (x[s] + (inc * (double)k) / (double)L) - x[s + k];
+    err = err + r * r;
+  }
+  return err;
+}
+
+int jo_piece_admissible(const double* x, int64_t s, int64_t e, double tol) {
+  return jo_piece_error(x, s, e) <= (double)(e - s - 1) * (tol * tol);
+}
+
+int64_t jo_compress_domain(const double* x, int64_t b, int64_t e_dom, double tol,
+                           int32_t* len_out, double* inc_out) {
+  int64_t n = 0, s = b;
+  while (s < e_dom) {
+    int64_t e = s + 1;                         /* a one-interval piece is always admissible */
+    while (e + 1 <= e_dom && jo_piece_admissible(x, s, e + 1, tol)) ++e;
+    len_out[n] = (int32_t)(e - s);
+    inc_out[n] = x[e] - x[s];
+    ++n;
+    s = e;
+  }
+  return n;
+}
+
+/* Compress every domain; domain d writes its pieces at slot dom_cap_off[d]
+ * (capacity = its interval count) and its count to dom_count[d].  Domains
+ * are independent (Alg. 1 Phase II "in parallel"); n_threads > 1 splits them
+ * over POSIX threads exactly as the paper's multicore compression does. */
+typedef struct {
+  const double* x; const int64_t* b; const int64_t* e; const int64_t* cap_off;
+  double tol; int32_t* len; double* inc; int64_t* count; int64_t d0, d1;
+} jo_cjob;
+
+static void* compress_worker(void* p) {
+  jo_cjob* j = (jo_cjob*)p;
+  for (int64_t d = j->d0; d < j->d1; ++d)
+    j->count[d] = jo_compress_domain(j->x, j->b[d], j->e[d], j->tol, j->len + j->cap_off[d], j->inc + j->cap_off[d]);
+  return NULL;
+}
+
+void jo_compress_all(const double* x, const int64_t* dom_begin, const int64_t* dom_end, int64_t n_domains,
+                     const int64_t* dom_cap_off, double tol, int32_t* len, double* inc, int64_t* dom_count,
+                     int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  jo_cjob jobs[256];
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t] = (jo_cjob){x, dom_begin, dom_end, dom_cap_off, tol, len, inc, dom_count,
+                        n_domains * t / n_threads, n_domains * (t + 1) / n_threads};
+    if (n_threads == 1) compress_worker(&jobs[t]);
+    else pthread_create(&th[t], NULL, compress_worker, &jobs[t]);
+  }
+  if (n_threads > 1)
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Normalisation (Sec. 3.2, Eq. 4): sigma_len, sigma_inc are the population  */
+/* standard deviations of all pieces of all domains (the dictionary is       */
+/* shared).  Sums are exact (integers for len, fixed point for inc), so the  */
+/* result does not depend on summation order; then                          */
+/*   m = S1 / N;  v = S2 / N - m * m;  sigma = sqrt(v), or 1 when v <= 0.     */
+/* ------------------------------------------------------------------------ */
+static double sigma_from(double s1, double s2, double n) {
+  double m = s1 / n;
+  double v = s2 / n - m * m;
+  if (!(v > 0.0)) return 1.0;
+  return sqrt(v);
+}
+
+void jo_sigma(const int32_t* len, const double* inc, int64_t n, double* sigma_len, double* sigma_inc) {
+  int64_t s1 = 0;
+  unsigned __int128 s2 = 0;
+  jo_fx i1, i2;
+  fx_zero(&i1);
+  fx_zero(&i2);
+  for (int64_t j = 0; j < n; ++j) {
+    s1 += len[j];
+    s2 += (unsigned __int128)((int64_t)len[j] * (int64_t)len[j]);
+    fx_add_double(&i1, inc[j]);
+    fx_add_double(&i2, inc[j] * inc[j]);
+  }
+  double dn = (double)n;
+  *sigma_len = sigma_from((double)s1, u128_to_double(s2), dn);
+  *sigma_inc = sigma_from(fx_to_double(&i1), fx_to_double(&i2), dn);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Greedy aggregation (Sec. 3.2, fABBA; pruning rule of Sec. 5).             */
+/* Points p = (X, Y): X = (scl * len) / sigma_len, Y = inc / sigma_inc        */
+/* (Eq. 4).  Sort key: the squared norm X*X + Y*Y (orders exactly as the     */
+/* norm).  Order: key ascending, ties by position.  In that order each       */
+/* unassigned point starts a new group; every later unassigned point q with  */
+/* (X_q - X_p)^2 + (Y_q - Y_p)^2 <= alpha^2 joins it.  The scan of later     */
+/* points stops once norm(q) - norm(p) exceeds alpha (Sec. 5 pruning); the   */
+/* stop test carries a 2^-40 relative margin so that, despite rounding, it   */
+/* never skips a point that the distance test would accept: the result is   */
+/* that of the unpruned greedy (checked in the tests).                       */
+/* ------------------------------------------------------------------------ */
+typedef struct { double key; int64_t pos; } jo_kp;
+
+static int kp_cmp(const void* a, const void* b) {
+  const jo_kp* u = (const jo_kp*)a;
+  const jo_kp* v = (const jo_kp*)b;
+  if (u->key < v->key) return -1;
+  if (u->key > v->key) return 1;
+  return (u->pos > v->pos) - (u->pos < v->pos);
+}
+
+static double dist2(double xa, double ya, double xb, double yb) {
+  double dx = xb - xa, dy = yb - ya;
+  return dx * dx + dy * dy;
+}
+
+/* Generic greedy over n points (X[], Y[]); labels[i] receives the group id in
+ * creation order; returns the number of groups; starts[g] = first point.
+ * prune = 0 gives the unpruned greedy (used only by the tests). */
+int64_t jo_greedy(const double* X, const double* Y, int64_t n, double alpha, int prune,
+                  int64_t* labels, int64_t* starts) {
+  jo_kp* o = (jo_kp*)malloc(sizeof(jo_kp) * (size_t)(n ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    o[i].key = X[i] * X[i] + Y[i] * Y[i];
+    o[i].pos = i;
+    labels[i] = -1;
+  }
+  qsort(o, (size_t)n, sizeof(jo_kp), kp_cmp);
+  double a2 = alpha * alpha;
+  int64_t g = 0;
+  for (int64_t a = 0; a < n; ++a) {
+    int64_t i = o[a].pos;
+    if (labels[i] >= 0) continue;
+    labels[i] = g;
+    if (starts) starts[g] = i;
+    double ri = sqrt(o[a].key);
+    for (int64_t b = a + 1; b < n; ++b) {
+      int64_t j = o[b].pos;
+      if (prune) {
+        double rj = sqrt(o[b].key);
+        if (rj - ri > alpha + 0x1p-40 * (alpha + rj)) break;
+      }
+      if (labels[j] < 0 && dist2(X[i], Y[i], X[j], Y[j]) <= a2) labels[j] = g;
+    }
+    ++g;
+  }
+  free(o);
+  return g;
+}
+
+/* Normalised coordinates of a piece (Eq. 4). */
+static double norm_len(double len, double scl, double sigma_len) { return (scl * len) / sigma_len; }
+static double norm_inc(double inc, double sigma_inc) { return inc / sigma_inc; }
+
+/* Stage I, per domain (Sec. 5; per-domain blocks): aggregate the pieces of one
+ * domain.  Group sums: count, lensum (exact int), incacc (exact fixed point).
+ * Returns the number of local groups. */
+int64_t jo_local_aggregate(const int32_t* len, const double* inc, int64_t n, double sigma_len,
+                           double sigma_inc, double alpha, double scl, int32_t* label,
+                           int64_t* grp_count, int64_t* grp_lensum, uint64_t* grp_incacc /* 4 limbs/group */) {
+  double* X = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double* Y = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  int64_t* lab = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    X[i] = norm_len((double)len[i], scl, sigma_len);
+    Y[i] = norm_inc(inc[i], sigma_inc);
+  }
+  int64_t G = jo_greedy(X, Y, n, alpha, 1, lab, NULL);
+  for (int64_t g = 0; g < G; ++g) {
+    grp_count[g] = 0;
+    grp_lensum[g] = 0;
+    memset(grp_incacc + 4 * g, 0, 32);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t g = lab[i];
+    label[i] = (int32_t)g;
+    grp_count[g] += 1;
+    grp_lensum[g] += len[i];
+    fx_add_double((jo_fx*)(grp_incacc + 4 * g), inc[i]);
+  }
+  free(X);
+  free(Y);
+  free(lab);
+  return G;
+}
+
+/* Centre of a group in original units: (lensum / count, round(incacc) / count). */
+void jo_centre(int64_t count, int64_t lensum, const uint64_t* incacc, double* c_len, double* c_inc) {
+  *c_len = (double)lensum / (double)count;
+  *c_inc = fx_to_double((const jo_fx*)incacc) / (double)count;
+}
+
+/* Stage II (Sec. 5 "global merging"): the same greedy over all local groups
+ * taken as points at their normalised centres, in (domain, local id) order.
+ * Reading: the weighted local centres are merged (membership unweighted, the
+ * weights enter the merged centres through the exact sums).  l2g[g] = global
+ * group (creation order); dictionary entry = exact mean of its pieces. */
+int64_t jo_merge(const int64_t* grp_count, const int64_t* grp_lensum, const uint64_t* grp_incacc, int64_t G,
+                 double sigma_len, double sigma_inc, double alpha, double scl, int32_t* l2g,
+                 double* dict_len, double* dict_inc, int64_t* dict_count) {
+  double* X = (double*)malloc(sizeof(double) * (size_t)(G ? G : 1));
+  double* Y = (double*)malloc(sizeof(double) * (size_t)(G ? G : 1));
+  int64_t* lab = (int64_t*)malloc(sizeof(int64_t) * (size_t)(G ? G : 1));
+  for (int64_t g = 0; g < G; ++g) {
+    double cl, ci;
+    jo_centre(grp_count[g], grp_lensum[g], grp_incacc + 4 * g, &cl, &ci);
+    X[g] = norm_len(cl, scl, sigma_len);
+    Y[g] = norm_inc(ci, sigma_inc);
+  }
+  int64_t k = jo_greedy(X, Y, G, alpha, 1, lab, NULL);
+  int64_t* cnt = (int64_t*)calloc((size_t)(k ? k : 1), sizeof(int64_t));
+  int64_t* ls = (int64_t*)calloc((size_t)(k ? k : 1), sizeof(int64_t));
+  jo_fx* ia = (jo_fx*)calloc((size_t)(k ? k : 1), sizeof(jo_fx));
+  for (int64_t g = 0; g < G; ++g) {
+    int64_t c = lab[g];
+    l2g[g] = (int32_t)c;
+    cnt[c] += grp_count[g];
+    ls[c] += grp_lensum[g];
+    fx_add_fx(&ia[c], (const jo_fx*)(grp_incacc + 4 * g));
+  }
+  for (int64_t c = 0; c < k; ++c) {
+    jo_centre(cnt[c], ls[c], ia[c].w, &dict_len[c], &dict_inc[c]);
+    dict_count[c] = cnt[c];
+  }
+  free(X);
+  free(Y);
+  free(lab);
+  free(cnt);
+  free(ls);
+  free(ia);
+  return k;
+}
+
+/* Label propagation (Sec. 5): l_i = l~_g for a piece in local group g. */
+void jo_symbolize(const int32_t* local_label, const int64_t* dom_piece_off, const int64_t* dom_group_off,
+                  int64_t n_domains, const int32_t* l2g, int32_t* symbol) {
+  for (int64_t d = 0; d < n_domains; ++d)
+    for (int64_t p = dom_piece_off[d]; p < dom_piece_off[d + 1]; ++p)
+      symbol[p] = l2g[dom_group_off[d] + local_label[p]];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inverse symbolization of one series (Sec. 3.3).                          */
+/* inverse digitization: (l~, i~) = dictionary entry of each symbol;         */
+/* quantization: v = l~_j + e; l^_j = round(v); e = v - l^_j (e_0 = 0)        */
+/*   (the consistent sign of the carry; round_mode 0 = half away from zero,  */
+/*   1 = half to even);                                                      */
+/* inverse compression from t_0: x^_{pos+q} = level + (i~_j * q) / l^_j,      */
+/*   q = 1..l^_j; level += i~_j; pos += l^_j.  Points past the series end are */
+/*   dropped; a short chain leaves the tail at the final level.               */
+/* qlen receives l^_j.                                                        */
+/* ------------------------------------------------------------------------ */
+static double round_half_even(double v) { return rint(v); } /* default mode: nearest, ties to even */
+
+void jo_reconstruct_series(const int32_t* symbol, int64_t n_pieces, const double* dict_len, const double* dict_inc,
+                           double x0, int64_t n_s, int round_mode, int32_t* qlen, double* xhat) {
+  if (n_s <= 0) return;
+  xhat[0] = x0;
+  double e = 0.0, level = x0;
+  int64_t pos = 0;
+  for (int64_t j = 0; j < n_pieces; ++j) {
+    double lt = dict_len[symbol[j]];
+    double it = dict_inc[symbol[j]];
+    double v = lt + e;
+    double lh = round_mode ? round_half_even(v) : round(v);
+    e = v - lh;
+    int64_t L = (int64_t)lh;
+    qlen[j] = (int32_t)L;
+    for (int64_t q = 1; q <= L && pos + q <= n_s - 1; ++q) xhat[pos + q] = level + (it * (double)q) / lh;
+    level = level + it;
+    pos += L;
+  }
+  for (int64_t i = pos + 1; i <= n_s - 1; ++i) xhat[i] = level;
+}
+
+/* Reconstruction MSE over all series (Sec. 3.3): sum of squared differences
+ * over all points divided by the total number of points. */
+double jo_mse(const double* x, const double* xhat, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double d = x[i] - xhat[i];
+    s = s + d * d;
+  }
+  return s / (double)n;
+}
+
+/* Gradient of the MSE with respect to dict_inc, with the quantized lengths
+ * held fixed (x^ is then affine in dict_inc).  For piece j of a series with
+ * start pos_j and length l^_j, d x^_{pos_j+q} / d i~_{a_j} = q / l^_j for
+ * q <= l^_j and 1 for every later point of the series.  Accumulates
+ * (2 / n_total) * sum_i (x^_i - x_i) * d x^_i / d i~ into grad. */
+void jo_reconstruct_grad_series(const double* x, const double* xhat, const int32_t* symbol, const int32_t* qlen,
+                                int64_t n_pieces, int64_t n_s, double n_total, double* grad) {
+  /* suffix[i] = sum_{i' >= i} r_i' */
+  double* suffix = (double*)malloc(sizeof(double) * (size_t)(n_s + 1));
+  suffix[n_s] = 0.0;
+  for (int64_t i = n_s - 1; i >= 0; --i) suffix[i] = suffix[i + 1] + (xhat[i] - x[i]);
+  int64_t pos = 0;
+  for (int64_t j = 0; j < n_pieces; ++j) {
+    int64_t L = qlen[j];
+    double acc = 0.0;
+    for (int64_t q = 1; q <= L && pos + q <= n_s - 1; ++q) acc = acc + ((double)q / (double)L) * (xhat[pos + q] - x[pos + q]);
+    int64_t after = pos + L + 1;
+    if (after <= n_s - 1) acc = acc + suffix[after];
+    grad[symbol[j]] += (2.0 / n_total) * acc;
+    pos += L;
+  }
+  free(suffix);
+}

@@ -1,0 +1,236 @@
+"""Pins for the oracle's normalisation, greedy aggregation, two-stage merge and
+label propagation (Sec. 3.2 Eqs. 4-9, Sec. 5).  Checks use exact sums
+(math.fsum / Fraction), numpy's own std, hand fixtures, brute force and the
+invariants that characterize the greedy."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _golden import load
+
+
+def test_fixed_point_exact():
+    rng = np.random.default_rng(0)
+    for v in list(rng.standard_normal(200) * 10.0 ** rng.integers(-20, 15, 200)) + [0.0, -0.0, 1.5, -2.75, 2.0**-96, -(2.0**-97)]:
+        got = oracle.fx_of(v)
+        f = Fraction(v) * 2**96
+        want = math.floor(f) if f >= 0 else -math.floor(-f)            # truncate toward zero
+        assert got == want
+    vals = rng.standard_normal(10000) * 3.0
+    assert oracle.fx_sum(vals) == math.fsum(vals)                    # correctly rounded exact sum
+    vals = np.concatenate([vals, -vals[:5000], [1e10, -1e10, 0.1]])
+    assert oracle.fx_sum(vals) == math.fsum(vals)
+    assert oracle.fx_sum(np.array([1.0, 2.0**-60, 2.0**-60])) == 1.0 + 2.0**-59
+
+
+def test_fixed_point_rounding_ties_even():
+    # 2^53 + 1 (in units of 2^-96) is a tie between 2^53 and 2^53 + 2
+    u = (2**53 + 1)
+    limbs = np.array([u & (2**64 - 1), u >> 64, 0, 0], np.uint64)
+    assert oracle.fx_round(limbs) == float(2**53) * 2.0**-96
+    u = (2**53 + 3)
+    limbs = np.array([u, 0, 0, 0], np.uint64)
+    assert oracle.fx_round(limbs) == float(2**53 + 4) * 2.0**-96
+    neg = (1 << 256) - (2**54 + 1)                                   # -(2^54 + 1): rounds to -2^54
+    limbs = np.array([(neg >> (64 * i)) & (2**64 - 1) for i in range(4)], np.uint64)
+    assert oracle.fx_round(limbs) == -float(2**54) * 2.0**-96
+
+
+def test_sigma_population_std():
+    x, off, p = synth.make("small")
+    b, e, _ = oracle.domains(off, 0, 4)
+    ln, inc, po = oracle.compress(x, b, e, p["tol"])
+    sl, si = oracle.sigma(ln, inc)
+    assert abs(sl - np.std(ln.astype(np.float64))) <= 1e-12 * sl
+    assert abs(si - np.std(inc)) <= 1e-12 * si
+    # exact definition: mean-of-squares minus squared mean from exact sums
+    n = len(ln)
+    m = math.fsum(inc) / n
+    v = math.fsum(inc * inc) / n - m * m
+    assert si == math.sqrt(v)
+    # degenerate: all lengths equal -> sigma_len = 1 (divisor 1)
+    assert oracle.sigma(np.full(7, 3, np.int32), np.arange(7.0))[0] == 1.0
+
+
+def test_greedy_hand():
+    g = load("aggregate_hand.txt")
+    lab, st = oracle.greedy(g["X"], g["Y"], float(g["alpha"][0]))
+    assert lab.tolist() == g["labels"].astype(int).tolist()
+
+
+def brute_labels(X, Y, alpha):
+    """Characterization of the greedy by its invariants, computed by brute
+    force in exact rational arithmetic on the FP64 coordinates: in key order,
+    a point joins the earliest start before it within alpha, else starts."""
+    n = len(X)
+    key = [Fraction(X[i]) ** 2 + Fraction(Y[i]) ** 2 for i in range(n)]
+    order = sorted(range(n), key=lambda i: (key[i], i))
+    a2 = Fraction(alpha) ** 2
+    lab = [-1] * n
+    starts = []
+    for i in order:
+        for g, s in enumerate(starts):
+            if (Fraction(X[i]) - Fraction(X[s])) ** 2 + (Fraction(Y[i]) - Fraction(Y[s])) ** 2 <= a2:
+                lab[i] = g
+                break
+        else:
+            lab[i] = len(starts)
+            starts.append(i)
+    return np.array(lab)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_matches_bruteforce_and_unpruned(seed):
+    rng = np.random.default_rng(seed)
+    n = 120
+    if seed % 2:
+        # points on a dyadic grid with a dyadic alpha: every FP64 operation is
+        # exact, so ties at distance exactly alpha occur and must agree
+        X = np.round(rng.uniform(0, 1, n) * 64) / 64
+        Y = np.round(rng.normal(0, 0.5, n) * 64) / 64
+        alpha = [0.0625, 0.125, 0.25][seed % 3]
+    else:
+        X = rng.uniform(0, 1, n)
+        Y = rng.normal(0, 0.5, n)
+        alpha = [0.05, 0.1, 0.2][seed % 3]
+    lab, st = oracle.greedy(X, Y, alpha, prune=True)
+    lab0, _ = oracle.greedy(X, Y, alpha, prune=False)
+    assert np.array_equal(lab, lab0)                      # Sec. 5 pruning is lossless
+    ref = brute_labels(X, Y, alpha)
+    # exact-arithmetic decisions can differ from FP64 only for distances within
+    # a few ulp of alpha; these fixtures have none
+    assert np.array_equal(lab, ref)
+
+
+def test_greedy_invariants_and_sse_bound():
+    rng = np.random.default_rng(11)
+    X = rng.uniform(0, 3, 2000)
+    Y = rng.normal(0, 1, 2000)
+    alpha = 0.1
+    lab, st = oracle.greedy(X, Y, alpha)
+    k = len(st)
+    P = np.stack([X, Y], 1)
+    S = P[st]
+    d2 = ((P - S[lab]) ** 2).sum(1)
+    assert np.all(d2 <= alpha * alpha * (1 + 1e-12))             # members within alpha of start
+    dd = ((S[:, None, :] - S[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(dd, np.inf)
+    assert np.all(dd > alpha * alpha)                              # starts pairwise > alpha apart
+    sse = 0.0
+    for g in range(k):
+        m = P[lab == g]
+        c = m.mean(0)
+        var = ((m - c) ** 2).sum(1).mean()
+        assert var <= alpha * alpha * (1 + 1e-12)                  # Eq. 9: Var <= alpha^2
+        sse += ((m - c) ** 2).sum()
+    assert sse <= alpha * alpha * (len(X) - k) * (1 + 1e-12)       # SSE <= alpha^2 (N - k)
+
+
+def test_greedy_degenerate():
+    X = np.array([0.0, 1.0, 1.0, 0.0, 2.0])
+    Y = np.array([0.0, 1.0, 1.0, 0.0, 2.0])
+    lab, st = oracle.greedy(X, Y, 0.0)                            # alpha = 0: exact duplicates only
+    assert lab.tolist() == [0, 1, 1, 0, 2]
+    # scl = 0 ignores lengths (Eq. 4)
+    X0, Y0 = oracle.normalised(np.array([1, 50, 3]), np.array([0.1, 0.1, 0.5]), 2.0, 1.0, 0.0)
+    assert np.all(X0 == 0.0)
+    lab, _ = oracle.greedy(X0, Y0, 0.01)
+    assert lab[0] == lab[1] != lab[2]
+
+
+def test_exhaustive_optimal_grouping_tiny():
+    """On <= 7 points, no partition into groups of radius alpha (around one of
+    their points) uses fewer groups than... the greedy is a cover: k_opt <= k_greedy
+    and the greedy SSE is no better than the optimum over all alpha-partitions."""
+    rng = np.random.default_rng(2)
+    for trial in range(8):
+        n = 6
+        X = rng.uniform(0, 0.3, n)
+        Y = rng.uniform(0, 0.3, n)
+        alpha = 0.12
+        lab, st = oracle.greedy(X, Y, alpha)
+        P = np.stack([X, Y], 1)
+
+        def partitions(items):
+            if not items:
+                yield []
+                return
+            first, rest = items[0], items[1:]
+            for p in partitions(rest):
+                for i in range(len(p)):
+                    yield p[:i] + [[first] + p[i]] + p[i + 1:]
+                yield [[first]] + p
+
+        best_k, best_sse = n + 1, math.inf
+        for part in partitions(list(range(n))):
+            ok = all(any(all(((P[m] - P[c]) ** 2).sum() <= alpha ** 2 for m in grp) for c in grp) for grp in part)
+            if not ok:
+                continue
+            sse = sum(((P[grp] - P[grp].mean(0)) ** 2).sum() for grp in part)
+            if len(part) < best_k or (len(part) == best_k and sse < best_sse):
+                best_k, best_sse = len(part), sse
+        assert best_k <= len(st)
+        g_sse = sum(((P[lab == g] - P[lab == g].mean(0)) ** 2).sum() for g in range(len(st)))
+        if best_k == len(st):
+            assert best_sse <= g_sse + 1e-15
+
+
+def test_two_stage_small_config():
+    x, off, p = synth.make("small")
+    r = oracle.pipeline(x, off, p["tol"], p["alpha"], p["scl"], p["domain_mode"], p["domain_value"])
+    po, go = r["dom_piece_off"], r["dom_group_off"]
+    N = len(r["piece_len"])
+    # label propagation = composition (Sec. 5)
+    for d in range(len(po) - 1):
+        for q in range(po[d], po[d + 1]):
+            assert r["symbol"][q] == r["l2g"][go[d] + r["local_label"][q]]
+    # every dictionary entry is the exact mean of its member pieces
+    k = len(r["dict_len"])
+    assert r["dict_count"].sum() == N
+    for c in range(k):
+        m = r["symbol"] == c
+        assert r["dict_count"][c] == m.sum()
+        assert r["dict_len"][c] == float(Fraction(int(r["piece_len"][m].sum()), int(m.sum())))
+        assert r["dict_inc"][c] == math.fsum(r["piece_inc"][m]) / float(m.sum())
+    # local groups: exact sums of their pieces
+    for d in range(0, len(po) - 1, 7):
+        for g in range(go[d], go[d + 1]):
+            m = np.zeros(N, bool)
+            m[po[d]:po[d + 1]] = r["local_label"][po[d]:po[d + 1]] == g - go[d]
+            assert r["grp_count"][g] == m.sum()
+            assert r["grp_lensum"][g] == r["piece_len"][m].sum()
+            assert oracle.fx_value(r["grp_incacc"][g]) == sum(oracle.fx_of(v) for v in r["piece_inc"][m])
+
+
+def test_merge_singletons_equal_local():
+    """One domain with alpha below every pairwise distance: every local group is
+    a singleton and the merge reproduces the single-stage greedy."""
+    rng = np.random.default_rng(4)
+    ln = rng.integers(1, 40, 200).astype(np.int32)
+    inc = rng.standard_normal(200)
+    sl, si = oracle.sigma(ln, inc)
+    po = np.array([0, 200], np.int64)
+    lab, go, gc, gl, gi = oracle.local_aggregate(ln, inc, po, sl, si, 0.0, 1.0)
+    l2g, dl, di, dc = oracle.merge(gc, gl, gi, sl, si, 0.0, 1.0)
+    X, Y = oracle.normalised(ln, inc, sl, si, 1.0)
+    ref, _ = oracle.greedy(X, Y, 0.0)
+    sym = oracle.symbolize(lab, po, go, l2g)
+    # identical points (same len, inc) are merged either way; partitions must agree
+    assert np.array_equal(sym, ref)
+
+
+def test_merge_alpha0_merges_identical_only():
+    gc = np.array([1, 2, 1, 3], np.int64)
+    gl = np.array([5, 10, 5, 9], np.int64)
+    def limbs(v):
+        u = oracle.fx_of(v) % (1 << 256)
+        return np.array([(u >> (64 * i)) & (2**64 - 1) for i in range(4)], np.uint64)
+    gi = np.stack([limbs(v) for v in [1.0, 2.0, 1.0, 0.5]])
+    l2g, dl, di, dc = oracle.merge(gc, gl, gi, 1.0, 1.0, 0.0, 1.0)
+    assert l2g[0] == l2g[1] == l2g[2] != l2g[3]          # centres (5, 1) x3 identical; (3, 1/6) differs
+    # the centre (3, 1/6) has the smaller norm, so its global group is created first
+    assert l2g[3] == 0 and dc.tolist() == [3, 4]
