@@ -21,11 +21,11 @@
 
 /* ------------------------------------------------------------------------ */
 /* Exact fixed-point accumulator (order-independent sums of doubles).        */
-/* A value v is represented by the integer floor_toward_zero(v * 2^96) held  */
-/* in 256-bit two's complement (4 little-endian 64-bit limbs).  Sums of such */
-/* integers are exact, so any summation order gives the same total; the     */
-/* total is rounded once to double (round to nearest, ties to even).        */
-/* Range contract: |v| < 2^120 per term (callers guarantee far less).        */
+/* A value v is represented by the integer trunc(v * 2^64) (truncation       */
+/* toward zero) held in 256-bit two's complement (4 little-endian 64-bit     */
+/* limbs).  Sums of such integers are exact, so any summation order gives   */
+/* the same total; the total is rounded once to double (nearest, ties to    */
+/* even).  Range contract: |v| < 2^120 per term (callers guarantee far less).*/
 /* ------------------------------------------------------------------------ */
 typedef struct { uint64_t w[4]; } jo_fx;
 
@@ -49,23 +49,50 @@ static void fx_neg(jo_fx* a) {
   }
 }
 
-/* Exact magnitude |v| * 2^96 truncated toward zero, with the sign of v. */
-static void fx_from_double(jo_fx* out, double v) {
+/* out = (neg ? -1 : 1) * trunc(mag * 2^sh), mag < 2^110. */
+static void fx_from_scaled(jo_fx* out, unsigned __int128 mag, int sh, int neg) {
   fx_zero(out);
-  if (v == 0.0) return;
-  int e;
-  double f = frexp(fabs(v), &e);          /* |v| = f * 2^e, f in [0.5, 1) */
-  uint64_t m = (uint64_t)ldexp(f, 53);    /* exact 53-bit integer          */
-  int sh = e - 53 + 96;                   /* |v| * 2^96 = m * 2^sh         */
-  if (sh <= -64) return;                  /* below resolution: zero        */
   if (sh < 0) {
-    m >>= -sh;                            /* truncate toward zero          */
+    if (sh <= -128) return;
+    mag >>= -sh;                               /* truncate toward zero */
     sh = 0;
   }
-  int limb = sh / 64, bit = sh % 64;
-  if (limb < 4) out->w[limb] = m << bit;
-  if (bit && limb + 1 < 4) out->w[limb + 1] = m >> (64 - bit);
-  if (v < 0) fx_neg(out);
+  if (!mag) return;
+  for (int i = 0; i < 4; ++i) {                /* place mag << sh into 256 bits */
+    int lo = 64 * i;
+    unsigned __int128 part;
+    if (sh >= lo + 64) part = 0;
+    else if (sh >= lo) part = mag << (sh - lo);
+    else part = (sh - lo) <= -128 ? 0 : mag >> (lo - sh);
+    out->w[i] = (uint64_t)part;
+  }
+  if (neg) fx_neg(out);
+}
+
+/* v = m * 2^E with m an integer of at most 53 bits. */
+static void split_double(double v, uint64_t* m, int* E) {
+  int e;
+  double f = frexp(fabs(v), &e);               /* |v| = f * 2^e, f in [0.5, 1) */
+  *m = (uint64_t)ldexp(f, 53);
+  *E = e - 53;
+}
+
+/* Fixed-point image of v: trunc(v * 2^64). */
+static void fx_from_double(jo_fx* out, double v) {
+  if (v == 0.0) { fx_zero(out); return; }
+  uint64_t m;
+  int E;
+  split_double(v, &m, &E);
+  fx_from_scaled(out, m, E + 64, v < 0);
+}
+
+/* Fixed-point image of the EXACT square of v: trunc(v^2 * 2^64). */
+static void fx_from_square(jo_fx* out, double v) {
+  if (v == 0.0) { fx_zero(out); return; }
+  uint64_t m;
+  int E;
+  split_double(v, &m, &E);
+  fx_from_scaled(out, (unsigned __int128)m * m, 2 * E + 64, 0);
 }
 
 static void fx_add_double(jo_fx* a, double v) {
@@ -78,7 +105,7 @@ static void fx_add_double(jo_fx* a, double v) {
 static int fx_bit(const jo_fx* m, int b) { return (int)((m->w[b / 64] >> (b % 64)) & 1u); }
 
 /* Round the 256-bit integer to double (nearest, ties to even), then scale by
- * 2^-96 (exact: results here are far from the subnormal range). */
+ * 2^-64 (exact: results here are far from the subnormal range). */
 static double fx_to_double(const jo_fx* a) {
   jo_fx m = *a;
   int neg = (int)(m.w[3] >> 63);
@@ -89,7 +116,7 @@ static double fx_to_double(const jo_fx* a) {
   if (top < 0) return 0.0;
   double r;
   if (top <= 52) {
-    r = ldexp((double)m.w[0], -96);              /* fewer than 54 bits: exact */
+    r = ldexp((double)m.w[0], -64);              /* fewer than 54 bits: exact */
   } else {
     int lo = top - 52;                            /* keep bits lo..top         */
     uint64_t sig = 0;
@@ -97,7 +124,7 @@ static double fx_to_double(const jo_fx* a) {
     int rb = fx_bit(&m, lo - 1), sticky = 0;
     for (int b = lo - 2; b >= 0 && !sticky; --b) sticky = fx_bit(&m, b);
     if (rb && (sticky || (sig & 1u))) sig += 1;   /* 2^53 is still exact       */
-    r = ldexp((double)sig, lo - 96);
+    r = ldexp((double)sig, lo - 64);
   }
   return neg ? -r : r;
 }
@@ -252,8 +279,9 @@ void jo_compress_all(const double* x, const int64_t* dom_begin, const int64_t* d
 /* ------------------------------------------------------------------------ */
 /* Normalisation (Sec. 3.2, Eq. 4): sigma_len, sigma_inc are the population  */
 /* standard deviations of all pieces of all domains (the dictionary is       */
-/* shared).  Sums are exact (integers for len, fixed point for inc), so the  */
-/* result does not depend on summation order; then                          */
+/* shared).  Sums are exact (integers for len; fixed point, of inc and of    */
+/* the exact square of inc, for inc), so the result does not depend on      */
+/* summation order; then, in FP64,                                          */
 /*   m = S1 / N;  v = S2 / N - m * m;  sigma = sqrt(v), or 1 when v <= 0.     */
 /* ------------------------------------------------------------------------ */
 static double sigma_from(double s1, double s2, double n) {
@@ -273,7 +301,9 @@ void jo_sigma(const int32_t* len, const double* inc, int64_t n, double* sigma_le
     s1 += len[j];
     s2 += (unsigned __int128)((int64_t)len[j] * (int64_t)len[j]);
     fx_add_double(&i1, inc[j]);
-    fx_add_double(&i2, inc[j] * inc[j]);
+    jo_fx sq;
+    fx_from_square(&sq, inc[j]);
+    fx_add_fx(&i2, &sq);
   }
   double dn = (double)n;
   *sigma_len = sigma_from((double)s1, u128_to_double(s2), dn);

@@ -15,29 +15,34 @@ from _golden import load
 
 def test_fixed_point_exact():
     rng = np.random.default_rng(0)
-    for v in list(rng.standard_normal(200) * 10.0 ** rng.integers(-20, 15, 200)) + [0.0, -0.0, 1.5, -2.75, 2.0**-96, -(2.0**-97)]:
+    for v in list(rng.standard_normal(200) * 10.0 ** rng.integers(-20, 15, 200)) + [0.0, -0.0, 1.5, -2.75, 2.0**-64, -(2.0**-65)]:
         got = oracle.fx_of(v)
-        f = Fraction(v) * 2**96
+        f = Fraction(v) * 2**64
         want = math.floor(f) if f >= 0 else -math.floor(-f)            # truncate toward zero
         assert got == want
-    vals = rng.standard_normal(10000) * 3.0
+    # multiples of 2^-40: no bits below the 2^-64 resolution, so the fixed-point
+    # total is the exact sum, and its rounding must equal math.fsum's
+    vals = np.round(rng.standard_normal(10000) * 3.0 * 2**40) / 2**40
     assert oracle.fx_sum(vals) == math.fsum(vals)                    # correctly rounded exact sum
-    vals = np.concatenate([vals, -vals[:5000], [1e10, -1e10, 0.1]])
+    vals = np.concatenate([vals, -vals[:5000], [1e10, -1e10, 0.125]])
     assert oracle.fx_sum(vals) == math.fsum(vals)
     assert oracle.fx_sum(np.array([1.0, 2.0**-60, 2.0**-60])) == 1.0 + 2.0**-59
 
 
 def test_fixed_point_rounding_ties_even():
-    # 2^53 + 1 (in units of 2^-96) is a tie between 2^53 and 2^53 + 2
+    # 2^53 + 1 (in units of 2^-64) is a tie between 2^53 and 2^53 + 2
     u = (2**53 + 1)
     limbs = np.array([u & (2**64 - 1), u >> 64, 0, 0], np.uint64)
-    assert oracle.fx_round(limbs) == float(2**53) * 2.0**-96
+    assert oracle.fx_round(limbs) == float(2**53) * 2.0**-64
     u = (2**53 + 3)
     limbs = np.array([u, 0, 0, 0], np.uint64)
-    assert oracle.fx_round(limbs) == float(2**53 + 4) * 2.0**-96
+    assert oracle.fx_round(limbs) == float(2**53 + 4) * 2.0**-64
     neg = (1 << 256) - (2**54 + 1)                                   # -(2^54 + 1): rounds to -2^54
     limbs = np.array([(neg >> (64 * i)) & (2**64 - 1) for i in range(4)], np.uint64)
-    assert oracle.fx_round(limbs) == -float(2**54) * 2.0**-96
+    assert oracle.fx_round(limbs) == -float(2**54) * 2.0**-64
+    big = (2**70 + 2**17 + 1) << 3                                   # above-half remainder rounds up
+    limbs = np.array([(big >> (64 * i)) & (2**64 - 1) for i in range(4)], np.uint64)
+    assert oracle.fx_round(limbs) == float(Fraction(big, 2**64))
 
 
 def test_sigma_population_std():
@@ -47,11 +52,20 @@ def test_sigma_population_std():
     sl, si = oracle.sigma(ln, inc)
     assert abs(sl - np.std(ln.astype(np.float64))) <= 1e-12 * sl
     assert abs(si - np.std(inc)) <= 1e-12 * si
-    # exact definition: mean-of-squares minus squared mean from exact sums
+    # exact definition: mean-of-squares minus squared mean from exact sums of
+    # inc and of the exact squares, each term truncated at 2^-64
     n = len(ln)
-    m = math.fsum(inc) / n
-    v = math.fsum(inc * inc) / n - m * m
+
+    def trunc64(f):
+        f = f * 2**64
+        return (math.floor(f) if f >= 0 else -math.floor(-f))
+
+    s1 = float(Fraction(sum(trunc64(Fraction(v)) for v in inc), 2**64))
+    s2 = float(Fraction(sum(trunc64(Fraction(v) ** 2) for v in inc), 2**64))
+    m = s1 / n
+    v = s2 / n - m * m
     assert si == math.sqrt(v)
+    assert sl == math.sqrt(float(int((ln.astype(np.int64) ** 2).sum())) / n - (float(int(ln.sum())) / n) ** 2)
     # degenerate: all lengths equal -> sigma_len = 1 (divisor 1)
     assert oracle.sigma(np.full(7, 3, np.int32), np.arange(7.0))[0] == 1.0
 
