@@ -1,0 +1,377 @@
+"""Throughput benchmark of the JABBA symbolization path on GB300.
+
+Metric: series points symbolized per second (Gpts/s) through the whole
+forward path (domains, Eq. 1 compression, normalisation, per-domain greedy
+aggregation, global merge, label propagation), with the input resident in HBM
+(`value`), and end to end through the same C-ABI calls with the input copied
+from pinned host memory and the symbols + dictionary read back inside the
+timed region (`e2e`).  Workload: the scale-stress collection (100,000 series,
+log-uniform lengths in [100, 100,000], ~1.44e9 points, 11.5 GB of float64 --
+far larger than L2, so no flush is needed between steps).
+
+Forms timed: "batched" = the whole step captured once in a CUDA graph and
+replayed (persistent work-stealing kernels); "plain" = the same C-ABI calls
+issued eagerly.  The CPU oracle is timed on a bounded sample of the same
+workload on the host cores (`cpu_baseline`); `--impl reference` times only
+that oracle, as the reference arm.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the path is timed per GPU; replicas only), the max time over ranks
+is taken and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "series points symbolized/sec (Gpts/s) and % of HBM roofline, batched vs plain, 1 GB300"
+WORKLOAD_DESC = {
+    "scale": "scale stress: 100,000 series, lengths log-uniform [100, 100,000], walk/sinusoid+AR(1)/level-shift "
+             "generators, z-normalised, FIXED_LEN 4,096-interval domains, tol=0.1 alpha=0.1 scl=1",
+    "uneven": "uneven batch: 10,000 series, lengths U[500, 50,000], walk + level shifts, FIXED_LEN 1,000, "
+              "tol=alpha=0.05",
+    "multivar": "multivariate: 64 channels x 2^20, 3 sinusoids + AR(1), 1,024 equal domains per channel, "
+                "tol=0.1 alpha=0.2",
+    "diff": "1,024 x 10,000 walk + sinusoid, 4 equal domains, tol=alpha=0.1",
+    "small": "16 x 2,000 walk + sinusoid, 4 equal domains, tol=alpha=0.1",
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+def oracle_step(x, off, cfg, threads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.pipeline(x, off, cfg["tol"], cfg["alpha"], cfg["scl"], cfg["domain_mode"], cfg["domain_value"],
+                    threads=threads, with_reconstruct=False)
+    return time.perf_counter() - t0
+
+
+def cpu_sample(workload, sample_series):
+    import synth
+    x, off, cfg = synth.make(workload, max_series=sample_series)
+    return x, off, cfg
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the FP64 CPU oracle (the paper's multicore design:
+    parallel compression over domains, serial digitization) on a bounded
+    sample of the same workload per step."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    x, off, cfg = cpu_sample(args.workload, args.cpu_series)
+    for _ in range(args.warmup):
+        oracle_step(x, off, cfg, threads)
+    t = 0.0
+    for _ in range(args.steps):
+        t += oracle_step(x, off, cfg, threads)
+    n = len(x)
+    value = n * args.steps / t / 1e9
+    sample = f"first {args.cpu_series} series of the workload ({n} points) per step"
+    line = dict(metric=METRIC, value=value, unit="Gpts/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD_DESC[args.workload], sample=sample),
+                cpu_baseline=dict(value=value, unit="Gpts/s", cores=threads, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="Gpts/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2401_00109_gb300 as jb
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    S, n = synth.sizes(args.workload, args.max_series)
+    # pinned host input (the e2e leg copies it every step)
+    x_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    t_gen = time.perf_counter()
+    _, off_np, cfg = synth.make(args.workload, max_series=args.max_series, out=x_host.numpy())
+    t_gen = time.perf_counter() - t_gen
+    off_host = torch.from_numpy(off_np).pin_memory()
+    p = jb.Params(tol=cfg["tol"], alpha=cfg["alpha"], scl=cfg["scl"], domain_mode=cfg["domain_mode"],
+                  domain_value=cfg["domain_value"])
+    ctx = jb.Context(local)
+    # size the group table from one sizing pass (capacity = 1.25 x observed)
+    pl = jb.Pipeline(ctx, off_np, n, p, group_capacity=max(1 << 16, n // 16))
+    pl.x.copy_(x_host, non_blocking=True)
+    pl.enqueue()
+    try:
+        ctx.sync_status(where="sizing step")
+        need = int(pl.b["n_groups"][0].item())
+    except jb.JabbaError as e:
+        if e.code != jb.ERR_CAPACITY:
+            raise
+        need = int(pl.b["n_groups"][0].item())
+    gcap = int(need * 1.25) + 1024
+    if gcap > pl.gcap or gcap < pl.gcap // 4:
+        del pl
+        torch.cuda.empty_cache()
+        pl = jb.Pipeline(ctx, off_np, n, p, group_capacity=gcap)
+        pl.x.copy_(x_host, non_blocking=True)
+    st = torch.cuda.current_stream()
+
+    # ---- batched: graph capture of the whole step; one graph per timed step
+    # so each keeps its own event pair around the compression kernel
+    pl.enqueue()
+    ctx.sync_status(where="eager step")
+    graphs = []
+    for i in range(args.warmup + args.steps):
+        ctx.profile_slot(i if i < 256 else -1)
+        graphs.append(pl.capture())
+    ctx.profile_slot(-1)
+    kernels_per_step = jb.graph_kernel_nodes(graphs[0])
+    for i in range(args.warmup):
+        graphs[i].replay()
+    torch.cuda.synchronize()
+    ctx.sync_status(where="warm-up")
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(args.steps):
+        graphs[args.warmup + i].replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ctx.sync_status(where="timed steps")
+    ms_all = max_over_ranks(ms, ws)
+    comp_ms = [ctx.profile_elapsed(args.warmup + i, 0) for i in range(args.steps)]
+    fin_ms = [ctx.profile_elapsed(args.warmup + i, 1) for i in range(args.steps)]
+    loc_ms = [ctx.profile_elapsed(args.warmup + i, 2) for i in range(args.steps)]
+    mrg_ms = [ctx.profile_elapsed(args.warmup + i, 3) for i in range(args.steps)]
+    sym_ms = [ctx.profile_elapsed(args.warmup + i, 4) for i in range(args.steps)]
+    res = pl.results()
+    N, G, k = res["n_pieces"], res["n_groups"], res["k"]
+    value = ws * n / (ms_all * 1e-3) / 1e9
+
+    # ---- plain: the same calls issued eagerly, no graph
+    plain = None
+    if not args.no_plain:
+        for _ in range(2):
+            pl.enqueue()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            pl.enqueue()
+        e1.record(st)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+        plain = dict(value=ws * n / (pms * 1e-3) / 1e9, unit="Gpts/s", ms_per_step=pms,
+                     form="same C-ABI calls issued eagerly per step (no CUDA graph)")
+
+    # ---- e2e: H2D of the series from pinned memory, the step, D2H of the
+    # symbols and dictionary, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        sym_host = torch.empty(max(N, 1), dtype=torch.int32, pin_memory=True)
+        dl_host = torch.empty(max(k, 1), dtype=torch.float64, pin_memory=True)
+        di_host = torch.empty(max(k, 1), dtype=torch.float64, pin_memory=True)
+        dc_host = torch.empty(max(k, 1), dtype=torch.int64, pin_memory=True)
+
+        def e2e_step():
+            pl.x.copy_(x_host, non_blocking=True)
+            pl.series_off.copy_(off_host, non_blocking=True)
+            graphs[-1].replay()
+            sym_host[:N].copy_(pl.b["symbol"][:N], non_blocking=True)
+            dl_host[:k].copy_(pl.b["dict_len"][:k], non_blocking=True)
+            di_host[:k].copy_(pl.b["dict_inc"][:k], non_blocking=True)
+            dc_host[:k].copy_(pl.b["dict_count"][:k], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0.record(st)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+        bi = 8 * n + 8 * (S + 1)
+        bo = 4 * N + 24 * k
+        e2e = dict(value=ws * n / (ems * 1e-3) / 1e9, unit="Gpts/s", h2d_bytes_per_step=bi, d2h_bytes_per_step=bo,
+                   ms_per_step=ems)
+        ctx.sync_status(where="e2e steps")
+
+    # ---- roofline of the dominant kernel (compression): algorithmic bytes =
+    # 8 B per point read + 12 B per piece written (len int32, end value f64)
+    peak, peak_kind = peaks()
+    comp_avg = float(np.mean(comp_ms))
+    alg_bytes = 8.0 * n + 12.0 * N
+    achieved = alg_bytes / (comp_avg * 1e-3) / 1e9
+    roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                    traffic=None, kernel="k_compress", peak_source=peak_kind,
+                    algorithmic_bytes_per_launch=alg_bytes, ms_per_launch=comp_avg,
+                    path_frac_of_point_roofline=value / ws / (peak / 8.0))
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        xs, offs, cfgs = cpu_sample(args.workload, args.cpu_series)
+        tcpu = oracle_step(xs, offs, cfgs, threads)
+        cpu = dict(value=len(xs) / tcpu / 1e9, unit="Gpts/s", cores=threads, kind="oracle",
+                   sample=f"first {args.cpu_series} series of the workload ({len(xs)} points), one pass; "
+                          f"compression on {threads} threads, digitization serial")
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="Gpts/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms_all, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                    data="synthetic",
+                    config=dict(workload=WORKLOAD_DESC[args.workload], n_series=S, n_points=n, pieces=N,
+                                local_groups=G, dictionary=k, parallelism=f"replicas x{ws}",
+                                l2="input 8 B/point >> L2 (no flush needed)" if 8 * n > 2e9 else "input fits L2",
+                                form="batched: CUDA-graph replay of the whole step"),
+                    roofline=roofline, cpu_baseline=cpu, e2e=e2e, plain=plain, clocks=clocks,
+                    gpu_launches=kernels_per_step * args.steps,
+                    stage_ms=dict(compress=float(np.mean(comp_ms)), finish=float(np.mean(fin_ms)),
+                                  local=float(np.mean(loc_ms)), merge=float(np.mean(mrg_ms)),
+                                  symbolize=float(np.mean(sym_ms))),
+                    input_gen_s=t_gen)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="scale")
+    ap.add_argument("--max-series", type=int, default=None)
+    ap.add_argument("--cpu-series", type=int, default=2000)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

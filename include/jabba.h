@@ -1,0 +1,229 @@
+/*
+ * jabba.h -- C ABI of the GB300 (sm_103a) JABBA symbolization library.
+ *
+ * JABBA (joint adaptive Brownian-bridge-based aggregation, arXiv 2401.00109)
+ * turns many time series into symbols over ONE shared dictionary:
+ *   1. domains      series are cut into domains with shared endpoints
+ *                   (Alg. 1 Phase I; Sec. 4.1.1)
+ *   2. compress     each domain becomes (len, inc) pieces under tol
+ *                   (Sec. 3.1 Eq. 1; Alg. 1 Phase II; Sec. 4.1.2)
+ *   3. digitize     pieces are normalised by their standard deviations
+ *      (local)      (Sec. 3.2 Eq. 4) and greedily aggregated within alpha,
+ *                   separately in each domain (Sec. 5 Stage I)
+ *   4. merge        the local groups, taken at their centres, are aggregated
+ *                   once more into the shared dictionary (Sec. 5 Stage II)
+ *   5. symbolize    labels are composed through the local->global map
+ *                   (Sec. 5 label propagation; no reassignment pass)
+ *   6. reconstruct  symbols -> quantized chain -> series (Sec. 3.3)
+ *
+ * Conventions for every call below.
+ *  - Pointers are DEVICE pointers (caller-owned, e.g. torch tensor storage)
+ *    unless the name ends in _host.  The library never frees them.
+ *  - Calls are asynchronous and ordered on `stream`.  Argument errors are
+ *    returned synchronously.  Errors found on the device (non-finite input,
+ *    values out of range, capacity overflow, a bounded wait that timed out)
+ *    set the context's device status word; jabba_sync_status() synchronizes
+ *    `stream` and returns (and clears) it.
+ *  - Counts that depend on the data (pieces, groups, dictionary size) are
+ *    written to device scalars so that a whole step can be captured in a
+ *    CUDA graph; the context owns only scratch space, allocated by
+ *    jabba_reserve() (or grown by a call made outside graph capture).
+ *  - Floating point is IEEE binary64.  Every decision the paper's method
+ *    takes (breakpoints, orderings, memberships) equals the decision of the
+ *    FP64 definition stated at each call.
+ *  - Layout: a collection of S series is CSR: x[n_points] (float64) and
+ *    series_off[S+1] (int64); series s is x[series_off[s] .. series_off[s+1]).
+ *    Contract: every x is finite with |x| < 2^31; a series has < 2^31 points.
+ *  - Pieces and per-piece labels are SLOTTED: the pieces of domain d occupy
+ *    slots [dom_slot_off[d], dom_slot_off[d] + dom_piece_cnt[d]) of arrays
+ *    sized n_slots = total number of intervals (an upper bound on pieces).
+ *    dom_piece_off[d] (exclusive scan of dom_piece_cnt) is the compact
+ *    concatenation P = P^(1) + ... + P^(M) of Sec. 4.1.3, used by the symbols.
+ *  - One context per stream at a time; contexts are not thread-safe.
+ */
+#ifndef JABBA_H
+#define JABBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* jabba_stream; /* same type as cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  JABBA_OK = 0,
+  JABBA_ERR_INVALID_ARG = 1, /* bad argument (returned synchronously)                          */
+  JABBA_ERR_CAPACITY = 2,    /* an output or scratch capacity is too small                      */
+  JABBA_ERR_NONFINITE = 3,   /* NaN or infinity in the input series                             */
+  JABBA_ERR_CUDA = 4,        /* a CUDA runtime call failed                                      */
+  JABBA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                              */
+  JABBA_ERR_STATE = 6,       /* call out of order (e.g. missing reservation during capture)     */
+  JABBA_ERR_RANGE = 7        /* an input value is outside the documented range (|x| >= 2^31)    */
+} jabba_status;
+
+typedef struct jabba_ctx jabba_ctx;
+
+typedef struct {
+  double tol;           /* compression tolerance, >= 0 (Eq. 1)                                 */
+  double alpha;         /* aggregation radius in normalised units, >= 0 (Sec. 3.2)              */
+  double scl;           /* length weight, >= 0 (Eq. 4); 0 ignores lengths                      */
+  int32_t domain_mode;  /* 0 = EQUAL_COUNT: min(value, n_s-1) domains per series,
+                           boundaries floor(k (n_s-1) / M_s);
+                           1 = FIXED_LEN: domains of `value` intervals (last one shorter)      */
+  int32_t round_mode;   /* quantization rounding (Sec. 3.3): 0 = half away from zero, 1 = half to even */
+  int64_t domain_value; /* M (EQUAL_COUNT) or interval count (FIXED_LEN), >= 1                  */
+} jabba_params;
+
+/* Local group record (Sec. 5 Stage I output), 48 bytes.  Exact sums make every
+ * centre independent of summation order. */
+typedef struct {
+  uint64_t inc[3];  /* sum of member increments, signed 192-bit two's complement in units of 2^-64
+                       (each increment truncated toward zero at 2^-64)                          */
+  int64_t lensum;   /* sum of member lengths                                                     */
+  int32_t count;    /* member count                                                              */
+  int32_t local_id; /* id within its domain (creation order of the greedy)                       */
+  int32_t domain;   /* domain index                                                              */
+  int32_t pad;
+} jabba_group;
+
+#define JABBA_PIECE_STATS_BYTES 256 /* opaque exact-sum accumulators of jabba_compress */
+
+/* ---------------------------------------------------------------- context */
+jabba_status jabba_create(jabba_ctx** ctx, int device);
+void jabba_destroy(jabba_ctx* ctx);
+const char* jabba_status_string(jabba_status s);
+const char* jabba_version(void);
+
+/* Synchronize `stream`, return the device status word (first error wins) and
+ * clear it. */
+jabba_status jabba_sync_status(jabba_ctx* ctx, jabba_stream stream);
+
+/* Host-side planning (Alg. 1 Phase I): number of domains, of slots (total
+ * intervals) and the largest domain (in intervals) for
+ * series_off_host[n_series+1].  max_dom_intervals may be NULL. */
+jabba_status jabba_plan(const int64_t* series_off_host, int64_t n_series, const jabba_params* p,
+                        int64_t* n_domains, int64_t* n_slots, int64_t* max_dom_intervals);
+
+/* Pre-allocate the context's scratch for collections up to these sizes, so
+ * that later calls allocate nothing (required before CUDA-graph capture).
+ * max_dom_intervals (from jabba_plan) sizes the scratch of domains with more
+ * pieces than the on-chip tile (4096); a domain above the reservation makes
+ * jabba_digitize_local report JABBA_ERR_CAPACITY. */
+jabba_status jabba_reserve(jabba_ctx* ctx, int64_t n_points, int64_t n_series, int64_t n_domains,
+                           int64_t n_slots, int64_t group_capacity, int64_t max_dom_intervals);
+
+/* ---------------------------------------------------------------- 1+2. compress
+ * Builds the domain table (Alg. 1 Phase I, Sec. 4.1.1: consecutive domains of
+ * one series share an endpoint, s_{k+1} = e_k) and compresses every domain
+ * independently (Sec. 3.1 Eq. 1, greedy extension): from start s the end e
+ * grows while the next end is admissible,
+ *     sum_{k=1}^{L-1} ((x_s + (inc * k) / L) - x_{s+k})^2 <= (L - 1) * (tol * tol),
+ * L = e - s, inc = x_e - x_s (FP64, evaluated in that order), and stops at the
+ * first inadmissible end.  A piece is (len = L, inc).
+ * Outputs (device):
+ *   dom_begin, dom_end [n_domains]  inclusive global indices into x
+ *   dom_series [n_domains]          series of each domain
+ *   series_dom_off [n_series+1]     first domain of each series
+ *   dom_slot_off [n_domains+1]      first slot of each domain (exclusive scan of intervals)
+ *   piece_len, piece_inc [n_slots]  slotted pieces
+ *   dom_piece_cnt [n_domains]       pieces per domain
+ *   dom_piece_off [n_domains+1]     compact offsets (exclusive scan of counts)
+ *   piece_stats [JABBA_PIECE_STATS_BYTES]  exact sums for the normalisation
+ * n_domains, n_slots must equal jabba_plan()'s values for this series_off. */
+jabba_status jabba_compress(jabba_ctx* ctx, const double* x, int64_t n_points, const int64_t* series_off,
+                            int64_t n_series, const jabba_params* p, int64_t n_domains, int64_t n_slots,
+                            int64_t* dom_begin, int64_t* dom_end, int32_t* dom_series, int64_t* series_dom_off,
+                            int64_t* dom_slot_off, int32_t* piece_len, double* piece_inc, int32_t* dom_piece_cnt,
+                            int64_t* dom_piece_off, void* piece_stats, jabba_stream stream);
+
+/* ---------------------------------------------------------------- 3. local digitization
+ * Normalisation (Sec. 3.2 Eq. 4): sigma_len, sigma_inc = population standard
+ * deviations over ALL pieces (from exact sums: m = S1/N, v = S2/N - m*m,
+ * sigma = sqrt(v), or 1 when v <= 0), X = (scl * len) / sigma_len,
+ * Y = inc / sigma_inc.  Greedy aggregation per domain (Sec. 3.2, Sec. 5
+ * Stage I with one block per domain): pieces in order of X*X + Y*Y (ties by
+ * position); each unassigned piece starts a group and every later unassigned
+ * piece q with (X_q - X_p)^2 + (Y_q - Y_p)^2 <= alpha^2 joins it.
+ * Outputs: sigma[2] = {sigma_len, sigma_inc}; local_label [n_slots] (slotted,
+ * group id within the domain); dom_group_cnt [n_domains]; dom_group_off
+ * [n_domains+1] (exclusive scan); groups[group_capacity] (one record per
+ * local group, in no particular order; record identity = (domain, local_id));
+ * n_groups (device scalar).  Overflow of group_capacity -> JABBA_ERR_CAPACITY. */
+jabba_status jabba_digitize_local(jabba_ctx* ctx, const int32_t* piece_len, const double* piece_inc,
+                                  const int64_t* dom_slot_off, const int32_t* dom_piece_cnt, int64_t n_domains,
+                                  const void* piece_stats, const jabba_params* p, double* sigma,
+                                  int32_t* local_label, int32_t* dom_group_cnt, int64_t* dom_group_off,
+                                  jabba_group* groups, int64_t group_capacity, int64_t* n_groups,
+                                  jabba_stream stream);
+
+/* ---------------------------------------------------------------- 4. global merge
+ * Sec. 5 Stage II: the same greedy over all local groups, each taken as the
+ * point (X, Y) of its centre (c_len = lensum / count, c_inc = round(inc) / count,
+ * X = (scl * c_len) / sigma_len, Y = c_inc / sigma_inc), ordered by X*X + Y*Y
+ * with ties broken by compact group index dom_group_off[domain] + local_id.
+ * Global ids follow creation order.  Outputs: l2g [G] indexed by compact
+ * group index; dictionary entry c = exact mean of its member pieces:
+ * dict_len[c] = lensum / count, dict_inc[c] = round(sum inc) / count,
+ * dict_count[c] = count; k (device scalar).  k > dict_capacity ->
+ * JABBA_ERR_CAPACITY. */
+jabba_status jabba_merge_global(jabba_ctx* ctx, const jabba_group* groups, const int64_t* n_groups,
+                                int64_t group_capacity, const int64_t* dom_group_off, const double* sigma,
+                                const jabba_params* p, int32_t* l2g, double* dict_len, double* dict_inc,
+                                int64_t* dict_count, int64_t dict_capacity, int64_t* k, jabba_stream stream);
+
+/* ---------------------------------------------------------------- 5. symbolize
+ * Sec. 5 label propagation: symbol[dom_piece_off[d] + j] =
+ * l2g[dom_group_off[d] + local_label[dom_slot_off[d] + j]], j < dom_piece_cnt[d].
+ * symbol is compact (length = total pieces). */
+jabba_status jabba_symbolize(jabba_ctx* ctx, const int32_t* local_label, const int64_t* dom_slot_off,
+                             const int32_t* dom_piece_cnt, const int64_t* dom_piece_off,
+                             const int64_t* dom_group_off, int64_t n_domains, const int32_t* l2g,
+                             int32_t* symbol, jabba_stream stream);
+
+/* ---------------------------------------------------------------- 6. reconstruct
+ * Sec. 3.3, per series: inverse digitization (l~, i~) = dictionary entry of
+ * each symbol; quantization v = l~ + e, l^ = round(v) (round_mode), e = v - l^,
+ * e_0 = 0; inverse compression from t_0 = x[series_off[s]]:
+ * xhat[pos + q] = level + (i~ * q) / l^ for q = 1..l^, then level += i~ and
+ * pos += l^; points past the series end are dropped, a short chain leaves the
+ * tail at the final level.  The pieces of series s are compact symbols
+ * [dom_piece_off[series_dom_off[s]], dom_piece_off[series_dom_off[s+1]]).
+ * Outputs: qlen (compact, l^ per piece), xhat [n_points]. */
+jabba_status jabba_reconstruct(jabba_ctx* ctx, const double* x, int64_t n_points, const int64_t* series_off,
+                               int64_t n_series, const int64_t* series_dom_off, const int64_t* dom_piece_off,
+                               const int32_t* symbol, const double* dict_len, const double* dict_inc,
+                               const jabba_params* p, int32_t* qlen, double* xhat, jabba_stream stream);
+
+/* Adjoint of the reconstruction MSE = (1/n) sum (xhat - x)^2 with respect to
+ * dict_inc, lengths l^ (qlen from jabba_reconstruct) held fixed: xhat is then
+ * affine in dict_inc and d xhat_{pos_j+q} / d i~_{a_j} = q / l^_j (q <= l^_j),
+ * = 1 for every later point of the series.  Recomputes xhat on the fly (no
+ * per-point activations are stored).  grad_dict_inc [k] is overwritten. */
+jabba_status jabba_reconstruct_backward(jabba_ctx* ctx, const double* x, int64_t n_points,
+                                        const int64_t* series_off, int64_t n_series,
+                                        const int64_t* series_dom_off, const int64_t* dom_piece_off,
+                                        const int32_t* symbol, const int32_t* qlen, const double* dict_inc,
+                                        int64_t k, double* grad_dict_inc, jabba_stream stream);
+
+/* Timing hooks for benchmarks (no counterpart in the paper).  While
+ * `slot` >= 0 (0..255), every call of a step records a pair of CUDA events
+ * around its main kernel on the call's stream, into that slot; the records
+ * use cudaEventRecordExternal, so a graph captured meanwhile keeps them.
+ * slot = -1 stops recording.  jabba_profile_elapsed synchronizes the events
+ * of (slot, stage) and returns the milliseconds between them.  Stages:
+ * 0 = compression kernel, 1 = increments + exact sums, 2 = local aggregation,
+ * 3 = global merge (whole call), 4 = label propagation. */
+jabba_status jabba_profile_slot(jabba_ctx* ctx, int slot);
+jabba_status jabba_profile_elapsed(jabba_ctx* ctx, int slot, int stage, float* ms);
+
+/* Reconstruction error (Sec. 3.3): *out (device scalar) = (1/n) sum (x - xhat)^2,
+ * summed in a fixed order (the same result on every call on a device). */
+jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int64_t n_points, double* out,
+                       jabba_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JABBA_H */

@@ -1,0 +1,392 @@
+// api.cu -- the C ABI (include/jabba.h): argument checks, the context and its
+// scratch, and the stream-ordered launches of each step.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+
+using namespace jabba;
+
+constexpr int kProfSlots = 256;
+constexpr int kProfStages = 5;
+
+struct jabba_ctx {
+  int device = 0;
+  int prof_slot = -1;
+  cudaEvent_t prof[kProfSlots][kProfStages][2] = {};
+  unsigned* status = nullptr;  // device status word
+  Scratch ws;
+  void* pool = nullptr;        // one allocation backing the scratch
+  size_t pool_bytes = 0;
+};
+
+namespace {
+
+jabba_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? JABBA_OK : JABBA_ERR_CUDA; }
+
+// Event pair of (current slot, stage), created on first use; null when off.
+cudaEvent_t prof_event(jabba_ctx* c, int stage, int which) {
+  if (c->prof_slot < 0) return nullptr;
+  cudaEvent_t& e = c->prof[c->prof_slot][stage][which];
+  if (!e && cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+  return e;
+}
+
+bool params_ok(const jabba_params* p) {
+  if (!p) return false;
+  if (!(p->tol >= 0.0) || !(p->alpha >= 0.0) || !(p->scl >= 0.0)) return false;  // also rejects NaN
+  if (p->tol > 1e300 || p->alpha > 1e150 || p->scl > 1e300) return false;
+  if (p->domain_mode != 0 && p->domain_mode != 1) return false;
+  if (p->round_mode != 0 && p->round_mode != 1) return false;
+  if (p->domain_value < 1) return false;
+  return true;
+}
+
+long long series_domains_host(long long n_s, int mode, long long value) {
+  if (n_s < 2 || value < 1) return 0;
+  const long long iv = n_s - 1;
+  if (mode == 0) return value < iv ? value : iv;
+  return (iv + value - 1) / value;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve the scratch out of one pool.  Returns the bytes needed; assigns the
+// pointers when `base` is non-null.
+size_t layout(Scratch& w, long long S, long long D, long long slots, long long G, long long big,
+              unsigned char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char* {
+    unsigned char* p = base ? base + off : nullptr;
+    off += align_up(bytes ? bytes : 1);
+    return p;
+  };
+  const long long scan_n = scan_scratch_elems((S > D ? S : D) + 1) + scan_scratch_elems(256 * ((G + 4095) / 4096) + 1) + 8;
+  w.series_a = (long long*)take(8 * (S + 1));
+  w.series_b = (long long*)take(8 * (S + 1));
+  w.series_c = (long long*)take(8 * (S + 1));
+  w.scan_tiles = (long long*)take(8 * scan_n);
+  w.counters = (unsigned*)take(64);
+  w.big = take(big > 0 ? (size_t)big * 44 + 16 : 16);
+  w.m_key = (double*)take(8 * G);
+  w.m_X = (double*)take(8 * G);
+  w.m_Y = (double*)take(8 * G);
+  w.m_idx = (int*)take(4 * G);
+  w.m_k0 = (unsigned long long*)take(8 * G);
+  w.m_k1 = (unsigned long long*)take(8 * G);
+  w.m_v0 = (int*)take(4 * G);
+  w.m_v1 = (int*)take(4 * G);
+  w.m_label = (int*)take(4 * G);
+  w.m_rec = (int*)take(4 * G);
+  w.m_hist = (unsigned*)take(4 * 256 * ((G + 4095) / 4096 + 1));
+  {
+    const long long tiles = (G + 4095) / 4096;
+    const long long acc_elems = 8 * (G > 1 ? G : 1);
+    const long long off_elems = 512 * tiles + 2;
+    w.d_acc = (long long*)take(8 * (acc_elems > off_elems ? acc_elems : off_elems) + 64);
+  }
+  w.r_level = (double*)take(8 * slots);
+  w.r_pos = (long long*)take(8 * slots);
+  w.r_tsum = (double*)take(8 * slots);
+  w.r_wsum = (double*)take(8 * slots);
+  w.r_tail = (double*)take(8 * (S + 1 > 512 ? S + 1 : 512));
+  w.r_tailpos = (long long*)take(8 * (S + 1));
+  w.r_tail_level = (double*)take(8 * (S + 1));
+  return off;
+}
+
+jabba_status ensure(jabba_ctx* c, long long S, long long D, long long slots, long long G, long long big,
+                    cudaStream_t st) {
+  Scratch& w = c->ws;
+  if (S <= w.cap_series && D <= w.cap_domains && slots <= w.cap_slots && G <= w.cap_groups && big <= w.cap_big)
+    return JABBA_OK;
+  if (st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return JABBA_ERR_STATE;  // no allocation during capture
+  }
+  S = S > w.cap_series ? S : w.cap_series;
+  D = D > w.cap_domains ? D : w.cap_domains;
+  slots = slots > w.cap_slots ? slots : w.cap_slots;
+  G = G > w.cap_groups ? G : w.cap_groups;
+  big = big > w.cap_big ? big : w.cap_big;
+  Scratch tmp = w;
+  const size_t bytes = layout(tmp, S, D, slots, G, big, nullptr);
+  if (cudaDeviceSynchronize() != cudaSuccess) return JABBA_ERR_CUDA;
+  if (c->pool) cudaFree(c->pool);
+  c->pool = nullptr;
+  if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
+    c->pool_bytes = 0;
+    w.cap_series = w.cap_domains = w.cap_slots = w.cap_groups = w.cap_big = 0;
+    return JABBA_ERR_CUDA;
+  }
+  c->pool_bytes = bytes;
+  layout(w, S, D, slots, G, big, (unsigned char*)c->pool);
+  w.cap_series = S;
+  w.cap_domains = D;
+  w.cap_slots = slots;
+  w.cap_groups = G;
+  w.cap_big = big;
+  return JABBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* jabba_version(void) { return "jabba-gb300 0.1 (sm_103a)"; }
+
+const char* jabba_status_string(jabba_status s) {
+  switch (s) {
+    case JABBA_OK: return "ok";
+    case JABBA_ERR_INVALID_ARG: return "invalid argument";
+    case JABBA_ERR_CAPACITY: return "capacity exceeded";
+    case JABBA_ERR_NONFINITE: return "non-finite input value";
+    case JABBA_ERR_CUDA: return "CUDA runtime error";
+    case JABBA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case JABBA_ERR_STATE: return "call out of order or allocation needed during graph capture";
+    case JABBA_ERR_RANGE: return "input value out of range (|x| >= 2^31)";
+  }
+  return "unknown status";
+}
+
+jabba_status jabba_create(jabba_ctx** out, int device) {
+  if (!out) return JABBA_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return JABBA_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return JABBA_ERR_CUDA;
+  jabba_ctx* c = new (std::nothrow) jabba_ctx();
+  if (!c) return JABBA_ERR_CUDA;
+  c->device = device;
+  if (cudaMalloc(&c->status, sizeof(unsigned)) != cudaSuccess || cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) {
+    delete c;
+    return JABBA_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->ws.num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (c->ws.num_sms <= 0) c->ws.num_sms = 1;
+  *out = c;
+  return JABBA_OK;
+}
+
+void jabba_destroy(jabba_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (int i = 0; i < kProfSlots; ++i)
+    for (int j = 0; j < kProfStages; ++j)
+      for (int k = 0; k < 2; ++k)
+        if (c->prof[i][j][k]) cudaEventDestroy(c->prof[i][j][k]);
+  if (c->pool) cudaFree(c->pool);
+  if (c->status) cudaFree(c->status);
+  delete c;
+}
+
+jabba_status jabba_sync_status(jabba_ctx* c, jabba_stream stream) {
+  if (!c) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned h = 0;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return JABBA_ERR_CUDA;
+  if (cudaMemcpy(&h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return JABBA_ERR_CUDA;
+  if (cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) return JABBA_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return JABBA_ERR_CUDA;
+  return (jabba_status)h;
+}
+
+jabba_status jabba_plan(const int64_t* series_off_host, int64_t n_series, const jabba_params* p,
+                        int64_t* n_domains, int64_t* n_slots, int64_t* max_dom_intervals) {
+  if (!series_off_host || n_series < 0 || !params_ok(p) || !n_domains || !n_slots) return JABBA_ERR_INVALID_ARG;
+  if (series_off_host[0] != 0) return JABBA_ERR_INVALID_ARG;
+  long long D = 0, slots = 0, mx = 0;
+  for (long long s = 0; s < n_series; ++s) {
+    const long long n_s = series_off_host[s + 1] - series_off_host[s];
+    if (n_s < 0) return JABBA_ERR_INVALID_ARG;
+    if (n_s > 0x7FFFFFFFll) return JABBA_ERR_RANGE;
+    const long long M = series_domains_host(n_s, p->domain_mode, p->domain_value);
+    D += M;
+    slots += n_s > 1 ? n_s - 1 : 0;
+    if (M > 0) {
+      const long long iv = n_s - 1;
+      const long long longest = p->domain_mode == 0 ? (iv + M - 1) / M : (p->domain_value < iv ? p->domain_value : iv);
+      if (longest > mx) mx = longest;
+    }
+  }
+  *n_domains = D;
+  *n_slots = slots;
+  if (max_dom_intervals) *max_dom_intervals = mx;
+  return JABBA_OK;
+}
+
+jabba_status jabba_reserve(jabba_ctx* c, int64_t n_points, int64_t n_series, int64_t n_domains, int64_t n_slots,
+                           int64_t group_capacity, int64_t max_dom_intervals) {
+  if (!c || n_points < 0 || n_series < 0 || n_domains < 0 || n_slots < 0 || group_capacity < 0 ||
+      max_dom_intervals < 0)
+    return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  c->ws.cap_points = n_points > c->ws.cap_points ? n_points : c->ws.cap_points;
+  long long big = 0;
+  if (max_dom_intervals > 4096) {
+    big = 1;
+    while (big < max_dom_intervals) big <<= 1;
+  }
+  return ensure(c, n_series, n_domains, n_slots > n_points ? n_slots : n_points, group_capacity, big, nullptr);
+}
+
+jabba_status jabba_compress(jabba_ctx* c, const double* x, int64_t n_points, const int64_t* series_off,
+                            int64_t n_series, const jabba_params* p, int64_t n_domains, int64_t n_slots,
+                            int64_t* dom_begin, int64_t* dom_end, int32_t* dom_series, int64_t* series_dom_off,
+                            int64_t* dom_slot_off, int32_t* piece_len, double* piece_inc, int32_t* dom_piece_cnt,
+                            int64_t* dom_piece_off, void* piece_stats, jabba_stream stream) {
+  if (!c || !params_ok(p) || n_points < 0 || n_series < 0 || n_domains < 0 || n_slots < 0) return JABBA_ERR_INVALID_ARG;
+  if (!series_off || !series_dom_off || !dom_slot_off || !dom_piece_off || !piece_stats) return JABBA_ERR_INVALID_ARG;
+  if (n_domains > 0 && (!x || !dom_begin || !dom_end || !dom_series || !dom_piece_cnt)) return JABBA_ERR_INVALID_ARG;
+  if (n_slots > 0 && (!piece_len || !piece_inc)) return JABBA_ERR_INVALID_ARG;
+  if (n_slots > 0x7FFFFFFFll * 64) return JABBA_ERR_RANGE;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  jabba_status r = ensure(c, n_series, n_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  launch_build_domains((const long long*)series_off, n_series, p->domain_mode, p->domain_value,
+                       (long long*)series_dom_off, (long long*)dom_begin, (long long*)dom_end, dom_series,
+                       (long long*)dom_slot_off, n_domains, c->ws, st);
+  Marks mk;
+  mk.a0 = prof_event(c, 0, 0);
+  mk.a1 = prof_event(c, 0, 1);
+  mk.b0 = prof_event(c, 1, 0);
+  mk.b1 = prof_event(c, 1, 1);
+  launch_compress(x, n_points, (const long long*)dom_begin, (const long long*)dom_end,
+                  (const long long*)dom_slot_off, n_domains, p->tol, piece_len, piece_inc, dom_piece_cnt,
+                  (long long*)dom_piece_off, (long long*)piece_stats, c->ws, c->status, st, mk);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_digitize_local(jabba_ctx* c, const int32_t* piece_len, const double* piece_inc,
+                                  const int64_t* dom_slot_off, const int32_t* dom_piece_cnt, int64_t n_domains,
+                                  const void* piece_stats, const jabba_params* p, double* sigma,
+                                  int32_t* local_label, int32_t* dom_group_cnt, int64_t* dom_group_off,
+                                  jabba_group* groups, int64_t group_capacity, int64_t* n_groups,
+                                  jabba_stream stream) {
+  if (!c || !params_ok(p) || n_domains < 0 || group_capacity < 0) return JABBA_ERR_INVALID_ARG;
+  if (!piece_stats || !sigma || !dom_group_off || !n_groups) return JABBA_ERR_INVALID_ARG;
+  if (n_domains > 0 && (!piece_len || !piece_inc || !dom_slot_off || !dom_piece_cnt || !local_label ||
+                        !dom_group_cnt || (group_capacity > 0 && !groups)))
+    return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // domains above the shared-memory tile use the scratch sized by jabba_reserve
+  jabba_status r = ensure(c, c->ws.cap_series, n_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  mark(prof_event(c, 2, 0), st);
+  launch_sigma((const long long*)piece_stats, sigma, st);
+  launch_local(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt, n_domains, sigma, p->alpha,
+               p->scl, local_label, dom_group_cnt, (long long*)dom_group_off, groups, group_capacity,
+               (long long*)n_groups, c->ws, c->status, st);
+  mark(prof_event(c, 2, 1), st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const int64_t* n_groups,
+                                int64_t group_capacity, const int64_t* dom_group_off, const double* sigma,
+                                const jabba_params* p, int32_t* l2g, double* dict_len, double* dict_inc,
+                                int64_t* dict_count, int64_t dict_capacity, int64_t* k, jabba_stream stream) {
+  if (!c || !params_ok(p) || group_capacity < 0 || dict_capacity < 0) return JABBA_ERR_INVALID_ARG;
+  if (!n_groups || !dom_group_off || !sigma || !k) return JABBA_ERR_INVALID_ARG;
+  if (group_capacity > 0 && (!groups || !l2g)) return JABBA_ERR_INVALID_ARG;
+  if (dict_capacity > 0 && (!dict_len || !dict_inc || !dict_count)) return JABBA_ERR_INVALID_ARG;
+  if (group_capacity >= 0x7FFFFFFFll) return JABBA_ERR_RANGE;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  jabba_status r = ensure(c, c->ws.cap_series, c->ws.cap_domains, c->ws.cap_slots, group_capacity, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  mark(prof_event(c, 3, 0), st);
+  launch_merge(groups, (const long long*)n_groups, group_capacity, (const long long*)dom_group_off, sigma, p->alpha,
+               p->scl, l2g, dict_len, dict_inc, (long long*)dict_count, dict_capacity, (long long*)k, c->ws,
+               c->status, st);
+  mark(prof_event(c, 3, 1), st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_symbolize(jabba_ctx* c, const int32_t* local_label, const int64_t* dom_slot_off,
+                             const int32_t* dom_piece_cnt, const int64_t* dom_piece_off,
+                             const int64_t* dom_group_off, int64_t n_domains, const int32_t* l2g,
+                             int32_t* symbol, jabba_stream stream) {
+  if (!c || n_domains < 0) return JABBA_ERR_INVALID_ARG;
+  if (n_domains > 0 && (!local_label || !dom_slot_off || !dom_piece_cnt || !dom_piece_off || !dom_group_off ||
+                        !l2g || !symbol))
+    return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  mark(prof_event(c, 4, 0), (cudaStream_t)stream);
+  launch_symbolize(local_label, (const long long*)dom_slot_off, dom_piece_cnt, (const long long*)dom_piece_off,
+                   (const long long*)dom_group_off, n_domains, l2g, symbol, c->ws, (cudaStream_t)stream);
+  mark(prof_event(c, 4, 1), (cudaStream_t)stream);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_reconstruct(jabba_ctx* c, const double* x, int64_t n_points, const int64_t* series_off,
+                               int64_t n_series, const int64_t* series_dom_off, const int64_t* dom_piece_off,
+                               const int32_t* symbol, const double* dict_len, const double* dict_inc,
+                               const jabba_params* p, int32_t* qlen, double* xhat, jabba_stream stream) {
+  if (!c || !params_ok(p) || n_points < 0 || n_series < 0) return JABBA_ERR_INVALID_ARG;
+  if (n_series > 0 && (!x || !series_off || !series_dom_off || !dom_piece_off || !xhat)) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // pieces never outnumber the slots (intervals)
+  jabba_status r = ensure(c, n_series, c->ws.cap_domains, n_points, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  launch_reconstruct(x, n_points, (const long long*)series_off, n_series, (const long long*)series_dom_off,
+                     (const long long*)dom_piece_off, symbol, dict_len, dict_inc, p->round_mode, qlen, xhat, c->ws,
+                     st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_reconstruct_backward(jabba_ctx* c, const double* x, int64_t n_points,
+                                        const int64_t* series_off, int64_t n_series,
+                                        const int64_t* series_dom_off, const int64_t* dom_piece_off,
+                                        const int32_t* symbol, const int32_t* qlen, const double* dict_inc,
+                                        int64_t k, double* grad_dict_inc, jabba_stream stream) {
+  if (!c || n_points < 0 || n_series < 0 || k < 0) return JABBA_ERR_INVALID_ARG;
+  if (k > 0 && !grad_dict_inc) return JABBA_ERR_INVALID_ARG;
+  if (n_series > 0 && (!x || !series_off || !series_dom_off || !dom_piece_off)) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  jabba_status r = ensure(c, n_series, c->ws.cap_domains, n_points, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  launch_reconstruct_backward(x, n_points, (const long long*)series_off, n_series, (const long long*)series_dom_off,
+                              (const long long*)dom_piece_off, symbol, qlen, dict_inc, k, grad_dict_inc, c->ws, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_profile_slot(jabba_ctx* c, int slot) {
+  if (!c || slot < -1 || slot >= kProfSlots) return JABBA_ERR_INVALID_ARG;
+  c->prof_slot = slot;
+  return JABBA_OK;
+}
+
+jabba_status jabba_profile_elapsed(jabba_ctx* c, int slot, int stage, float* ms) {
+  if (!c || !ms || slot < 0 || slot >= kProfSlots || stage < 0 || stage >= kProfStages) return JABBA_ERR_INVALID_ARG;
+  cudaEvent_t a = c->prof[slot][stage][0], b = c->prof[slot][stage][1];
+  if (!a || !b) return JABBA_ERR_STATE;
+  cudaSetDevice(c->device);
+  if (cudaEventSynchronize(b) != cudaSuccess) return JABBA_ERR_CUDA;
+  return cuda_ok(cudaEventElapsedTime(ms, a, b));
+}
+
+jabba_status jabba_mse(jabba_ctx* c, const double* x, const double* xhat, int64_t n_points, double* out,
+                       jabba_stream stream) {
+  if (!c || n_points < 0 || !out || (n_points > 0 && (!x || !xhat))) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  jabba_status r = ensure(c, c->ws.cap_series, c->ws.cap_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  if (!c->ws.r_tail) {
+    r = ensure(c, 1, c->ws.cap_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+    if (r != JABBA_OK) return r;
+  }
+  launch_mse(x, xhat, n_points, out, c->ws, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // extern "C"

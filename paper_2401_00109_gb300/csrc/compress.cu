@@ -1,0 +1,487 @@
+// compress.cu -- domain construction (Alg. 1 Phase I, Sec. 4.1.1) and the
+// per-domain adaptive polygonal-chain compression (Sec. 3.1 Eq. 1; Alg. 1
+// Phase II) of the JABBA path, plus the exact-sum statistics that the
+// normalisation (Sec. 3.2 Eq. 4) needs.
+#include "kernels.cuh"
+#include <cmath>
+
+namespace jabba {
+
+// ------------------------------------------------------------------ domains
+__device__ __forceinline__ long long series_domains(long long n_s, int mode, long long value) {
+  if (n_s < 2 || value < 1) return 0;
+  const long long iv = n_s - 1;
+  if (mode == 0) return value < iv ? value : iv;
+  return (iv + value - 1) / value;
+}
+
+__global__ void k_series_counts(const long long* series_off, long long n_series, int mode, long long value,
+                                long long* dom_cnt, long long* slot_cnt) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_series) return;
+  const long long n_s = series_off[s + 1] - series_off[s];
+  dom_cnt[s] = series_domains(n_s, mode, value);
+  slot_cnt[s] = n_s > 1 ? n_s - 1 : 0;
+}
+
+// Boundaries b_k of domain k of a series with iv intervals split into M domains.
+__device__ __forceinline__ long long domain_bound(long long k, long long M, long long iv, int mode, long long value) {
+  if (mode == 0) return (long long)(((unsigned __int128)k * (unsigned long long)iv) / (unsigned long long)M);
+  const long long b = k * value;
+  return b < iv ? b : iv;
+}
+
+__global__ void k_fill_domains(const long long* series_off, long long n_series, int mode, long long value,
+                               const long long* series_dom_off, const long long* series_slot_off,
+                               long long* dom_begin, long long* dom_end, int* dom_series, long long* dom_slot_off) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_series) return;
+  const long long base = series_off[s], n_s = series_off[s + 1] - base;
+  const long long M = series_domains(n_s, mode, value), iv = n_s - 1;
+  const long long d0 = series_dom_off[s], slot0 = series_slot_off[s];
+  for (long long k = 0; k < M; ++k) {
+    const long long b0 = domain_bound(k, M, iv, mode, value);
+    const long long b1 = domain_bound(k + 1, M, iv, mode, value);
+    dom_begin[d0 + k] = base + b0;
+    dom_end[d0 + k] = base + b1;
+    dom_series[d0 + k] = (int)s;
+    dom_slot_off[d0 + k] = slot0 + b0;
+  }
+}
+
+__global__ void k_copy_scalar(const long long* src, long long* dst) { *dst = *src; }
+
+void launch_build_domains(const long long* series_off, long long n_series, int mode, long long value,
+                          long long* series_dom_off, long long* dom_begin, long long* dom_end, int* dom_series,
+                          long long* dom_slot_off, long long n_domains, Scratch& ws, cudaStream_t st) {
+  long long* dcnt = ws.series_a;
+  long long* scnt = ws.series_b;
+  long long* slot_off = ws.series_c;
+  const unsigned g = (unsigned)((n_series + 255) / 256);
+  if (g) k_series_counts<<<g, 256, 0, st>>>(series_off, n_series, mode, value, dcnt, scnt);
+  exclusive_scan<long long>(dcnt, n_series, series_dom_off, ws.scan_tiles, st);
+  exclusive_scan<long long>(scnt, n_series, slot_off, ws.scan_tiles, st);
+  if (g) k_fill_domains<<<g, 256, 0, st>>>(series_off, n_series, mode, value, series_dom_off, slot_off, dom_begin,
+                                           dom_end, dom_series, dom_slot_off);
+  k_copy_scalar<<<1, 1, 0, st>>>(slot_off + n_series, dom_slot_off + n_domains);
+}
+
+// ------------------------------------------------------------------ compression
+// One lane compresses one domain; a warp owns 32 domains at a time (work is
+// stolen in tasks of 32 domains from a global counter).  The greedy consumes
+// exactly one point per step whatever the breakpoints, so the 32 lanes stay
+// in lockstep.  Each lane streams its domain through shared memory in chunks
+// of kChunk points with a TMA bulk copy (cp.async.bulk) completing on a
+// per-warp mbarrier, double-buffered.
+//
+// Admissibility of the candidate piece (s, e) (Eq. 1) is decided by a
+// certified FP32 test, falling back to the exact FP64 evaluation (the
+// definition's own operation order) only when the FP32 result cannot decide.
+// With D_i = x_{s+i} - x_s and L = e - s, L^2 * err = F(D) where
+//   F(D) = L^2 S2 - 2 L D_L SK + D_L^2 K2,  S2 = sum D_i^2, SK = sum i D_i,
+//   K2 = sum i^2 over the interior i = 1..L-1.
+// The FP32 evaluation E of F from truncated FP32 copies d_i of D_i obeys
+//   |E - F(d)| <= A = 2.2 (L + 8) 2^-24 (L^2 S2 + d_L^2 K2)       (rounding;
+//   Cauchy-Schwarz bounds the cross term), and |sqrt F(d) - sqrt F(D)| <= h =
+//   2 tau L sqrt(L - 1), tau = 2^-20 max|x~| (conversion, subtraction and the
+//   FP64 definition's own rounding of the residuals).
+// With theta = 2^-10, (sqrt q + h)^2 <= (1 + theta) q + 1025 h^2 and
+// (sqrt q - h)^2 >= (1 - theta) q - 1025 h^2, so
+//   admissible   if (1 + theta)(E + A) + H < L^2 (L - 1) tol^2 (1 - 2^-18),
+//   inadmissible if (1 - theta)(E - A) - H > L^2 (L - 1) tol^2 (1 + 2^-18),
+// H = 1025 h^2 (rounded up); the 2^-18 slack covers the remaining FP32 and
+// FP64 roundings.  Otherwise the exact FP64 sum decides.
+constexpr int kChunk = 16;                 // points per lane per stage
+constexpr int kRow = kChunk + 2;           // doubles per staged row (16-byte multiple, alignment slack)
+constexpr int kWarpsPerCta = 8;
+constexpr int kStages = 2;
+
+struct CompressParams {
+  const double* x;
+  long long n_points;
+  const long long* dom_begin;
+  const long long* dom_end;
+  const long long* dom_slot_off;
+  long long n_domains;
+  double tol2;        // tol * tol, binary64
+  float tol2_lo;      // tol2 (1 - 2^-18) rounded down
+  float tol2_hi;      // tol2 (1 + 2^-18) rounded up
+  int* piece_len;
+  double* piece_end;  // end value of each piece; turned into increments afterwards
+  int* dom_piece_cnt;
+  unsigned* status;
+  unsigned* task_counter;
+  unsigned long long* n_exact;  // number of candidates decided by the exact FP64 path
+};
+
+// Exact FP64 evaluation of Eq. 1 for (s, e) with the definition's operation
+// order: r = (x_s + (inc * k) / L) - x_{s+k}, err += r * r, ascending k.
+__device__ __noinline__ bool exact_admissible(const double* xb, int s, int e, double tol2) {
+  const int L = e - s;
+  const double xs = xb[s];
+  const double inc = __dsub_rn(xb[e], xs);
+  const double dL = (double)L;
+  double err = 0.0;
+  for (int k = 1; k < L; ++k) {
+    const double r = __dsub_rn(__dadd_rn(xs, __ddiv_rn(__dmul_rn(inc, (double)k), dL)), xb[s + k]);
+    err = __dadd_rn(err, __dmul_rn(r, r));
+  }
+  return err <= __dmul_rn((double)(L - 1), tol2);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+struct LaneDomain {
+  long long b;      // global index of the domain's first point
+  int n_int;        // intervals (points - 1); 0 = inactive lane
+};
+
+// Issue the staging copy of chunk c (local points 1 + c*kChunk ...) of this
+// lane's domain into its row of buffer `buf`; every lane arrives once.
+__device__ __forceinline__ int stage_chunk(const CompressParams& P, const LaneDomain& D, int c, double* row,
+                                          unsigned bar) {
+  const int p0 = 1 + c * kChunk;
+  if (D.n_int <= 0 || p0 > D.n_int) {
+    mbar_arrive(bar);
+    return 0;
+  }
+  // 16-byte aligned start at or just below the first needed point (doubles
+  // are 8-byte aligned, so at most one extra point is copied in front)
+  const double* first = P.x + D.b + p0;
+  const double* base = (const double*)((uintptr_t)first & ~(uintptr_t)15);
+  const int off = (int)(first - base);
+  long long end_needed = D.b + p0 + kChunk;
+  if (end_needed > D.b + D.n_int + 1) end_needed = D.b + D.n_int + 1;
+  const int cnt = (int)((P.x + end_needed) - base);
+  int cnt_even = (cnt + 1) & ~1;
+  bool manual = false;
+  if (base + cnt_even > P.x + P.n_points) {  // never read past the end of x
+    cnt_even = cnt - 1;
+    manual = true;
+  }
+  const unsigned bytes = (unsigned)cnt_even * 8u;
+  if (manual) row[cnt - 1] = base[cnt - 1];
+  if (bytes) {
+    mbar_arrive_tx(bar, bytes);
+    bulk_g2s(smem_u32(row), base, bytes, bar);
+  } else {
+    mbar_arrive(bar);
+  }
+  return off;
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P) {
+  __shared__ __align__(16) double stage[kWarpsPerCta][kStages][32][kRow];
+  __shared__ __align__(8) unsigned long long bars[kWarpsPerCta][kStages];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane < kStages) mbar_init(smem_u32(&bars[warp][lane]), 32);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  unsigned phase[kStages] = {0, 0};
+  const unsigned bar0 = smem_u32(&bars[warp][0]);
+  const unsigned bar1 = smem_u32(&bars[warp][1]);
+  const long long n_tasks = (P.n_domains + 31) / 32;
+  const float G1 = 2.2f * 0x1p-24f, G0 = 2.2f * 8.0f * 0x1p-24f;
+  const float HC = 4200.0f * 0x1p-40f;
+  const float ONE_P = 1.0f + 0x1p-10f, ONE_M = 1.0f - 0x1p-10f;
+  unsigned amax = 0;  // largest |x| high word seen (range / finiteness check)
+
+  for (;;) {
+    long long task = 0;
+    if (lane == 0) task = (long long)atomicAdd(P.task_counter, 1u);
+    task = __shfl_sync(0xFFFFFFFFu, task, 0);
+    if (task >= n_tasks) break;
+    const long long d = task * 32 + lane;
+    LaneDomain D;
+    long long slot = 0;
+    D.b = 0;
+    D.n_int = 0;
+    if (d < P.n_domains) {
+      D.b = P.dom_begin[d];
+      D.n_int = (int)(P.dom_end[d] - D.b);
+      slot = P.dom_slot_off[d];
+    }
+    int max_int = D.n_int;
+    for (int o = 16; o > 0; o >>= 1) max_int = max(max_int, __shfl_xor_sync(0xFFFFFFFFu, max_int, o));
+    const int n_chunks = (max_int + kChunk - 1) / kChunk;
+    const double* xb = P.x + D.b;
+
+    // lane state
+    double prevd = 0.0;
+    float xs = 0.f, prevf = 0.f, S2 = 0.f, SK = 0.f, K2 = 0.f, Lf = 0.f, M = 0.f;
+    int s = 0, cnt = 0;
+    if (D.n_int > 0) {
+      prevd = xb[0];
+      unsigned mh;
+      xs = f64_to_f32_trunc(prevd, mh);
+      amax = max(amax, mh);
+      prevf = xs;
+      M = fabsf(xs);
+    }
+
+    int off[kStages] = {0, 0};
+    if (n_chunks > 0) off[0] = stage_chunk(P, D, 0, stage[warp][0][lane], bar0);
+    for (int c = 0; c < n_chunks; ++c) {
+      const int buf = c & 1;
+      if (c + 1 < n_chunks) {
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        off[buf ^ 1] = stage_chunk(P, D, c + 1, stage[warp][buf ^ 1][lane], buf ? bar0 : bar1);
+      }
+      // wait for this chunk (bounded); on timeout every lane leaves together
+      {
+        const unsigned bar = buf ? bar1 : bar0;
+        unsigned spins = 0;
+        bool ok = true;
+        while (!mbar_try_wait(bar, phase[buf])) {
+          if (++spins > kSpinLimit) { ok = false; break; }
+        }
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+          set_status(P.status, JABBA_ERR_TIMEOUT);
+          // give the copies still in flight a bounded time to land before the
+          // CTA's shared memory is released
+          for (int b = 0; b < kStages; ++b) {
+            const unsigned bb = b ? bar1 : bar0;
+            unsigned sp = 0;
+            while (!mbar_try_wait(bb, phase[b]) && ++sp < kSpinLimit) {}
+          }
+          return;
+        }
+        phase[buf] ^= 1u;
+      }
+      const double* row = stage[warp][buf][lane] + off[buf];
+      const int p0 = 1 + c * kChunk;
+#pragma unroll 4
+      for (int j = 0; j < kChunk; ++j) {
+        const int p = p0 + j;
+        if (p <= D.n_int) {
+          const double vd = row[j];
+          unsigned mh;
+          const float v = f64_to_f32_trunc(vd, mh);
+          amax = max(amax, mh);
+          float d = v - xs;
+          Lf += 1.0f;
+          const float L2 = Lf * Lf;
+          const float dd = d * d;
+          const float t3 = dd * K2;
+          const float cc = (Lf + Lf) * d;
+          const float E = fmaf(L2, S2, fmaf(-cc, SK, t3));
+          const float Pp = fmaf(L2, S2, t3);
+          const float B0 = L2 * (Lf - 1.0f);
+          const float A = fmaf(Lf, G1, G0) * Pp;
+          const float Mx = fmaxf(M, fabsf(v));
+          const float H = (Mx * Mx * HC) * B0;
+          bool feas = fmaf(E + A, ONE_P, H) < B0 * P.tol2_lo;
+          bool infeas = fmaf(E - A, ONE_M, -H) > B0 * P.tol2_hi;
+          const bool fast_ok = (Mx >= 0x1p-60f) && (Mx < 0x1p31f) && (Lf < 1048576.0f);
+          feas = (feas && fast_ok) || (Lf == 1.0f);
+          infeas = infeas && fast_ok && !feas;
+          if (!feas && !infeas) {
+            feas = exact_admissible(xb, s, p, P.tol2);
+            atomicAdd(P.n_exact, 1ull);
+          }
+          if (feas) {
+            S2 = fmaf(d, d, S2);
+            SK = fmaf(Lf, d, SK);
+            K2 = fmaf(Lf, Lf, K2);
+            M = Mx;
+          } else {
+            // piece (s, p - 1) ends; restart at p - 1 with p as its first candidate
+            P.piece_len[slot + cnt] = (p - 1) - s;
+            P.piece_end[slot + cnt] = prevd;
+            ++cnt;
+            s = p - 1;
+            xs = prevf;
+            d = v - xs;
+            S2 = d * d;
+            SK = d;
+            K2 = 1.0f;
+            Lf = 1.0f;
+            M = fmaxf(fabsf(prevf), fabsf(v));
+          }
+          prevf = v;
+          prevd = vd;
+          if (p == D.n_int) {  // domain end: the open piece ends here
+            P.piece_len[slot + cnt] = p - s;
+            P.piece_end[slot + cnt] = vd;
+            ++cnt;
+          }
+        }
+      }
+    }
+    if (d < P.n_domains) P.dom_piece_cnt[d] = cnt;
+  }
+  // range / finiteness of every value this lane read
+  if (amax >= 0x7FF00000u) set_status(P.status, JABBA_ERR_NONFINITE);
+  else if (amax >= (1054u << 20)) set_status(P.status, JABBA_ERR_RANGE);
+}
+
+// ------------------------------------------------------------------ increments + statistics
+// One warp per domain (grid-stride): turns the end values written by
+// k_compress into increments inc_j = x_{e_j} - x_{s_j} (binary64, full-warp
+// FP64) and accumulates the exact sums of the normalisation: N, sum len,
+// sum len^2 (integers) and sum inc, sum inc^2 (exact squares), the latter two
+// as 2^-64 fixed point.  stats layout (int64): [0] N, [1] sum len,
+// [2..5] sum len^2 in four 32-bit deferred-carry limbs, [6..11] sum inc and
+// [12..17] sum inc^2 in six 32-bit deferred-carry limbs each.
+__global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const long long* dom_begin,
+                                                       const long long* dom_slot_off, const int* dom_piece_cnt,
+                                                       long long n_domains, const int* piece_len, double* piece_inc,
+                                                       long long* stats) {
+  const int lane = threadIdx.x & 31;
+  const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long n = 0, s1 = 0;
+  U128 s2 = {0, 0};
+  I192 a1 = {0, 0, 0}, a2 = {0, 0, 0};
+  for (long long d = warp_g; d < n_domains; d += n_warps) {
+    const int cnt = dom_piece_cnt[d];
+    const long long slot = dom_slot_off[d];
+    double prev_end = x[dom_begin[d]];
+    for (int base = 0; base < cnt; base += 32) {
+      const int j = base + lane;
+      const bool valid = j < cnt;
+      const int len = valid ? piece_len[slot + j] : 0;
+      const double endv = valid ? piece_inc[slot + j] : 0.0;
+      double startv = __shfl_up_sync(0xFFFFFFFFu, endv, 1);
+      if (lane == 0) startv = prev_end;
+      const double inc = __dsub_rn(endv, startv);
+      const int last = min(31, cnt - 1 - base);
+      prev_end = __shfl_sync(0xFFFFFFFFu, endv, last);
+      if (valid) {
+        piece_inc[slot + j] = inc;
+        n += 1;
+        s1 += (unsigned long long)len;
+        const unsigned long long l2 = (unsigned long long)len * (unsigned long long)len;
+        s2.lo += l2;
+        s2.hi += (s2.lo < l2) ? 1ull : 0ull;
+        bool neg;
+        const U128 m = fx_mag(inc, neg);
+        acc_signed(a1, m, neg);
+        const U128 q = fx_square(inc);
+        add192(a2, q.lo, q.hi, 0);
+      }
+    }
+  }
+  // warp reduction of limbs, then one set of atomics per warp
+  i64 L[18];
+  L[0] = (i64)n;
+  L[1] = (i64)s1;
+  L[2] = (i64)(s2.lo & 0xFFFFFFFFull);
+  L[3] = (i64)(s2.lo >> 32);
+  L[4] = (i64)(s2.hi & 0xFFFFFFFFull);
+  L[5] = (i64)(s2.hi >> 32);
+  limbs6(a1, L + 6);
+  limbs6(a2, L + 12);
+#pragma unroll
+  for (int i = 0; i < 18; ++i) {
+    i64 v = L[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    L[i] = v;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i)
+      if (L[i]) atomicAdd((unsigned long long*)&stats[i], (unsigned long long)L[i]);
+  }
+}
+
+// sigma_len, sigma_inc from the exact sums (Sec. 3.2 Eq. 4): m = S1 / N,
+// v = S2 / N - m * m, sigma = sqrt(v), or 1 when v <= 0 (binary64, IEEE ops).
+__device__ double sigma_from(double s1, double s2, double n) {
+  const double m = __ddiv_rn(s1, n);
+  const double v = __dsub_rn(__ddiv_rn(s2, n), __dmul_rn(m, m));
+  if (!(v > 0.0)) return 1.0;
+  return __dsqrt_rn(v);
+}
+
+__global__ void k_sigma(const long long* stats, double* sigma) {
+  const double n = __ll2double_rn(stats[0]);
+  const double s1 = __ll2double_rn(stats[1]);
+  // sum len^2 from four unsigned 32-bit deferred-carry limbs
+  u64 w[4];
+  u64 carry = 0;
+  for (int i = 0; i < 4; ++i) {
+    const u64 v = (u64)stats[2 + i] + carry;
+    w[i] = v & 0xFFFFFFFFull;
+    carry = v >> 32;
+  }
+  const u64 lo = w[0] | (w[1] << 32), hi = w[2] | (w[3] << 32);
+  const double s2 = round_u192(lo, hi, carry, 0, false);
+  i64 L1[6], L2[6];
+  for (int i = 0; i < 6; ++i) {
+    L1[i] = stats[6 + i];
+    L2[i] = stats[12 + i];
+  }
+  const double i1 = i192_to_double(from_limbs6(L1));
+  const double i2 = i192_to_double(from_limbs6(L2));
+  sigma[0] = sigma_from(s1, s2, n);
+  sigma[1] = sigma_from(i1, i2, n);
+}
+
+void launch_compress(const double* x, long long n_points, const long long* dom_begin, const long long* dom_end,
+                     const long long* dom_slot_off, long long n_domains, double tol, int* piece_len,
+                     double* piece_inc, int* dom_piece_cnt, long long* dom_piece_off, long long* stats,
+                     Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk) {
+  CompressParams P;
+  P.x = x;
+  P.n_points = n_points;
+  P.dom_begin = dom_begin;
+  P.dom_end = dom_end;
+  P.dom_slot_off = dom_slot_off;
+  P.n_domains = n_domains;
+  P.tol2 = tol * tol;
+  P.tol2_lo = (float)(P.tol2 * (1.0 - 0x1p-18));
+  if ((double)P.tol2_lo > P.tol2 * (1.0 - 0x1p-18)) P.tol2_lo = nextafterf(P.tol2_lo, 0.0f);
+  P.tol2_hi = (float)(P.tol2 * (1.0 + 0x1p-18));
+  if ((double)P.tol2_hi < P.tol2 * (1.0 + 0x1p-18)) P.tol2_hi = nextafterf(P.tol2_hi, INFINITY);
+  P.piece_len = piece_len;
+  P.piece_end = piece_inc;
+  P.dom_piece_cnt = dom_piece_cnt;
+  P.status = status;
+  P.task_counter = ws.counters;
+  P.n_exact = (unsigned long long*)(ws.counters + 2);
+  cudaMemsetAsync(ws.counters, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(stats, 0, JABBA_PIECE_STATS_BYTES, st);
+  const long long n_tasks = (n_domains + 31) / 32;
+  long long ctas = (long long)ws.num_sms * 3;
+  const long long need = (n_tasks + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (ctas > need) ctas = need;
+  mark(mk.a0, st);
+  if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, 0, st>>>(P);
+  mark(mk.a1, st);
+  mark(mk.b0, st);
+  if (n_domains > 0) {
+    long long blocks = (n_domains + 7) / 8;
+    if (blocks > (long long)ws.num_sms * 16) blocks = (long long)ws.num_sms * 16;
+    k_finish_pieces<<<(unsigned)blocks, 256, 0, st>>>(x, dom_begin, dom_slot_off, dom_piece_cnt, n_domains,
+                                                      piece_len, piece_inc, stats);
+  }
+  exclusive_scan<int>(dom_piece_cnt, n_domains, dom_piece_off, ws.scan_tiles, st);
+  mark(mk.b1, st);
+}
+
+void launch_sigma(const long long* stats, double* sigma, cudaStream_t st) { k_sigma<<<1, 1, 0, st>>>(stats, sigma); }
+
+}  // namespace jabba

@@ -1,0 +1,91 @@
+// kernels.cuh -- launch interfaces between the C ABI (api.cu) and the CUDA
+// kernels of the JABBA path.
+#pragma once
+#include "jabba_dev.cuh"
+#include "scan.cuh"
+
+namespace jabba {
+
+// Scratch owned by a context (device memory).  Sized by jabba_reserve().
+struct Scratch {
+  int num_sms = 0;
+  long long cap_series = 0, cap_domains = 0, cap_slots = 0, cap_groups = 0, cap_points = 0;
+  long long cap_big = 0;          // elements of the big-domain aggregation scratch
+  long long* series_a = nullptr;  // [cap_series + 1]
+  long long* series_b = nullptr;
+  long long* series_c = nullptr;
+  long long* scan_tiles = nullptr;
+  unsigned* counters = nullptr;   // [16]: task counters, diagnostics
+  // local aggregation of domains larger than the shared-memory tile
+  unsigned char* big = nullptr;
+  // merge
+  double* m_key = nullptr;        // [cap_groups] sort keys, then sorted keys
+  double* m_X = nullptr;          // [cap_groups] normalised centre coordinates (compact index)
+  double* m_Y = nullptr;
+  int* m_idx = nullptr;           // [cap_groups] compact index, sorted by key
+  unsigned long long* m_k0 = nullptr;  // radix sort ping-pong
+  unsigned long long* m_k1 = nullptr;
+  int* m_v0 = nullptr;
+  int* m_v1 = nullptr;
+  int* m_label = nullptr;         // [cap_groups] global id per compact index
+  int* m_rec = nullptr;           // [cap_groups] record of each compact index
+  unsigned* m_hist = nullptr;     // radix histograms
+  long long* d_acc = nullptr;     // [cap_groups * 8] dictionary accumulators
+  // reconstruction
+  double* r_level = nullptr;      // [cap_slots] level before each piece (compact)
+  long long* r_pos = nullptr;     // [cap_slots] position of each piece in its series
+  double* r_tsum = nullptr;       // [cap_slots] per-piece residual sums (backward)
+  double* r_wsum = nullptr;
+  double* r_tail = nullptr;       // [cap_series]
+  long long* r_tailpos = nullptr; // [cap_series]
+  double* r_tail_level = nullptr; // [cap_series]
+};
+
+void launch_build_domains(const long long* series_off, long long n_series, int mode, long long value,
+                          long long* series_dom_off, long long* dom_begin, long long* dom_end, int* dom_series,
+                          long long* dom_slot_off, long long n_domains, Scratch& ws, cudaStream_t st);
+
+// Optional event pairs recorded around kernels (benchmark timing).
+struct Marks {
+  cudaEvent_t a0 = nullptr, a1 = nullptr;  // around the compression kernel
+  cudaEvent_t b0 = nullptr, b1 = nullptr;  // around increments + exact sums
+};
+
+void launch_compress(const double* x, long long n_points, const long long* dom_begin, const long long* dom_end,
+                     const long long* dom_slot_off, long long n_domains, double tol, int* piece_len,
+                     double* piece_inc, int* dom_piece_cnt, long long* dom_piece_off, long long* stats,
+                     Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk);
+
+inline void mark(cudaEvent_t e, cudaStream_t st) {
+  if (e) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+}
+
+void launch_sigma(const long long* stats, double* sigma, cudaStream_t st);
+
+void launch_local(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
+                  const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
+                  int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
+                  long long group_capacity, long long* n_groups, Scratch& ws, unsigned* status, cudaStream_t st);
+
+void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
+                  const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
+                  double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,
+                  Scratch& ws, unsigned* status, cudaStream_t st);
+
+void launch_symbolize(const int* local_label, const long long* dom_slot_off, const int* dom_piece_cnt,
+                      const long long* dom_piece_off, const long long* dom_group_off, long long n_domains,
+                      const int* l2g, int* symbol, Scratch& ws, cudaStream_t st);
+
+void launch_reconstruct(const double* x, long long n_points, const long long* series_off, long long n_series,
+                        const long long* series_dom_off, const long long* dom_piece_off, const int* symbol,
+                        const double* dict_len, const double* dict_inc, int round_mode, int* qlen, double* xhat,
+                        Scratch& ws, cudaStream_t st);
+
+void launch_reconstruct_backward(const double* x, long long n_points, const long long* series_off,
+                                 long long n_series, const long long* series_dom_off,
+                                 const long long* dom_piece_off, const int* symbol, const int* qlen,
+                                 const double* dict_inc, long long k, double* grad, Scratch& ws, cudaStream_t st);
+
+void launch_mse(const double* x, const double* xhat, long long n, double* out, Scratch& ws, cudaStream_t st);
+
+}  // namespace jabba

@@ -1,0 +1,229 @@
+// reconstruct.cu -- inverse symbolization (Sec. 3.3) and the adjoint of the
+// reconstruction MSE with respect to the dictionary increments.
+#include "kernels.cuh"
+
+namespace jabba {
+
+// Pieces of series s: [spo[s], spo[s+1]) with spo[s] = dom_piece_off[series_dom_off[s]].
+__global__ void k_series_piece_off(const long long* series_dom_off, const long long* dom_piece_off,
+                                   long long n_series, long long* spo) {
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s <= n_series;
+       s += (long long)gridDim.x * blockDim.x)
+    spo[s] = dom_piece_off[series_dom_off[s]];
+}
+
+// Sequential pass per series (one thread): quantization with the carry
+// v = l~ + e, l^ = round(v), e = v - l^ (Sec. 3.3), and the chain's level and
+// position before each piece.  With qlen_in given, the lengths are taken as
+// they are (the adjoint holds them fixed).
+__global__ void k_recon_seq(const double* x, const long long* series_off, long long n_series, const long long* spo,
+                            const int* symbol, const double* dict_len, const double* dict_inc, int round_mode,
+                            const int* qlen_in, int* qlen_out, double* level_out, long long* pos_out,
+                            long long* tail_pos, double* tail_level) {
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n_series;
+       s += (long long)gridDim.x * blockDim.x) {
+    const long long o = series_off[s];
+    if (series_off[s + 1] - o <= 0) {
+      tail_pos[s] = 0;
+      tail_level[s] = 0.0;
+      continue;
+    }
+    double e = 0.0, level = x[o];
+    long long pos = 0;
+    for (long long j = spo[s]; j < spo[s + 1]; ++j) {
+      const int c = symbol[j];
+      long long L;
+      if (qlen_in) {
+        L = qlen_in[j];
+      } else {
+        const double v = __dadd_rn(dict_len[c], e);
+        const double lh = round_mode ? rint(v) : round(v);
+        e = __dsub_rn(v, lh);
+        L = (long long)lh;
+        qlen_out[j] = (int)L;
+      }
+      level_out[j] = level;
+      pos_out[j] = pos;
+      level = __dadd_rn(level, dict_inc[c]);
+      pos += L;
+    }
+    tail_pos[s] = pos;
+    tail_level[s] = level;
+  }
+}
+
+__device__ __forceinline__ long long find_series(const long long* spo, long long n_series, long long j) {
+  long long lo = 0, hi = n_series - 1;  // largest s with spo[s] <= j
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) >> 1;
+    if (spo[mid] <= j) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Inverse compression, one thread per piece: xhat[pos + q] = level + (i~ q) / l^.
+__global__ void k_recon_fill(const long long* series_off, long long n_series, const long long* spo,
+                             long long n_pieces_hint, const int* symbol, const double* dict_inc, const int* qlen,
+                             const double* level, const long long* pos, double* xhat) {
+  const long long N = spo[n_series];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+    const long long s = find_series(spo, n_series, j);
+    const long long o = series_off[s], n_s = series_off[s + 1] - o;
+    const int L = qlen[j];
+    const double lh = (double)L, inc = dict_inc[symbol[j]], lv = level[j];
+    const long long p = pos[j];
+    for (int q = 1; q <= L && p + q <= n_s - 1; ++q) xhat[o + p + q] = __dadd_rn(lv, __ddiv_rn(__dmul_rn(inc, (double)q), lh));
+  }
+  (void)n_pieces_hint;
+}
+
+// t_0 and the tail after the last piece (final level), one warp per series.
+__global__ void k_recon_ends(const double* x, const long long* series_off, long long n_series,
+                             const long long* tail_pos, const double* tail_level, double* xhat) {
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long s = w; s < n_series; s += nw) {
+    const long long o = series_off[s], n_s = series_off[s + 1] - o;
+    if (n_s <= 0) continue;
+    if (lane == 0) xhat[o] = x[o];
+    for (long long i = tail_pos[s] + 1 + lane; i <= n_s - 1; i += 32) xhat[o + i] = tail_level[s];
+  }
+}
+
+void launch_reconstruct(const double* x, long long n_points, const long long* series_off, long long n_series,
+                        const long long* series_dom_off, const long long* dom_piece_off, const int* symbol,
+                        const double* dict_len, const double* dict_inc, int round_mode, int* qlen, double* xhat,
+                        Scratch& ws, cudaStream_t st) {
+  if (n_series <= 0) return;
+  long long* spo = ws.series_a;
+  const unsigned g = (unsigned)(ws.num_sms * 8);
+  k_series_piece_off<<<g, 256, 0, st>>>(series_dom_off, dom_piece_off, n_series, spo);
+  k_recon_seq<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(x, series_off, n_series, spo, symbol, dict_len,
+                                                                   dict_inc, round_mode, nullptr, qlen, ws.r_level,
+                                                                   ws.r_pos, ws.r_tailpos, ws.r_tail_level);
+  k_recon_fill<<<g, 256, 0, st>>>(series_off, n_series, spo, 0, symbol, dict_inc, qlen, ws.r_level, ws.r_pos, xhat);
+  k_recon_ends<<<g, 256, 0, st>>>(x, series_off, n_series, ws.r_tailpos, ws.r_tail_level, xhat);
+  (void)n_points;
+}
+
+// ------------------------------------------------------------------ adjoint
+// Per piece j (one thread): recompute xhat on the piece's points and form
+// T_j = sum_q r_{pos+q} and U_j = sum_q (q / l^) r_{pos+q}, r = xhat - x.
+__global__ void k_grad_piece(const double* x, const long long* series_off, long long n_series, const long long* spo,
+                             const int* symbol, const double* dict_inc, const int* qlen, const double* level,
+                             const long long* pos, double* T, double* U) {
+  const long long N = spo[n_series];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+    const long long s = find_series(spo, n_series, j);
+    const long long o = series_off[s], n_s = series_off[s + 1] - o;
+    const int L = qlen[j];
+    const double lh = (double)L, inc = dict_inc[symbol[j]], lv = level[j];
+    const long long p = pos[j];
+    double t = 0.0, u = 0.0;
+    for (int q = 1; q <= L && p + q <= n_s - 1; ++q) {
+      const double xh = __dadd_rn(lv, __ddiv_rn(__dmul_rn(inc, (double)q), lh));
+      const double r = __dsub_rn(xh, x[o + p + q]);
+      t = __dadd_rn(t, r);
+      u = __dadd_rn(u, __dmul_rn(__ddiv_rn((double)q, lh), r));
+    }
+    T[j] = t;
+    U[j] = u;
+  }
+}
+
+// Residual sum of the tail (points after the last piece), one warp per series.
+__global__ void k_grad_tail(const double* x, const long long* series_off, long long n_series,
+                            const long long* tail_pos, const double* tail_level, double* tail_sum) {
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long s = w; s < n_series; s += nw) {
+    const long long o = series_off[s], n_s = series_off[s + 1] - o;
+    double acc = 0.0;
+    if (n_s > 0)
+      for (long long i = tail_pos[s] + 1 + lane; i <= n_s - 1; i += 32) acc += tail_level[s] - x[o + i];
+    acc = warp_sum(acc);
+    if (lane == 0) tail_sum[s] = acc;
+  }
+}
+
+// Reverse pass per series: grad[a_j] += (2 / n) (U_j + sum_{j' > j} T_j' + tail).
+__global__ void k_grad_series(long long n_series, const long long* spo, const int* symbol, const double* T,
+                              const double* U, const double* tail_sum, double scale, double* grad) {
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n_series;
+       s += (long long)gridDim.x * blockDim.x) {
+    double after = tail_sum[s];
+    for (long long j = spo[s + 1] - 1; j >= spo[s]; --j) {
+      atomicAdd(&grad[symbol[j]], scale * (U[j] + after));
+      after += T[j];
+    }
+  }
+}
+
+void launch_reconstruct_backward(const double* x, long long n_points, const long long* series_off,
+                                 long long n_series, const long long* series_dom_off,
+                                 const long long* dom_piece_off, const int* symbol, const int* qlen,
+                                 const double* dict_inc, long long k, double* grad, Scratch& ws, cudaStream_t st) {
+  cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)(k > 0 ? k : 0), st);
+  if (n_series <= 0 || n_points <= 0) return;
+  long long* spo = ws.series_a;
+  const unsigned g = (unsigned)(ws.num_sms * 8);
+  k_series_piece_off<<<g, 256, 0, st>>>(series_dom_off, dom_piece_off, n_series, spo);
+  k_recon_seq<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(x, series_off, n_series, spo, symbol, nullptr,
+                                                                   dict_inc, 0, qlen, nullptr, ws.r_level, ws.r_pos,
+                                                                   ws.r_tailpos, ws.r_tail_level);
+  k_grad_piece<<<g, 256, 0, st>>>(x, series_off, n_series, spo, symbol, dict_inc, qlen, ws.r_level, ws.r_pos,
+                                   ws.r_tsum, ws.r_wsum);
+  k_grad_tail<<<g, 256, 0, st>>>(x, series_off, n_series, ws.r_tailpos, ws.r_tail_level, ws.r_tail);
+  k_grad_series<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(n_series, spo, symbol, ws.r_tsum, ws.r_wsum,
+                                                                     ws.r_tail, 2.0 / (double)n_points, grad);
+}
+
+}  // namespace jabba
+
+namespace jabba {
+
+// MSE = (1/n) sum (x - xhat)^2 (Sec. 3.3), two fixed-shape passes so the
+// summation order (and the result) is the same on every call.
+constexpr int kMseBlocks = 512;
+
+__global__ void __launch_bounds__(256) k_mse_partial(const double* x, const double* xhat, long long n,
+                                                     double* partial) {
+  __shared__ double sw[8];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = x[i] - xhat[i];
+    acc = fma(d, d, acc);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sw[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_mse_final(const double* partial, long long n, double* out) {
+  __shared__ double sw[8];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < kMseBlocks; i += blockDim.x) acc += partial[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sw[w];
+    *out = n > 0 ? t / (double)n : 0.0;
+  }
+}
+
+void launch_mse(const double* x, const double* xhat, long long n, double* out, Scratch& ws, cudaStream_t st) {
+  double* partial = ws.r_tail;  // >= kMseBlocks doubles is guaranteed by the reservation
+  k_mse_partial<<<kMseBlocks, 256, 0, st>>>(x, xhat, n, partial);
+  k_mse_final<<<1, 256, 0, st>>>(partial, n, out);
+}
+
+}  // namespace jabba

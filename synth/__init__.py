@@ -180,6 +180,20 @@ def make(name: str, max_series: int | None = None, seed: int | None = None,
     return x, off, cfg
 
 
+def sizes(name: str, max_series: int | None = None, seed: int | None = None):
+    """(n_series, n_points) of workload `name` (or of its first max_series
+    series) without generating the data."""
+    cfg = CONFIGS[name]
+    if seed is None:
+        seed = cfg["seed"]
+    root = np.random.SeedSequence([seed, cfg["index"]])
+    len_ss, _, _ = root.spawn(3)
+    lengths = _lengths(name, np.random.default_rng(len_ss))
+    if max_series is not None:
+        lengths = lengths[:max_series]
+    return len(lengths), int(lengths.sum())
+
+
 def series_kinds(name: str, seed: int | None = None) -> np.ndarray:
     """Generator index per series (scale workload: 0 walk, 1 sinusoids, 2 level shifts)."""
     cfg = CONFIGS[name]

@@ -1,0 +1,109 @@
+"""GPU-vs-oracle parity of the whole forward path (domains, Eq. 1
+compression, normalisation, Stage I and II aggregation, label propagation)
+and of the inverse symbolization, through the C ABI, on seeded inputs of the
+five workloads (bounded samples) and on edge cases."""
+import numpy as np
+import pytest
+
+import synth
+from _gpu import assert_parity, ctx, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    return ctx()
+
+
+@pytest.mark.parametrize("name,max_series", [("small", None), ("uneven", 40), ("multivar", 2), ("diff", 48),
+                                             ("scale", 150)])
+def test_workload_parity(C, name, max_series):
+    x, off, cfg = synth.make(name, max_series=max_series)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert len(r["piece_len"]) > 0
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("round_mode", [0, 1])
+def test_round_modes(C, round_mode):
+    x, off, cfg = synth.make("small", max_series=5)
+    cfg = dict(cfg, round_mode=round_mode)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert_parity(g, r)
+
+
+def test_edge_series_lengths(C):
+    """Empty, one-point and two-point series, a constant series and a straight
+    line next to ordinary ones."""
+    rng = np.random.default_rng(9)
+    parts = [np.zeros(0), np.array([1.5]), np.array([0.25, -0.5]), np.full(37, 0.75), 0.01 * np.arange(300.0),
+             np.cumsum(rng.standard_normal(1001)) * 0.1, np.zeros(0), rng.standard_normal(65)]
+    x = np.concatenate(parts)
+    off = np.concatenate([[0], np.cumsum([len(p) for p in parts])]).astype(np.int64)
+    for mode, val in [(0, 1), (0, 3), (1, 16), (1, 1)]:
+        cfg = dict(tol=0.05, alpha=0.1, scl=1.0, domain_mode=mode, domain_value=val)
+        g, *_ = run_gpu(C, x, off, cfg)
+        r = run_oracle(x, off, cfg)
+        assert_parity(g, r)
+
+
+def test_tol_zero_exact_path(C):
+    """tol = 0 on an integer piecewise-linear series: every admissible piece
+    has error exactly 0, which only the exact FP64 path can certify."""
+    rng = np.random.default_rng(2)
+    x = [0.0]
+    while len(x) < 3000:
+        slope = float(rng.integers(-4, 5))
+        for _ in range(int(rng.integers(1, 40))):
+            x.append(x[-1] + slope)
+    x = np.array(x)
+    off = np.array([0, len(x)], np.int64)
+    cfg = dict(tol=0.0, alpha=0.0, scl=1.0, domain_mode=0, domain_value=5)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert_parity(g, r)
+
+
+def test_large_domain_global_scratch(C):
+    """A domain with more pieces than the shared-memory tile (white noise,
+    small tol: almost every interval is a piece)."""
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(9000)
+    off = np.array([0, 9000], np.int64)
+    cfg = dict(tol=0.01, alpha=0.05, scl=1.0, domain_mode=0, domain_value=1)
+    g, *_ = run_gpu(C, x, off, cfg, recon=False)
+    r = run_oracle(x, off, cfg, recon=False)
+    assert len(r["piece_len"]) > 4096
+    assert_parity(g, r, recon=False)
+
+
+def test_ragged_many_series(C):
+    rng = np.random.default_rng(12)
+    lens = rng.integers(0, 3000, 400)
+    x = np.concatenate([np.cumsum(rng.standard_normal(n)) * 0.05 for n in lens]) if lens.sum() else np.zeros(0)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    cfg = dict(tol=0.1, alpha=0.1, scl=1.0, domain_mode=1, domain_value=257)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert_parity(g, r)
+
+
+def test_nonfinite_and_range_errors(C):
+    import paper_2401_00109_gb300 as jb
+    import torch
+    x = np.cumsum(np.random.default_rng(0).standard_normal(500))
+    off = np.array([0, 500], np.int64)
+    p = jb.Params(tol=0.1, alpha=0.1)
+    for bad, code in [(np.nan, 3), (np.inf, 3), (2.0 ** 40, 7)]:
+        y = x.copy()
+        y[123] = bad
+        c = C.compress(torch.from_numpy(y).cuda(), torch.from_numpy(off).cuda(), p, series_off_host=off)
+        with pytest.raises(jb.JabbaError) as e:
+            C.sync_status(where="compress")
+        assert e.value.code == code
+    # the context stays usable
+    c = C.compress(torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda(), p, series_off_host=off)
+    C.sync_status(where="compress")
