@@ -60,6 +60,7 @@ def lib():
                 "jo_count_domains": (C.c_int64, [I64, C.c_int64, C.c_int, C.c_int64]),
                 "jo_build_domains": (C.c_int64, [I64, C.c_int64, C.c_int, C.c_int64, I64, I64, I32]),
                 "jo_piece_error": (C.c_double, [F64, C.c_int64, C.c_int64]),
+                "jo_piece_error_l2": (C.c_double, [F64, C.c_int64, C.c_int64]),
                 "jo_piece_admissible": (C.c_int, [F64, C.c_int64, C.c_int64, C.c_double]),
                 "jo_compress_domain": (C.c_int64, [F64, C.c_int64, C.c_int64, C.c_double, I32, F64]),
                 "jo_compress_all": (None, [F64, I64, I64, C.c_int64, I64, C.c_double, I32, F64, I64, C.c_int]),

@@ -210,23 +210,58 @@ int64_t jo_build_domains(const int64_t* series_off, int64_t n_series, int mode, 
 /*    end reached by extension, which keeps the method linear);              */
 /*  - the sum runs over interior points only (the endpoint residuals are     */
 /*    zero in exact arithmetic);                                             */
-/*  - residual r_i = (x_s + (inc * k) / L) - x_i, k = i - s, L = e - s,      */
-/*    inc = x_e - x_s, evaluated in that order, summed in ascending i;       */
+/*  - Eq. 1 is used multiplied through by L^2 (L = e - s > 0), which leaves   */
+/*    the criterion unchanged in exact arithmetic and needs no division:     */
+/*      sum_{k=1}^{L-1} n_k^2 <= ((L - 1) tol^2) L^2,                         */
+/*      n_k = (x_s L + inc k) - x_{s+k} L,  inc = x_e - x_s,                  */
+/*    every n_k and n_k^2 evaluated in binary64 in that order, the squares   */
+/*    summed exactly (fixed point, resolution 2^-96, each term truncated)    */
+/*    and the total rounded once, so the sum has no order;                  */
 /*  - no slack on "<=".                                                      */
 /* ------------------------------------------------------------------------ */
-double jo_piece_error(const double* x, int64_t s, int64_t e) {
-  int64_t L = e - s;
-  double inc = x[e] - x[s];
-  double err = 0.0;
-  for (int64_t k = 1; k < L; ++k) {
-    double r = (x[s] + (inc * (double)k) / (double)L) - x[s + k];
-    err = err + r * r;
+
+/* Exact sum of non-negative doubles at resolution 2^-96, rounded once. */
+static double exact_sum96(const double* v, int64_t n) {
+  jo_fx a;
+  fx_zero(&a);
+  for (int64_t i = 0; i < n; ++i) {
+    if (v[i] == 0.0) continue;
+    uint64_t m;
+    int E;
+    split_double(v[i], &m, &E);
+    jo_fx t;
+    fx_from_scaled(&t, m, E + 96, 0);
+    fx_add_fx(&a, &t);
   }
-  return err;
+  return ldexp(fx_to_double(&a), -32);   /* fx_to_double scales by 2^-64; 2^-96 in total */
+}
+
+/* L^2 times the Eq. 1 error of piece (s, e). */
+double jo_piece_error_l2(const double* x, int64_t s, int64_t e) {
+  int64_t L = e - s;
+  if (L < 2) return 0.0;
+  double dL = (double)L;
+  double inc = x[e] - x[s];
+  double xsL = x[s] * dL;
+  double* sq = (double*)malloc(sizeof(double) * (size_t)(L - 1));
+  for (int64_t k = 1; k < L; ++k) {
+    double n = (xsL + inc * (double)k) - x[s + k] * dL;
+    sq[k - 1] = n * n;
+  }
+  double r = exact_sum96(sq, L - 1);
+  free(sq);
+  return r;
+}
+
+/* The Eq. 1 error itself (reporting and tests). */
+double jo_piece_error(const double* x, int64_t s, int64_t e) {
+  double dL = (double)(e - s);
+  return jo_piece_error_l2(x, s, e) / (dL * dL);
 }
 
 int jo_piece_admissible(const double* x, int64_t s, int64_t e, double tol) {
-  return jo_piece_error(x, s, e) <= (double)(e - s - 1) * (tol * tol);
+  double dL = (double)(e - s);
+  return jo_piece_error_l2(x, s, e) <= ((double)(e - s - 1) * (tol * tol)) * (dL * dL);
 }
 
 int64_t jo_compress_domain(const double* x, int64_t b, int64_t e_dom, double tol,
