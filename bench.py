@@ -232,7 +232,7 @@ def run_ours(args, ws, rank, local):
         ctx.profile_slot(i if i < 256 else -1)
         graphs.append(pl.capture())
     ctx.profile_slot(-1)
-    kernels_per_step = jb.graph_kernel_nodes(graphs[0])
+    kernels_per_step = jb.graph_kernel_nodes(pl.capture(keep_graph=True))
     for i in range(args.warmup):
         graphs[i].replay()
     torch.cuda.synchronize()
@@ -332,6 +332,9 @@ def run_ours(args, ws, rank, local):
                    sample=f"first {args.cpu_series} series of the workload ({len(xs)} points), one pass; "
                           f"compression on {threads} threads, digitization serial")
 
+    if args.verify and rank == 0:
+        verify_sample(pl, x_host.numpy(), off_np, cfg, args.verify)
+
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="Gpts/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms_all, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
@@ -349,6 +352,32 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def verify_sample(pl, x, off, cfg, n_dom):
+    """Full-size parity on a sample: the oracle compresses n_dom domains drawn
+    at random and must reproduce their pieces bit for bit."""
+    import oracle
+    b = pl.b
+    D = pl.D
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(D, min(n_dom, D), replace=False))
+    db = b["dom_begin"].cpu().numpy()
+    de = b["dom_end"].cpu().numpy()
+    so = b["dom_slot_off"].cpu().numpy()
+    cnt = b["dom_piece_cnt"][:D].cpu().numpy()
+    plen = b["piece_len"].cpu().numpy()
+    pinc = b["piece_inc"].cpu().numpy()
+    bad = 0
+    for d in pick:
+        ln, inc, _ = oracle.compress(x, db[d:d + 1], de[d:d + 1], cfg["tol"])
+        g_ln = plen[so[d]:so[d] + cnt[d]]
+        g_inc = pinc[so[d]:so[d] + cnt[d]]
+        if not (np.array_equal(ln, g_ln) and np.array_equal(inc, g_inc)):
+            bad += 1
+    print(json.dumps(dict(verify_domains=len(pick), mismatched=bad)), file=sys.stderr, flush=True)
+    if bad:
+        raise SystemExit(f"parity failure on {bad} of {len(pick)} sampled domains")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,6 +390,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--verify", type=int, default=0, help="oracle-check this many sampled domains")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

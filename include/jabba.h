@@ -218,6 +218,11 @@ jabba_status jabba_reconstruct_backward(jabba_ctx* ctx, const double* x, int64_t
 jabba_status jabba_profile_slot(jabba_ctx* ctx, int slot);
 jabba_status jabba_profile_elapsed(jabba_ctx* ctx, int slot, int stage, float* ms);
 
+/* Diagnostic counters of the last calls (no counterpart in the paper);
+ * synchronizes the device.  out[0] = admissibility decisions that needed the
+ * exact FP64 evaluation in the last jabba_compress.  n = entries wanted. */
+jabba_status jabba_diagnostics(jabba_ctx* ctx, int64_t* out, int n);
+
 /* Reconstruction error (Sec. 3.3): *out (device scalar) = (1/n) sum (x - xhat)^2,
  * summed in a fixed order (the same result on every call on a device). */
 jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int64_t n_points, double* out,

@@ -100,6 +100,7 @@ def load():
                 "jabba_reconstruct_backward": (C.c_int, [V, V, I64, V, I64, V, V, V, V, V, I64, V, V]),
                 "jabba_mse": (C.c_int, [V, V, V, I64, V, V]),
                 "jabba_profile_slot": (C.c_int, [V, C.c_int]),
+                "jabba_diagnostics": (C.c_int, [V, C.POINTER(C.c_int64), C.c_int]),
                 "jabba_profile_elapsed": (C.c_int, [V, C.c_int, C.c_int, C.POINTER(C.c_float)]),
             }
             for name, (res, args) in sig.items():
@@ -299,6 +300,12 @@ class Context:
             self._stream(stream)), "jabba_reconstruct_backward")
         return grad[:k]
 
+    def diagnostics(self):
+        """{'exact_decisions': ...} of the last compress call."""
+        out = (C.c_int64 * 1)()
+        _check(self.lib.jabba_diagnostics(self.h, out, 1), "jabba_diagnostics")
+        return dict(exact_decisions=int(out[0]))
+
     def profile_slot(self, slot: int):
         _check(self.lib.jabba_profile_slot(self.h, int(slot)), "jabba_profile_slot")
 
@@ -415,10 +422,11 @@ class Pipeline:
                                  P(b["dom_piece_off"]), P(b["dom_group_off"]), self.D, P(b["l2g"]), P(b["symbol"]), st),
                "jabba_symbolize")
 
-    def capture(self):
-        """Capture one step into a CUDA graph (call after one eager step)."""
+    def capture(self, keep_graph: bool = False):
+        """Capture one step into a CUDA graph (call after one eager step).
+        keep_graph=True keeps the graph for inspection (graph_kernel_nodes)."""
         torch = _torch()
-        g = torch.cuda.CUDAGraph()
+        g = torch.cuda.CUDAGraph(keep_graph=keep_graph) if keep_graph else torch.cuda.CUDAGraph()
         s = torch.cuda.Stream(device=self.x.device)
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):

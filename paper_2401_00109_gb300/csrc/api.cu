@@ -57,6 +57,9 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // pointers when `base` is non-null.
 size_t layout(Scratch& w, long long S, long long D, long long slots, long long G, long long big,
               unsigned char* base) {
+  // big = largest domain in intervals (bounds both piece lengths and pieces per domain)
+  const long long cap_len = big > 0 ? big : 1;
+  const long long loc_warps = (long long)w.loc_ctas * local_warps_per_cta();
   size_t off = 0;
   auto take = [&](size_t bytes) -> unsigned char* {
     unsigned char* p = base ? base + off : nullptr;
@@ -69,7 +72,15 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.series_c = (long long*)take(8 * (S + 1));
   w.scan_tiles = (long long*)take(8 * scan_n);
   w.counters = (unsigned*)take(64);
-  w.big = take(big > 0 ? (size_t)big * 44 + 16 : 16);
+  w.big = nullptr;
+  w.arena = (unsigned*)take(4 * (size_t)local_arena_words(cap_len, loc_warps));
+  w.xtab64 = (double*)take(8 * (cap_len + 1));
+  w.xtab32 = (float*)take(4 * (cap_len + 1));
+  w.rinv32 = (float*)take(16);
+  if (base) {
+    w.cap_len = cap_len;
+    w.cap_items = cap_len;
+  }
   w.m_key = (double*)take(8 * G);
   w.m_X = (double*)take(8 * G);
   w.m_Y = (double*)take(8 * G);
@@ -167,6 +178,7 @@ jabba_status jabba_create(jabba_ctx** out, int device) {
   }
   cudaDeviceGetAttribute(&c->ws.num_sms, cudaDevAttrMultiProcessorCount, device);
   if (c->ws.num_sms <= 0) c->ws.num_sms = 1;
+  c->ws.loc_ctas = c->ws.num_sms * 2;
   *out = c;
   return JABBA_OK;
 }
@@ -227,12 +239,8 @@ jabba_status jabba_reserve(jabba_ctx* c, int64_t n_points, int64_t n_series, int
     return JABBA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   c->ws.cap_points = n_points > c->ws.cap_points ? n_points : c->ws.cap_points;
-  long long big = 0;
-  if (max_dom_intervals > 4096) {
-    big = 1;
-    while (big < max_dom_intervals) big <<= 1;
-  }
-  return ensure(c, n_series, n_domains, n_slots > n_points ? n_slots : n_points, group_capacity, big, nullptr);
+  return ensure(c, n_series, n_domains, n_slots > n_points ? n_slots : n_points, group_capacity, max_dom_intervals,
+                nullptr);
 }
 
 jabba_status jabba_compress(jabba_ctx* c, const double* x, int64_t n_points, const int64_t* series_off,
@@ -357,6 +365,18 @@ jabba_status jabba_reconstruct_backward(jabba_ctx* c, const double* x, int64_t n
   launch_reconstruct_backward(x, n_points, (const long long*)series_off, n_series, (const long long*)series_dom_off,
                               (const long long*)dom_piece_off, symbol, qlen, dict_inc, k, grad_dict_inc, c->ws, st);
   return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_diagnostics(jabba_ctx* c, int64_t* out, int n) {
+  if (!c || !out || n < 0) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  for (int i = 0; i < n; ++i) out[i] = 0;
+  if (!c->ws.counters || n == 0) return JABBA_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return JABBA_ERR_CUDA;
+  unsigned long long v = 0;
+  if (cudaMemcpy(&v, c->ws.counters + 2, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return JABBA_ERR_CUDA;
+  out[0] = (int64_t)v;
+  return JABBA_OK;
 }
 
 jabba_status jabba_profile_slot(jabba_ctx* c, int slot) {

@@ -74,23 +74,25 @@ void launch_build_domains(const long long* series_off, long long n_series, int m
 // of kChunk points with a TMA bulk copy (cp.async.bulk) completing on a
 // per-warp mbarrier, double-buffered.
 //
-// Admissibility of the candidate piece (s, e) (Eq. 1) is decided by a
-// certified FP32 test, falling back to the exact FP64 evaluation (the
-// definition's own operation order) only when the FP32 result cannot decide.
-// With D_i = x_{s+i} - x_s and L = e - s, L^2 * err = F(D) where
-//   F(D) = L^2 S2 - 2 L D_L SK + D_L^2 K2,  S2 = sum D_i^2, SK = sum i D_i,
-//   K2 = sum i^2 over the interior i = 1..L-1.
-// The FP32 evaluation E of F from truncated FP32 copies d_i of D_i obeys
-//   |E - F(d)| <= A = 2.2 (L + 8) 2^-24 (L^2 S2 + d_L^2 K2)       (rounding;
-//   Cauchy-Schwarz bounds the cross term), and |sqrt F(d) - sqrt F(D)| <= h =
-//   2 tau L sqrt(L - 1), tau = 2^-20 max|x~| (conversion, subtraction and the
-//   FP64 definition's own rounding of the residuals).
-// With theta = 2^-10, (sqrt q + h)^2 <= (1 + theta) q + 1025 h^2 and
-// (sqrt q - h)^2 >= (1 - theta) q - 1025 h^2, so
-//   admissible   if (1 + theta)(E + A) + H < L^2 (L - 1) tol^2 (1 - 2^-18),
-//   inadmissible if (1 - theta)(E - A) - H > L^2 (L - 1) tol^2 (1 + 2^-18),
-// H = 1025 h^2 (rounded up); the 2^-18 slack covers the remaining FP32 and
-// FP64 roundings.  Otherwise the exact FP64 sum decides.
+// Admissibility of the candidate piece (s, e) (Eq. 1 multiplied by L^2,
+// L = e - s): with D_i = x_{s+i} - x_s,
+//   F(D) = sum_{i=1}^{L-1} (L D_i - i D_L)^2 = L^2 S2 - 2 L D_L SK + D_L^2 K2,
+//   S2 = sum D_i^2, SK = sum i D_i, K2 = sum i^2,
+// and the piece is admissible when F <= L^2 (L - 1) tol^2.  The lane keeps
+// S2, SK, K2 of FP32 copies d_i (truncated conversion of x, FP32 difference)
+// and evaluates E ~ F(d) in FP32 per point.  Certified bounds:
+//   |E - F(d)| <= A = 2.2 (L + 8) 2^-24 (L^2 S2 + d_L^2 K2)    (rounding; the
+//     cross term is bounded by Cauchy-Schwarz),
+//   |sqrt F(d) - sqrt F(D)| <= h = 2 tau L sqrt(L - 1),  tau = 2^-20 max|x~|
+//     over the piece (conversion and subtraction errors of the d_i, and the
+//     binary64 rounding of the definition's own terms, with margin 2).
+// Hence, squaring sqrt F +- h against sqrt(L^2 (L-1)) tol,
+//   admissible   if E + A < L^2 (L - 1) (tol (1 - 2^-18) - 2^-19 M)^2,
+//   inadmissible if E - A > L^2 (L - 1) (tol (1 + 2^-18) + 2^-19 M)^2,
+// (M = max|x~|; the 2^-18 slack covers the FP32 roundings of the tests
+// themselves and the binary64 roundings of the definition's bound and sum).
+// Otherwise the whole warp evaluates the binary64 definition for that lane
+// (32 terms at a time, exact fixed-point sum): see warp_exact_admissible.
 constexpr int kChunk = 16;                 // points per lane per stage
 constexpr int kRow = kChunk + 2;           // doubles per staged row (16-byte multiple, alignment slack)
 constexpr int kWarpsPerCta = 8;
@@ -104,29 +106,58 @@ struct CompressParams {
   const long long* dom_slot_off;
   long long n_domains;
   double tol2;        // tol * tol, binary64
-  float tol2_lo;      // tol2 (1 - 2^-18) rounded down
-  float tol2_hi;      // tol2 (1 + 2^-18) rounded up
+  float tol_lo;       // tol (1 - 2^-18) rounded down
+  float tol_hi;       // tol (1 + 2^-18) rounded up
   int* piece_len;
   double* piece_end;  // end value of each piece; turned into increments afterwards
   int* dom_piece_cnt;
   unsigned* status;
   unsigned* task_counter;
-  unsigned long long* n_exact;  // number of candidates decided by the exact FP64 path
+  unsigned long long* n_exact;  // number of candidates decided by the exact binary64 path
 };
 
-// Exact FP64 evaluation of Eq. 1 for (s, e) with the definition's operation
-// order: r = (x_s + (inc * k) / L) - x_{s+k}, err += r * r, ascending k.
-__device__ __noinline__ bool exact_admissible(const double* xb, int s, int e, double tol2) {
+// trunc(v * 2^96) of a finite double v >= 0 with v < 2^95, as 192 bits.
+__device__ __forceinline__ I192 fx96(double v) {
+  const u64 bits = (u64)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  I192 r = {0, 0, 0};
+  if (e == 0) return r;
+  const u64 m = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = e - 1075 + 96;
+  if (sh <= -64) return r;
+  if (sh < 0) { r.w0 = m >> (-sh); return r; }
+  if (sh < 64) { r.w0 = m << sh; r.w1 = sh ? (m >> (64 - sh)) : 0; return r; }
+  if (sh < 128) { const int t = sh - 64; r.w1 = m << t; r.w2 = t ? (m >> (64 - t)) : 0; return r; }
+  r.w2 = m << (sh - 128);
+  return r;
+}
+
+// The binary64 definition (Eq. 1 times L^2) for piece (s, e) of the domain
+// starting at xb, evaluated by the whole warp: lane t computes the terms
+// k = 1 + t, 33 + t, ... ; the squares are summed exactly (fixed point at
+// 2^-96) and rounded once, so the result does not depend on the order.
+__device__ __noinline__ bool warp_exact_admissible(const double* xb, int s, int e, double tol2) {
+  const int lane = threadIdx.x & 31;
   const int L = e - s;
+  const double dL = (double)L;
   const double xs = xb[s];
   const double inc = __dsub_rn(xb[e], xs);
-  const double dL = (double)L;
-  double err = 0.0;
-  for (int k = 1; k < L; ++k) {
-    const double r = __dsub_rn(__dadd_rn(xs, __ddiv_rn(__dmul_rn(inc, (double)k), dL)), xb[s + k]);
-    err = __dadd_rn(err, __dmul_rn(r, r));
+  const double xsL = __dmul_rn(xs, dL);
+  I192 acc = {0, 0, 0};
+  for (int k = 1 + lane; k < L; k += 32) {
+    const double n = __dsub_rn(__dadd_rn(xsL, __dmul_rn(inc, (double)k)), __dmul_rn(xb[s + k], dL));
+    const I192 t = fx96(__dmul_rn(n, n));
+    add192(acc, t.w0, t.w1, t.w2);
   }
-  return err <= __dmul_rn((double)(L - 1), tol2);
+  for (int o = 16; o > 0; o >>= 1) {
+    const u64 b0 = __shfl_xor_sync(0xFFFFFFFFu, acc.w0, o);
+    const u64 b1 = __shfl_xor_sync(0xFFFFFFFFu, acc.w1, o);
+    const u64 b2 = __shfl_xor_sync(0xFFFFFFFFu, acc.w2, o);
+    add192(acc, b0, b1, b2);
+  }
+  const double err_l2 = round_u192(acc.w0, acc.w1, acc.w2, -96, false);
+  const double bound = __dmul_rn(__dmul_rn((double)(L - 1), tol2), __dmul_rn(dL, dL));
+  return err_l2 <= bound;
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -198,13 +229,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P
   if (lane < kStages) mbar_init(smem_u32(&bars[warp][lane]), 32);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  unsigned phase[kStages] = {0, 0};
+  unsigned phase0 = 0, phase1 = 0;
   const unsigned bar0 = smem_u32(&bars[warp][0]);
   const unsigned bar1 = smem_u32(&bars[warp][1]);
   const long long n_tasks = (P.n_domains + 31) / 32;
   const float G1 = 2.2f * 0x1p-24f, G0 = 2.2f * 8.0f * 0x1p-24f;
-  const float HC = 4200.0f * 0x1p-40f;
-  const float ONE_P = 1.0f + 0x1p-10f, ONE_M = 1.0f - 0x1p-10f;
   unsigned amax = 0;  // largest |x| high word seen (range / finiteness check)
 
   for (;;) {
@@ -240,71 +269,82 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P
       M = fabsf(xs);
     }
 
-    int off[kStages] = {0, 0};
-    if (n_chunks > 0) off[0] = stage_chunk(P, D, 0, stage[warp][0][lane], bar0);
+    int off_a = 0, off_b = 0;
+    if (n_chunks > 0) off_a = stage_chunk(P, D, 0, stage[warp][0][lane], bar0);
     for (int c = 0; c < n_chunks; ++c) {
       const int buf = c & 1;
       if (c + 1 < n_chunks) {
         __syncwarp();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        off[buf ^ 1] = stage_chunk(P, D, c + 1, stage[warp][buf ^ 1][lane], buf ? bar0 : bar1);
+        const int o = stage_chunk(P, D, c + 1, stage[warp][buf ^ 1][lane], buf ? bar0 : bar1);
+        if (buf) off_a = o; else off_b = o;
       }
       // wait for this chunk (bounded); on timeout every lane leaves together
       {
         const unsigned bar = buf ? bar1 : bar0;
+        const unsigned ph = buf ? phase1 : phase0;
         unsigned spins = 0;
         bool ok = true;
-        while (!mbar_try_wait(bar, phase[buf])) {
+        while (!mbar_try_wait(bar, ph)) {
           if (++spins > kSpinLimit) { ok = false; break; }
         }
         if (!__all_sync(0xFFFFFFFFu, ok)) {
           set_status(P.status, JABBA_ERR_TIMEOUT);
           // give the copies still in flight a bounded time to land before the
           // CTA's shared memory is released
-          for (int b = 0; b < kStages; ++b) {
-            const unsigned bb = b ? bar1 : bar0;
-            unsigned sp = 0;
-            while (!mbar_try_wait(bb, phase[b]) && ++sp < kSpinLimit) {}
-          }
+          unsigned sp = 0;
+          while (!mbar_try_wait(bar0, phase0) && ++sp < kSpinLimit) {}
+          sp = 0;
+          while (!mbar_try_wait(bar1, phase1) && ++sp < kSpinLimit) {}
           return;
         }
-        phase[buf] ^= 1u;
+        if (buf) phase1 ^= 1u; else phase0 ^= 1u;
       }
-      const double* row = stage[warp][buf][lane] + off[buf];
+      const double* row = stage[warp][buf][lane] + (buf ? off_b : off_a);
       const int p0 = 1 + c * kChunk;
-#pragma unroll 4
+#pragma unroll 2
       for (int j = 0; j < kChunk; ++j) {
         const int p = p0 + j;
-        if (p <= D.n_int) {
-          const double vd = row[j];
-          unsigned mh;
-          const float v = f64_to_f32_trunc(vd, mh);
-          amax = max(amax, mh);
-          float d = v - xs;
-          Lf += 1.0f;
-          const float L2 = Lf * Lf;
-          const float dd = d * d;
-          const float t3 = dd * K2;
-          const float cc = (Lf + Lf) * d;
-          const float E = fmaf(L2, S2, fmaf(-cc, SK, t3));
-          const float Pp = fmaf(L2, S2, t3);
-          const float B0 = L2 * (Lf - 1.0f);
-          const float A = fmaf(Lf, G1, G0) * Pp;
-          const float Mx = fmaxf(M, fabsf(v));
-          const float H = (Mx * Mx * HC) * B0;
-          bool feas = fmaf(E + A, ONE_P, H) < B0 * P.tol2_lo;
-          bool infeas = fmaf(E - A, ONE_M, -H) > B0 * P.tol2_hi;
-          const bool fast_ok = (Mx >= 0x1p-60f) && (Mx < 0x1p31f) && (Lf < 1048576.0f);
-          feas = (feas && fast_ok) || (Lf == 1.0f);
-          infeas = infeas && fast_ok && !feas;
-          if (!feas && !infeas) {
-            feas = exact_admissible(xb, s, p, P.tol2);
-            atomicAdd(P.n_exact, 1ull);
-          }
+        const bool act = p <= D.n_int;
+        const double vd = row[j];
+        unsigned mh;
+        const float v = f64_to_f32_trunc(vd, mh);
+        if (act) amax = max(amax, mh);
+        float dd_ = v - xs;
+        const float Ln = Lf + 1.0f;
+        const float L2 = Ln * Ln;
+        const float sq = dd_ * dd_;
+        const float t3 = sq * K2;
+        const float cc = (Ln + Ln) * dd_;
+        const float E = fmaf(L2, S2, fmaf(-cc, SK, t3));
+        const float Pp = fmaf(L2, S2, t3);
+        const float B0 = L2 * (Ln - 1.0f);
+        const float A = fmaf(Ln, G1, G0) * Pp;
+        const float Mx = fmaxf(M, fabsf(v));
+        const float clo = fmaf(-0x1p-19f, Mx, P.tol_lo);
+        const float chi = fmaf(0x1p-19f, Mx, P.tol_hi);
+        bool feas = (E + A < B0 * (clo * clo)) && clo > 0.f;
+        bool infeas = E - A > B0 * (chi * chi);
+        const bool fast_ok = (Mx >= 0x1p-60f) && (Mx < 0x1p31f) && (Ln < 1048576.0f);
+        feas = (feas && fast_ok) || (Ln == 1.0f);
+        infeas = infeas && fast_ok && !feas;
+        unsigned amb = __ballot_sync(0xFFFFFFFFu, act && !feas && !infeas);
+        while (amb) {
+          const int l = __ffs(amb) - 1;
+          amb &= amb - 1;
+          const long long gb = __shfl_sync(0xFFFFFFFFu, D.b, l);
+          const int sl = __shfl_sync(0xFFFFFFFFu, s, l);
+          const int pl = __shfl_sync(0xFFFFFFFFu, p, l);
+          const bool r = warp_exact_admissible(P.x + gb, sl, pl, P.tol2);
+          if (lane == l) feas = r;
+          if (lane == 0) atomicAdd(P.n_exact, 1ull);
+        }
+        if (act) {
           if (feas) {
-            S2 = fmaf(d, d, S2);
-            SK = fmaf(Lf, d, SK);
-            K2 = fmaf(Lf, Lf, K2);
+            S2 = fmaf(dd_, dd_, S2);
+            SK = fmaf(Ln, dd_, SK);
+            K2 = fmaf(Ln, Ln, K2);
+            Lf = Ln;
             M = Mx;
           } else {
             // piece (s, p - 1) ends; restart at p - 1 with p as its first candidate
@@ -313,9 +353,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P
             ++cnt;
             s = p - 1;
             xs = prevf;
-            d = v - xs;
-            S2 = d * d;
-            SK = d;
+            dd_ = v - xs;
+            S2 = dd_ * dd_;
+            SK = dd_;
             K2 = 1.0f;
             Lf = 1.0f;
             M = fmaxf(fabsf(prevf), fabsf(v));
@@ -452,17 +492,21 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   P.dom_slot_off = dom_slot_off;
   P.n_domains = n_domains;
   P.tol2 = tol * tol;
-  P.tol2_lo = (float)(P.tol2 * (1.0 - 0x1p-18));
-  if ((double)P.tol2_lo > P.tol2 * (1.0 - 0x1p-18)) P.tol2_lo = nextafterf(P.tol2_lo, 0.0f);
-  P.tol2_hi = (float)(P.tol2 * (1.0 + 0x1p-18));
-  if ((double)P.tol2_hi < P.tol2 * (1.0 + 0x1p-18)) P.tol2_hi = nextafterf(P.tol2_hi, INFINITY);
+  {
+    const double lo = tol * (1.0 - 0x1p-18), hi = tol * (1.0 + 0x1p-18);
+    P.tol_lo = (float)lo;
+    if ((double)P.tol_lo > lo) P.tol_lo = nextafterf(P.tol_lo, 0.0f);
+    P.tol_hi = (float)hi;
+    if ((double)P.tol_hi < hi) P.tol_hi = nextafterf(P.tol_hi, INFINITY);
+    if (!(hi < 3.0e38)) P.tol_hi = INFINITY;
+  }
   P.piece_len = piece_len;
   P.piece_end = piece_inc;
   P.dom_piece_cnt = dom_piece_cnt;
   P.status = status;
   P.task_counter = ws.counters;
   P.n_exact = (unsigned long long*)(ws.counters + 2);
-  cudaMemsetAsync(ws.counters, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(ws.counters, 0, 4 * sizeof(unsigned), st);
   cudaMemsetAsync(stats, 0, JABBA_PIECE_STATS_BYTES, st);
   const long long n_tasks = (n_domains + 31) / 32;
   long long ctas = (long long)ws.num_sms * 3;

@@ -16,7 +16,14 @@ struct Scratch {
   long long* series_c = nullptr;
   long long* scan_tiles = nullptr;
   unsigned* counters = nullptr;   // [16]: task counters, diagnostics
-  // local aggregation of domains larger than the shared-memory tile
+  // local aggregation: per-warp arenas and the FP32 normalisation tables
+  long long cap_len = 0;          // largest piece length covered by the X table
+  long long cap_items = 0;        // largest domain (pieces) an arena holds
+  int loc_ctas = 0;               // CTAs of the local-aggregation kernel
+  unsigned* arena = nullptr;
+  double* xtab64 = nullptr;
+  float* xtab32 = nullptr;
+  float* rinv32 = nullptr;
   unsigned char* big = nullptr;
   // merge
   double* m_key = nullptr;        // [cap_groups] sort keys, then sorted keys
@@ -56,11 +63,20 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
                      double* piece_inc, int* dom_piece_cnt, long long* dom_piece_off, long long* stats,
                      Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk);
 
+// Records an event on `st`; inside stream capture the record becomes a graph
+// node (external record) so that replays time the same kernels.
 inline void mark(cudaEvent_t e, cudaStream_t st) {
-  if (e) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  if (!e) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
 }
 
 void launch_sigma(const long long* stats, double* sigma, cudaStream_t st);
+
+long long local_arena_words(long long cap_items, long long n_warps);
+int local_warps_per_cta();
 
 void launch_local(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
                   const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
