@@ -66,7 +66,13 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     off += align_up(bytes ? bytes : 1);
     return p;
   };
-  const long long scan_n = scan_scratch_elems((S > D ? S : D) + 1) + scan_scratch_elems(256 * ((G + 4095) / 4096) + 1) + 8;
+  long long scan_n = scan_scratch_elems((S > D ? S : D) + 1);
+  {
+    const long long a = scan_scratch_elems(256 * ((G + 4095) / 4096) + 1), b = scan_scratch_elems(G + 1);
+    if (a > scan_n) scan_n = a;
+    if (b > scan_n) scan_n = b;
+    scan_n += 8;
+  }
   w.series_a = (long long*)take(8 * (S + 1));
   w.series_b = (long long*)take(8 * (S + 1));
   w.series_c = (long long*)take(8 * (S + 1));
@@ -92,6 +98,39 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.m_label = (int*)take(4 * G);
   w.m_rec = (int*)take(4 * G);
   w.m_hist = (unsigned*)take(4 * 256 * ((G + 4095) / 4096 + 1));
+  w.m_X32 = (float*)take(4 * G);
+  w.m_Y32 = (float*)take(4 * G);
+  {
+    const long long cells = G > 0 ? (1ll << 23) : 1;
+    if (base) w.cap_cells = cells;
+    MergeBufs& B = w.mb;
+    B.bounds = (int*)take(16);
+    B.bar = (unsigned*)take(64);
+    B.rinv = (float*)take(16);
+    B.geom = (struct GridGeom*)take(64);
+    B.flags = (int*)take(16);
+    B.sX = (float*)take(4 * G);
+    B.sY = (float*)take(4 * G);
+    B.rank = (int*)take(4 * G);
+    B.ck1 = (unsigned long long*)take(8 * G);
+    B.cv1 = (int*)take(4 * G);
+    B.head = (int*)take(4 * G);
+    B.head_off = (long long*)take(8 * (G + 1));
+    B.cell_of_id = (int*)take(4 * cells);
+    B.cell_beg = (int*)take(4 * G);
+    B.cell_end = (int*)take(4 * G);
+    B.cell_id = (int*)take(4 * G);
+    B.state = (unsigned long long*)take(8 * G);
+    B.cov = (unsigned char*)take(G > 0 ? G : 1);
+    B.new_list = (int*)take(8 * (G > 0 ? G : 1));
+    B.lab = (int*)take(4 * G);
+    B.is_start = (int*)take(4 * G);
+    B.start_off = (long long*)take(8 * (G + 1));
+    B.gid_c = (int*)take(4 * G);
+    B.eX = (double*)take(8 * G);
+    B.eY = (double*)take(8 * G);
+    B.ekey = (double*)take(8 * G);
+  }
   {
     const long long tiles = (G + 4095) / 4096;
     const long long acc_elems = 8 * (G > 1 ? G : 1);

@@ -6,6 +6,36 @@
 
 namespace jabba {
 
+// Buffers of the global merge (sizes: cap = group capacity, cells = grid cells).
+struct MergeBufs {
+  int* bounds = nullptr;             // [4] ordered-int min/max of the FP32 coordinates
+  unsigned* bar = nullptr;           // [8] grid barrier and round counters
+  float* rinv = nullptr;             // [2] 1/sigma in FP32
+  struct GridGeom* geom = nullptr;   // grid geometry (device)
+  int* flags = nullptr;              // [4] [0] = sequential fallback
+  float* sX = nullptr;               // [cap] FP32 coordinates in key order
+  float* sY = nullptr;
+  int* rank = nullptr;               // [cap] key-order position of compact index c
+  unsigned long long* ck1 = nullptr; // [cap] cell sort ping-pong
+  int* cv1 = nullptr;
+  int* head = nullptr;               // [cap]
+  long long* head_off = nullptr;     // [cap + 1]
+  int* cell_of_id = nullptr;         // [cells]
+  int* cell_beg = nullptr;           // [cap]
+  int* cell_end = nullptr;
+  int* cell_id = nullptr;
+  unsigned long long* state = nullptr;  // [cap]
+  unsigned char* cov = nullptr;      // [cap] covered flags (cell order)
+  int* new_list = nullptr;           // [2 * cap] cells that created a start (per round parity)
+  int* lab = nullptr;                // [cap]
+  int* is_start = nullptr;           // [cap]
+  long long* start_off = nullptr;    // [cap + 1]
+  int* gid_c = nullptr;              // [cap]
+  double* eX = nullptr;              // [cap] binary64 coordinates (fallback only)
+  double* eY = nullptr;
+  double* ekey = nullptr;
+};
+
 // Scratch owned by a context (device memory).  Sized by jabba_reserve().
 struct Scratch {
   int num_sms = 0;
@@ -35,6 +65,10 @@ struct Scratch {
   int* m_v0 = nullptr;
   int* m_v1 = nullptr;
   int* m_label = nullptr;         // [cap_groups] global id per compact index
+  float* m_X32 = nullptr;         // [cap_groups] FP32 centre coordinates (compact index)
+  float* m_Y32 = nullptr;
+  long long cap_cells = 0;        // grid cells of the merge
+  MergeBufs mb;
   int* m_rec = nullptr;           // [cap_groups] record of each compact index
   unsigned* m_hist = nullptr;     // radix histograms
   long long* d_acc = nullptr;     // [cap_groups * 8] dictionary accumulators

@@ -1,49 +1,182 @@
 // merge.cu -- Stage II of the two-stage digitization (Sec. 5): the local
-// groups, taken at their centres, are aggregated once more by the same
-// greedy; the result maps every local group to a global group and the
+// groups, taken at their centres, are aggregated once more by the same greedy
+// (Sec. 3.2); the result maps every local group to a global group, and the
 // dictionary entries are the exact means of their member pieces.
+//
+// The greedy in key order is the lexicographically first maximal set of
+// "starts" pairwise farther than alpha apart; every other item joins the
+// earliest start within alpha.  It is computed in parallel:
+//  1. FP32 centre coordinates with rigorous relative error 2^-20 (binary64
+//     values are computed only for undecided comparisons);
+//  2. the exact order: radix sort by the FP32 key, then every run of
+//     neighbours whose key intervals overlap is re-sorted by binary64 keys;
+//  3. a uniform grid of cells of side h = alpha/2 (1 + 2^-7): two items in one
+//     cell are within alpha, so a cell holds at most one start, and it is the
+//     first of its items (in key order) not covered by an earlier start of a
+//     neighbouring cell (within 2 cells);
+//  4. rounds (one cooperative kernel, bounded grid barriers): each undecided
+//     cell skips its items covered by known neighbouring starts; its next item
+//     becomes a start once no undecided neighbouring item that precedes it in
+//     key order lies within alpha (such an item could still become a start);
+//  5. every item's label is the earliest start within alpha among the starts
+//     of its 5 x 5 cell neighbourhood; global ids follow key order.
+// If the coordinates span too many cells for the grid, or their error
+// exceeds 2^-8 of a cell, a sequential single-CTA greedy on the binary64
+// coordinates runs instead (same result).
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 namespace jabba {
 
-// ------------------------------------------------------------------ centres, keys
-// One thread per group record: compact index c = dom_group_off[domain] +
-// local_id, centre (lensum / count, round(inc) / count), normalised point
-// X = (scl * c_len) / sigma_len, Y = c_inc / sigma_inc, key X*X + Y*Y.
+// ------------------------------------------------------------------ binary64 definition
+struct ExactCentre {
+  double X, Y;
+};
+
+// Centre (lensum / count, round(inc) / count) normalised by Eq. 4, binary64.
+__device__ __forceinline__ ExactCentre exact_centre(const jabba_group& g, double sl, double si, double scl) {
+  I192 inc;
+  inc.w0 = g.inc[0];
+  inc.w1 = g.inc[1];
+  inc.w2 = g.inc[2];
+  const double cnt = (double)g.count;
+  const double c_len = __ddiv_rn((double)g.lensum, cnt);
+  const double c_inc = __ddiv_rn(i192_to_double(inc), cnt);
+  ExactCentre e;
+  e.X = __ddiv_rn(__dmul_rn(scl, c_len), sl);
+  e.Y = __ddiv_rn(c_inc, si);
+  return e;
+}
+
+__device__ __forceinline__ double exact_key(const ExactCentre& e) {
+  return __dadd_rn(__dmul_rn(e.X, e.X), __dmul_rn(e.Y, e.Y));
+}
+
+__device__ __forceinline__ bool exact_within_c(const ExactCentre& a, const ExactCentre& b, double a2) {
+  const double dx = __dsub_rn(b.X, a.X), dy = __dsub_rn(b.Y, a.Y);
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= a2;
+}
+
+struct MergeView {
+  const jabba_group* groups;
+  const int* rec;       // record of compact index c
+  const int* sidx;      // compact index at sorted position a
+  const float* sX;      // FP32 coordinates at sorted position a
+  const float* sY;
+  const double* sigma;  // binary64 sigma_len, sigma_inc
+  double scl, a2;
+  float a2lo, a2hi;
+};
+
+// 1 = within alpha, 0 = not, decided exactly when the FP32 interval straddles.
+__device__ __noinline__ bool exact_within_sorted(const MergeView& V, int a, int b) {
+  const double sl = V.sigma[0], si = V.sigma[1];
+  const ExactCentre ea = exact_centre(V.groups[V.rec[V.sidx[a]]], sl, si, V.scl);
+  const ExactCentre eb = exact_centre(V.groups[V.rec[V.sidx[b]]], sl, si, V.scl);
+  return exact_within_c(ea, eb, V.a2);
+}
+
+// FP32 filter: |X32 - X| <= 2^-20 |X32|, same for Y.
+__device__ __forceinline__ int filter_c(float xa, float ya, float xb, float yb, float a2lo, float a2hi) {
+  const float dx = fabsf(xb - xa), dy = fabsf(yb - ya);
+  const float ex = 0x1p-19f * (fabsf(xa) + fabsf(xb)) + 0x1p-126f;
+  const float ey = 0x1p-19f * (fabsf(ya) + fabsf(yb)) + 0x1p-126f;
+  const float hx = dx + ex, hy = dy + ey;
+  const float lx = fmaxf(dx - ex, 0.f), ly = fmaxf(dy - ey, 0.f);
+  const float hi = fmaf(hx, hx, hy * hy) * (1.0f + 0x1p-21f);
+  const float lo = fmaf(lx, lx, ly * ly) * (1.0f - 0x1p-21f);
+  if (hi < a2lo) return 1;
+  if (lo > a2hi) return 0;
+  return 2;
+}
+
+__device__ __forceinline__ bool within_sorted(const MergeView& V, int a, int b) {
+  const int f = filter_c(V.sX[a], V.sY[a], V.sX[b], V.sY[b], V.a2lo, V.a2hi);
+  if (f != 2) return f == 1;
+  return exact_within_sorted(V, a, b);
+}
+
+__device__ __forceinline__ bool maybe_within_sorted(const MergeView& V, int a, int b) {
+  return filter_c(V.sX[a], V.sY[a], V.sX[b], V.sY[b], V.a2lo, V.a2hi) != 0;
+}
+
 __device__ __forceinline__ long long clamp_groups(const long long* n_p, long long cap) {
   const long long g = *n_p;
   return g < cap ? g : cap;  // past capacity the records were not written (status already set)
 }
 
-__global__ void k_merge_prep(const jabba_group* groups, const long long* n_groups_p, long long cap,
-                             const long long* dom_group_off, const double* sigma, double scl, double* X, double* Y,
-                             unsigned long long* keys, int* vals, int* rec_of) {
-  const long long G = clamp_groups(n_groups_p, cap);
-  const double sl = sigma[0], si = sigma[1];
+// ------------------------------------------------------------------ 1. FP32 centres
+// flags[0]: use the sequential fallback; bounds: float min/max encoded as ordered ints.
+__device__ __forceinline__ int ord_of(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : (int)(0x80000000u - (unsigned)i) ;
+}
+__device__ __forceinline__ float of_ord(int o) {
+  return o >= 0 ? __int_as_float(o) : __int_as_float((int)(0x80000000u - (unsigned)o));
+}
+
+__global__ void k_mprep(const jabba_group* groups, const long long* n_p, long long cap, const long long* dom_group_off,
+                        const float* rinv, double scl, unsigned long long* keys, int* vals, int* rec_of, float* X32,
+                        float* Y32, int* bounds, const int* flags) {
+  if (flags[1]) return;
+  const long long G = clamp_groups(n_p, cap);
+  const float rl = rinv[0], ri = rinv[1], sc = (float)scl;
+  int mnx = 0x7FFFFFFF, mxx = -0x7FFFFFFF, mny = 0x7FFFFFFF, mxy = -0x7FFFFFFF;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < G; r += (long long)gridDim.x * blockDim.x) {
     const jabba_group g = groups[r];
     const long long c = dom_group_off[g.domain] + g.local_id;
-    I192 inc;
-    inc.w0 = g.inc[0];
-    inc.w1 = g.inc[1];
-    inc.w2 = g.inc[2];
-    const double cnt = (double)g.count;
-    const double c_len = __ddiv_rn((double)g.lensum, cnt);
-    const double c_inc = __ddiv_rn(i192_to_double(inc), cnt);
-    const double x = __ddiv_rn(__dmul_rn(scl, c_len), sl);
-    const double y = __ddiv_rn(c_inc, si);
-    const double key = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
-    X[c] = x;
-    Y[c] = y;
-    keys[c] = (unsigned long long)__double_as_longlong(key);  // key >= 0: bit order = value order
+    const float cnt = (float)g.count;
+    const float clen = __fdiv_rn(__ll2float_rn(g.lensum), cnt);
+    const float x = (sc * clen) * rl;
+    // FP32 image of the 192-bit increment sum (truncated to 24 bits), 2^-64 units
+    I192 v;
+    v.w0 = g.inc[0];
+    v.w1 = g.inc[1];
+    v.w2 = g.inc[2];
+    const bool neg = (long long)v.w2 < 0;
+    if (neg) {
+      v.w0 = ~v.w0; v.w1 = ~v.w1; v.w2 = ~v.w2;
+      add192(v, 1, 0, 0);
+    }
+    int top;
+    if (v.w2) top = 128 + 63 - __clzll((long long)v.w2);
+    else if (v.w1) top = 64 + 63 - __clzll((long long)v.w1);
+    else if (v.w0) top = 63 - __clzll((long long)v.w0);
+    else top = -1;
+    float incf = 0.f;
+    if (top >= 0) {
+      const int lo = top > 23 ? top - 23 : 0;
+      const u64 sig = shr192_lo(v.w0, v.w1, v.w2, lo);
+      incf = ldexpf((float)(unsigned)sig, lo - 64);
+    }
+    if (neg) incf = -incf;
+    const float y = __fdiv_rn(incf, cnt) * ri;
+    X32[c] = x;
+    Y32[c] = y;
+    keys[c] = (unsigned long long)__float_as_uint(fmaf(x, x, y * y));
     vals[c] = (int)c;
     rec_of[c] = (int)r;
+    mnx = min(mnx, ord_of(x));
+    mxx = max(mxx, ord_of(x));
+    mny = min(mny, ord_of(y));
+    mxy = max(mxy, ord_of(y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mnx = min(mnx, __shfl_xor_sync(0xFFFFFFFFu, mnx, o));
+    mxx = max(mxx, __shfl_xor_sync(0xFFFFFFFFu, mxx, o));
+    mny = min(mny, __shfl_xor_sync(0xFFFFFFFFu, mny, o));
+    mxy = max(mxy, __shfl_xor_sync(0xFFFFFFFFu, mxy, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&bounds[0], mnx);
+    atomicMax(&bounds[1], mxx);
+    atomicMin(&bounds[2], mny);
+    atomicMax(&bounds[3], mxy);
   }
 }
 
 // ------------------------------------------------------------------ LSD radix sort (stable)
-// 8-bit digits; per pass: tile histograms, one scan over (digit, tile), and a
-// stable scatter in which each warp owns a contiguous run of its tile.
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -51,9 +184,9 @@ constexpr int kSortWarps = kSortThreads / 32;
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long long* keys, const long long* n_p,
                                                             long long cap, int shift, unsigned* hist,
-                                                            long long n_tiles) {
+                                                            long long n_tiles, const int* flags) {
   __shared__ unsigned h[256];
-  const long long n = clamp_groups(n_p, cap);
+  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * kSortTile;
@@ -68,9 +201,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned long long* kin, const int* vin,
                                                                unsigned long long* kout, int* vout,
                                                                const long long* n_p, long long cap, int shift,
-                                                               const long long* offs, long long n_tiles) {
+                                                               const long long* offs, long long n_tiles,
+                                                               const int* flags) {
   __shared__ unsigned wh[kSortWarps][256];
-  const long long n = clamp_groups(n_p, cap);
+  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long base = (long long)blockIdx.x * kSortTile;
   const int per_warp = kSortTile / kSortWarps;
@@ -82,7 +216,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned l
     if (k < n) atomicAdd(&wh[warp][(kin[k] >> shift) & 255u], 1u);
   }
   __syncthreads();
-  // exclusive prefix over warps per digit, plus the global offset of (digit, tile)
   for (int dgt = threadIdx.x; dgt < 256; dgt += blockDim.x) {
     unsigned run = (unsigned)offs[(long long)dgt * n_tiles + blockIdx.x];
     for (int w = 0; w < kSortWarps; ++w) {
@@ -117,35 +250,401 @@ __global__ void k_u32_to_i64(const unsigned* in, long long n, long long* out) {
     out[i] = in[i];
 }
 
-// ------------------------------------------------------------------ greedy (one CTA)
-// Items in sorted order; each unassigned item starts a global group and
-// every later unassigned item within alpha joins it (Sec. 3.2), scanning
-// until the conservative key-gap threshold (Sec. 5 pruning).
-__device__ __forceinline__ double dist2m(double xa, double ya, double xb, double yb) {
-  const double dx = __dsub_rn(xb, xa), dy = __dsub_rn(yb, ya);
-  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+// Stable sort of (keys, vals) by the low `bits` bits of the keys; the result
+// ends in the buffers returned through kres/vres.
+static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, const long long* n_p,
+                       long long cap, int bits, Scratch& ws, long long* offs, unsigned long long** kres, int** vres,
+                       const int* flags, cudaStream_t st) {
+  const long long n_tiles = (cap + kSortTile - 1) / kSortTile;
+  const unsigned grid = (unsigned)(ws.num_sms * 8);
+  unsigned long long* kin = k0;
+  unsigned long long* kout = k1;
+  int* vin = v0;
+  int* vout = v1;
+  for (int shift = 0; shift < bits && n_tiles > 0; shift += 8) {
+    k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n_p, cap, shift, ws.m_hist, n_tiles, flags);
+    k_u32_to_i64<<<grid, 256, 0, st>>>(ws.m_hist, 256 * n_tiles, offs + 256 * n_tiles + 1);
+    exclusive_scan<long long>(offs + 256 * n_tiles + 1, 256 * n_tiles, offs, ws.scan_tiles, st);
+    k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_p, cap, shift, offs, n_tiles, flags);
+    unsigned long long* tk = kin; kin = kout; kout = tk;
+    int* tv = vin; vin = vout; vout = tv;
+  }
+  *kres = kin;
+  *vres = vin;
 }
 
-__global__ void __launch_bounds__(1024) k_merge_greedy(const unsigned long long* skeys, const int* sidx,
-                                                      const double* X, const double* Y, const long long* n_p,
-                                                      long long cap, double alpha, int* label_c, long long* k_out,
-                                                      long long dict_capacity, unsigned* status) {
+// ------------------------------------------------------------------ 2. exact order
+__device__ __forceinline__ bool keys_overlap(unsigned k0, unsigned k1) {
+  // intervals key32 (1 +- 2^-18) overlap (with FP32 rounding slack)
+  return __uint_as_float(k1) * (1.0f - 0x1p-18f) <= __uint_as_float(k0) * (1.0f + 0x1p-18f) * (1.0f + 0x1p-22f);
+}
+
+// Runs of overlapping neighbours, marked from the untouched sorted keys:
+// link[a] = 1 when the intervals of a and a + 1 overlap.
+__global__ void k_mlinks(const unsigned long long* skey, const long long* n_p, long long cap, const int* flags,
+                         int* link) {
+  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < cap; a += (long long)gridDim.x * blockDim.x)
+    link[a] = (a + 1 < n && keys_overlap((unsigned)skey[a], (unsigned)skey[a + 1])) ? 1 : 0;
+}
+
+// Each run is re-sorted by binary64 keys (ties by compact index) by the
+// thread that owns its first element; runs are read from link[], never from
+// keys another thread may be moving.
+__global__ void k_mfix(unsigned long long* skey, int* sidx, const int* link, const long long* n_p, long long cap,
+                       const jabba_group* groups, const int* rec_of, const double* sigma, double scl,
+                       const int* flags) {
+  if (flags[1]) return;
+  const long long n = clamp_groups(n_p, cap);
+  const double sl = sigma[0], si = sigma[1];
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a + 1 < n; a += (long long)gridDim.x * blockDim.x) {
+    if (!link[a] || (a > 0 && link[a - 1])) continue;  // not the head of a run
+    long long b = a + 1;
+    while (b + 1 < n && link[b]) ++b;
+    for (long long u = a + 1; u <= b; ++u) {
+      const int cu = sidx[u];
+      const unsigned long long ku32 = skey[u];
+      const double ku = exact_key(exact_centre(groups[rec_of[cu]], sl, si, scl));
+      long long v = u - 1;
+      while (v >= a) {
+        const int cv = sidx[v];
+        const double kv = exact_key(exact_centre(groups[rec_of[cv]], sl, si, scl));
+        if (kv > ku || (kv == ku && cv > cu)) {
+          sidx[v + 1] = cv;
+          skey[v + 1] = skey[v];
+          --v;
+        } else {
+          break;
+        }
+      }
+      sidx[v + 1] = cu;
+      skey[v + 1] = ku32;
+    }
+  }
+}
+
+// Sorted-order copies of the coordinates, the cell of each item, and checks
+// that the grid is usable (else flags[0] = 1: sequential fallback).
+struct GridGeom {
+  float x0, y0, inv_h;
+  int ncx, ncy;
+};
+
+__global__ void k_mgeom(const int* bounds, double alpha, long long cap_cells, GridGeom* geom, int* flags,
+                        const long long* n_p, long long cap) {
+  const long long n = clamp_groups(n_p, cap);
+  const float xmin = of_ord(bounds[0]), xmax = of_ord(bounds[1]);
+  const float ymin = of_ord(bounds[2]), ymax = of_ord(bounds[3]);
+  const double h = alpha * 0.5 * (1.0 + 0x1p-7);
+  GridGeom g;
+  g.x0 = xmin;
+  g.y0 = ymin;
+  g.inv_h = (float)(1.0 / h);
+  const double nx = n > 0 ? floor(((double)xmax - xmin) / h) + 1 : 1;
+  const double ny = n > 0 ? floor(((double)ymax - ymin) / h) + 1 : 1;
+  const double maxc = fmax(fmax(fabs((double)xmin), fabs((double)xmax)), fmax(fabs((double)ymin), fabs((double)ymax)));
+  int fb = 0;
+  if (!(alpha > 0.0) || !(nx * ny <= (double)cap_cells) || !(maxc * 0x1p-19 <= h * 0x1p-8) || !(h > 1e-30)) fb = 1;
+  g.ncx = fb ? 1 : (int)nx;
+  g.ncy = fb ? 1 : (int)ny;
+  *geom = g;
+  flags[0] = flags[1] ? 0 : fb;
+}
+
+__device__ __forceinline__ int cell_of(const GridGeom& g, float x, float y) {
+  int cx = (int)floorf((x - g.x0) * g.inv_h);
+  int cy = (int)floorf((y - g.y0) * g.inv_h);
+  cx = min(max(cx, 0), g.ncx - 1);
+  cy = min(max(cy, 0), g.ncy - 1);
+  return cy * g.ncx + cx;
+}
+
+__global__ void k_msorted(const int* sidx, const float* X32, const float* Y32, const long long* n_p, long long cap,
+                          const GridGeom* geom, const int* flags, float* sX, float* sY, int* rank_of,
+                          unsigned long long* ckey, int* cval) {
+  if (flags[1]) return;
+  const long long n = clamp_groups(n_p, cap);
+  const GridGeom g = *geom;
+  const bool fb = flags[0] != 0;
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
+    const int c = sidx[a];
+    const float x = X32[c], y = Y32[c];
+    sX[a] = x;
+    sY[a] = y;
+    rank_of[c] = (int)a;
+    ckey[a] = fb ? 0ull : (unsigned long long)cell_of(g, x, y);
+    cval[a] = (int)a;
+  }
+}
+
+// Cell table: cells in id order; cell_of_id[id] = cell index or -1.
+__global__ void k_mcell_heads(const unsigned long long* ckey_sorted, const long long* n_p, long long cap,
+                              const int* flags, int* head) {
+  const long long n = clamp_groups(n_p, cap);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cap; t += (long long)gridDim.x * blockDim.x)
+    head[t] = t < n && flags[0] == 0 && flags[1] == 0 && (t == 0 || ckey_sorted[t] != ckey_sorted[t - 1]) ? 1 : 0;
+}
+
+__global__ void k_mcell_fill(const unsigned long long* ckey_sorted, const int* head, const long long* head_off,
+                             const long long* n_p, long long cap, int* cell_beg, int* cell_end, int* cell_id,
+                             int* cell_of_id, unsigned long long* state) {
+  const long long n = clamp_groups(n_p, cap);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    if (!head[t]) continue;
+    const long long j = head_off[t];
+    cell_beg[j] = (int)t;
+    cell_id[j] = (int)ckey_sorted[t];
+    cell_of_id[ckey_sorted[t]] = (int)j;
+    state[j] = ((unsigned long long)(unsigned)t << 32) | 0xFFFFFFFFull;  // ptr = t, undecided
+  }
+}
+
+__global__ void k_mcell_end(const int* cell_beg, const long long* n_cells_p, const long long* n_p, long long cap,
+                            int* cell_end) {
+  const long long nc = *n_cells_p;
+  const long long n = clamp_groups(n_p, cap);
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += (long long)gridDim.x * blockDim.x)
+    cell_end[j] = j + 1 < nc ? cell_beg[j + 1] : (int)n;
+}
+
+__global__ void k_clear_i32(int* p, long long n, int v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// ------------------------------------------------------------------ 4. rounds
+// state[j] = (ptr << 32) | s, s = 0xFFFFFFFF undecided, 0xFFFFFFFE no start,
+// else the sorted position of the cell's start.
+constexpr unsigned kUndecided = 0xFFFFFFFFu;
+constexpr unsigned kNoStart = 0xFFFFFFFEu;
+
+struct RoundArgs {
+  MergeView V;
+  const int* cord;          // item (sorted position) at cell-order index t
+  const int* cell_beg;
+  const int* cell_end;
+  const int* cell_id;
+  const int* cell_of_id;
+  unsigned long long* state;
+  unsigned char* cov;       // [t] item covered by a start (not a start itself)
+  int* new_list;            // [2][n_cells] cells that created a start this round
+  unsigned* counters;       // [0..1] new-start counts, [2..3] undecided counts (by round parity)
+  const long long* n_cells_p;
+  const GridGeom* geom;
+  const int* flags;
+  unsigned* bar;            // [0] arrival counter, [1] generation
+  unsigned* status;
+  unsigned max_rounds;
+};
+
+__device__ __forceinline__ unsigned long long ld_state(const unsigned long long* p) {
+  return *((volatile const unsigned long long*)p);
+}
+
+// Bounded grid-wide barrier for a co-resident (cooperative) grid.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      unsigned spins = 0;
+      while (*gen == g) {
+        if (++spins > kSpinLimit) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+constexpr int kCoverChunk = 1024;  // items of one neighbour cell per phase-B work unit
+
+// Rounds of the cell greedy.  Phase A (a warp per undecided cell): skip the
+// cell's covered items; its first uncovered item p becomes the cell's start
+// unless an uncovered item of an undecided neighbouring cell precedes p and
+// may lie within alpha (it could still become a start covering p).  Phase B
+// (warps over (new start, neighbouring cell, chunk)): every later item within
+// alpha of a new start is marked covered (the start's own cell entirely: any
+// two of its items are within alpha).  Items are covered only by true starts,
+// and a start is declared only when no undecided earlier item can cover it,
+// so the starts are exactly those of the sequential greedy.
+__global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
+  if (R.flags[0] || R.flags[1]) return;
+  const long long n_cells = *R.n_cells_p;
+  const GridGeom g = *R.geom;
+  const unsigned nblocks = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned round = 0; round < R.max_rounds; ++round) {
+    const int par = round & 1;
+    int* list = R.new_list + (size_t)par * (size_t)(n_cells > 0 ? n_cells : 1);
+    // ---- phase A
+    unsigned my_und = 0;
+    for (long long j = warp_g; j < n_cells; j += n_warps) {
+      const unsigned long long st = ld_state(&R.state[j]);
+      if ((unsigned)st != kUndecided) continue;
+      int t = (int)(st >> 32);
+      const int end = R.cell_end[j];
+      for (;;) {  // first uncovered item
+        const int u = t + lane;
+        const bool fr = u < end && !__ldcg(&R.cov[u]);  // L2: flags written by other SMs last round
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, fr);
+        if (m) { t += __ffs(m) - 1; break; }
+        t += 32;
+        if (t >= end) { t = end; break; }
+      }
+      unsigned result = kUndecided;
+      if (t >= end) {
+        result = kNoStart;
+      } else {
+        const int p = R.cord[t];
+        const int id = R.cell_id[j];
+        const int cx = id % g.ncx, cy = id / g.ncx;
+        bool blocked = false;
+        for (int k = 0; k < 25 && !blocked; ++k) {
+          const int dx = k % 5 - 2, dy = k / 5 - 2;
+          if (dx == 0 && dy == 0) continue;
+          const int xx = cx + dx, yy = cy + dy;
+          if (xx < 0 || xx >= g.ncx || yy < 0 || yy >= g.ncy) continue;
+          const int q = R.cell_of_id[yy * g.ncx + xx];
+          if (q < 0) continue;
+          const unsigned long long sq = ld_state(&R.state[q]);
+          if ((unsigned)sq != kUndecided) continue;
+          const int qe = R.cell_end[q];
+          for (int u0 = (int)(sq >> 32); u0 < qe; u0 += 32) {
+            const int u = u0 + lane;
+            bool past = true, hit = false;
+            if (u < qe) {
+              const int r = R.cord[u];
+              past = r >= p;
+              if (!past && !__ldcg(&R.cov[u]) && maybe_within_sorted(R.V, r, p)) hit = true;
+            }
+            if (__any_sync(0xFFFFFFFFu, hit)) { blocked = true; break; }
+            if (__any_sync(0xFFFFFFFFu, past)) break;
+          }
+        }
+        if (!blocked) result = (unsigned)p;
+      }
+      if (lane == 0) {
+        const unsigned long long ns = ((unsigned long long)(unsigned)t << 32) | result;
+        if (ns != st) atomicExch(&R.state[j], ns);
+        if (result < kNoStart) list[atomicAdd(&R.counters[par], 1u)] = (int)j;
+        if (result == kUndecided) ++my_und;
+      }
+    }
+    if (lane == 0 && my_und) atomicAdd(&R.counters[2 + par], my_und);
+    if (!grid_barrier(R.bar, nblocks, R.status)) return;
+    // ---- phase B
+    const unsigned n_new = *((volatile unsigned*)&R.counters[par]);
+    const unsigned und = *((volatile unsigned*)&R.counters[2 + par]);
+    // work units: (new start, neighbour k, chunk c); chunk counts bounded per cell
+    for (long long w = warp_g; w < (long long)n_new * 25 * 64; w += n_warps) {
+      const long long si = w / (25 * 64);
+      const int k = (int)((w / 64) % 25);
+      const int c = (int)(w % 64);
+      const int j = __ldcg(&list[si]);
+      const unsigned sp = (unsigned)ld_state(&R.state[j]);
+      const int id = R.cell_id[j];
+      const int cx = id % g.ncx + k % 5 - 2, cy = id / g.ncx + k / 5 - 2;
+      if (cx < 0 || cx >= g.ncx || cy < 0 || cy >= g.ncy) continue;
+      const int q = R.cell_of_id[cy * g.ncx + cx];
+      if (q < 0) continue;
+      const int qb = R.cell_beg[q], qe = R.cell_end[q];
+      const int span = qe - qb;
+      const int per = ((span + 63) / 64 + kCoverChunk - 1) / kCoverChunk * kCoverChunk;  // chunk length, multiple of 1024
+      const int lo = qb + c * (per > 0 ? per : kCoverChunk);
+      const int hi = min(qe, lo + (per > 0 ? per : kCoverChunk));
+      for (int u = lo + lane; u < hi; u += 32) {
+        const int r = R.cord[u];
+        if (r <= (int)sp || __ldcg(&R.cov[u])) continue;
+        if (q == j || within_sorted(R.V, (int)sp, r)) R.cov[u] = 1;
+      }
+    }
+    if (!grid_barrier(R.bar, nblocks, R.status)) return;
+    if (und == 0) return;
+    // the other parity's counters are reset here; they are next used after the next barrier
+    if (warp_g == 0 && lane == 0) {
+      R.counters[par ^ 1] = 0;
+      R.counters[2 + (par ^ 1)] = 0;
+    }
+  }
+  if (warp_g == 0 && lane == 0) set_status(R.status, JABBA_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------------ 5. labels
+// lab[a] = sorted position of the earliest start within alpha (a itself for a start).
+__global__ void __launch_bounds__(256) k_mlabel(MergeView V, const unsigned long long* ckey, const int* cell_of_id,
+                         const unsigned long long* state, const GridGeom* geom, const int* flags,
+                         const long long* n_p, long long cap, int* lab, int* is_start) {
+  if (flags[0] || flags[1]) return;
+  const long long n = clamp_groups(n_p, cap);
+  const GridGeom g = *geom;
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
+    const int id = cell_of(g, V.sX[a], V.sY[a]);
+    const int cx = id % g.ncx, cy = id / g.ncx;
+    int best = 0x7FFFFFFF;
+    for (int dy = -2; dy <= 2; ++dy) {
+      const int yy = cy + dy;
+      if (yy < 0 || yy >= g.ncy) continue;
+      for (int dx = -2; dx <= 2; ++dx) {
+        const int xx = cx + dx;
+        if (xx < 0 || xx >= g.ncx) continue;
+        const int q = cell_of_id[yy * g.ncx + xx];
+        if (q < 0) continue;
+        const unsigned s = (unsigned)state[q];
+        if (s >= kNoStart || (int)s > (int)a || (int)s >= best) continue;
+        if ((int)s == (int)a || within_sorted(V, (int)s, (int)a)) best = (int)s;
+      }
+    }
+    lab[a] = best;
+    is_start[a] = best == (int)a ? 1 : 0;
+    (void)ckey;
+  }
+}
+
+// ------------------------------------------------------------------ fallback: sequential greedy (binary64)
+__global__ void k_mexact_prep(const jabba_group* groups, const int* rec_of, const int* sidx, const long long* n_p,
+                              long long cap, const double* sigma, double scl, const int* flags, double* eX,
+                              double* eY, double* ekey) {
+  if (!flags[0] || flags[1]) return;
+  const long long n = clamp_groups(n_p, cap);
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
+    const ExactCentre e = exact_centre(groups[rec_of[sidx[a]]], sigma[0], sigma[1], scl);
+    eX[a] = e.X;
+    eY[a] = e.Y;
+    ekey[a] = exact_key(e);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_mexact_greedy(const double* eX, const double* eY, const double* ekey,
+                                                       const long long* n_p, long long cap, double alpha,
+                                                       const int* flags, int* lab, int* is_start) {
+  if (!flags[0] || flags[1]) return;
   __shared__ int s_next;
   __shared__ int s_stop;
   const long long n = clamp_groups(n_p, cap);
   const int tid = threadIdx.x, nt = blockDim.x;
   const double a2 = __dmul_rn(alpha, alpha);
-  for (long long i = tid; i < n; i += nt) label_c[i] = -1;
+  for (long long i = tid; i < n; i += nt) lab[i] = -1;
   __syncthreads();
   long long a = 0;
-  int g = 0;
   for (;;) {
-    // next unassigned sorted entry at or after a
     for (;;) {
       if (tid == 0) s_next = 0x7FFFFFFF;
       __syncthreads();
       const long long aa = a + tid;
-      if (aa < n && label_c[sidx[aa]] < 0) atomicMin(&s_next, tid);
+      if (aa < n && lab[aa] < 0) atomicMin(&s_next, tid);
       __syncthreads();
       const int nx = s_next;
       __syncthreads();
@@ -154,23 +653,20 @@ __global__ void __launch_bounds__(1024) k_merge_greedy(const unsigned long long*
       if (a >= n) break;
     }
     if (a >= n) break;
-    const int ci = sidx[a];
-    const double xi = X[ci], yi = Y[ci];
-    const double ks = __longlong_as_double((long long)skeys[a]);
-    const double r = __dadd_rn(__dsqrt_rn(ks), alpha);
+    const double xi = eX[a], yi = eY[a];
+    const double r = __dadd_rn(__dsqrt_rn(ekey[a]), alpha);
     const double T = __dmul_rn(__dmul_rn(r, r), 1.0 + 0x1p-30);
-    if (tid == 0) label_c[ci] = g;
+    if (tid == 0) { lab[a] = (int)a; is_start[a] = 1; }
     for (long long b = a + 1; b < n; b += nt) {
       if (tid == 0) s_stop = 0;
       __syncthreads();
       const long long bb = b + tid;
       if (bb < n) {
-        const double kb = __longlong_as_double((long long)skeys[bb]);
-        if (kb > T) {
+        if (ekey[bb] > T) {
           s_stop = 1;
-        } else {
-          const int cj = sidx[bb];
-          if (label_c[cj] < 0 && dist2m(xi, yi, X[cj], Y[cj]) <= a2) label_c[cj] = g;
+        } else if (lab[bb] < 0) {
+          const double dx = __dsub_rn(eX[bb], xi), dy = __dsub_rn(eY[bb], yi);
+          if (__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= a2) lab[bb] = (int)a;
         }
       } else {
         s_stop = 1;
@@ -180,25 +676,46 @@ __global__ void __launch_bounds__(1024) k_merge_greedy(const unsigned long long*
       __syncthreads();
       if (stop) break;
     }
-    ++g;
     ++a;
-  }
-  if (tid == 0) {
-    *k_out = g;
-    if (g > dict_capacity) set_status(status, JABBA_ERR_CAPACITY);
   }
 }
 
-// ------------------------------------------------------------------ dictionary
-__global__ void k_dict_accumulate(const jabba_group* groups, const int* rec_of, const int* label_c,
-                                  const long long* n_p, long long cap, const long long* k_p,
-                                  long long dict_capacity, int* l2g, long long* acc) {
+// ------------------------------------------------------------------ ids, map, dictionary
+__global__ void k_mids(const int* lab, const long long* start_off, const int* sidx, const long long* n_p, long long cap,
+                       long long dict_capacity, int* l2g, int* gid_c, long long* k_out, unsigned* status,
+                       const int* flags) {
+  if (flags[1]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *k_out = 0;
+    return;
+  }
+  const long long n = clamp_groups(n_p, cap);
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
+    int la = lab[a];
+    if (la < 0 || la >= n) {  // unresolved (a bounded wait gave up): status is already set
+      set_status(status, JABBA_ERR_TIMEOUT);
+      la = 0;
+    }
+    const int gid = (int)start_off[la];
+    const int c = sidx[a];
+    l2g[c] = gid;
+    gid_c[c] = gid;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long K = start_off[n];
+    *k_out = K;
+    if (K > dict_capacity) set_status(status, JABBA_ERR_CAPACITY);
+  }
+}
+
+__global__ void k_dict_accumulate(const jabba_group* groups, const int* rec_of, const int* gid_c, const long long* n_p,
+                                  long long cap, const long long* k_p, long long dict_capacity, long long* acc,
+                                  const int* flags) {
+  if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
   const long long K = *k_p;
+  if (K > dict_capacity) return;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < G; c += (long long)gridDim.x * blockDim.x) {
-    const int gid = label_c[c];
-    l2g[c] = gid;
-    if (K > dict_capacity) continue;
+    const int gid = gid_c[c];
     const jabba_group g = groups[rec_of[c]];
     long long* a = acc + (long long)gid * 8;
     atomicAdd((unsigned long long*)&a[0], (unsigned long long)g.count);
@@ -229,34 +746,127 @@ __global__ void k_dict_finalize(const long long* acc, const long long* k_p, long
   }
 }
 
+__global__ void k_minit(int* bounds, unsigned* bar, int* flags, const unsigned* status, const long long* n_p,
+                        long long cap) {
+  for (int i = 3; i < 8; ++i) bar[i] = 0;
+  flags[0] = 0;
+  flags[1] = (*status != 0u || *n_p > cap) ? 1 : 0;  // earlier error: leave the merge outputs alone
+  bounds[0] = 0x7FFFFFFF;
+  bounds[1] = -0x7FFFFFFF;
+  bounds[2] = 0x7FFFFFFF;
+  bounds[3] = -0x7FFFFFFF;
+  bar[0] = 0;
+  bar[1] = 0;
+  bar[2] = 0;
+}
+
+__global__ void k_mrinv(const double* sigma, float* rinv) {
+  rinv[0] = __double2float_rn(__ddiv_rn(1.0, sigma[0]));
+  rinv[1] = __double2float_rn(__ddiv_rn(1.0, sigma[1]));
+}
+
+static float rdown(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = nextafterf(f, 0.0f);
+  return f;
+}
+static float rup(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = nextafterf(f, INFINITY);
+  return f;
+}
+
 void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
                   const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
                   double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,
                   Scratch& ws, unsigned* status, cudaStream_t st) {
   const long long cap = group_capacity;
   const unsigned grid = (unsigned)(ws.num_sms * 8);
-  k_merge_prep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, sigma, scl, ws.m_X, ws.m_Y, ws.m_k0,
-                                      ws.m_v0, ws.m_rec);
-  // radix sort over the capacity-sized tiling; tiles past n do nothing
-  const long long n_tiles = (cap + kSortTile - 1) / kSortTile;
+  MergeBufs& B = ws.mb;
   long long* offs = (long long*)ws.d_acc;  // reused before the dictionary accumulation
-  unsigned long long* kin = ws.m_k0;
-  unsigned long long* kout = ws.m_k1;
-  int* vin = ws.m_v0;
-  int* vout = ws.m_v1;
-  for (int pass = 0; pass < 8 && n_tiles > 0; ++pass) {
-    const int shift = pass * 8;
-    k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n_groups, cap, shift, ws.m_hist, n_tiles);
-    k_u32_to_i64<<<grid, 256, 0, st>>>(ws.m_hist, 256 * n_tiles, offs + 256 * n_tiles + 1);
-    exclusive_scan<long long>(offs + 256 * n_tiles + 1, 256 * n_tiles, offs, ws.scan_tiles, st);
-    k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_groups, cap, shift, offs, n_tiles);
-    unsigned long long* tk = kin; kin = kout; kout = tk;
-    int* tv = vin; vin = vout; vout = tv;
+  k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.flags, status, n_groups, cap);
+  k_mrinv<<<1, 1, 0, st>>>(sigma, B.rinv);
+  k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, B.rinv, scl, ws.m_k0, ws.m_v0, ws.m_rec,
+                                ws.m_X32, ws.m_Y32, B.bounds, B.flags);
+  unsigned long long* skey;
+  int* sidx;
+  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 32, ws, offs, &skey, &sidx, B.flags, st);
+  k_mlinks<<<grid, 256, 0, st>>>(skey, n_groups, cap, B.flags, B.head);
+  k_mfix<<<grid, 256, 0, st>>>(skey, sidx, B.head, n_groups, cap, groups, ws.m_rec, sigma, scl, B.flags);
+  k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
+  // the cell sort ping-pongs in the buffers the key sort left free
+  unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
+  int* cv0 = sidx == ws.m_v0 ? ws.m_v1 : ws.m_v0;
+  k_msorted<<<grid, 256, 0, st>>>(sidx, ws.m_X32, ws.m_Y32, n_groups, cap, B.geom, B.flags, B.sX, B.sY, B.rank,
+                                  ck0, cv0);
+  unsigned long long* ckey;
+  int* cord;
+  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 32, ws, offs, &ckey, &cord, B.flags, st);
+  k_mcell_heads<<<grid, 256, 0, st>>>(ckey, n_groups, cap, B.flags, B.head);
+  exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
+  k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
+  cudaMemsetAsync(B.cov, 0, (size_t)(cap > 0 ? cap : 1), st);
+  k_mcell_fill<<<grid, 256, 0, st>>>(ckey, B.head, B.head_off, n_groups, cap, B.cell_beg, B.cell_end, B.cell_id,
+                                     B.cell_of_id, B.state);
+  k_mcell_end<<<grid, 256, 0, st>>>(B.cell_beg, B.head_off + cap, n_groups, cap, B.cell_end);
+  MergeView V;
+  V.groups = groups;
+  V.rec = ws.m_rec;
+  V.sidx = sidx;
+  V.sX = B.sX;
+  V.sY = B.sY;
+  V.sigma = sigma;
+  V.scl = scl;
+  V.a2 = alpha * alpha;
+  V.a2lo = rdown(V.a2 * (1.0 - 0x1p-20));
+  V.a2hi = rup(V.a2 * (1.0 + 0x1p-20));
+  RoundArgs R;
+  R.V = V;
+  R.cord = cord;
+  R.cell_beg = B.cell_beg;
+  R.cell_end = B.cell_end;
+  R.cell_id = B.cell_id;
+  R.cell_of_id = B.cell_of_id;
+  R.state = B.state;
+  R.cov = (unsigned char*)B.cov;
+  R.new_list = B.new_list;
+  R.counters = B.bar + 4;
+  R.n_cells_p = B.head_off + cap;
+  R.geom = B.geom;
+  R.flags = B.flags;
+  R.bar = B.bar;
+  R.status = status;
+  R.max_rounds = 1u << 22;
+  {
+    // cooperative launch: every block resident, so the bounded grid barrier can complete
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_mrounds, 256, 0);
+      if (blocks_per_sm < 1) blocks_per_sm = 1;
+      if (blocks_per_sm > 4) blocks_per_sm = 4;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ws.num_sms * blocks_per_sm));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_mrounds, R);
   }
-  k_merge_greedy<<<1, 1024, 0, st>>>(kin, vin, ws.m_X, ws.m_Y, n_groups, cap, alpha, ws.m_label, k, dict_capacity,
-                                     status);
-  cudaMemsetAsync(ws.d_acc, 0, sizeof(long long) * 8 * (size_t)cap, st);
-  k_dict_accumulate<<<grid, 256, 0, st>>>(groups, ws.m_rec, ws.m_label, n_groups, cap, k, dict_capacity, l2g, ws.d_acc);
+  k_clear_i32<<<grid, 256, 0, st>>>(B.is_start, cap, 0);
+  k_mlabel<<<grid, 256, 0, st>>>(V, ckey, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab, B.is_start);
+  // sequential fallback (only acts when flags[0] is set)
+  k_mexact_prep<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, n_groups, cap, sigma, scl, B.flags, B.eX, B.eY, B.ekey);
+  k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, B.flags, B.lab, B.is_start);
+  exclusive_scan<int>(B.is_start, cap, B.start_off, ws.scan_tiles, st);
+  k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, n_groups, cap, dict_capacity, l2g, B.gid_c, k, status,
+                               B.flags);
+  cudaMemsetAsync(ws.d_acc, 0, sizeof(long long) * 8 * (size_t)(cap > 0 ? cap : 1), st);
+  k_dict_accumulate<<<grid, 256, 0, st>>>(groups, ws.m_rec, B.gid_c, n_groups, cap, k, dict_capacity, ws.d_acc, B.flags);
   k_dict_finalize<<<grid, 256, 0, st>>>(ws.d_acc, k, dict_capacity, dict_len, dict_inc, dict_count);
 }
 

@@ -107,3 +107,28 @@ def test_nonfinite_and_range_errors(C):
     # the context stays usable
     c = C.compress(torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda(), p, series_off_host=off)
     C.sync_status(where="compress")
+
+
+def test_duplicate_pieces_and_ties(C):
+    """Integer walks with steps in {-1, 0, 1}: many identical pieces and
+    centres, so keys tie exactly and the binary64 re-sort of overlapping key
+    runs decides the order (ties by position / compact index)."""
+    rng = np.random.default_rng(21)
+    lens = rng.integers(50, 3000, 60)
+    x = np.concatenate([np.cumsum(rng.integers(-1, 2, n)).astype(np.float64) for n in lens])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    for alpha in (0.05, 0.5):
+        cfg = dict(tol=0.5, alpha=alpha, scl=1.0, domain_mode=1, domain_value=128)
+        g, *_ = run_gpu(C, x, off, cfg)
+        r = run_oracle(x, off, cfg)
+        assert_parity(g, r)
+
+
+def test_merge_sequential_fallback(C):
+    """A length weight so large that the merge grid would need too many cells:
+    the merge runs its sequential binary64 greedy instead; same result."""
+    x, off, cfg = synth.make("small", max_series=6)
+    cfg = dict(cfg, scl=1e7)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert_parity(g, r)
