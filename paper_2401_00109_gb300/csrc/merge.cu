@@ -471,8 +471,10 @@ constexpr int kCoverChunk = 1024;  // items of one neighbour cell per phase-B wo
 
 // Rounds of the cell greedy.  Phase A (a warp per undecided cell): skip the
 // cell's covered items; its first uncovered item p becomes the cell's start
-// unless an uncovered item of an undecided neighbouring cell precedes p and
-// may lie within alpha (it could still become a start covering p).  Phase B
+// unless a neighbouring start that precedes p covers it (decided in this
+// round, so its coverage is not marked yet), or an uncovered item of an
+// undecided neighbouring cell precedes p and may lie within alpha (it could
+// still become a start covering p).  Phase B
 // (warps over (new start, neighbouring cell, chunk)): every later item within
 // alpha of a new start is marked covered (the start's own cell entirely: any
 // two of its items are within alpha).  Items are covered only by true starts,
@@ -520,7 +522,13 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
           const int q = R.cell_of_id[yy * g.ncx + xx];
           if (q < 0) continue;
           const unsigned long long sq = ld_state(&R.state[q]);
-          if ((unsigned)sq != kUndecided) continue;
+          const unsigned sv = (unsigned)sq;
+          if (sv < kNoStart) {
+            // a start decided this round has not marked its coverage yet
+            if ((int)sv < p && within_sorted(R.V, (int)sv, p)) blocked = true;
+            continue;
+          }
+          if (sv != kUndecided) continue;
           const int qe = R.cell_end[q];
           for (int u0 = (int)(sq >> 32); u0 < qe; u0 += 32) {
             const int u = u0 + lane;
