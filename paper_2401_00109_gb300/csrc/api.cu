@@ -67,6 +67,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     return p;
   };
   long long scan_n = scan_scratch_elems((S > D ? S : D) + 1);
+  if (scan_scratch_elems(pack_buckets() + 1) > scan_n) scan_n = scan_scratch_elems(pack_buckets() + 1);
   {
     const long long a = scan_scratch_elems(256 * ((G + 4095) / 4096) + 1), b = scan_scratch_elems(G + 1);
     if (a > scan_n) scan_n = a;
@@ -78,6 +79,9 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.series_c = (long long*)take(8 * (S + 1));
   w.scan_tiles = (long long*)take(8 * scan_n);
   w.counters = (unsigned*)take(64);
+  w.dom_order = (int*)take(4 * (D > 0 ? D : 1));
+  w.pack_hist = (int*)take(4 * pack_buckets());
+  w.pack_off = (long long*)take(8 * (pack_buckets() + 1));
   w.big = nullptr;
   w.arena = (unsigned*)take(4 * (size_t)local_arena_words(cap_len, loc_warps));
   w.xtab64 = (double*)take(8 * (cap_len + 1));
@@ -123,6 +127,9 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.state = (unsigned long long*)take(8 * G);
     B.cov = (unsigned char*)take(G > 0 ? G : 1);
     B.new_list = (int*)take(8 * (G > 0 ? G : 1));
+    B.chg_list = (int*)take(8 * (G > 0 ? G : 1));
+    B.eval_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
+    B.chg_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.lab = (int*)take(4 * G);
     B.is_start = (int*)take(4 * G);
     B.start_off = (long long*)take(8 * (G + 1));

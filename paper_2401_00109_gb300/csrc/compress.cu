@@ -104,6 +104,7 @@ struct CompressParams {
   const long long* dom_begin;
   const long long* dom_end;
   const long long* dom_slot_off;
+  const int* dom_order;  // domains, longest first
   long long n_domains;
   double tol2;        // tol * tol, binary64
   float tol_lo;       // tol (1 - 2^-18) rounded down
@@ -222,7 +223,7 @@ __device__ __forceinline__ int stage_chunk(const CompressParams& P, const LaneDo
   return off;
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParams P) {
   __shared__ __align__(16) double stage[kWarpsPerCta][kStages][32][kRow];
   __shared__ __align__(8) unsigned long long bars[kWarpsPerCta][kStages];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -241,7 +242,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P
     if (lane == 0) task = (long long)atomicAdd(P.task_counter, 1u);
     task = __shfl_sync(0xFFFFFFFFu, task, 0);
     if (task >= n_tasks) break;
-    const long long d = task * 32 + lane;
+    const long long dt = task * 32 + lane;
+    const long long d = dt < P.n_domains ? (long long)P.dom_order[dt] : P.n_domains;
     LaneDomain D;
     long long slot = 0;
     D.b = 0;
@@ -377,6 +379,75 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_compress(CompressParams P
   else if (amax >= (1054u << 20)) set_status(P.status, JABBA_ERR_RANGE);
 }
 
+// ------------------------------------------------------------------ domain packing
+// Domains are handed to warps longest first, 32 of similar length per task,
+// so that the lanes of a warp finish together and the longest tasks start
+// first.  Counting sort on length buckets of 64 intervals (descending).
+constexpr int kLenBuckets = 1 << 16;
+
+__device__ __forceinline__ int len_key(long long n_int) {
+  long long b = n_int >> 6;
+  if (b > kLenBuckets - 1) b = kLenBuckets - 1;
+  return kLenBuckets - 1 - (int)b;  // descending length
+}
+
+// Warp-aggregated atomic add on counters[key]; returns this lane's slot.
+__device__ __forceinline__ int agg_atomic(int* counters, int key, bool active) {
+  const int lane = threadIdx.x & 31;
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
+  int slot = 0;
+  if (active) {
+    const unsigned peers = __match_any_sync(act, key);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&counters[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    slot = base + rank;
+  }
+  return slot;
+}
+
+__global__ void k_dom_hist(const long long* dom_begin, const long long* dom_end, long long n_domains, int* hist) {
+  for (long long d0 = (long long)blockIdx.x * blockDim.x; d0 < n_domains; d0 += (long long)gridDim.x * blockDim.x) {
+    const long long d = d0 + threadIdx.x;
+    const bool v = d < n_domains;
+    const int key = v ? len_key(dom_end[d] - dom_begin[d]) : 0;
+    agg_atomic(hist, key, v);
+  }
+}
+
+__global__ void k_dom_cursor(const long long* off, int* cursor) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kLenBuckets; i += gridDim.x * blockDim.x)
+    cursor[i] = (int)off[i];
+}
+
+__global__ void k_dom_scatter(const long long* dom_begin, const long long* dom_end, long long n_domains, int* cursor,
+                              int* order) {
+  for (long long d0 = (long long)blockIdx.x * blockDim.x; d0 < n_domains; d0 += (long long)gridDim.x * blockDim.x) {
+    const long long d = d0 + threadIdx.x;
+    const bool v = d < n_domains;
+    const int key = v ? len_key(dom_end[d] - dom_begin[d]) : 0;
+    const int slot = agg_atomic(cursor, key, v);
+    if (v) order[slot] = (int)d;
+  }
+}
+
+void launch_pack_domains(const long long* dom_begin, const long long* dom_end, long long n_domains, Scratch& ws,
+                         cudaStream_t st) {
+  if (n_domains <= 0) return;
+  int* hist = ws.pack_hist;
+  long long* off = ws.pack_off;
+  cudaMemsetAsync(hist, 0, sizeof(int) * kLenBuckets, st);
+  const unsigned g = (unsigned)(ws.num_sms * 4);
+  k_dom_hist<<<g, 256, 0, st>>>(dom_begin, dom_end, n_domains, hist);
+  exclusive_scan<int>(hist, kLenBuckets, off, ws.scan_tiles, st);
+  k_dom_cursor<<<64, 256, 0, st>>>(off, hist);
+  k_dom_scatter<<<g, 256, 0, st>>>(dom_begin, dom_end, n_domains, hist, ws.dom_order);
+}
+
+long long pack_buckets() { return kLenBuckets; }
+
 // ------------------------------------------------------------------ increments + statistics
 // One warp per domain (grid-stride): turns the end values written by
 // k_compress into increments inc_j = x_{e_j} - x_{s_j} (binary64, full-warp
@@ -490,6 +561,7 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   P.dom_begin = dom_begin;
   P.dom_end = dom_end;
   P.dom_slot_off = dom_slot_off;
+  P.dom_order = ws.dom_order;
   P.n_domains = n_domains;
   P.tol2 = tol * tol;
   {
@@ -512,6 +584,7 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   long long ctas = (long long)ws.num_sms * 3;
   const long long need = (n_tasks + kWarpsPerCta - 1) / kWarpsPerCta;
   if (ctas > need) ctas = need;
+  launch_pack_domains(dom_begin, dom_end, n_domains, ws, st);
   mark(mk.a0, st);
   if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, 0, st>>>(P);
   mark(mk.a1, st);

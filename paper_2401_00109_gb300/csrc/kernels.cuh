@@ -27,6 +27,9 @@ struct MergeBufs {
   unsigned long long* state = nullptr;  // [cap]
   unsigned char* cov = nullptr;      // [cap] covered flags (cell order)
   int* new_list = nullptr;           // [2 * cap] cells that created a start (per round parity)
+  int* chg_list = nullptr;           // [2 * cap] cells that changed (per round parity)
+  unsigned* eval_stamp = nullptr;    // [cap]
+  unsigned* chg_stamp = nullptr;     // [cap]
   int* lab = nullptr;                // [cap]
   int* is_start = nullptr;           // [cap]
   long long* start_off = nullptr;    // [cap + 1]
@@ -46,6 +49,9 @@ struct Scratch {
   long long* series_c = nullptr;
   long long* scan_tiles = nullptr;
   unsigned* counters = nullptr;   // [16]: task counters, diagnostics
+  int* dom_order = nullptr;       // [cap_domains] domains, longest first
+  int* pack_hist = nullptr;       // [65536] length buckets
+  long long* pack_off = nullptr;  // [65537]
   // local aggregation: per-warp arenas and the FP32 normalisation tables
   long long cap_len = 0;          // largest piece length covered by the X table
   long long cap_items = 0;        // largest domain (pieces) an arena holds
@@ -91,6 +97,10 @@ struct Marks {
   cudaEvent_t a0 = nullptr, a1 = nullptr;  // around the compression kernel
   cudaEvent_t b0 = nullptr, b1 = nullptr;  // around increments + exact sums
 };
+
+long long pack_buckets();
+void launch_pack_domains(const long long* dom_begin, const long long* dom_end, long long n_domains, Scratch& ws,
+                         cudaStream_t st);
 
 void launch_compress(const double* x, long long n_points, const long long* dom_begin, const long long* dom_end,
                      const long long* dom_slot_off, long long n_domains, double tol, int* piece_len,

@@ -326,7 +326,7 @@ __global__ void k_mfix(unsigned long long* skey, int* sidx, const int* link, con
 // Sorted-order copies of the coordinates, the cell of each item, and checks
 // that the grid is usable (else flags[0] = 1: sequential fallback).
 struct GridGeom {
-  float x0, y0, inv_h;
+  float x0, y0, inv_h, h;
   int ncx, ncy;
 };
 
@@ -340,6 +340,7 @@ __global__ void k_mgeom(const int* bounds, double alpha, long long cap_cells, Gr
   g.x0 = xmin;
   g.y0 = ymin;
   g.inv_h = (float)(1.0 / h);
+  g.h = (float)h;
   const double nx = n > 0 ? floor(((double)xmax - xmin) / h) + 1 : 1;
   const double ny = n > 0 ? floor(((double)ymax - ymin) / h) + 1 : 1;
   const double maxc = fmax(fmax(fabs((double)xmin), fabs((double)xmax)), fmax(fabs((double)ymin), fabs((double)ymax)));
@@ -427,7 +428,10 @@ struct RoundArgs {
   unsigned long long* state;
   unsigned char* cov;       // [t] item covered by a start (not a start itself)
   int* new_list;            // [2][n_cells] cells that created a start this round
-  unsigned* counters;       // [0..1] new-start counts, [2..3] undecided counts (by round parity)
+  int* chg_list;            // [2][n_cells] cells whose state or coverage changed this round
+  unsigned* eval_stamp;     // [n_cells] last round + 1 in which the cell was evaluated
+  unsigned* chg_stamp;      // [n_cells] last round + 1 in which the cell was listed as changed
+  unsigned* counters;       // [0..1] new-start counts, [2..3] changed counts (by round parity)
   const long long* n_cells_p;
   const GridGeom* geom;
   const int* flags;
@@ -469,17 +473,98 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) 
 
 constexpr int kCoverChunk = 1024;  // items of one neighbour cell per phase-B work unit
 
-// Rounds of the cell greedy.  Phase A (a warp per undecided cell): skip the
-// cell's covered items; its first uncovered item p becomes the cell's start
-// unless a neighbouring start that precedes p covers it (decided in this
-// round, so its coverage is not marked yet), or an uncovered item of an
-// undecided neighbouring cell precedes p and may lie within alpha (it could
-// still become a start covering p).  Phase B
-// (warps over (new start, neighbouring cell, chunk)): every later item within
-// alpha of a new start is marked covered (the start's own cell entirely: any
-// two of its items are within alpha).  Items are covered only by true starts,
-// and a start is declared only when no undecided earlier item can cover it,
-// so the starts are exactly those of the sequential greedy.
+// Evaluate one undecided cell (whole warp): skip its covered items; its first
+// uncovered item p becomes the cell's start unless a neighbouring start that
+// precedes p covers it (decided in this round, so its coverage is not marked
+// yet), or an uncovered item of an undecided neighbouring cell precedes p and
+// may lie within alpha (it could still become a start covering p).  Lane k
+// examines neighbour k of the 5 x 5 block.  Returns whether the state changed.
+__device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g, long long j, int* list,
+                                          unsigned* n_list) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long st = ld_state(&R.state[j]);
+  if ((unsigned)st != kUndecided) return false;
+  int t = (int)(st >> 32);
+  const int end = R.cell_end[j];
+  for (;;) {  // first uncovered item
+    const int u = t + lane;
+    const bool fr = u < end && !__ldcg(&R.cov[u]);  // L2: flags written by other SMs last round
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, fr);
+    if (m) { t += __ffs(m) - 1; break; }
+    t += 32;
+    if (t >= end) { t = end; break; }
+  }
+  unsigned result = kUndecided;
+  if (t >= end) {
+    result = kNoStart;
+  } else {
+    const int p = R.cord[t];
+    const int id = R.cell_id[j];
+    const int cx = id % g.ncx, cy = id / g.ncx;
+    const float px = R.V.sX[p], py = R.V.sY[p];
+    // squared distance beyond which a neighbouring cell cannot hold an item
+    // within alpha of p (margins cover the FP32 coordinates and cell mapping)
+    const float reach = sqrtf(R.V.a2hi) * (1.0f + 0x1p-10f) +
+                        0x1p-16f * (fabsf(px) + fabsf(py) + fabsf(g.x0) + fabsf(g.y0) + 4.0f * g.h);
+    bool blocked = false;
+    for (int k = 0; k < 25 && !blocked; ++k) {
+      if (k == 12) continue;
+      const int xx = cx + k % 5 - 2, yy = cy + k / 5 - 2;
+      if (xx < 0 || xx >= g.ncx || yy < 0 || yy >= g.ncy) continue;
+      {  // distance from p to the cell rectangle
+        const float rx0 = g.x0 + xx * g.h, ry0 = g.y0 + yy * g.h;
+        const float ddx = fmaxf(fmaxf(rx0 - px, px - (rx0 + g.h)), 0.f);
+        const float ddy = fmaxf(fmaxf(ry0 - py, py - (ry0 + g.h)), 0.f);
+        if (ddx > reach || ddy > reach || fmaf(ddx, ddx, ddy * ddy) > reach * reach) continue;
+      }
+      const int q = R.cell_of_id[yy * g.ncx + xx];
+      if (q < 0) continue;
+      const unsigned long long sq = ld_state(&R.state[q]);
+      const unsigned sv = (unsigned)sq;
+      if (sv < kNoStart) {
+        // a start decided this round has not marked its coverage yet
+        if ((int)sv < p && within_sorted(R.V, (int)sv, p)) blocked = true;
+        continue;
+      }
+      if (sv != kUndecided) continue;
+      const int qe = R.cell_end[q];
+      for (int u0 = (int)(sq >> 32); u0 < qe; u0 += 32) {
+        const int u = u0 + lane;
+        bool past = true, hit = false;
+        if (u < qe) {
+          const int r = R.cord[u];
+          past = r >= p;
+          if (!past && !__ldcg(&R.cov[u]) && maybe_within_sorted(R.V, r, p)) hit = true;
+        }
+        if (__any_sync(0xFFFFFFFFu, hit)) { blocked = true; break; }
+        if (__any_sync(0xFFFFFFFFu, past)) break;
+      }
+    }
+    if (!blocked) result = (unsigned)p;
+  }
+  const unsigned long long ns = ((unsigned long long)(unsigned)t << 32) | result;
+  const bool changed = ns != st;
+  if (lane == 0) {
+    if (changed) atomicExch(&R.state[j], ns);
+    if (result < kNoStart) list[atomicAdd(n_list, 1u)] = (int)j;
+  }
+  return changed;
+}
+
+// Append cell q to the changed list of this round once (stamp = round + 1).
+__device__ __forceinline__ void mark_changed(const RoundArgs& R, long long q, unsigned round, int* chg,
+                                             unsigned* n_chg) {
+  if (atomicExch(&R.chg_stamp[q], round + 1) != round + 1) chg[atomicAdd(n_chg, 1u)] = (int)q;
+}
+
+// Rounds of the cell greedy with worklists: round r evaluates only the
+// undecided cells of the 5 x 5 blocks around cells that changed in round r-1
+// (their state, or the coverage of their items); a cell whose neighbourhood
+// did not change would reach the same verdict.  Phase A evaluates (each cell
+// once per round: eval_stamp), phase B marks the coverage of the new starts.
+// Items are covered only by true starts, and a start is declared only when no
+// undecided earlier item can cover it, so the starts are exactly those of the
+// sequential greedy.
 __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
   if (R.flags[0] || R.flags[1]) return;
   const long long n_cells = *R.n_cells_p;
@@ -488,75 +573,45 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
   const int lane = threadIdx.x & 31;
   const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const size_t stride = (size_t)(n_cells > 0 ? n_cells : 1);
   for (unsigned round = 0; round < R.max_rounds; ++round) {
     const int par = round & 1;
-    int* list = R.new_list + (size_t)par * (size_t)(n_cells > 0 ? n_cells : 1);
+    int* list = R.new_list + (size_t)par * stride;         // new starts of this round
+    int* chg = R.chg_list + (size_t)par * stride;          // cells changed in this round
+    const int* prev = R.chg_list + (size_t)(par ^ 1) * stride;
+    unsigned* n_list = &R.counters[par];
+    unsigned* n_chg = &R.counters[2 + par];
+    const unsigned n_prev = round ? *((volatile unsigned*)&R.counters[2 + (par ^ 1)]) : 0u;
     // ---- phase A
-    unsigned my_und = 0;
-    for (long long j = warp_g; j < n_cells; j += n_warps) {
-      const unsigned long long st = ld_state(&R.state[j]);
-      if ((unsigned)st != kUndecided) continue;
-      int t = (int)(st >> 32);
-      const int end = R.cell_end[j];
-      for (;;) {  // first uncovered item
-        const int u = t + lane;
-        const bool fr = u < end && !__ldcg(&R.cov[u]);  // L2: flags written by other SMs last round
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, fr);
-        if (m) { t += __ffs(m) - 1; break; }
-        t += 32;
-        if (t >= end) { t = end; break; }
-      }
-      unsigned result = kUndecided;
-      if (t >= end) {
-        result = kNoStart;
-      } else {
-        const int p = R.cord[t];
-        const int id = R.cell_id[j];
-        const int cx = id % g.ncx, cy = id / g.ncx;
-        bool blocked = false;
-        for (int k = 0; k < 25 && !blocked; ++k) {
-          const int dx = k % 5 - 2, dy = k / 5 - 2;
-          if (dx == 0 && dy == 0) continue;
-          const int xx = cx + dx, yy = cy + dy;
-          if (xx < 0 || xx >= g.ncx || yy < 0 || yy >= g.ncy) continue;
-          const int q = R.cell_of_id[yy * g.ncx + xx];
-          if (q < 0) continue;
-          const unsigned long long sq = ld_state(&R.state[q]);
-          const unsigned sv = (unsigned)sq;
-          if (sv < kNoStart) {
-            // a start decided this round has not marked its coverage yet
-            if ((int)sv < p && within_sorted(R.V, (int)sv, p)) blocked = true;
-            continue;
-          }
-          if (sv != kUndecided) continue;
-          const int qe = R.cell_end[q];
-          for (int u0 = (int)(sq >> 32); u0 < qe; u0 += 32) {
-            const int u = u0 + lane;
-            bool past = true, hit = false;
-            if (u < qe) {
-              const int r = R.cord[u];
-              past = r >= p;
-              if (!past && !__ldcg(&R.cov[u]) && maybe_within_sorted(R.V, r, p)) hit = true;
-            }
-            if (__any_sync(0xFFFFFFFFu, hit)) { blocked = true; break; }
-            if (__any_sync(0xFFFFFFFFu, past)) break;
-          }
-        }
-        if (!blocked) result = (unsigned)p;
-      }
-      if (lane == 0) {
-        const unsigned long long ns = ((unsigned long long)(unsigned)t << 32) | result;
-        if (ns != st) atomicExch(&R.state[j], ns);
-        if (result < kNoStart) list[atomicAdd(&R.counters[par], 1u)] = (int)j;
-        if (result == kUndecided) ++my_und;
+    if (round == 0) {
+      for (long long j = warp_g; j < n_cells; j += n_warps)
+        if (eval_cell(R, g, j, list, n_list) && lane == 0) mark_changed(R, j, round, chg, n_chg);
+    } else {
+      for (long long w = warp_g; w < (long long)n_prev * 25; w += n_warps) {
+        const int c = __ldcg(&prev[w / 25]);
+        const int k = (int)(w % 25);
+        const int id = R.cell_id[c];
+        const int xx = id % g.ncx + k % 5 - 2, yy = id / g.ncx + k / 5 - 2;
+        if (xx < 0 || xx >= g.ncx || yy < 0 || yy >= g.ncy) continue;
+        const int q = R.cell_of_id[yy * g.ncx + xx];
+        if (q < 0) continue;
+        if ((unsigned)ld_state(&R.state[q]) != kUndecided) continue;
+        unsigned claim = 0;
+        if (lane == 0) claim = atomicExch(&R.eval_stamp[q], round + 1);
+        claim = __shfl_sync(0xFFFFFFFFu, claim, 0);
+        if (claim == round + 1) continue;                    // already evaluated this round
+        if (eval_cell(R, g, q, list, n_list) && lane == 0) mark_changed(R, q, round, chg, n_chg);
       }
     }
-    if (lane == 0 && my_und) atomicAdd(&R.counters[2 + par], my_und);
     if (!grid_barrier(R.bar, nblocks, R.status)) return;
     // ---- phase B
-    const unsigned n_new = *((volatile unsigned*)&R.counters[par]);
-    const unsigned und = *((volatile unsigned*)&R.counters[2 + par]);
-    // work units: (new start, neighbour k, chunk c); chunk counts bounded per cell
+    // every read of the other parity's counters (n_prev) happened before the
+    // barrier; they are written again only after the next barrier
+    if (warp_g == 0 && lane == 0) {
+      R.counters[par ^ 1] = 0;
+      R.counters[2 + (par ^ 1)] = 0;
+    }
+    const unsigned n_new = *((volatile unsigned*)n_list);
     for (long long w = warp_g; w < (long long)n_new * 25 * 64; w += n_warps) {
       const long long si = w / (25 * 64);
       const int k = (int)((w / 64) % 25);
@@ -570,24 +625,35 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
       if (q < 0) continue;
       const int qb = R.cell_beg[q], qe = R.cell_end[q];
       const int span = qe - qb;
-      const int per = ((span + 63) / 64 + kCoverChunk - 1) / kCoverChunk * kCoverChunk;  // chunk length, multiple of 1024
-      const int lo = qb + c * (per > 0 ? per : kCoverChunk);
-      const int hi = min(qe, lo + (per > 0 ? per : kCoverChunk));
+      const int per = ((span + 63) / 64 + kCoverChunk - 1) / kCoverChunk * kCoverChunk;
+      const int lo = qb + c * per;
+      const int hi = min(qe, lo + per);
+      bool any = false;
       for (int u = lo + lane; u < hi; u += 32) {
         const int r = R.cord[u];
         if (r <= (int)sp || __ldcg(&R.cov[u])) continue;
-        if (q == j || within_sorted(R.V, (int)sp, r)) R.cov[u] = 1;
+        if (q == j || within_sorted(R.V, (int)sp, r)) {
+          R.cov[u] = 1;
+          any = true;
+        }
       }
+      if (__any_sync(0xFFFFFFFFu, any) && lane == 0 && q != j) mark_changed(R, q, round, chg, n_chg);
     }
     if (!grid_barrier(R.bar, nblocks, R.status)) return;
-    if (und == 0) return;
-    // the other parity's counters are reset here; they are next used after the next barrier
-    if (warp_g == 0 && lane == 0) {
-      R.counters[par ^ 1] = 0;
-      R.counters[2 + (par ^ 1)] = 0;
-    }
+    // nothing changed: a fixed point, where every cell is decided (the
+    // earliest undecided candidate always progresses); k_mcheck verifies it
+    if (*((volatile unsigned*)n_chg) == 0) return;
   }
   if (warp_g == 0 && lane == 0) set_status(R.status, JABBA_ERR_TIMEOUT);
+}
+
+// Count of cells left undecided (0 after a complete run).
+__global__ void k_mcheck(const unsigned long long* state, const long long* n_cells_p, const int* flags,
+                         unsigned* status) {
+  if (flags[0] || flags[1]) return;
+  const long long n = *n_cells_p;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    if ((unsigned)state[j] == kUndecided) set_status(status, JABBA_ERR_TIMEOUT);
 }
 
 // ------------------------------------------------------------------ 5. labels
@@ -814,6 +880,8 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
   cudaMemsetAsync(B.cov, 0, (size_t)(cap > 0 ? cap : 1), st);
+  cudaMemsetAsync(B.eval_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
+  cudaMemsetAsync(B.chg_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   k_mcell_fill<<<grid, 256, 0, st>>>(ckey, B.head, B.head_off, n_groups, cap, B.cell_beg, B.cell_end, B.cell_id,
                                      B.cell_of_id, B.state);
   k_mcell_end<<<grid, 256, 0, st>>>(B.cell_beg, B.head_off + cap, n_groups, cap, B.cell_end);
@@ -838,6 +906,9 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   R.state = B.state;
   R.cov = (unsigned char*)B.cov;
   R.new_list = B.new_list;
+  R.chg_list = B.chg_list;
+  R.eval_stamp = B.eval_stamp;
+  R.chg_stamp = B.chg_stamp;
   R.counters = B.bar + 4;
   R.n_cells_p = B.head_off + cap;
   R.geom = B.geom;
@@ -865,6 +936,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_mrounds, R);
   }
+  k_mcheck<<<grid, 256, 0, st>>>(B.state, B.head_off + cap, B.flags, status);
   k_clear_i32<<<grid, 256, 0, st>>>(B.is_start, cap, 0);
   k_mlabel<<<grid, 256, 0, st>>>(V, ckey, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab, B.is_start);
   // sequential fallback (only acts when flags[0] is set)
