@@ -87,10 +87,13 @@ void launch_build_domains(const long long* series_off, long long n_series, int m
 //     over the piece (conversion and subtraction errors of the d_i, and the
 //     binary64 rounding of the definition's own terms, with margin 2).
 // Hence, squaring sqrt F +- h against sqrt(L^2 (L-1)) tol,
-//   admissible   if E + A < L^2 (L - 1) (tol (1 - 2^-18) - 2^-19 M)^2,
-//   inadmissible if E - A > L^2 (L - 1) (tol (1 + 2^-18) + 2^-19 M)^2,
-// (M = max|x~|; the 2^-18 slack covers the FP32 roundings of the tests
-// themselves and the binary64 roundings of the definition's bound and sum).
+//   admissible   if E + A < L^2 (L - 1) (tol (1 - 2^-18) - 2^-99 - 2^-19 M)^2,
+//   inadmissible if E - A > L^2 (L - 1) (tol (1 + 2^-18) + 2^-99 + 2^-19 M')^2,
+// (M = max|x~|, M' = max(M, 2^-40); the 2^-18 slack covers the FP32 roundings
+// of the tests themselves and the binary64 roundings of the definition's bound
+// and sum, 2^-99 the absolute error of tiny values, and A carries an absolute
+// 2^-100 for FP32 underflow).  Domains of 2^24 or more intervals (FP32
+// lengths no longer exact) take the exact path at every point.
 // Otherwise the whole warp evaluates the binary64 definition for that lane
 // (32 terms at a time, exact fixed-point sum): see warp_exact_admissible.
 constexpr int kChunk = 16;                 // points per lane per stage
@@ -223,6 +226,87 @@ __device__ __forceinline__ int stage_chunk(const CompressParams& P, const LaneDo
   return off;
 }
 
+// Per-lane state of the greedy on one domain.
+struct LaneState {
+  double prevd;                 // x at the previous point (end value of a piece)
+  float xs, prevf, S2, SK, K2, Lf, M;
+  int s;                        // start of the open piece (domain-local index)
+  int* out_len;                 // next output slot
+  double* out_end;
+  float tlo, thi;               // tol (1 -+ 2^-18) -+ 2^-99; (-1, inf) forces the exact path
+  unsigned amax;
+};
+
+// One point p (domain-local) of the lane's domain, value vd.  TAIL: lanes may
+// be past their domain end (act = false) and a lane may reach its end.
+template <bool TAIL>
+__device__ __forceinline__ void step(const CompressParams& P, LaneState& L, const LaneDomain& D, int p, double vd,
+                                     unsigned long long* n_exact) {
+  const int lane = threadIdx.x & 31;
+  const bool act = !TAIL || p <= D.n_int;
+  unsigned mh;
+  const float v = f64_to_f32_trunc(vd, mh);
+  if (!TAIL || act) L.amax = max(L.amax, mh);
+  float dd = v - L.xs;
+  const float Ln = L.Lf + 1.0f;
+  const float L2 = Ln * Ln;
+  const float sq = dd * dd;
+  const float t3 = sq * L.K2;
+  const float cc = (Ln + Ln) * dd;
+  const float E = fmaf(L2, L.S2, fmaf(-cc, L.SK, t3));
+  const float Pp = fmaf(L2, L.S2, t3);
+  const float B0 = L2 * (Ln - 1.0f);
+  // rounding bound of E (relative, plus an absolute 2^-100 for FP32 underflow)
+  const float A = fmaf(fmaf(Ln, 2.2f * 0x1p-24f, 2.2f * 8.0f * 0x1p-24f), Pp, 0x1p-100f);
+  const float Mx = fmaxf(L.M, fabsf(v));
+  const float clo = fmaf(-0x1p-19f, Mx, L.tlo);
+  // at least 2^-40 in the inadmissibility margin: keeps chi^2 a normal number
+  const float chi = fmaf(0x1p-19f, fmaxf(Mx, 0x1p-40f), L.thi);
+  bool feas = (E + A < B0 * (clo * clo) && clo > 0.f) || Ln == 1.0f;
+  const bool infeas = E - A > B0 * (chi * chi);
+  const unsigned amb = __ballot_sync(0xFFFFFFFFu, act && !feas && !infeas);
+  if (amb) {
+    unsigned m = amb;
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+      const long long gb = __shfl_sync(0xFFFFFFFFu, D.b, l);
+      const int sl = __shfl_sync(0xFFFFFFFFu, L.s, l);
+      const int pl = __shfl_sync(0xFFFFFFFFu, p, l);
+      const bool r = warp_exact_admissible(P.x + gb, sl, pl, P.tol2);
+      if (lane == l) feas = r;
+    }
+    if (lane == 0) atomicAdd(n_exact, (unsigned long long)__popc(amb));
+  }
+  if (act) {
+    if (feas) {
+      L.S2 = fmaf(dd, dd, L.S2);
+      L.SK = fmaf(Ln, dd, L.SK);
+      L.K2 = fmaf(Ln, Ln, L.K2);
+      L.Lf = Ln;
+      L.M = Mx;
+    } else {
+      // piece (s, p - 1) ends; restart at p - 1 with p as its first candidate
+      *L.out_len++ = (p - 1) - L.s;
+      *L.out_end++ = L.prevd;
+      L.s = p - 1;
+      L.xs = L.prevf;
+      dd = v - L.xs;
+      L.S2 = dd * dd;
+      L.SK = dd;
+      L.K2 = 1.0f;
+      L.Lf = 1.0f;
+      L.M = fmaxf(fabsf(L.prevf), fabsf(v));
+    }
+    L.prevf = v;
+    L.prevd = vd;
+    if (TAIL && p == D.n_int) {  // domain end: the open piece ends here
+      *L.out_len++ = p - L.s;
+      *L.out_end++ = vd;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParams P) {
   __shared__ __align__(16) double stage[kWarpsPerCta][kStages][32][kRow];
   __shared__ __align__(8) unsigned long long bars[kWarpsPerCta][kStages];
@@ -234,8 +318,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
   const unsigned bar0 = smem_u32(&bars[warp][0]);
   const unsigned bar1 = smem_u32(&bars[warp][1]);
   const long long n_tasks = (P.n_domains + 31) / 32;
-  const float G1 = 2.2f * 0x1p-24f, G0 = 2.2f * 8.0f * 0x1p-24f;
-  unsigned amax = 0;  // largest |x| high word seen (range / finiteness check)
+  LaneState L;
+  L.amax = 0;
 
   for (;;) {
     long long task = 0;
@@ -253,23 +337,31 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
       D.n_int = (int)(P.dom_end[d] - D.b);
       slot = P.dom_slot_off[d];
     }
-    int max_int = D.n_int;
-    for (int o = 16; o > 0; o >>= 1) max_int = max(max_int, __shfl_xor_sync(0xFFFFFFFFu, max_int, o));
+    int max_int = D.n_int, min_int = D.n_int;
+    for (int o = 16; o > 0; o >>= 1) {
+      max_int = max(max_int, __shfl_xor_sync(0xFFFFFFFFu, max_int, o));
+      min_int = min(min_int, __shfl_xor_sync(0xFFFFFFFFu, min_int, o));
+    }
     const int n_chunks = (max_int + kChunk - 1) / kChunk;
     const double* xb = P.x + D.b;
 
-    // lane state
-    double prevd = 0.0;
-    float xs = 0.f, prevf = 0.f, S2 = 0.f, SK = 0.f, K2 = 0.f, Lf = 0.f, M = 0.f;
-    int s = 0, cnt = 0;
+    L.out_len = P.piece_len + slot;
+    L.out_end = P.piece_end + slot;
+    // FP32 lengths are exact below 2^24: longer domains take the exact path throughout
+    L.tlo = D.n_int < (1 << 24) ? P.tol_lo : -1.0f;
+    L.thi = D.n_int < (1 << 24) ? P.tol_hi : INFINITY;
+    L.prevd = 0.0;
+    L.xs = L.prevf = L.S2 = L.SK = L.K2 = L.Lf = L.M = 0.f;
+    L.s = 0;
     if (D.n_int > 0) {
-      prevd = xb[0];
+      L.prevd = xb[0];
       unsigned mh;
-      xs = f64_to_f32_trunc(prevd, mh);
-      amax = max(amax, mh);
-      prevf = xs;
-      M = fabsf(xs);
+      L.xs = f64_to_f32_trunc(L.prevd, mh);
+      L.amax = max(L.amax, mh);
+      L.prevf = L.xs;
+      L.M = fabsf(L.xs);
     }
+    unsigned long long* n_exact = P.n_exact;
 
     int off_a = 0, off_b = 0;
     if (n_chunks > 0) off_a = stage_chunk(P, D, 0, stage[warp][0][lane], bar0);
@@ -304,79 +396,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
       }
       const double* row = stage[warp][buf][lane] + (buf ? off_b : off_a);
       const int p0 = 1 + c * kChunk;
+      if (p0 + kChunk - 1 < min_int) {
+        // every lane has all kChunk points and none reaches its domain end
 #pragma unroll 2
-      for (int j = 0; j < kChunk; ++j) {
-        const int p = p0 + j;
-        const bool act = p <= D.n_int;
-        const double vd = row[j];
-        unsigned mh;
-        const float v = f64_to_f32_trunc(vd, mh);
-        if (act) amax = max(amax, mh);
-        float dd_ = v - xs;
-        const float Ln = Lf + 1.0f;
-        const float L2 = Ln * Ln;
-        const float sq = dd_ * dd_;
-        const float t3 = sq * K2;
-        const float cc = (Ln + Ln) * dd_;
-        const float E = fmaf(L2, S2, fmaf(-cc, SK, t3));
-        const float Pp = fmaf(L2, S2, t3);
-        const float B0 = L2 * (Ln - 1.0f);
-        const float A = fmaf(Ln, G1, G0) * Pp;
-        const float Mx = fmaxf(M, fabsf(v));
-        const float clo = fmaf(-0x1p-19f, Mx, P.tol_lo);
-        const float chi = fmaf(0x1p-19f, Mx, P.tol_hi);
-        bool feas = (E + A < B0 * (clo * clo)) && clo > 0.f;
-        bool infeas = E - A > B0 * (chi * chi);
-        const bool fast_ok = (Mx >= 0x1p-60f) && (Mx < 0x1p31f) && (Ln < 1048576.0f);
-        feas = (feas && fast_ok) || (Ln == 1.0f);
-        infeas = infeas && fast_ok && !feas;
-        unsigned amb = __ballot_sync(0xFFFFFFFFu, act && !feas && !infeas);
-        while (amb) {
-          const int l = __ffs(amb) - 1;
-          amb &= amb - 1;
-          const long long gb = __shfl_sync(0xFFFFFFFFu, D.b, l);
-          const int sl = __shfl_sync(0xFFFFFFFFu, s, l);
-          const int pl = __shfl_sync(0xFFFFFFFFu, p, l);
-          const bool r = warp_exact_admissible(P.x + gb, sl, pl, P.tol2);
-          if (lane == l) feas = r;
-          if (lane == 0) atomicAdd(P.n_exact, 1ull);
-        }
-        if (act) {
-          if (feas) {
-            S2 = fmaf(dd_, dd_, S2);
-            SK = fmaf(Ln, dd_, SK);
-            K2 = fmaf(Ln, Ln, K2);
-            Lf = Ln;
-            M = Mx;
-          } else {
-            // piece (s, p - 1) ends; restart at p - 1 with p as its first candidate
-            P.piece_len[slot + cnt] = (p - 1) - s;
-            P.piece_end[slot + cnt] = prevd;
-            ++cnt;
-            s = p - 1;
-            xs = prevf;
-            dd_ = v - xs;
-            S2 = dd_ * dd_;
-            SK = dd_;
-            K2 = 1.0f;
-            Lf = 1.0f;
-            M = fmaxf(fabsf(prevf), fabsf(v));
-          }
-          prevf = v;
-          prevd = vd;
-          if (p == D.n_int) {  // domain end: the open piece ends here
-            P.piece_len[slot + cnt] = p - s;
-            P.piece_end[slot + cnt] = vd;
-            ++cnt;
-          }
-        }
+        for (int j = 0; j < kChunk; ++j) step<false>(P, L, D, p0 + j, row[j], n_exact);
+      } else {
+#pragma unroll 1
+        for (int j = 0; j < kChunk; ++j) step<true>(P, L, D, p0 + j, row[j], n_exact);
       }
     }
-    if (d < P.n_domains) P.dom_piece_cnt[d] = cnt;
+    if (d < P.n_domains) P.dom_piece_cnt[d] = (int)(L.out_len - (P.piece_len + slot));
   }
   // range / finiteness of every value this lane read
-  if (amax >= 0x7FF00000u) set_status(P.status, JABBA_ERR_NONFINITE);
-  else if (amax >= (1054u << 20)) set_status(P.status, JABBA_ERR_RANGE);
+  if (L.amax >= 0x7FF00000u) set_status(P.status, JABBA_ERR_NONFINITE);
+  else if (L.amax >= (1054u << 20)) set_status(P.status, JABBA_ERR_RANGE);
 }
 
 // ------------------------------------------------------------------ domain packing
@@ -565,7 +598,9 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   P.n_domains = n_domains;
   P.tol2 = tol * tol;
   {
-    const double lo = tol * (1.0 - 0x1p-18), hi = tol * (1.0 + 0x1p-18);
+    // tau also carries an absolute 2^-100 (conversion of |x| < 2^-126), so the
+    // certified margins subtract / add 2^-99 in tol units
+    const double lo = tol * (1.0 - 0x1p-18) - 0x1p-99, hi = tol * (1.0 + 0x1p-18) + 0x1p-99;
     P.tol_lo = (float)lo;
     if ((double)P.tol_lo > lo) P.tol_lo = nextafterf(P.tol_lo, 0.0f);
     P.tol_hi = (float)hi;

@@ -53,7 +53,8 @@ struct LocalParams {
   long long cap_items;
 };
 
-constexpr int kArenaWords = 8;  // key, X32, Y32, sidx, label, tmp key, tmp val, members
+constexpr int kArenaWords = 8;           // key, X32, Y32, sidx, label, tmp key, tmp val, members
+constexpr int kSmemItemsArena = 2048;   // domains up to this many pieces use k_local_smem
 
 __device__ __forceinline__ double x64_of(const LocalParams& P, int len) {
   if (len <= P.cap_len) return P.xtab64[len];
@@ -187,13 +188,10 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
     d = __shfl_sync(0xFFFFFFFFu, d, 0);
     if (d >= P.n_domains) break;
     const int n = P.dom_piece_cnt[d];
+    if (n <= kSmemItemsArena) continue;           // the shared-memory kernel takes it
     const long long slot = P.dom_slot_off[d];
     const int* plen = P.piece_len + slot;
     const double* pinc = P.piece_inc + slot;
-    if (n == 0) {
-      if (lane == 0) P.dom_group_cnt[d] = 0;
-      continue;
-    }
     if (n > P.cap_items) {
       if (lane == 0) {
         set_status(P.status, JABBA_ERR_CAPACITY);
@@ -370,6 +368,267 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
   (void)cl_flag;
 }
 
+// ------------------------------------------------------------------ shared-memory path
+// Domains of at most kSmemItems pieces: the same steps with every per-piece
+// array in the warp's slice of shared memory, the coordinates permuted into
+// key order after the sort so that the greedy reads contiguous entries.
+constexpr int kSmemItems = 2048;
+constexpr int kSmemWarps = 4;
+// bytes per item: key 4, X/sX 4, Y/sY 4, tmp key 4, idx 2, tmp idx 2, label 2, pad 2
+constexpr size_t kSmemPerWarp = (size_t)kSmemItems * 24 + 1024;
+
+__device__ void warp_radix_sort16(unsigned* key, unsigned short* val, unsigned* tk, unsigned short* tv, int n,
+                                  unsigned* hist) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned* kin = key;
+  unsigned short* vin = val;
+  unsigned* kout = tk;
+  unsigned short* vout = tv;
+  for (int shift = 0; shift < 32; shift += 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) atomicAdd(&hist[(kin[i] >> shift) & 255u], 1u);
+    __syncwarp();
+    unsigned loc[8], sum = 0;
+    for (int j = 0; j < 8; ++j) { loc[j] = hist[lane * 8 + j]; sum += loc[j]; }
+    unsigned incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    unsigned run = incl - sum;
+    __syncwarp();
+    for (int j = 0; j < 8; ++j) { hist[lane * 8 + j] = run; run += loc[j]; }
+    __syncwarp();
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      const bool v = i < n;
+      const unsigned k = v ? kin[i] : 0u;
+      const unsigned short vv = v ? vin[i] : 0;
+      const unsigned d = v ? ((k >> shift) & 255u) : 256u + lane;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+      const unsigned r = __popc(peers & lt);
+      if (v) {
+        const unsigned pos = hist[d] + r;
+        kout[pos] = k;
+        vout[pos] = vv;
+      }
+      __syncwarp();
+      if (v && r == 0) hist[d] += __popc(peers);
+      __syncwarp();
+    }
+    unsigned* t = kin; kin = kout; kout = t;
+    unsigned short* tt = vin; vin = vout; vout = tt;
+  }
+}
+
+__global__ void __launch_bounds__(kSmemWarps * 32) k_local_smem(LocalParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem_raw + (size_t)warp * kSmemPerWarp;
+  unsigned* hist = (unsigned*)base;                                    // 256 words
+  unsigned* key = (unsigned*)(base + 1024);                            // [n] sorted keys
+  float* X = (float*)(key + kSmemItems);                               // [n] by position, then sY
+  float* Y = X + kSmemItems;                                           // [n] by position, then labels/scratch
+  unsigned* tk = (unsigned*)(Y + kSmemItems);                          // [n] sort temp, then sX
+  unsigned short* idx = (unsigned short*)(tk + kSmemItems);            // [n] sorted index -> position
+  unsigned short* tv = idx + kSmemItems;                               // [n] sort temp
+  short* lab = (short*)(tv + kSmemItems);                              // [n] label by sorted index
+  float* sX = (float*)tk;
+  float* sY = X;
+  const double a2 = __dmul_rn(P.alpha, P.alpha);
+  const float rinv = *P.rinv32;
+  for (;;) {
+    long long d = 0;
+    if (lane == 0) d = (long long)atomicAdd(P.task_counter, 1u);
+    d = __shfl_sync(0xFFFFFFFFu, d, 0);
+    if (d >= P.n_domains) break;
+    const int n = P.dom_piece_cnt[d];
+    if (n > kSmemItems) continue;                 // the arena kernel takes it
+    const long long slot = P.dom_slot_off[d];
+    const int* plen = P.piece_len + slot;
+    const double* pinc = P.piece_inc + slot;
+    if (n == 0) {
+      if (lane == 0) P.dom_group_cnt[d] = 0;
+      continue;
+    }
+    // 1. FP32 coordinates and keys by position
+    for (int i = lane; i < n; i += 32) {
+      unsigned mh;
+      const float x = x32_of(P, plen[i]);
+      const float y = f64_to_f32_trunc(pinc[i], mh) * rinv;
+      X[i] = x;
+      Y[i] = y;
+      key[i] = __float_as_uint(fmaf(x, x, y * y));
+      idx[i] = (unsigned short)i;
+    }
+    __syncwarp();
+    // 2. sort by (key32, position)
+    if (n > 1) warp_radix_sort16(key, idx, tk, tv, n, hist);
+    __syncwarp();
+    // 3. runs of overlapping key intervals: re-sort by the binary64 keys (rare)
+    {
+      bool any = false;
+      for (int a = lane; a + 1 < n; a += 32) {
+        const float k0 = __uint_as_float(key[a]), k1 = __uint_as_float(key[a + 1]);
+        if (k1 * (1.0f - kKeyRel) <= k0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f)) any = true;
+      }
+      if (__any_sync(0xFFFFFFFFu, any) && lane == 0) {
+        int a = 0;
+        while (a + 1 < n) {
+          int b = a;
+          while (b + 1 < n) {
+            const float k0 = __uint_as_float(key[b]), k1 = __uint_as_float(key[b + 1]);
+            if (k1 * (1.0f - kKeyRel) <= k0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f)) ++b; else break;
+          }
+          for (int u = a + 1; u <= b; ++u) {
+            const int pu = idx[u];
+            const unsigned ku32 = key[u];
+            const double ku = key64_of(P, plen[pu], pinc[pu]);
+            int v = u - 1;
+            while (v >= a) {
+              const int pv = idx[v];
+              const double kv = key64_of(P, plen[pv], pinc[pv]);
+              if (kv > ku || (kv == ku && pv > pu)) {
+                idx[v + 1] = (unsigned short)pv;
+                key[v + 1] = key[v];
+                --v;
+              } else {
+                break;
+              }
+            }
+            idx[v + 1] = (unsigned short)pu;
+            key[v + 1] = ku32;
+          }
+          a = b + 1;
+        }
+      }
+      __syncwarp();
+    }
+    // 4. coordinates in key order (sX in the sort temp; Y's slot keeps sY after X is read)
+    for (int a = lane; a < n; a += 32) sX[a] = X[idx[a]];
+    __syncwarp();
+    float yv[kSmemItems / 32];
+#pragma unroll
+    for (int r = 0; r < kSmemItems / 32; ++r) {
+      const int a = r * 32 + lane;
+      yv[r] = a < n ? Y[idx[a]] : 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kSmemItems / 32; ++r) {
+      const int a = r * 32 + lane;
+      if (a < n) sY[a] = yv[r];
+    }
+    for (int a = lane; a < n; a += 32) lab[a] = -1;
+    __syncwarp();
+    // 5. greedy in key order
+    int G = 0;
+    {
+      int a = 0;
+      for (;;) {
+        for (;;) {
+          const int aa = a + lane;
+          const bool fr = aa < n && lab[aa] < 0;
+          const unsigned m = __ballot_sync(0xFFFFFFFFu, fr);
+          if (m) { a += __ffs(m) - 1; break; }
+          a += 32;
+          if (a >= n) break;
+        }
+        if (a >= n) break;
+        const float xs = sX[a], ys = sY[a];
+        const float T = key_stop(__uint_as_float(key[a]), P.alpha_up);
+        if (lane == 0) lab[a] = (short)G;
+        for (int b0 = a + 1; b0 < n; b0 += 32) {
+          const int b = b0 + lane;
+          bool stop = true;
+          if (b < n) {
+            stop = __uint_as_float(key[b]) * (1.0f - kKeyRel) > T;
+            if (!stop && lab[b] < 0) {
+              int w = filter_within(xs, ys, sX[b], sY[b], P.a2lo, P.a2hi);
+              if (w == 2) {
+                const int ps = idx[a], pb = idx[b];
+                w = exact_within(P, plen[ps], pinc[ps], plen[pb], pinc[pb], a2) ? 1 : 0;
+              }
+              if (w) lab[b] = (short)G;
+            }
+          }
+          if (__any_sync(0xFFFFFFFFu, stop)) break;
+        }
+        __syncwarp();
+        ++G;
+        ++a;
+      }
+    }
+    __syncwarp();
+    // 6. labels to positions, member lists (counting sort by label), exact sums
+    int* cnt = (int*)key;        // [G + 1] offsets (keys no longer needed)
+    unsigned short* mem = tv;    // [n] positions grouped by label
+    for (int a = lane; a < n; a += 32) P.local_label[slot + idx[a]] = lab[a];
+    for (int g = lane; g <= G; g += 32) cnt[g] = 0;
+    __syncwarp();
+    for (int a = lane; a < n; a += 32) atomicAdd(&cnt[lab[a]], 1);
+    __syncwarp();
+    {
+      int carry = 0;
+      for (int g0 = 0; g0 < G; g0 += 32) {
+        const int g = g0 + lane;
+        const int c = g < G ? cnt[g] : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (g < G) cnt[g] = carry + incl - c;
+        carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+      }
+    }
+    __syncwarp();
+    for (int a = lane; a < n; a += 32) {
+      const int r = atomicAdd(&cnt[lab[a]], 1);
+      mem[r] = idx[a];
+    }
+    __syncwarp();
+    long long gbase = 0;
+    if (lane == 0) {
+      gbase = (long long)atomicAdd((unsigned long long*)P.n_groups, (unsigned long long)G);
+      if (gbase + G > P.group_capacity) {
+        set_status(P.status, JABBA_ERR_CAPACITY);
+        gbase = -1;
+      }
+      P.dom_group_cnt[d] = G;
+    }
+    gbase = __shfl_sync(0xFFFFFFFFu, gbase, 0);
+    if (gbase >= 0) {
+      for (int g = lane; g < G; g += 32) {
+        const int e = cnt[g];
+        const int s0 = g ? cnt[g - 1] : 0;
+        I192 acc = {0, 0, 0};
+        long long lensum = 0;
+        for (int q = s0; q < e; ++q) {
+          const int i = mem[q];
+          lensum += plen[i];
+          bool neg;
+          const U128 m = fx_mag(pinc[i], neg);
+          acc_signed(acc, m, neg);
+        }
+        jabba_group rec;
+        rec.inc[0] = acc.w0;
+        rec.inc[1] = acc.w1;
+        rec.inc[2] = acc.w2;
+        rec.lensum = lensum;
+        rec.count = e - s0;
+        rec.local_id = g;
+        rec.domain = (int)d;
+        rec.pad = 0;
+        P.groups[gbase + g] = rec;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // X table and 1/sigma_inc for the FP32 filters (binary64 definitions).
 __global__ void k_norm_tables(const double* sigma, double scl, long long cap_len, double* xtab64, float* xtab32,
                               float* rinv32) {
@@ -427,7 +686,17 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
   P.task_counter = ws.counters + 4;
   P.arena = ws.arena;
   P.cap_items = ws.cap_items;
-  if (n_domains > 0) k_local_warp<<<(unsigned)ws.loc_ctas, kLocWarps * 32, 0, st>>>(P);
+  if (n_domains > 0) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_local_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemPerWarp * kSmemWarps));
+      attr = true;
+    }
+    k_local_smem<<<(unsigned)(ws.num_sms * 1), kSmemWarps * 32, kSmemPerWarp * kSmemWarps, st>>>(P);
+    cudaMemsetAsync(ws.counters + 4, 0, sizeof(unsigned), st);
+    k_local_warp<<<(unsigned)ws.loc_ctas, kLocWarps * 32, 0, st>>>(P);
+  }
   exclusive_scan<int>(dom_group_cnt, n_domains, dom_group_off, ws.scan_tiles, st);
 }
 

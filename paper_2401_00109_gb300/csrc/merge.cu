@@ -8,8 +8,9 @@
 // earliest start within alpha.  It is computed in parallel:
 //  1. FP32 centre coordinates with rigorous relative error 2^-20 (binary64
 //     values are computed only for undecided comparisons);
-//  2. the exact order: radix sort by the FP32 key, then every run of
-//     neighbours whose key intervals overlap is re-sorted by binary64 keys;
+//  2. the exact order: a stable radix sort of the binary64 keys (computed
+//     once per item: at 10^7 centres the keys are denser than any FP32
+//     interval), ties in compact-index order;
 //  3. a uniform grid of cells of side h = alpha/2 (1 + 2^-7): two items in one
 //     cell are within alpha, so a cell holds at most one start, and it is the
 //     first of its items (in key order) not covered by an earlier start of a
@@ -117,8 +118,8 @@ __device__ __forceinline__ float of_ord(int o) {
 }
 
 __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long long cap, const long long* dom_group_off,
-                        const float* rinv, double scl, unsigned long long* keys, int* vals, int* rec_of, float* X32,
-                        float* Y32, int* bounds, const int* flags) {
+                        const float* rinv, const double* sigma, double scl, unsigned long long* keys, int* vals,
+                        int* rec_of, float* X32, float* Y32, int* bounds, const int* flags) {
   if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
   const float rl = rinv[0], ri = rinv[1], sc = (float)scl;
@@ -154,7 +155,9 @@ __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long lo
     const float y = __fdiv_rn(incf, cnt) * ri;
     X32[c] = x;
     Y32[c] = y;
-    keys[c] = (unsigned long long)__float_as_uint(fmaf(x, x, y * y));
+    // the order needs the binary64 key itself: 2e7 centres are denser than any
+    // FP32 key interval, so every item computes it (4 divisions, once)
+    keys[c] = (unsigned long long)__double_as_longlong(exact_key(exact_centre(g, sigma[0], sigma[1], scl)));
     vals[c] = (int)c;
     rec_of[c] = (int)r;
     mnx = min(mnx, ord_of(x));
@@ -271,56 +274,6 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
   }
   *kres = kin;
   *vres = vin;
-}
-
-// ------------------------------------------------------------------ 2. exact order
-__device__ __forceinline__ bool keys_overlap(unsigned k0, unsigned k1) {
-  // intervals key32 (1 +- 2^-18) overlap (with FP32 rounding slack)
-  return __uint_as_float(k1) * (1.0f - 0x1p-18f) <= __uint_as_float(k0) * (1.0f + 0x1p-18f) * (1.0f + 0x1p-22f);
-}
-
-// Runs of overlapping neighbours, marked from the untouched sorted keys:
-// link[a] = 1 when the intervals of a and a + 1 overlap.
-__global__ void k_mlinks(const unsigned long long* skey, const long long* n_p, long long cap, const int* flags,
-                         int* link) {
-  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
-  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < cap; a += (long long)gridDim.x * blockDim.x)
-    link[a] = (a + 1 < n && keys_overlap((unsigned)skey[a], (unsigned)skey[a + 1])) ? 1 : 0;
-}
-
-// Each run is re-sorted by binary64 keys (ties by compact index) by the
-// thread that owns its first element; runs are read from link[], never from
-// keys another thread may be moving.
-__global__ void k_mfix(unsigned long long* skey, int* sidx, const int* link, const long long* n_p, long long cap,
-                       const jabba_group* groups, const int* rec_of, const double* sigma, double scl,
-                       const int* flags) {
-  if (flags[1]) return;
-  const long long n = clamp_groups(n_p, cap);
-  const double sl = sigma[0], si = sigma[1];
-  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a + 1 < n; a += (long long)gridDim.x * blockDim.x) {
-    if (!link[a] || (a > 0 && link[a - 1])) continue;  // not the head of a run
-    long long b = a + 1;
-    while (b + 1 < n && link[b]) ++b;
-    for (long long u = a + 1; u <= b; ++u) {
-      const int cu = sidx[u];
-      const unsigned long long ku32 = skey[u];
-      const double ku = exact_key(exact_centre(groups[rec_of[cu]], sl, si, scl));
-      long long v = u - 1;
-      while (v >= a) {
-        const int cv = sidx[v];
-        const double kv = exact_key(exact_centre(groups[rec_of[cv]], sl, si, scl));
-        if (kv > ku || (kv == ku && cv > cu)) {
-          sidx[v + 1] = cv;
-          skey[v + 1] = skey[v];
-          --v;
-        } else {
-          break;
-        }
-      }
-      sidx[v + 1] = cu;
-      skey[v + 1] = ku32;
-    }
-  }
 }
 
 // Sorted-order copies of the coordinates, the cell of each item, and checks
@@ -860,13 +813,13 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   long long* offs = (long long*)ws.d_acc;  // reused before the dictionary accumulation
   k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.flags, status, n_groups, cap);
   k_mrinv<<<1, 1, 0, st>>>(sigma, B.rinv);
-  k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, B.rinv, scl, ws.m_k0, ws.m_v0, ws.m_rec,
+  k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, B.rinv, sigma, scl, ws.m_k0, ws.m_v0, ws.m_rec,
                                 ws.m_X32, ws.m_Y32, B.bounds, B.flags);
   unsigned long long* skey;
   int* sidx;
-  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 32, ws, offs, &skey, &sidx, B.flags, st);
-  k_mlinks<<<grid, 256, 0, st>>>(skey, n_groups, cap, B.flags, B.head);
-  k_mfix<<<grid, 256, 0, st>>>(skey, sidx, B.head, n_groups, cap, groups, ws.m_rec, sigma, scl, B.flags);
+  // keys are non-negative binary64: their bit patterns order as the values;
+  // the sort is stable and starts in compact-index order, so ties keep it
+  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws, offs, &skey, &sidx, B.flags, st);
   k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
   // the cell sort ping-pongs in the buffers the key sort left free
   unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
