@@ -98,6 +98,66 @@ __device__ __forceinline__ float key_stop(float key_start, float alpha_up) {
   return r * r * (1.0f + 0x1p-18f);
 }
 
+
+// Runs of neighbours whose key intervals overlap, found 32 pairs at a time;
+// lane 0 re-sorts each run (insertion sort) by the binary64 keys, ties by
+// position.  KeyT/IdxT: the key (FP32 bits) and position arrays of the view.
+__device__ __forceinline__ bool keys_overlap32(unsigned k0, unsigned k1) {
+  return __uint_as_float(k1) * (1.0f - kKeyRel) <= __uint_as_float(k0) * (1.0f + kKeyRel) * (1.0f + 0x1p-22f);
+}
+
+template <typename IdxT>
+__device__ void sort_run(const LocalParams& P, const int* plen, const double* pinc, unsigned* key, IdxT* idx, int a,
+                         int b) {
+  for (int u = a + 1; u <= b; ++u) {
+    const int pu = idx[u];
+    const unsigned ku32 = key[u];
+    const double ku = key64_of(P, plen[pu], pinc[pu]);
+    int v = u - 1;
+    while (v >= a) {
+      const int pv = idx[v];
+      const double kv = key64_of(P, plen[pv], pinc[pv]);
+      if (kv > ku || (kv == ku && pv > pu)) {
+        idx[v + 1] = (IdxT)pv;
+        key[v + 1] = key[v];
+        --v;
+      } else {
+        break;
+      }
+    }
+    idx[v + 1] = (IdxT)pu;
+    key[v + 1] = ku32;
+  }
+}
+
+// Runs of neighbours whose key intervals overlap, found 32 pairs at a time
+// (links from the keys as sorted: a run's last key bounds all its members, so
+// the order across runs is settled by the FP32 keys); lane 0 re-sorts each
+// run by the binary64 keys, ties by position.
+template <typename IdxT>
+__device__ void fix_runs(const LocalParams& P, const int* plen, const double* pinc, unsigned* key, IdxT* idx, int n) {
+  const int lane = threadIdx.x & 31;
+  int run_start = -1;                          // run open across chunks (uniform)
+  for (int a0 = 0; a0 + 1 < n; a0 += 32) {
+    const int a = a0 + lane;
+    const bool link = a + 1 < n && keys_overlap32(key[a], key[a + 1]);
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, link);
+    if (m == 0 && run_start < 0) continue;
+    for (int l = 0; l < 32 && a0 + l + 1 < n; ++l) {
+      const bool lk = (m >> l) & 1u;
+      if (lk && run_start < 0) {
+        run_start = a0 + l;
+      } else if (!lk && run_start >= 0) {
+        if (lane == 0) sort_run<IdxT>(P, plen, pinc, key, idx, run_start, a0 + l);
+        __syncwarp();
+        run_start = -1;
+      }
+    }
+  }
+  if (run_start >= 0 && lane == 0) sort_run<IdxT>(P, plen, pinc, key, idx, run_start, n - 1);
+  __syncwarp();
+}
+
 // Counting-sort scratch view of one warp's arena.
 struct Arena {
   unsigned* key;   // key32 bits (sorted in place with sidx)
@@ -215,48 +275,7 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
     if (n > 1) warp_radix_sort(A.key, A.sidx, A.tk, A.tv, n, hist);
     __syncwarp();
     // 3. runs of overlapping key intervals: re-sort by the binary64 keys
-    {
-      bool any = false;
-      for (int a = lane; a + 1 < n; a += 32) {
-        const float k0 = __uint_as_float(A.key[a]), k1 = __uint_as_float(A.key[a + 1]);
-        if (k1 * (1.0f - kKeyRel) <= k0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f)) any = true;
-      }
-      if (__any_sync(0xFFFFFFFFu, any) && lane == 0) {
-        // sequential pass over the sorted list (rare): find runs, insertion-sort each
-        int a = 0;
-        while (a + 1 < n) {
-          int b = a;
-          while (b + 1 < n) {
-            const float k0 = __uint_as_float(A.key[b]), k1 = __uint_as_float(A.key[b + 1]);
-            if (k1 * (1.0f - kKeyRel) <= k0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f)) ++b; else break;
-          }
-          if (b > a) {
-            // run a..b: insertion sort by (key64, position); key32 moves with its piece
-            for (int u = a + 1; u <= b; ++u) {
-              const int pu = A.sidx[u];
-              const unsigned ku32 = A.key[u];
-              const double ku = key64_of(P, plen[pu], pinc[pu]);
-              int v = u - 1;
-              while (v >= a) {
-                const int pv = A.sidx[v];
-                const double kv = key64_of(P, plen[pv], pinc[pv]);
-                if (kv > ku || (kv == ku && pv > pu)) {
-                  A.sidx[v + 1] = pv;
-                  A.key[v + 1] = A.key[v];
-                  --v;
-                } else {
-                  break;
-                }
-              }
-              A.sidx[v + 1] = pu;
-              A.key[v + 1] = ku32;
-            }
-          }
-          a = b + 1;
-        }
-      }
-      __syncwarp();
-    }
+    fix_runs<int>(P, plen, pinc, A.key, A.sidx, n);
     // 4. greedy in key order
     int G = 0;
     {
@@ -468,59 +487,12 @@ __global__ void __launch_bounds__(kSmemWarps * 32) k_local_smem(LocalParams P) {
     if (n > 1) warp_radix_sort16(key, idx, tk, tv, n, hist);
     __syncwarp();
     // 3. runs of overlapping key intervals: re-sort by the binary64 keys (rare)
-    {
-      bool any = false;
-      for (int a = lane; a + 1 < n; a += 32) {
-        const float k0 = __uint_as_float(key[a]), k1 = __uint_as_float(key[a + 1]);
-        if (k1 * (1.0f - kKeyRel) <= k0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f)) any = true;
-      }
-      if (__any_sync(0xFFFFFFFFu, any) && lane == 0) {
-        int a = 0;
-        while (a + 1 < n) {
-          int b = a;
-          while (b + 1 < n) {
-            const float k0 = __uint_as_float(key[b]), k1 = __uint_as_float(key[b + 1]);
-            if (k1 * (1.0f - kKeyRel) <= k0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f)) ++b; else break;
-          }
-          for (int u = a + 1; u <= b; ++u) {
-            const int pu = idx[u];
-            const unsigned ku32 = key[u];
-            const double ku = key64_of(P, plen[pu], pinc[pu]);
-            int v = u - 1;
-            while (v >= a) {
-              const int pv = idx[v];
-              const double kv = key64_of(P, plen[pv], pinc[pv]);
-              if (kv > ku || (kv == ku && pv > pu)) {
-                idx[v + 1] = (unsigned short)pv;
-                key[v + 1] = key[v];
-                --v;
-              } else {
-                break;
-              }
-            }
-            idx[v + 1] = (unsigned short)pu;
-            key[v + 1] = ku32;
-          }
-          a = b + 1;
-        }
-      }
-      __syncwarp();
-    }
-    // 4. coordinates in key order (sX in the sort temp; Y's slot keeps sY after X is read)
+    fix_runs<unsigned short>(P, plen, pinc, key, idx, n);
+    // 4. coordinates in key order: sX into the sort temp, then sY into X's slot
     for (int a = lane; a < n; a += 32) sX[a] = X[idx[a]];
     __syncwarp();
-    float yv[kSmemItems / 32];
-#pragma unroll
-    for (int r = 0; r < kSmemItems / 32; ++r) {
-      const int a = r * 32 + lane;
-      yv[r] = a < n ? Y[idx[a]] : 0.f;
-    }
+    for (int a = lane; a < n; a += 32) sY[a] = Y[idx[a]];
     __syncwarp();
-#pragma unroll
-    for (int r = 0; r < kSmemItems / 32; ++r) {
-      const int a = r * 32 + lane;
-      if (a < n) sY[a] = yv[r];
-    }
     for (int a = lane; a < n; a += 32) lab[a] = -1;
     __syncwarp();
     // 5. greedy in key order
@@ -606,6 +578,7 @@ __global__ void __launch_bounds__(kSmemWarps * 32) k_local_smem(LocalParams P) {
         const int s0 = g ? cnt[g - 1] : 0;
         I192 acc = {0, 0, 0};
         long long lensum = 0;
+#pragma unroll 4
         for (int q = s0; q < e; ++q) {
           const int i = mem[q];
           lensum += plen[i];

@@ -425,6 +425,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) 
 }
 
 constexpr int kCoverChunk = 1024;  // items of one neighbour cell per phase-B work unit
+constexpr int kScanChunks = 2;     // chunks of 32 a blocking scan reads before it waits instead
 
 // Evaluate one undecided cell (whole warp): skip its covered items; its first
 // uncovered item p becomes the cell's start unless a neighbouring start that
@@ -481,7 +482,11 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
       }
       if (sv != kUndecided) continue;
       const int qe = R.cell_end[q];
-      for (int u0 = (int)(sq >> 32); u0 < qe; u0 += 32) {
+      // bounded scan: if the first kScanChunks chunks do not settle it, wait
+      int u0 = (int)(sq >> 32);
+      for (int ch = 0;; ++ch, u0 += 32) {
+        if (u0 >= qe) break;
+        if (ch == kScanChunks) { blocked = true; break; }
         const int u = u0 + lane;
         bool past = true, hit = false;
         if (u < qe) {
