@@ -128,6 +128,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.cov = (unsigned char*)take(G > 0 ? G : 1);
     B.new_list = (int*)take(8 * (G > 0 ? G : 1));
     B.chg_list = (int*)take(8 * (G > 0 ? G : 1));
+    B.new_nb = (int*)take(8 * 25 * (G > 0 ? G : 1));
     B.eval_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.chg_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.lab = (int*)take(4 * G);

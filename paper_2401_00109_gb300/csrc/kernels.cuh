@@ -28,6 +28,7 @@ struct MergeBufs {
   unsigned char* cov = nullptr;      // [cap] covered flags (cell order)
   int* new_list = nullptr;           // [2 * cap] cells that created a start (per round parity)
   int* chg_list = nullptr;           // [2 * cap] cells that changed (per round parity)
+  int* new_nb = nullptr;             // [2 * 25 * cap] neighbour cells of the new starts
   unsigned* eval_stamp = nullptr;    // [cap]
   unsigned* chg_stamp = nullptr;     // [cap]
   int* lab = nullptr;                // [cap]

@@ -381,6 +381,7 @@ struct RoundArgs {
   unsigned long long* state;
   unsigned char* cov;       // [t] item covered by a start (not a start itself)
   int* new_list;            // [2][n_cells] cells that created a start this round
+  int* new_nb;              // [2][n_cells][25] their 5 x 5 neighbour cells
   int* chg_list;            // [2][n_cells] cells whose state or coverage changed this round
   unsigned* eval_stamp;     // [n_cells] last round + 1 in which the cell was evaluated
   unsigned* chg_stamp;      // [n_cells] last round + 1 in which the cell was listed as changed
@@ -432,9 +433,13 @@ constexpr int kScanChunks = 2;     // chunks of 32 a blocking scan reads before 
 // precedes p covers it (decided in this round, so its coverage is not marked
 // yet), or an uncovered item of an undecided neighbouring cell precedes p and
 // may lie within alpha (it could still become a start covering p).  Lane k
-// examines neighbour k of the 5 x 5 block.  Returns whether the state changed.
+// (< 25) looks after neighbour k of the 5 x 5 block (geometry, state, the
+// start test); the neighbours that need an item scan are then scanned by the
+// whole warp, at most kScanChunks chunks each (past that the cell waits).
+// A new start records its neighbour cells for phase B.  Returns whether the
+// state changed.
 __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g, long long j, int* list,
-                                          unsigned* n_list) {
+                                          unsigned* n_list, int* nb_list) {
   const int lane = threadIdx.x & 31;
   const unsigned long long st = ld_state(&R.state[j]);
   if ((unsigned)st != kUndecided) return false;
@@ -449,6 +454,7 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
     if (t >= end) { t = end; break; }
   }
   unsigned result = kUndecided;
+  int myq = -1;
   if (t >= end) {
     result = kNoStart;
   } else {
@@ -460,30 +466,40 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
     // within alpha of p (margins cover the FP32 coordinates and cell mapping)
     const float reach = sqrtf(R.V.a2hi) * (1.0f + 0x1p-10f) +
                         0x1p-16f * (fabsf(px) + fabsf(py) + fabsf(g.x0) + fabsf(g.y0) + 4.0f * g.h);
-    bool blocked = false;
-    for (int k = 0; k < 25 && !blocked; ++k) {
-      if (k == 12) continue;
-      const int xx = cx + k % 5 - 2, yy = cy + k / 5 - 2;
-      if (xx < 0 || xx >= g.ncx || yy < 0 || yy >= g.ncy) continue;
-      {  // distance from p to the cell rectangle
-        const float rx0 = g.x0 + xx * g.h, ry0 = g.y0 + yy * g.h;
-        const float ddx = fmaxf(fmaxf(rx0 - px, px - (rx0 + g.h)), 0.f);
-        const float ddy = fmaxf(fmaxf(ry0 - py, py - (ry0 + g.h)), 0.f);
-        if (ddx > reach || ddy > reach || fmaf(ddx, ddx, ddy * ddy) > reach * reach) continue;
+    bool blk = false, scan = false;
+    unsigned long long sq = 0;
+    if (lane < 25) {
+      const int xx = cx + lane % 5 - 2, yy = cy + lane / 5 - 2;
+      if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) {
+        const int q = R.cell_of_id[yy * g.ncx + xx];
+        myq = q;
+        if (q >= 0 && lane != 12) {
+          const float rx0 = g.x0 + xx * g.h, ry0 = g.y0 + yy * g.h;
+          const float ddx = fmaxf(fmaxf(rx0 - px, px - (rx0 + g.h)), 0.f);
+          const float ddy = fmaxf(fmaxf(ry0 - py, py - (ry0 + g.h)), 0.f);
+          if (!(ddx > reach || ddy > reach || fmaf(ddx, ddx, ddy * ddy) > reach * reach)) {
+            sq = ld_state(&R.state[q]);
+            const unsigned sv = (unsigned)sq;
+            if (sv < kNoStart) {
+              // a start decided this round has not marked its coverage yet
+              if ((int)sv < p && within_sorted(R.V, (int)sv, p)) blk = true;
+            } else if (sv == kUndecided) {
+              const int u0 = (int)(sq >> 32);
+              scan = u0 < R.cell_end[q] && R.cord[u0] < p;
+            }
+          }
+        }
       }
-      const int q = R.cell_of_id[yy * g.ncx + xx];
-      if (q < 0) continue;
-      const unsigned long long sq = ld_state(&R.state[q]);
-      const unsigned sv = (unsigned)sq;
-      if (sv < kNoStart) {
-        // a start decided this round has not marked its coverage yet
-        if ((int)sv < p && within_sorted(R.V, (int)sv, p)) blocked = true;
-        continue;
-      }
-      if (sv != kUndecided) continue;
+    }
+    bool blocked = __any_sync(0xFFFFFFFFu, blk);
+    unsigned sm = __ballot_sync(0xFFFFFFFFu, scan);
+    while (!blocked && sm) {
+      const int l = __ffs(sm) - 1;
+      sm &= sm - 1;
+      const int q = __shfl_sync(0xFFFFFFFFu, myq, l);
+      const unsigned long long qs = __shfl_sync(0xFFFFFFFFu, sq, l);
       const int qe = R.cell_end[q];
-      // bounded scan: if the first kScanChunks chunks do not settle it, wait
-      int u0 = (int)(sq >> 32);
+      int u0 = (int)(qs >> 32);
       for (int ch = 0;; ++ch, u0 += 32) {
         if (u0 >= qe) break;
         if (ch == kScanChunks) { blocked = true; break; }
@@ -502,9 +518,17 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
   }
   const unsigned long long ns = ((unsigned long long)(unsigned)t << 32) | result;
   const bool changed = ns != st;
+  int slot = 0;
   if (lane == 0) {
     if (changed) atomicExch(&R.state[j], ns);
-    if (result < kNoStart) list[atomicAdd(n_list, 1u)] = (int)j;
+    if (result < kNoStart) {
+      slot = (int)atomicAdd(n_list, 1u);
+      list[slot] = (int)j;
+    }
+  }
+  if (result < kNoStart) {
+    slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
+    if (lane < 25) nb_list[(size_t)slot * 25 + lane] = myq;     // neighbour cells for phase B (-1: none)
   }
   return changed;
 }
@@ -535,6 +559,7 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
   for (unsigned round = 0; round < R.max_rounds; ++round) {
     const int par = round & 1;
     int* list = R.new_list + (size_t)par * stride;         // new starts of this round
+    int* nbl = R.new_nb + (size_t)par * stride * 25;       // their 5 x 5 neighbour cells
     int* chg = R.chg_list + (size_t)par * stride;          // cells changed in this round
     const int* prev = R.chg_list + (size_t)(par ^ 1) * stride;
     unsigned* n_list = &R.counters[par];
@@ -543,7 +568,7 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
     // ---- phase A
     if (round == 0) {
       for (long long j = warp_g; j < n_cells; j += n_warps)
-        if (eval_cell(R, g, j, list, n_list) && lane == 0) mark_changed(R, j, round, chg, n_chg);
+        if (eval_cell(R, g, j, list, n_list, nbl) && lane == 0) mark_changed(R, j, round, chg, n_chg);
     } else {
       for (long long w = warp_g; w < (long long)n_prev * 25; w += n_warps) {
         const int c = __ldcg(&prev[w / 25]);
@@ -558,7 +583,7 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
         if (lane == 0) claim = atomicExch(&R.eval_stamp[q], round + 1);
         claim = __shfl_sync(0xFFFFFFFFu, claim, 0);
         if (claim == round + 1) continue;                    // already evaluated this round
-        if (eval_cell(R, g, q, list, n_list) && lane == 0) mark_changed(R, q, round, chg, n_chg);
+        if (eval_cell(R, g, q, list, n_list, nbl) && lane == 0) mark_changed(R, q, round, chg, n_chg);
       }
     }
     if (!grid_barrier(R.bar, nblocks, R.status)) return;
@@ -574,13 +599,10 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
       const long long si = w / (25 * 64);
       const int k = (int)((w / 64) % 25);
       const int c = (int)(w % 64);
+      const int q = __ldcg(&nbl[si * 25 + k]);
+      if (q < 0) continue;
       const int j = __ldcg(&list[si]);
       const unsigned sp = (unsigned)ld_state(&R.state[j]);
-      const int id = R.cell_id[j];
-      const int cx = id % g.ncx + k % 5 - 2, cy = id / g.ncx + k / 5 - 2;
-      if (cx < 0 || cx >= g.ncx || cy < 0 || cy >= g.ncy) continue;
-      const int q = R.cell_of_id[cy * g.ncx + cx];
-      if (q < 0) continue;
       const int qb = R.cell_beg[q], qe = R.cell_end[q];
       const int span = qe - qb;
       const int per = ((span + 63) / 64 + kCoverChunk - 1) / kCoverChunk * kCoverChunk;
@@ -864,6 +886,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   R.state = B.state;
   R.cov = (unsigned char*)B.cov;
   R.new_list = B.new_list;
+  R.new_nb = B.new_nb;
   R.chg_list = B.chg_list;
   R.eval_stamp = B.eval_stamp;
   R.chg_stamp = B.chg_stamp;
