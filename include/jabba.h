@@ -220,13 +220,39 @@ jabba_status jabba_profile_elapsed(jabba_ctx* ctx, int slot, int stage, float* m
 
 /* Diagnostic counters of the last calls (no counterpart in the paper);
  * synchronizes the device.  out[0] = admissibility decisions that needed the
- * exact FP64 evaluation in the last jabba_compress.  n = entries wanted. */
+ * exact FP64 evaluation in the last jabba_compress; out[1] = rounds of the
+ * last global merge.  n = entries wanted. */
 jabba_status jabba_diagnostics(jabba_ctx* ctx, int64_t* out, int n);
 
 /* Reconstruction error (Sec. 3.3): *out (device scalar) = (1/n) sum (x - xhat)^2,
  * summed in a fixed order (the same result on every call on a device). */
 jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int64_t n_points, double* out,
                        jabba_stream stream);
+
+/* ---------------------------------------------------------------- allocation-free reconstruction
+ * (No counterpart in the paper.)  The same result as jabba_reconstruct, for
+ * callers that cannot allocate device memory -- code that runs where
+ * cudaMalloc is not allowed or must not be called (inside a stream capture
+ * someone else owns, under an allocation-free memory budget, in a callback)
+ * and therefore cannot create a context, whose scratch comes from cudaMalloc.
+ * No context: the scratch is a fixed array in the library's own device
+ * memory (JABBA_NOALLOC_MAX_PIECES pieces and JABBA_NOALLOC_MAX_SERIES series,
+ * about 4.5 MB, held by every GPU that loads the library until the process
+ * exits).  Larger inputs return JABBA_ERR_CAPACITY; nothing is allocated or
+ * freed.  The first call on a device looks up the array's device address
+ * (set-up, once per device): make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, concurrent host threads)
+ * race and must be serialized by the caller.  Arguments as for
+ * jabba_reconstruct, plus n_pieces (host value, the number of compact
+ * symbols) and round_mode. */
+#define JABBA_NOALLOC_MAX_PIECES (1 << 18)
+#define JABBA_NOALLOC_MAX_SERIES (1 << 14)
+jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_points, const int64_t* series_off,
+                                       int64_t n_series, const int64_t* series_dom_off,
+                                       const int64_t* dom_piece_off, int64_t n_pieces, const int32_t* symbol,
+                                       const double* dict_len, const double* dict_inc, int32_t round_mode,
+                                       int32_t* qlen, double* xhat, jabba_stream stream);
 
 #ifdef __cplusplus
 }

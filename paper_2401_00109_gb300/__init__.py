@@ -101,6 +101,7 @@ def load():
                 "jabba_mse": (C.c_int, [V, V, V, I64, V, V]),
                 "jabba_profile_slot": (C.c_int, [V, C.c_int]),
                 "jabba_diagnostics": (C.c_int, [V, C.POINTER(C.c_int64), C.c_int]),
+                "jabba_reconstruct_noalloc": (C.c_int, [V, I64, V, I64, V, V, I64, V, V, V, C.c_int32, V, V, V]),
                 "jabba_profile_elapsed": (C.c_int, [V, C.c_int, C.c_int, C.POINTER(C.c_float)]),
             }
             for name, (res, args) in sig.items():
@@ -301,10 +302,10 @@ class Context:
         return grad[:k]
 
     def diagnostics(self):
-        """{'exact_decisions': ...} of the last compress call."""
-        out = (C.c_int64 * 1)()
-        _check(self.lib.jabba_diagnostics(self.h, out, 1), "jabba_diagnostics")
-        return dict(exact_decisions=int(out[0]))
+        """Counters of the last calls: exact compression decisions, merge rounds."""
+        out = (C.c_int64 * 2)()
+        _check(self.lib.jabba_diagnostics(self.h, out, 2), "jabba_diagnostics")
+        return dict(exact_decisions=int(out[0]), merge_rounds=int(out[1]))
 
     def profile_slot(self, slot: int):
         _check(self.lib.jabba_profile_slot(self.h, int(slot)), "jabba_profile_slot")
@@ -320,6 +321,32 @@ class Context:
         _check(self.lib.jabba_mse(self.h, _ptr(x), _ptr(xhat), x.numel(), _ptr(out), self._stream(stream)),
                "jabba_mse")
         return out
+
+
+NOALLOC_MAX_PIECES = 1 << 18
+NOALLOC_MAX_SERIES = 1 << 14
+
+
+def reconstruct_noalloc(x, series_off, out: dict, p: Params, qlen=None, xhat=None, dict_inc=None, stream=None):
+    """jabba_reconstruct_noalloc: the reconstruction without a context and
+    without any device allocation by the library (fixed internal scratch;
+    at most NOALLOC_MAX_PIECES pieces and NOALLOC_MAX_SERIES series).  The
+    output buffers may be passed in (qlen, xhat) so that nothing is
+    allocated on this path at all."""
+    torch = _torch()
+    L = load()
+    s = torch.cuda.current_stream(x.device) if stream is None else stream
+    N = int(out["n_pieces"])
+    if qlen is None:
+        qlen = torch.empty(max(N, 1), dtype=torch.int32, device=x.device)
+    if xhat is None:
+        xhat = torch.empty_like(x)
+    di = out["dict_inc"] if dict_inc is None else dict_inc
+    _check(L.jabba_reconstruct_noalloc(
+        _ptr(x), x.numel(), _ptr(series_off), out["n_series"], _ptr(out["series_dom_off"]), _ptr(out["dom_piece_off"]),
+        N, _ptr(out["symbol"]), _ptr(out["dict_len"]), _ptr(di), int(p.round_mode), _ptr(qlen), _ptr(xhat),
+        V(s.cuda_stream)), "jabba_reconstruct_noalloc")
+    return qlen[:N], xhat
 
 
 def _autograd_function():

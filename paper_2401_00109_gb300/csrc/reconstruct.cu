@@ -227,3 +227,82 @@ void launch_mse(const double* x, const double* xhat, long long n, double* out, S
 }
 
 }  // namespace jabba
+
+
+// ------------------------------------------------------------------ allocation-free reconstruction
+// Scratch of jabba_reconstruct_noalloc: a file-scope array in the library's
+// device memory instead of context memory.  Host code may not use the
+// symbol's name as a device address: set-up looks the address up once per
+// device (cudaGetSymbolAddress, that device current) and the kernels get it
+// as a plain pointer.
+#include <mutex>
+
+namespace {
+
+constexpr long long kNaPieces = JABBA_NOALLOC_MAX_PIECES;
+constexpr long long kNaSeries = JABBA_NOALLOC_MAX_SERIES;
+// layout (8-byte words): level[kNaPieces] | pos[kNaPieces] | spo[kNaSeries + 1] |
+// tail_pos[kNaSeries] | tail_level[kNaSeries]
+constexpr long long kNaWords = 2 * kNaPieces + 3 * (kNaSeries + 1);
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNaWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned long long* g_na_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device (set-up on first use).
+cudaError_t noalloc_scratch(unsigned long long** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_na_ptr[dev] = (unsigned long long*)p;
+  }
+  *out = g_na_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_points, const int64_t* series_off,
+                                                  int64_t n_series, const int64_t* series_dom_off,
+                                                  const int64_t* dom_piece_off, int64_t n_pieces,
+                                                  const int32_t* symbol, const double* dict_len,
+                                                  const double* dict_inc, int32_t round_mode, int32_t* qlen,
+                                                  double* xhat, jabba_stream stream) {
+  using namespace jabba;
+  if (n_points < 0 || n_series < 0 || n_pieces < 0 || (round_mode != 0 && round_mode != 1))
+    return JABBA_ERR_INVALID_ARG;
+  if (n_series > 0 && (!x || !series_off || !series_dom_off || !dom_piece_off || !xhat)) return JABBA_ERR_INVALID_ARG;
+  if (n_pieces > 0 && (!symbol || !dict_len || !dict_inc || !qlen)) return JABBA_ERR_INVALID_ARG;
+  if (n_pieces > kNaPieces || n_series > kNaSeries) return JABBA_ERR_CAPACITY;
+  if (n_series == 0) return JABBA_OK;
+  unsigned long long* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return JABBA_ERR_CUDA;
+  double* level = (double*)base;
+  long long* pos = (long long*)(base + kNaPieces);
+  long long* spo = (long long*)(base + 2 * kNaPieces);
+  long long* tail_pos = spo + (kNaSeries + 1);
+  double* tail_level = (double*)(tail_pos + kNaSeries);
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned g = (unsigned)(sms > 0 ? sms * 8 : 8);
+  // every scratch entry these kernels read is written earlier in the same call
+  k_series_piece_off<<<g, 256, 0, st>>>((const long long*)series_dom_off, (const long long*)dom_piece_off, n_series,
+                                        spo);
+  k_recon_seq<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(x, (const long long*)series_off, n_series, spo,
+                                                                   symbol, dict_len, dict_inc, round_mode, nullptr,
+                                                                   qlen, level, pos, tail_pos, tail_level);
+  k_recon_fill<<<g, 256, 0, st>>>((const long long*)series_off, n_series, spo, 0, symbol, dict_inc, qlen, level, pos,
+                                  xhat);
+  k_recon_ends<<<g, 256, 0, st>>>(x, (const long long*)series_off, n_series, tail_pos, tail_level, xhat);
+  return cudaGetLastError() == cudaSuccess ? JABBA_OK : JABBA_ERR_CUDA;
+}
