@@ -423,6 +423,11 @@ jabba_status jabba_diagnostics(jabba_ctx* c, int64_t* out, int n) {
   unsigned long long v = 0;
   if (cudaMemcpy(&v, c->ws.counters + 2, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return JABBA_ERR_CUDA;
   out[0] = (int64_t)v;
+  if (n > 1 && c->ws.mb.bar) {
+    unsigned r = 0;
+    if (cudaMemcpy(&r, c->ws.mb.bar + 2, sizeof r, cudaMemcpyDeviceToHost) != cudaSuccess) return JABBA_ERR_CUDA;
+    out[1] = (int64_t)r;
+  }
   return JABBA_OK;
 }
 

@@ -622,7 +622,10 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
     if (!grid_barrier(R.bar, nblocks, R.status)) return;
     // nothing changed: a fixed point, where every cell is decided (the
     // earliest undecided candidate always progresses); k_mcheck verifies it
-    if (*((volatile unsigned*)n_chg) == 0) return;
+    if (*((volatile unsigned*)n_chg) == 0) {
+      if (warp_g == 0 && lane == 0) R.bar[2] = round + 1;  // diagnostics: rounds used
+      return;
+    }
   }
   if (warp_g == 0 && lane == 0) set_status(R.status, JABBA_ERR_TIMEOUT);
 }
@@ -802,7 +805,7 @@ __global__ void k_dict_finalize(const long long* acc, const long long* k_p, long
 
 __global__ void k_minit(int* bounds, unsigned* bar, int* flags, const unsigned* status, const long long* n_p,
                         long long cap) {
-  for (int i = 3; i < 8; ++i) bar[i] = 0;
+  for (int i = 3; i < 8; ++i) bar[i] = 0;  // [2] rounds used, [4..5] new starts, [6..7] changed cells
   flags[0] = 0;
   flags[1] = (*status != 0u || *n_p > cap) ? 1 : 0;  // earlier error: leave the merge outputs alone
   bounds[0] = 0x7FFFFFFF;
