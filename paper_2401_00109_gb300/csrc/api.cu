@@ -91,15 +91,10 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     w.cap_len = cap_len;
     w.cap_items = cap_len;
   }
-  w.m_key = (double*)take(8 * G);
-  w.m_X = (double*)take(8 * G);
-  w.m_Y = (double*)take(8 * G);
-  w.m_idx = (int*)take(4 * G);
   w.m_k0 = (unsigned long long*)take(8 * G);
   w.m_k1 = (unsigned long long*)take(8 * G);
   w.m_v0 = (int*)take(4 * G);
   w.m_v1 = (int*)take(4 * G);
-  w.m_label = (int*)take(4 * G);
   w.m_rec = (int*)take(4 * G);
   w.m_hist = (unsigned*)take(4 * 256 * ((G + 4095) / 4096 + 1));
   w.m_X32 = (float*)take(4 * G);
@@ -115,7 +110,6 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.flags = (int*)take(16);
     B.sX = (float*)take(4 * G);
     B.sY = (float*)take(4 * G);
-    B.rank = (int*)take(4 * G);
     B.ck1 = (unsigned long long*)take(8 * G);
     B.cv1 = (int*)take(4 * G);
     B.head = (int*)take(4 * G);
@@ -125,10 +119,17 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.cell_end = (int*)take(4 * G);
     B.cell_id = (int*)take(4 * G);
     B.state = (unsigned long long*)take(8 * G);
-    B.cov = (unsigned char*)take(G > 0 ? G : 1);
-    B.new_list = (int*)take(8 * (G > 0 ? G : 1));
+    // a round creates at most one start per non-empty cell
+    const long long slots = (G < cells ? G : cells) + 1;
+    B.cX = (float*)take(4 * G);
+    B.cY = (float*)take(4 * G);
+    B.cov = (unsigned char*)take((G > 0 ? G : 1) + 64);  // 16-byte loads read past the last item
     B.chg_list = (int*)take(8 * (G > 0 ? G : 1));
-    B.new_nb = (int*)take(8 * 25 * (G > 0 ? G : 1));
+    B.s_pos = (int*)take(4 * slots);
+    B.s_base = (unsigned*)take(4 * slots);
+    B.s_pre = (unsigned*)take(4 * 26 * slots);
+    B.s_q = (int*)take(4 * 25 * slots);
+    B.s_lo = (int*)take(4 * 25 * slots);
     B.eval_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.chg_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.lab = (int*)take(4 * G);

@@ -15,7 +15,6 @@ struct MergeBufs {
   int* flags = nullptr;              // [4] [0] = sequential fallback
   float* sX = nullptr;               // [cap] FP32 coordinates in key order
   float* sY = nullptr;
-  int* rank = nullptr;               // [cap] key-order position of compact index c
   unsigned long long* ck1 = nullptr; // [cap] cell sort ping-pong
   int* cv1 = nullptr;
   int* head = nullptr;               // [cap]
@@ -25,10 +24,15 @@ struct MergeBufs {
   int* cell_end = nullptr;
   int* cell_id = nullptr;
   unsigned long long* state = nullptr;  // [cap]
-  unsigned char* cov = nullptr;      // [cap] covered flags (cell order)
-  int* new_list = nullptr;           // [2 * cap] cells that created a start (per round parity)
+  float* cX = nullptr;               // [cap] FP32 coordinates in cell order
+  float* cY = nullptr;
+  unsigned char* cov = nullptr;      // [cap + 64] covered flags (cell order)
   int* chg_list = nullptr;           // [2 * cap] cells that changed (per round parity)
-  int* new_nb = nullptr;             // [2 * 25 * cap] neighbour cells of the new starts
+  int* s_pos = nullptr;              // [slots] new starts of a round: sorted position
+  unsigned* s_base = nullptr;        // [slots] first coverage unit
+  unsigned* s_pre = nullptr;         // [26 * slots] coverage units per neighbour
+  int* s_q = nullptr;                // [25 * slots] neighbour cells to cover
+  int* s_lo = nullptr;               // [25 * slots] first item to test there
   unsigned* eval_stamp = nullptr;    // [cap]
   unsigned* chg_stamp = nullptr;     // [cap]
   int* lab = nullptr;                // [cap]
@@ -63,15 +67,10 @@ struct Scratch {
   float* rinv32 = nullptr;
   unsigned char* big = nullptr;
   // merge
-  double* m_key = nullptr;        // [cap_groups] sort keys, then sorted keys
-  double* m_X = nullptr;          // [cap_groups] normalised centre coordinates (compact index)
-  double* m_Y = nullptr;
-  int* m_idx = nullptr;           // [cap_groups] compact index, sorted by key
   unsigned long long* m_k0 = nullptr;  // radix sort ping-pong
   unsigned long long* m_k1 = nullptr;
   int* m_v0 = nullptr;
   int* m_v1 = nullptr;
-  int* m_label = nullptr;         // [cap_groups] global id per compact index
   float* m_X32 = nullptr;         // [cap_groups] FP32 centre coordinates (compact index)
   float* m_Y32 = nullptr;
   long long cap_cells = 0;        // grid cells of the merge

@@ -314,7 +314,7 @@ __device__ __forceinline__ int cell_of(const GridGeom& g, float x, float y) {
 }
 
 __global__ void k_msorted(const int* sidx, const float* X32, const float* Y32, const long long* n_p, long long cap,
-                          const GridGeom* geom, const int* flags, float* sX, float* sY, int* rank_of,
+                          const GridGeom* geom, const int* flags, float* sX, float* sY,
                           unsigned long long* ckey, int* cval) {
   if (flags[1]) return;
   const long long n = clamp_groups(n_p, cap);
@@ -325,18 +325,26 @@ __global__ void k_msorted(const int* sidx, const float* X32, const float* Y32, c
     const float x = X32[c], y = Y32[c];
     sX[a] = x;
     sY[a] = y;
-    rank_of[c] = (int)a;
     ckey[a] = fb ? 0ull : (unsigned long long)cell_of(g, x, y);
     cval[a] = (int)a;
   }
 }
 
-// Cell table: cells in id order; cell_of_id[id] = cell index or -1.
-__global__ void k_mcell_heads(const unsigned long long* ckey_sorted, const long long* n_p, long long cap,
-                              const int* flags, int* head) {
+// Cell table: cells in id order; cell_of_id[id] = cell index or -1.  Also
+// the FP32 coordinates in cell order.
+__global__ void k_mcell_heads(const unsigned long long* ckey_sorted, const int* cord, const float* sX,
+                              const float* sY, const long long* n_p, long long cap, const int* flags, int* head,
+                              float* cX, float* cY) {
   const long long n = clamp_groups(n_p, cap);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cap; t += (long long)gridDim.x * blockDim.x)
-    head[t] = t < n && flags[0] == 0 && flags[1] == 0 && (t == 0 || ckey_sorted[t] != ckey_sorted[t - 1]) ? 1 : 0;
+  const bool grid = flags[0] == 0 && flags[1] == 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cap; t += (long long)gridDim.x * blockDim.x) {
+    head[t] = t < n && grid && (t == 0 || ckey_sorted[t] != ckey_sorted[t - 1]) ? 1 : 0;
+    if (t < n && grid) {
+      const int a = cord[t];
+      cX[t] = sX[a];
+      cY[t] = sY[a];
+    }
+  }
 }
 
 __global__ void k_mcell_fill(const unsigned long long* ckey_sorted, const int* head, const long long* head_off,
@@ -367,29 +375,40 @@ __global__ void k_clear_i32(int* p, long long n, int v) {
 
 // ------------------------------------------------------------------ 4. rounds
 // state[j] = (ptr << 32) | s, s = 0xFFFFFFFF undecided, 0xFFFFFFFE no start,
-// else the sorted position of the cell's start.
+// else the sorted position of the cell's start; ptr = first item (cell order)
+// not known to be covered.
 constexpr unsigned kUndecided = 0xFFFFFFFFu;
 constexpr unsigned kNoStart = 0xFFFFFFFEu;
+constexpr int kCoverUnit = 256;    // items of one neighbour cell per phase-B work unit (8 per lane)
+constexpr int kScanChunks = 2;     // chunks of 32 a blocking scan reads before it waits instead
+constexpr unsigned long long kUnitMask = (1ull << 40) - 1;  // packed counter: starts << 40 | units
 
 struct RoundArgs {
   MergeView V;
   const int* cord;          // item (sorted position) at cell-order index t
-  const int* cell_beg;
+  const float* cX;          // FP32 coordinates at cell-order index t
+  const float* cY;
   const int* cell_end;
   const int* cell_id;
   const int* cell_of_id;
   unsigned long long* state;
-  unsigned char* cov;       // [t] item covered by a start (not a start itself)
-  int* new_list;            // [2][n_cells] cells that created a start this round
-  int* new_nb;              // [2][n_cells][25] their 5 x 5 neighbour cells
-  int* chg_list;            // [2][n_cells] cells whose state or coverage changed this round
+  unsigned char* cov;       // [t] item covered by a start; maintained for undecided cells only
+  // the starts created in the current round, in slot order (the order of the
+  // packed counter, so s_base is non-decreasing)
+  int* s_pos;               // [slots] sorted position of the start
+  unsigned* s_base;         // [slots] first coverage unit of the start
+  unsigned* s_pre;          // [slots][26] first unit per neighbour k (entry 25: end)
+  int* s_q;                 // [slots][25] neighbour cell to cover
+  int* s_lo;                // [slots][25] first item (cell order) to test there
+  int* chg_list;            // [2][n_cells] cells whose state or coverage changed (by round parity)
   unsigned* eval_stamp;     // [n_cells] last round + 1 in which the cell was evaluated
   unsigned* chg_stamp;      // [n_cells] last round + 1 in which the cell was listed as changed
-  unsigned* counters;       // [0..1] new-start counts, [2..3] changed counts (by round parity)
+  unsigned long long* nctr; // [2] packed new-start counters (by round parity)
+  unsigned* chg_cnt;        // [2] changed counts (by round parity)
   const long long* n_cells_p;
   const GridGeom* geom;
   const int* flags;
-  unsigned* bar;            // [0] arrival counter, [1] generation
+  unsigned* bar;            // [0] arrival counter, [1] generation, [2] rounds used
   unsigned* status;
   unsigned max_rounds;
 };
@@ -425,8 +444,34 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) 
   return ok_s != 0;
 }
 
-constexpr int kCoverChunk = 1024;  // items of one neighbour cell per phase-B work unit
-constexpr int kScanChunks = 2;     // chunks of 32 a blocking scan reads before it waits instead
+// Bits 0..3 = bytes 0..3 of w are zero (flags hold 0 or 1).
+__device__ __forceinline__ unsigned zero_nibble(unsigned w) {
+  const unsigned m = ~w & 0x01010101u;
+  return (m | (m >> 7) | (m >> 14) | (m >> 21)) & 0xFu;
+}
+
+// First index in [t, end) whose cov flag is 0, else end (whole warp; 16-byte
+// loads, 512 flags per step; the buffer is padded past its last item).
+__device__ __forceinline__ int first_uncovered(const unsigned char* cov, int t, int end) {
+  const int lane = threadIdx.x & 31;
+  for (int b = t & ~15; b < end; b += 512) {
+    const int o = b + lane * 16;
+    unsigned msk = 0;
+    if (o < end) {
+      const uint4 w = __ldcg((const uint4*)(cov + o));  // L2: flags written by other SMs
+      msk = zero_nibble(w.x) | (zero_nibble(w.y) << 4) | (zero_nibble(w.z) << 8) | (zero_nibble(w.w) << 12);
+      if (t > o) msk &= 0xFFFFu << (t - o < 16 ? t - o : 16);
+      if (end - o < 16) msk &= (1u << (end - o)) - 1u;
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, msk != 0);
+    if (bal) {
+      const int l = __ffs(bal) - 1;
+      const unsigned mm = __shfl_sync(0xFFFFFFFFu, msk, l);
+      return b + l * 16 + __ffs(mm) - 1;
+    }
+  }
+  return end;
+}
 
 // Evaluate one undecided cell (whole warp): skip its covered items; its first
 // uncovered item p becomes the cell's start unless a neighbouring start that
@@ -436,56 +481,51 @@ constexpr int kScanChunks = 2;     // chunks of 32 a blocking scan reads before 
 // (< 25) looks after neighbour k of the 5 x 5 block (geometry, state, the
 // start test); the neighbours that need an item scan are then scanned by the
 // whole warp, at most kScanChunks chunks each (past that the cell waits).
-// A new start records its neighbour cells for phase B.  Returns whether the
+// A new start takes a slot and lists, for phase B, the undecided neighbours
+// within reach with the work units their coverage needs.  Returns whether the
 // state changed.
-__device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g, long long j, int* list,
-                                          unsigned* n_list, int* nb_list) {
+__device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g, long long j,
+                                          unsigned long long* nctr) {
   const int lane = threadIdx.x & 31;
   const unsigned long long st = ld_state(&R.state[j]);
   if ((unsigned)st != kUndecided) return false;
-  int t = (int)(st >> 32);
   const int end = R.cell_end[j];
-  for (;;) {  // first uncovered item
-    const int u = t + lane;
-    const bool fr = u < end && !__ldcg(&R.cov[u]);  // L2: flags written by other SMs last round
-    const unsigned m = __ballot_sync(0xFFFFFFFFu, fr);
-    if (m) { t += __ffs(m) - 1; break; }
-    t += 32;
-    if (t >= end) { t = end; break; }
-  }
+  const int t = first_uncovered(R.cov, (int)(st >> 32), end);
   unsigned result = kUndecided;
-  int myq = -1;
+  int myq = -1, mylo = 0, myhi = 0, p = 0;
+  bool need = false;
   if (t >= end) {
     result = kNoStart;
   } else {
-    const int p = R.cord[t];
+    p = R.cord[t];
     const int id = R.cell_id[j];
     const int cx = id % g.ncx, cy = id / g.ncx;
-    const float px = R.V.sX[p], py = R.V.sY[p];
+    const float px = R.cX[t], py = R.cY[t];
     // squared distance beyond which a neighbouring cell cannot hold an item
     // within alpha of p (margins cover the FP32 coordinates and cell mapping)
     const float reach = sqrtf(R.V.a2hi) * (1.0f + 0x1p-10f) +
                         0x1p-16f * (fabsf(px) + fabsf(py) + fabsf(g.x0) + fabsf(g.y0) + 4.0f * g.h);
     bool blk = false, scan = false;
-    unsigned long long sq = 0;
-    if (lane < 25) {
+    if (lane < 25 && lane != 12) {
       const int xx = cx + lane % 5 - 2, yy = cy + lane / 5 - 2;
       if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) {
         const int q = R.cell_of_id[yy * g.ncx + xx];
-        myq = q;
-        if (q >= 0 && lane != 12) {
+        if (q >= 0) {
           const float rx0 = g.x0 + xx * g.h, ry0 = g.y0 + yy * g.h;
           const float ddx = fmaxf(fmaxf(rx0 - px, px - (rx0 + g.h)), 0.f);
           const float ddy = fmaxf(fmaxf(ry0 - py, py - (ry0 + g.h)), 0.f);
           if (!(ddx > reach || ddy > reach || fmaf(ddx, ddx, ddy * ddy) > reach * reach)) {
-            sq = ld_state(&R.state[q]);
+            const unsigned long long sq = ld_state(&R.state[q]);
             const unsigned sv = (unsigned)sq;
             if (sv < kNoStart) {
               // a start decided this round has not marked its coverage yet
               if ((int)sv < p && within_sorted(R.V, (int)sv, p)) blk = true;
             } else if (sv == kUndecided) {
-              const int u0 = (int)(sq >> 32);
-              scan = u0 < R.cell_end[q] && R.cord[u0] < p;
+              myq = q;
+              mylo = (int)(sq >> 32);
+              myhi = R.cell_end[q];
+              need = mylo < myhi;
+              scan = need && R.cord[mylo] < p;
             }
           }
         }
@@ -496,10 +536,8 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
     while (!blocked && sm) {
       const int l = __ffs(sm) - 1;
       sm &= sm - 1;
-      const int q = __shfl_sync(0xFFFFFFFFu, myq, l);
-      const unsigned long long qs = __shfl_sync(0xFFFFFFFFu, sq, l);
-      const int qe = R.cell_end[q];
-      int u0 = (int)(qs >> 32);
+      const int qe = __shfl_sync(0xFFFFFFFFu, myhi, l);
+      int u0 = __shfl_sync(0xFFFFFFFFu, mylo, l);
       for (int ch = 0;; ++ch, u0 += 32) {
         if (u0 >= qe) break;
         if (ch == kScanChunks) { blocked = true; break; }
@@ -508,7 +546,9 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
         if (u < qe) {
           const int r = R.cord[u];
           past = r >= p;
-          if (!past && !__ldcg(&R.cov[u]) && maybe_within_sorted(R.V, r, p)) hit = true;
+          if (!past && !__ldcg(&R.cov[u]) &&
+              filter_c(R.cX[u], R.cY[u], px, py, R.V.a2lo, R.V.a2hi) != 0)
+            hit = true;
         }
         if (__any_sync(0xFFFFFFFFu, hit)) { blocked = true; break; }
         if (__any_sync(0xFFFFFFFFu, past)) break;
@@ -518,17 +558,30 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
   }
   const unsigned long long ns = ((unsigned long long)(unsigned)t << 32) | result;
   const bool changed = ns != st;
-  int slot = 0;
-  if (lane == 0) {
-    if (changed) atomicExch(&R.state[j], ns);
-    if (result < kNoStart) {
-      slot = (int)atomicAdd(n_list, 1u);
-      list[slot] = (int)j;
-    }
-  }
+  if (lane == 0 && changed) atomicExch(&R.state[j], ns);
   if (result < kNoStart) {
-    slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
-    if (lane < 25) nb_list[(size_t)slot * 25 + lane] = myq;     // neighbour cells for phase B (-1: none)
+    // coverage work of the new start: ceil(items / kCoverUnit) units per neighbour
+    const unsigned cnt = need ? (unsigned)((myhi - mylo + kCoverUnit - 1) / kCoverUnit) : 0u;
+    unsigned incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(nctr, (1ull << 40) | (unsigned long long)total);
+    old = __shfl_sync(0xFFFFFFFFu, old, 0);
+    const long long slot = (long long)(old >> 40);
+    const unsigned base = (unsigned)(old & kUnitMask);
+    if (lane < 25) {
+      R.s_q[slot * 25 + lane] = need ? myq : -1;
+      R.s_lo[slot * 25 + lane] = mylo;
+    }
+    if (lane < 26) R.s_pre[slot * 26 + lane] = base + incl - cnt;
+    if (lane == 0) {
+      R.s_pos[slot] = p;
+      R.s_base[slot] = base;
+    }
   }
   return changed;
 }
@@ -539,13 +592,69 @@ __device__ __forceinline__ void mark_changed(const RoundArgs& R, long long q, un
   if (atomicExch(&R.chg_stamp[q], round + 1) != round + 1) chg[atomicAdd(n_chg, 1u)] = (int)q;
 }
 
+// Phase B: the coverage units [u, u_end) of this warp (whole warp).  Unit u of
+// start s, neighbour k, tests the items [lo + i * kCoverUnit, +kCoverUnit) of
+// cell q that follow the start in key order and are not yet covered.
+__device__ __forceinline__ void cover_units(const RoundArgs& R, unsigned u, unsigned u_end, unsigned n_new,
+                                           unsigned round, int* chg, unsigned* n_chg) {
+  const int lane = threadIdx.x & 31;
+  // the slot holding u: the last one whose first unit is <= u
+  int lo = 0, hi = (int)n_new - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldcg(&R.s_base[mid]) <= u) lo = mid; else hi = mid - 1;
+  }
+  int s = lo;
+  for (;;) {
+    const unsigned pre = lane < 26 ? __ldcg(&R.s_pre[(long long)s * 26 + lane]) : 0xFFFFFFFFu;
+    const int q_l = lane < 25 ? __ldcg(&R.s_q[(long long)s * 25 + lane]) : -1;
+    const int lo_l = lane < 25 ? __ldcg(&R.s_lo[(long long)s * 25 + lane]) : 0;
+    const int sp = __ldcg(&R.s_pos[s]);
+    const float spx = R.V.sX[sp], spy = R.V.sY[sp];
+    for (;;) {
+      const int k = 31 - __clz(__ballot_sync(0xFFFFFFFFu, pre <= u));
+      if (k >= 25) break;  // past this slot's units
+      const int q = __shfl_sync(0xFFFFFFFFu, q_l, k);
+      const unsigned pk = __shfl_sync(0xFFFFFFFFu, pre, k);
+      const int t0 = __shfl_sync(0xFFFFFFFFu, lo_l, k) + (int)(u - pk) * kCoverUnit;
+      const int t1 = min(t0 + kCoverUnit, R.cell_end[q]);
+      int rr[kCoverUnit / 32];
+      unsigned char cv[kCoverUnit / 32];
+#pragma unroll
+      for (int i = 0; i < kCoverUnit / 32; ++i) {
+        const int tt = t0 + i * 32 + lane;
+        rr[i] = tt < t1 ? __ldg(&R.cord[tt]) : -1;
+        cv[i] = tt < t1 ? __ldcg(&R.cov[tt]) : (unsigned char)1;
+      }
+      bool any = false;
+#pragma unroll
+      for (int i = 0; i < kCoverUnit / 32; ++i) {
+        const int tt = t0 + i * 32 + lane;
+        if (rr[i] > sp && !cv[i]) {
+          int f = filter_c(spx, spy, __ldg(&R.cX[tt]), __ldg(&R.cY[tt]), R.V.a2lo, R.V.a2hi);
+          if (f == 2) f = exact_within_sorted(R.V, sp, rr[i]) ? 1 : 0;
+          if (f) {
+            R.cov[tt] = 1;
+            any = true;
+          }
+        }
+      }
+      if (__any_sync(0xFFFFFFFFu, any) && lane == 0) mark_changed(R, q, round, chg, n_chg);
+      if (++u >= u_end) return;
+    }
+    if (++s >= (int)n_new) return;
+  }
+}
+
 // Rounds of the cell greedy with worklists: round r evaluates only the
 // undecided cells of the 5 x 5 blocks around cells that changed in round r-1
 // (their state, or the coverage of their items); a cell whose neighbourhood
 // did not change would reach the same verdict.  Phase A evaluates (each cell
-// once per round: eval_stamp), phase B marks the coverage of the new starts.
-// Items are covered only by true starts, and a start is declared only when no
-// undecided earlier item can cover it, so the starts are exactly those of the
+// once per round: eval_stamp), phase B marks the coverage of the new starts
+// in the undecided cells around them (a decided cell's items are all covered
+// and are not read again), split into equal units over all warps.  Items are
+// covered only by true starts, and a start is declared only when no undecided
+// earlier item can cover it, so the starts are exactly those of the
 // sequential greedy.
 __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
   if (R.flags[0] || R.flags[1]) return;
@@ -558,17 +667,15 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
   const size_t stride = (size_t)(n_cells > 0 ? n_cells : 1);
   for (unsigned round = 0; round < R.max_rounds; ++round) {
     const int par = round & 1;
-    int* list = R.new_list + (size_t)par * stride;         // new starts of this round
-    int* nbl = R.new_nb + (size_t)par * stride * 25;       // their 5 x 5 neighbour cells
     int* chg = R.chg_list + (size_t)par * stride;          // cells changed in this round
     const int* prev = R.chg_list + (size_t)(par ^ 1) * stride;
-    unsigned* n_list = &R.counters[par];
-    unsigned* n_chg = &R.counters[2 + par];
-    const unsigned n_prev = round ? *((volatile unsigned*)&R.counters[2 + (par ^ 1)]) : 0u;
+    unsigned long long* nctr = &R.nctr[par];
+    unsigned* n_chg = &R.chg_cnt[par];
+    const unsigned n_prev = round ? *((volatile unsigned*)&R.chg_cnt[par ^ 1]) : 0u;
     // ---- phase A
     if (round == 0) {
       for (long long j = warp_g; j < n_cells; j += n_warps)
-        if (eval_cell(R, g, j, list, n_list, nbl) && lane == 0) mark_changed(R, j, round, chg, n_chg);
+        if (eval_cell(R, g, j, nctr) && lane == 0) mark_changed(R, j, round, chg, n_chg);
     } else {
       for (long long w = warp_g; w < (long long)n_prev * 25; w += n_warps) {
         const int c = __ldcg(&prev[w / 25]);
@@ -583,41 +690,25 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
         if (lane == 0) claim = atomicExch(&R.eval_stamp[q], round + 1);
         claim = __shfl_sync(0xFFFFFFFFu, claim, 0);
         if (claim == round + 1) continue;                    // already evaluated this round
-        if (eval_cell(R, g, q, list, n_list, nbl) && lane == 0) mark_changed(R, q, round, chg, n_chg);
+        if (eval_cell(R, g, q, nctr) && lane == 0) mark_changed(R, q, round, chg, n_chg);
       }
     }
     if (!grid_barrier(R.bar, nblocks, R.status)) return;
     // ---- phase B
-    // every read of the other parity's counters (n_prev) happened before the
-    // barrier; they are written again only after the next barrier
+    // every read of the other parity's counters (n_prev, the previous
+    // round's new starts) happened before the barrier; they are written
+    // again only after the next barrier
     if (warp_g == 0 && lane == 0) {
-      R.counters[par ^ 1] = 0;
-      R.counters[2 + (par ^ 1)] = 0;
+      R.nctr[par ^ 1] = 0;
+      R.chg_cnt[par ^ 1] = 0;
     }
-    const unsigned n_new = *((volatile unsigned*)n_list);
-    for (long long w = warp_g; w < (long long)n_new * 25 * 64; w += n_warps) {
-      const long long si = w / (25 * 64);
-      const int k = (int)((w / 64) % 25);
-      const int c = (int)(w % 64);
-      const int q = __ldcg(&nbl[si * 25 + k]);
-      if (q < 0) continue;
-      const int j = __ldcg(&list[si]);
-      const unsigned sp = (unsigned)ld_state(&R.state[j]);
-      const int qb = R.cell_beg[q], qe = R.cell_end[q];
-      const int span = qe - qb;
-      const int per = ((span + 63) / 64 + kCoverChunk - 1) / kCoverChunk * kCoverChunk;
-      const int lo = qb + c * per;
-      const int hi = min(qe, lo + per);
-      bool any = false;
-      for (int u = lo + lane; u < hi; u += 32) {
-        const int r = R.cord[u];
-        if (r <= (int)sp || __ldcg(&R.cov[u])) continue;
-        if (q == j || within_sorted(R.V, (int)sp, r)) {
-          R.cov[u] = 1;
-          any = true;
-        }
-      }
-      if (__any_sync(0xFFFFFFFFu, any) && lane == 0 && q != j) mark_changed(R, q, round, chg, n_chg);
+    {
+      const unsigned long long ctr = *((volatile unsigned long long*)nctr);
+      const unsigned n_new = (unsigned)(ctr >> 40);
+      const unsigned total = (unsigned)(ctr & kUnitMask);
+      const unsigned per = (unsigned)(((long long)total + n_warps - 1) / n_warps);
+      const unsigned u0 = (unsigned)(warp_g * per);
+      if (per && u0 < total) cover_units(R, u0, min(total, u0 + per), n_new, round, chg, n_chg);
     }
     if (!grid_barrier(R.bar, nblocks, R.status)) return;
     // nothing changed: a fixed point, where every cell is decided (the
@@ -805,7 +896,7 @@ __global__ void k_dict_finalize(const long long* acc, const long long* k_p, long
 
 __global__ void k_minit(int* bounds, unsigned* bar, int* flags, const unsigned* status, const long long* n_p,
                         long long cap) {
-  for (int i = 3; i < 8; ++i) bar[i] = 0;  // [2] rounds used, [4..5] new starts, [6..7] changed cells
+  for (int i = 3; i < 16; ++i) bar[i] = 0;  // [2] rounds used, [4..5] changed cells, [8..11] new starts
   flags[0] = 0;
   flags[1] = (*status != 0u || *n_p > cap) ? 1 : 0;  // earlier error: leave the merge outputs alone
   bounds[0] = 0x7FFFFFFF;
@@ -854,15 +945,14 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   // the cell sort ping-pongs in the buffers the key sort left free
   unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
   int* cv0 = sidx == ws.m_v0 ? ws.m_v1 : ws.m_v0;
-  k_msorted<<<grid, 256, 0, st>>>(sidx, ws.m_X32, ws.m_Y32, n_groups, cap, B.geom, B.flags, B.sX, B.sY, B.rank,
-                                  ck0, cv0);
+  k_msorted<<<grid, 256, 0, st>>>(sidx, ws.m_X32, ws.m_Y32, n_groups, cap, B.geom, B.flags, B.sX, B.sY, ck0, cv0);
   unsigned long long* ckey;
   int* cord;
   radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 32, ws, offs, &ckey, &cord, B.flags, st);
-  k_mcell_heads<<<grid, 256, 0, st>>>(ckey, n_groups, cap, B.flags, B.head);
+  k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
-  cudaMemsetAsync(B.cov, 0, (size_t)(cap > 0 ? cap : 1), st);
+  cudaMemsetAsync(B.cov, 0, (size_t)(cap > 0 ? cap : 1) + 16, st);
   cudaMemsetAsync(B.eval_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   cudaMemsetAsync(B.chg_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   k_mcell_fill<<<grid, 256, 0, st>>>(ckey, B.head, B.head_off, n_groups, cap, B.cell_beg, B.cell_end, B.cell_id,
@@ -882,18 +972,23 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   RoundArgs R;
   R.V = V;
   R.cord = cord;
-  R.cell_beg = B.cell_beg;
+  R.cX = B.cX;
+  R.cY = B.cY;
   R.cell_end = B.cell_end;
   R.cell_id = B.cell_id;
   R.cell_of_id = B.cell_of_id;
   R.state = B.state;
-  R.cov = (unsigned char*)B.cov;
-  R.new_list = B.new_list;
-  R.new_nb = B.new_nb;
+  R.cov = B.cov;
+  R.s_pos = B.s_pos;
+  R.s_base = B.s_base;
+  R.s_pre = B.s_pre;
+  R.s_q = B.s_q;
+  R.s_lo = B.s_lo;
   R.chg_list = B.chg_list;
   R.eval_stamp = B.eval_stamp;
   R.chg_stamp = B.chg_stamp;
-  R.counters = B.bar + 4;
+  R.chg_cnt = B.bar + 4;
+  R.nctr = (unsigned long long*)(B.bar + 8);
   R.n_cells_p = B.head_off + cap;
   R.geom = B.geom;
   R.flags = B.flags;
