@@ -258,6 +258,7 @@ def run_ours(args, ws, rank, local):
     mrg_ms = [ctx.profile_elapsed(args.warmup + i, 3) for i in range(args.steps)]
     sym_ms = [ctx.profile_elapsed(args.warmup + i, 4) for i in range(args.steps)]
     res = pl.results()
+    diag = ctx.diagnostics()
     N, G, k = res["n_pieces"], res["n_groups"], res["k"]
     value = ws * n / (ms_all * 1e-3) / 1e9
 
@@ -348,7 +349,7 @@ def run_ours(args, ws, rank, local):
                     stage_ms=dict(compress=float(np.mean(comp_ms)), finish=float(np.mean(fin_ms)),
                                   local=float(np.mean(loc_ms)), merge=float(np.mean(mrg_ms)),
                                   symbolize=float(np.mean(sym_ms))),
-                    input_gen_s=t_gen)
+                    diagnostics=diag, input_gen_s=t_gen)
         print(json.dumps(line), flush=True)
 
 

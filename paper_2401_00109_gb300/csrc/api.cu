@@ -80,6 +80,8 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.scan_tiles = (long long*)take(8 * scan_n);
   w.counters = (unsigned*)take(64);
   w.dom_order = (int*)take(4 * (D > 0 ? D : 1));
+  w.loc_list = (int*)take(16 * (D > 0 ? D : 1));
+  if (base) w.loc_stride = D > 0 ? D : 1;
   w.pack_hist = (int*)take(4 * pack_buckets());
   w.pack_off = (long long*)take(8 * (pack_buckets() + 1));
   w.big = nullptr;
@@ -135,7 +137,6 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.lab = (int*)take(4 * G);
     B.is_start = (int*)take(4 * G);
     B.start_off = (long long*)take(8 * (G + 1));
-    B.gid_c = (int*)take(4 * G);
     B.eX = (double*)take(8 * G);
     B.eY = (double*)take(8 * G);
     B.ekey = (double*)take(8 * G);

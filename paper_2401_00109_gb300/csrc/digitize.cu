@@ -48,13 +48,14 @@ struct LocalParams {
   long long group_capacity;
   long long* n_groups;
   unsigned* status;
-  unsigned* task_counter;
+  unsigned* task_counter; // arena kernel: next entry of its domain list
+  const int* list;        // arena kernel: domains with more pieces than the largest tile
+  const unsigned* list_count;
   unsigned* arena;        // per-warp scratch, kArenaWords * cap_items words each
   long long cap_items;
 };
 
 constexpr int kArenaWords = 8;           // key, X32, Y32, sidx, label, tmp key, tmp val, members
-constexpr int kSmemItemsArena = 2048;   // domains up to this many pieces use k_local_smem
 
 __device__ __forceinline__ double x64_of(const LocalParams& P, int len) {
   if (len <= P.cap_len) return P.xtab64[len];
@@ -235,20 +236,20 @@ __device__ void warp_radix_sort(unsigned* key, int* val, unsigned* tk, int* tv, 
 
 __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
   __shared__ unsigned hist_all[kLocWarps][256];
-  __shared__ int cl_flag[kLocWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long warp_global = (long long)blockIdx.x * kLocWarps + warp;
   unsigned* hist = hist_all[warp];
   const Arena A = arena_of(P, warp_global);
   const double a2 = __dmul_rn(P.alpha, P.alpha);
   const float rinv = *P.rinv32;
+  const unsigned n_list = *P.list_count;
   for (;;) {
-    long long d = 0;
-    if (lane == 0) d = (long long)atomicAdd(P.task_counter, 1u);
-    d = __shfl_sync(0xFFFFFFFFu, d, 0);
-    if (d >= P.n_domains) break;
+    unsigned task = 0;
+    if (lane == 0) task = atomicAdd(P.task_counter, 1u);
+    task = __shfl_sync(0xFFFFFFFFu, task, 0);
+    if (task >= n_list) break;
+    const long long d = P.list[task];
     const int n = P.dom_piece_cnt[d];
-    if (n <= kSmemItemsArena) continue;           // the shared-memory kernel takes it
     const long long slot = P.dom_slot_off[d];
     const int* plen = P.piece_len + slot;
     const double* pinc = P.piece_inc + slot;
@@ -384,18 +385,21 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
     }
     __syncwarp();
   }
-  (void)cl_flag;
 }
 
-// ------------------------------------------------------------------ shared-memory path
-// Domains of at most kSmemItems pieces: the same steps with every per-piece
-// array in the warp's slice of shared memory, the coordinates permuted into
-// key order after the sort so that the greedy reads contiguous entries.
-constexpr int kSmemItems = 2048;
-constexpr int kSmemWarps = 4;
-// bytes per item: key 4, X/sX 4, Y/sY 4, tmp key 4, idx 2, tmp idx 2, label 2, pad 2
-constexpr size_t kSmemPerWarp = (size_t)kSmemItems * 24 + 1024;
-
+// ------------------------------------------------------------------ shared-memory tiles
+// Domains of at most CAP pieces: W warps (one warp, or a whole CTA) own one
+// domain at a time with every per-piece array in shared memory.  Domains are
+// routed to the tile size that holds them (k_local_classify), so that small
+// domains run many warps per SM and large ones spread their sort, greedy and
+// sums over a CTA.
+//
+// Per-domain shared memory (bytes): W * 1024 histograms, 4 CAP keys, 4 CAP X
+// (later sY), 4 CAP Y, 4 CAP sort temp (later sX), 2 CAP positions, 2 CAP sort
+// temp (later labels by position), 2 CAP labels by sorted index, 128 misc.
+// After the greedy, the 16 CAP bytes of keys and coordinates hold the group
+// accumulators (32 B per group), so CAP / 2 groups are summed per pass.
+// Stable LSD radix sort of (key, 16-bit val) by key, one warp (8-bit digits).
 __device__ void warp_radix_sort16(unsigned* key, unsigned short* val, unsigned* tk, unsigned short* tv, int n,
                                   unsigned* hist) {
   const int lane = threadIdx.x & 31;
@@ -442,38 +446,155 @@ __device__ void warp_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
   }
 }
 
-__global__ void __launch_bounds__(kSmemWarps * 32) k_local_smem(LocalParams P) {
+template <int W, int CAP>
+struct TileCfg {
+  static constexpr int kThreads = 32 * W;
+  static constexpr size_t kBytes = (size_t)W * 1024 + (size_t)CAP * 22 + 128;
+  static constexpr int kGroupsPerPass = CAP / 2;
+};
+
+// Accumulator of one group during the sums: three 32-bit limbs of the
+// increments' 2^-64 fixed-point images, each summed as a signed 64-bit
+// integer (deferred carries), the length sum and the member count.
+struct GroupAcc {
+  long long limb[3];
+  int lensum;
+  int count;
+};
+
+// Synchronization of the W warps that own one domain.
+template <int W>
+__device__ __forceinline__ void tile_sync() {
+  if (W == 1) __syncwarp(); else __syncthreads();
+}
+template <int W>
+__device__ __forceinline__ bool tile_sync_or(bool p) {
+  if (W == 1) {
+    __syncwarp();
+    return __any_sync(0xFFFFFFFFu, p);
+  }
+  return __syncthreads_or(p) != 0;
+}
+
+// Stable LSD radix sort of (key, val) by key with 8-bit digits over the W
+// warps of a tile: warp w sorts the contiguous segment [w seg, (w+1) seg) of
+// the input into digit-major, warp-minor positions, so equal digits keep
+// their input order.  hist holds W x 256 counters; wsum W words.
+template <int W>
+__device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* tk, unsigned short* tv, int n,
+                                  unsigned* hist, unsigned* wsum) {
+  static_assert(W == 8, "one digit per thread: 256 threads");
+  const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) % W;
+  const int t = (threadIdx.x) % (32 * W);
+  const unsigned lt = (1u << lane) - 1u;
+  const int seg = (((n + W - 1) / W) + 31) & ~31;
+  const int lo = w * seg;
+  const int hi = min(n, lo + seg);
+  unsigned* h = hist + w * 256;
+  unsigned* kin = key;
+  unsigned short* vin = val;
+  unsigned* kout = tk;
+  unsigned short* vout = tv;
+  for (int shift = 0; shift < 32; shift += 8) {
+    for (int i = lane; i < 256; i += 32) h[i] = 0;
+    __syncwarp();
+    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&h[(kin[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    // digit d = t (W = 8: one digit per thread): prefix over warps, then an
+    // exclusive scan of the digit totals over the CTA
+    {
+      const int d = t;
+      unsigned run = 0;
+      for (int v = 0; v < W; ++v) {
+        const unsigned c = hist[v * 256 + d];
+        hist[v * 256 + d] = run;
+        run += c;
+      }
+      unsigned incl = run;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) wsum[w] = incl;
+      __syncthreads();
+      unsigned before = 0;
+      for (int v = 0; v < w; ++v) before += wsum[v];
+      const unsigned base = before + incl - run;
+      for (int v = 0; v < W; ++v) hist[v * 256 + d] += base;
+    }
+    __syncthreads();
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+      const int i = i0 + lane;
+      const bool v = i < hi;
+      const unsigned k = v ? kin[i] : 0u;
+      const unsigned short vv = v ? vin[i] : 0;
+      const unsigned d = v ? ((k >> shift) & 255u) : 256u + lane;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+      const unsigned r = __popc(peers & lt);
+      if (v) {
+        const unsigned pos = h[d] + r;
+        kout[pos] = k;
+        vout[pos] = vv;
+      }
+      __syncwarp();
+      if (v && r == 0) h[d] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    unsigned* tt = kin; kin = kout; kout = tt;
+    unsigned short* tq = vin; vin = vout; vout = tq;
+  }
+  // four passes: the result is back in (key, val)
+}
+
+template <int W, int CAP>
+__global__ void __launch_bounds__(W == 1 ? 256 : 32 * W) k_local_tile(LocalParams P, const int* list,
+                                                                       const unsigned* list_count,
+                                                                       unsigned* task_counter) {
+  using Cfg = TileCfg<W, CAP>;
+  constexpr int T = Cfg::kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem_raw + (size_t)warp * kSmemPerWarp;
-  unsigned* hist = (unsigned*)base;                                    // 256 words
-  unsigned* key = (unsigned*)(base + 1024);                            // [n] sorted keys
-  float* X = (float*)(key + kSmemItems);                               // [n] by position, then sY
-  float* Y = X + kSmemItems;                                           // [n] by position, then labels/scratch
-  unsigned* tk = (unsigned*)(Y + kSmemItems);                          // [n] sort temp, then sX
-  unsigned short* idx = (unsigned short*)(tk + kSmemItems);            // [n] sorted index -> position
-  unsigned short* tv = idx + kSmemItems;                               // [n] sort temp
-  short* lab = (short*)(tv + kSmemItems);                              // [n] label by sorted index
+  const int tile = threadIdx.x / T;          // W == 1: one tile per warp
+  const int t = threadIdx.x % T;
+  unsigned char* base = smem_raw + (size_t)tile * Cfg::kBytes;
+  unsigned* hist = (unsigned*)base;                                  // W * 256 words
+  unsigned* key = (unsigned*)(base + W * 1024);                      // [CAP] sorted keys
+  float* X = (float*)(key + CAP);                                    // [CAP] by position, then sY
+  float* Y = X + CAP;                                                // [CAP] by position
+  unsigned* tk = (unsigned*)(Y + CAP);                               // [CAP] sort temp, then sX
+  unsigned short* idx = (unsigned short*)(tk + CAP);                 // [CAP] sorted index -> position
+  unsigned short* tv = idx + CAP;                                    // [CAP] sort temp, then labels by position
+  short* lab = (short*)(tv + CAP);                                   // [CAP] label by sorted index
+  int* misc = (int*)(lab + CAP);                                     // 32 words
   float* sX = (float*)tk;
   float* sY = X;
+  short* plab = (short*)tv;
+  GroupAcc* acc = (GroupAcc*)key;                                    // after the greedy: CAP / 2 groups
+  int* nx = misc;                                                    // [3] next-start candidates
+  unsigned* wsum = (unsigned*)(misc + 4);                            // [W] sort scan
+  long long* gbase_s = (long long*)(misc + 16);                      // group record base
   const double a2 = __dmul_rn(P.alpha, P.alpha);
   const float rinv = *P.rinv32;
+  const unsigned n_list = *list_count;
   for (;;) {
-    long long d = 0;
-    if (lane == 0) d = (long long)atomicAdd(P.task_counter, 1u);
-    d = __shfl_sync(0xFFFFFFFFu, d, 0);
-    if (d >= P.n_domains) break;
+    unsigned task = 0;
+    if (t == 0) task = atomicAdd(task_counter, 1u);
+    if (W == 1) {
+      task = __shfl_sync(0xFFFFFFFFu, task, 0);
+    } else {
+      if (t == 0) misc[12] = (int)task;
+      __syncthreads();
+      task = (unsigned)misc[12];
+      __syncthreads();
+    }
+    if (task >= n_list) break;
+    const int d = list[task];
     const int n = P.dom_piece_cnt[d];
-    if (n > kSmemItems) continue;                 // the arena kernel takes it
     const long long slot = P.dom_slot_off[d];
     const int* plen = P.piece_len + slot;
     const double* pinc = P.piece_inc + slot;
-    if (n == 0) {
-      if (lane == 0) P.dom_group_cnt[d] = 0;
-      continue;
-    }
     // 1. FP32 coordinates and keys by position
-    for (int i = lane; i < n; i += 32) {
+    for (int i = t; i < n; i += T) {
       unsigned mh;
       const float x = x32_of(P, plen[i]);
       const float y = f64_to_f32_trunc(pinc[i], mh) * rinv;
@@ -482,123 +603,178 @@ __global__ void __launch_bounds__(kSmemWarps * 32) k_local_smem(LocalParams P) {
       key[i] = __float_as_uint(fmaf(x, x, y * y));
       idx[i] = (unsigned short)i;
     }
-    __syncwarp();
+    tile_sync<W>();
     // 2. sort by (key32, position)
-    if (n > 1) warp_radix_sort16(key, idx, tk, tv, n, hist);
-    __syncwarp();
+    if (n > 1) {
+      if constexpr (W == 1) warp_radix_sort16(key, idx, tk, tv, n, hist);
+      else tile_radix_sort16<W>(key, idx, tk, tv, n, hist, wsum);
+    }
+    tile_sync<W>();
     // 3. runs of overlapping key intervals: re-sort by the binary64 keys (rare)
-    fix_runs<unsigned short>(P, plen, pinc, key, idx, n);
+    if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n);
+    tile_sync<W>();
     // 4. coordinates in key order: sX into the sort temp, then sY into X's slot
-    for (int a = lane; a < n; a += 32) sX[a] = X[idx[a]];
-    __syncwarp();
-    for (int a = lane; a < n; a += 32) sY[a] = Y[idx[a]];
-    __syncwarp();
-    for (int a = lane; a < n; a += 32) lab[a] = -1;
-    __syncwarp();
-    // 5. greedy in key order
+    for (int a = t; a < n; a += T) sX[a] = X[idx[a]];
+    tile_sync<W>();
+    for (int a = t; a < n; a += T) {
+      sY[a] = Y[idx[a]];
+      lab[a] = -1;
+    }
+    if (t == 0) {
+      nx[0] = 0x7FFFFFFF;
+      nx[1] = 0x7FFFFFFF;
+      nx[2] = 0x7FFFFFFF;
+    }
+    tile_sync<W>();
+    // 5. greedy in key order.  Item a is a start; one pass over (a, n) in
+    // chunks of T tests the window of a (members join), and the first item
+    // left free in the chunks passed is the next start (atomicMin into a
+    // triple-buffered slot: buffer it % 3 is written in pass it, reset in pass
+    // it - 1 and last read in pass it - 2).
     int G = 0;
     {
-      int a = 0;
-      for (;;) {
-        for (;;) {
-          const int aa = a + lane;
-          const bool fr = aa < n && lab[aa] < 0;
-          const unsigned m = __ballot_sync(0xFFFFFFFFu, fr);
-          if (m) { a += __ffs(m) - 1; break; }
-          a += 32;
-          if (a >= n) break;
-        }
-        if (a >= n) break;
+      int a = 0, it = 0;
+      while (a < n) {
+        if (t == 0) lab[a] = (short)G;
         const float xs = sX[a], ys = sY[a];
-        const float T = key_stop(__uint_as_float(key[a]), P.alpha_up);
-        if (lane == 0) lab[a] = (short)G;
-        for (int b0 = a + 1; b0 < n; b0 += 32) {
-          const int b = b0 + lane;
-          bool stop = true;
+        const float Tk = key_stop(__uint_as_float(key[a]), P.alpha_up);
+        int next = n;
+        int b0 = a + 1;
+        for (;;) {
+          int* slotp = &nx[it % 3];
+          if (t == 0) nx[(it + 1) % 3] = 0x7FFFFFFF;
+          const int b = b0 + t;
+          bool past = true;
           if (b < n) {
-            stop = __uint_as_float(key[b]) * (1.0f - kKeyRel) > T;
-            if (!stop && lab[b] < 0) {
-              int w = filter_within(xs, ys, sX[b], sY[b], P.a2lo, P.a2hi);
-              if (w == 2) {
-                const int ps = idx[a], pb = idx[b];
-                w = exact_within(P, plen[ps], pinc[ps], plen[pb], pinc[pb], a2) ? 1 : 0;
+            past = __uint_as_float(key[b]) * (1.0f - kKeyRel) > Tk;
+            if (lab[b] < 0) {
+              bool join = false;
+              if (!past) {
+                int w = filter_within(xs, ys, sX[b], sY[b], P.a2lo, P.a2hi);
+                if (w == 2) {
+                  const int ps = idx[a], pb = idx[b];
+                  w = exact_within(P, plen[ps], pinc[ps], plen[pb], pinc[pb], a2) ? 1 : 0;
+                }
+                join = w != 0;
               }
-              if (w) lab[b] = (short)G;
+              if (join) lab[b] = (short)G;
+              else atomicMin(slotp, b);
             }
           }
-          if (__any_sync(0xFFFFFFFFu, stop)) break;
+          const bool any_past = tile_sync_or<W>(past);
+          const int m = *slotp;
+          ++it;
+          if (m < next) next = m;
+          if (any_past) break;
+          b0 += T;
         }
-        __syncwarp();
+        // nothing left free up to the window's last chunk: search on
+        while (next == n) {
+          b0 += T;
+          if (b0 >= n) break;
+          int* slotp = &nx[it % 3];
+          if (t == 0) nx[(it + 1) % 3] = 0x7FFFFFFF;
+          const int b = b0 + t;
+          if (b < n && lab[b] < 0) atomicMin(slotp, b);
+          tile_sync<W>();
+          const int m = *slotp;
+          ++it;
+          if (m < next) next = m;
+        }
         ++G;
-        ++a;
+        a = next;
       }
     }
-    __syncwarp();
-    // 6. labels to positions, member lists (counting sort by label), exact sums
-    int* cnt = (int*)key;        // [G + 1] offsets (keys no longer needed)
-    unsigned short* mem = tv;    // [n] positions grouped by label
-    for (int a = lane; a < n; a += 32) P.local_label[slot + idx[a]] = lab[a];
-    for (int g = lane; g <= G; g += 32) cnt[g] = 0;
-    __syncwarp();
-    for (int a = lane; a < n; a += 32) atomicAdd(&cnt[lab[a]], 1);
-    __syncwarp();
-    {
-      int carry = 0;
-      for (int g0 = 0; g0 < G; g0 += 32) {
-        const int g = g0 + lane;
-        const int c = g < G ? cnt[g] : 0;
-        int incl = c;
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        if (g < G) cnt[g] = carry + incl - c;
-        carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
-      }
-    }
-    __syncwarp();
-    for (int a = lane; a < n; a += 32) {
-      const int r = atomicAdd(&cnt[lab[a]], 1);
-      mem[r] = idx[a];
-    }
-    __syncwarp();
-    long long gbase = 0;
-    if (lane == 0) {
-      gbase = (long long)atomicAdd((unsigned long long*)P.n_groups, (unsigned long long)G);
-      if (gbase + G > P.group_capacity) {
+    tile_sync<W>();
+    // 6. labels by position, written out coalesced
+    for (int a = t; a < n; a += T) plab[idx[a]] = lab[a];
+    tile_sync<W>();
+    for (int i = t; i < n; i += T) P.local_label[slot + i] = plab[i];
+    // 7. exact group sums (shared-memory atomics) and the group records
+    if (t == 0) {
+      long long gb = (long long)atomicAdd((unsigned long long*)P.n_groups, (unsigned long long)G);
+      if (gb + G > P.group_capacity) {
         set_status(P.status, JABBA_ERR_CAPACITY);
-        gbase = -1;
+        gb = -1;
       }
+      *gbase_s = gb;
       P.dom_group_cnt[d] = G;
     }
-    gbase = __shfl_sync(0xFFFFFFFFu, gbase, 0);
+    tile_sync<W>();
+    const long long gbase = *gbase_s;
     if (gbase >= 0) {
-      for (int g = lane; g < G; g += 32) {
-        const int e = cnt[g];
-        const int s0 = g ? cnt[g - 1] : 0;
-        I192 acc = {0, 0, 0};
-        long long lensum = 0;
-#pragma unroll 4
-        for (int q = s0; q < e; ++q) {
-          const int i = mem[q];
-          lensum += plen[i];
-          bool neg;
-          const U128 m = fx_mag(pinc[i], neg);
-          acc_signed(acc, m, neg);
+      for (int g0 = 0; g0 < G; g0 += Cfg::kGroupsPerPass) {
+        const int gn = min(G - g0, Cfg::kGroupsPerPass);
+        for (int g = t; g < gn; g += T) {
+          acc[g].limb[0] = 0;
+          acc[g].limb[1] = 0;
+          acc[g].limb[2] = 0;
+          acc[g].lensum = 0;
+          acc[g].count = 0;
         }
-        jabba_group rec;
-        rec.inc[0] = acc.w0;
-        rec.inc[1] = acc.w1;
-        rec.inc[2] = acc.w2;
-        rec.lensum = lensum;
-        rec.count = e - s0;
-        rec.local_id = g;
-        rec.domain = (int)d;
-        rec.pad = 0;
-        P.groups[gbase + g] = rec;
+        tile_sync<W>();
+        for (int i = t; i < n; i += T) {
+          const int g = plab[i] - g0;
+          if (g < 0 || g >= gn) continue;
+          bool neg;
+          const U128 m = fx_mag(pinc[i], neg);          // < 2^96 under the range contract
+          long long l0 = (long long)(m.lo & 0xFFFFFFFFull);
+          long long l1 = (long long)(m.lo >> 32);
+          long long l2 = (long long)(m.hi & 0xFFFFFFFFull);
+          if (neg) { l0 = -l0; l1 = -l1; l2 = -l2; }
+          atomicAdd((unsigned long long*)&acc[g].limb[0], (unsigned long long)l0);
+          atomicAdd((unsigned long long*)&acc[g].limb[1], (unsigned long long)l1);
+          atomicAdd((unsigned long long*)&acc[g].limb[2], (unsigned long long)l2);
+          atomicAdd(&acc[g].lensum, plen[i]);
+          atomicAdd(&acc[g].count, 1);
+        }
+        tile_sync<W>();
+        for (int g = t; g < gn; g += T) {
+          const long long L[6] = {acc[g].limb[0], acc[g].limb[1], acc[g].limb[2], 0, 0, 0};
+          const I192 s = from_limbs6(L);
+          jabba_group rec;
+          rec.inc[0] = s.w0;
+          rec.inc[1] = s.w1;
+          rec.inc[2] = s.w2;
+          rec.lensum = acc[g].lensum;
+          rec.count = acc[g].count;
+          rec.local_id = g0 + g;
+          rec.domain = d;
+          rec.pad = 0;
+          P.groups[gbase + g0 + g] = rec;
+        }
+        tile_sync<W>();
       }
     }
-    __syncwarp();
+    tile_sync<W>();
+  }
+}
+
+// Routes every domain to the kernel whose tile holds it: list 0 (<= 256
+// pieces, a warp per domain), 1 (<= 2048, a CTA), 2 (<= 4096, a CTA), 3
+// (larger: the global-memory arena kernel).  Empty domains get no groups here.
+constexpr int kTierCap0 = 256, kTierCap1 = 2048, kTierCap2 = 4096;
+
+__global__ void k_local_classify(const int* dom_piece_cnt, long long n_domains, int* dom_group_cnt, int* lists,
+                                 long long list_stride, unsigned* list_count) {
+  const int lane = threadIdx.x & 31;
+  for (long long d0 = (long long)blockIdx.x * blockDim.x; d0 < n_domains; d0 += (long long)gridDim.x * blockDim.x) {
+    const long long d = d0 + threadIdx.x;
+    int tier = -1;
+    if (d < n_domains) {
+      const int n = dom_piece_cnt[d];
+      if (n == 0) dom_group_cnt[d] = 0;
+      else tier = n <= kTierCap0 ? 0 : n <= kTierCap1 ? 1 : n <= kTierCap2 ? 2 : 3;
+    }
+    for (int k = 0; k < 4; ++k) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, tier == k);
+      if (!m) continue;
+      const int leader = __ffs(m) - 1;
+      unsigned b = 0;
+      if (lane == leader) b = atomicAdd(&list_count[k], (unsigned)__popc(m));
+      b = __shfl_sync(0xFFFFFFFFu, b, leader);
+      if (tier == k) lists[k * list_stride + b + __popc(m & ((1u << lane) - 1u))] = (int)d;
+    }
   }
 }
 
@@ -625,12 +801,30 @@ static float round_up_f(double v) {
   return f;
 }
 
+template <int W, int CAP>
+static void launch_tile(const LocalParams& P, const int* list, const unsigned* cnt, unsigned* ctr, int num_sms,
+                        cudaStream_t st) {
+  using Cfg = TileCfg<W, CAP>;
+  constexpr int kBlock = 256;
+  constexpr size_t kSmem = (size_t)(kBlock / Cfg::kThreads) * Cfg::kBytes;
+  static int blocks_per_sm = 0;
+  if (!blocks_per_sm) {
+    cudaFuncSetAttribute(k_local_tile<W, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_local_tile<W, CAP>, kBlock, kSmem);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  k_local_tile<W, CAP><<<(unsigned)(num_sms * blocks_per_sm), kBlock, kSmem, st>>>(P, list, cnt, ctr);
+}
+
 void launch_local(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
                   const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
                   int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
                   long long group_capacity, long long* n_groups, Scratch& ws, unsigned* status, cudaStream_t st) {
+  // counters[4..5] unused here; [6..9] list sizes of the four tiers, [10..13] their task counters
+  unsigned* list_cnt = ws.counters + 6;
+  unsigned* task_ctr = ws.counters + 10;
   cudaMemsetAsync(n_groups, 0, sizeof(long long), st);
-  cudaMemsetAsync(ws.counters + 4, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(ws.counters + 4, 0, 10 * sizeof(unsigned), st);
   k_norm_tables<<<(unsigned)((ws.cap_len + 256) / 256), 256, 0, st>>>(sigma, scl, ws.cap_len, ws.xtab64, ws.xtab32,
                                                                         ws.rinv32);
   LocalParams P;
@@ -656,18 +850,18 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
   P.group_capacity = group_capacity;
   P.n_groups = n_groups;
   P.status = status;
-  P.task_counter = ws.counters + 4;
+  P.task_counter = task_ctr + 3;
+  P.list = ws.loc_list + 3 * ws.loc_stride;
+  P.list_count = list_cnt + 3;
   P.arena = ws.arena;
   P.cap_items = ws.cap_items;
   if (n_domains > 0) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_local_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kSmemPerWarp * kSmemWarps));
-      attr = true;
-    }
-    k_local_smem<<<(unsigned)(ws.num_sms * 1), kSmemWarps * 32, kSmemPerWarp * kSmemWarps, st>>>(P);
-    cudaMemsetAsync(ws.counters + 4, 0, sizeof(unsigned), st);
+    const unsigned g = (unsigned)(ws.num_sms * 4);
+    k_local_classify<<<g, 256, 0, st>>>(dom_piece_cnt, n_domains, dom_group_cnt, ws.loc_list, ws.loc_stride,
+                                        list_cnt);
+    launch_tile<1, kTierCap0>(P, ws.loc_list, list_cnt + 0, task_ctr + 0, ws.num_sms, st);
+    launch_tile<8, kTierCap1>(P, ws.loc_list + ws.loc_stride, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
+    launch_tile<8, kTierCap2>(P, ws.loc_list + 2 * ws.loc_stride, list_cnt + 2, task_ctr + 2, ws.num_sms, st);
     k_local_warp<<<(unsigned)ws.loc_ctas, kLocWarps * 32, 0, st>>>(P);
   }
   exclusive_scan<int>(dom_group_cnt, n_domains, dom_group_off, ws.scan_tiles, st);

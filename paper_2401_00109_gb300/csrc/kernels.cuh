@@ -38,7 +38,6 @@ struct MergeBufs {
   int* lab = nullptr;                // [cap]
   int* is_start = nullptr;           // [cap]
   long long* start_off = nullptr;    // [cap + 1]
-  int* gid_c = nullptr;              // [cap]
   double* eX = nullptr;              // [cap] binary64 coordinates (fallback only)
   double* eY = nullptr;
   double* ekey = nullptr;
@@ -60,7 +59,9 @@ struct Scratch {
   // local aggregation: per-warp arenas and the FP32 normalisation tables
   long long cap_len = 0;          // largest piece length covered by the X table
   long long cap_items = 0;        // largest domain (pieces) an arena holds
-  int loc_ctas = 0;               // CTAs of the local-aggregation kernel
+  int loc_ctas = 0;               // CTAs of the arena local-aggregation kernel
+  int* loc_list = nullptr;        // [4 * loc_stride] domains routed to each local-aggregation tier
+  long long loc_stride = 0;
   unsigned* arena = nullptr;
   double* xtab64 = nullptr;
   float* xtab32 = nullptr;

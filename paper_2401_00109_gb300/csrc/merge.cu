@@ -201,50 +201,94 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long
   for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * n_tiles + blockIdx.x] = h[i];
 }
 
+// One tile of kSortTile items: every warp ranks its contiguous 512 items (in
+// input order, so the sort is stable), the tile is reordered by digit in
+// shared memory, and each digit's run is then written to its global offset
+// with consecutive threads writing consecutive addresses.
+struct ScatterSmem {
+  unsigned long long key[kSortTile];
+  int val[kSortTile];
+  unsigned wh[kSortWarps][256];
+  unsigned lstart[256];      // first local position of each digit
+  long long goff[256];       // global position of the tile's first item of each digit
+  unsigned wsum[kSortWarps];
+};
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned long long* kin, const int* vin,
                                                                unsigned long long* kout, int* vout,
                                                                const long long* n_p, long long cap, int shift,
                                                                const long long* offs, long long n_tiles,
                                                                const int* flags) {
-  __shared__ unsigned wh[kSortWarps][256];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScatterSmem& S = *(ScatterSmem*)smem_raw;
   const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long base = (long long)blockIdx.x * kSortTile;
-  const int per_warp = kSortTile / kSortWarps;
-  const long long wbase = base + (long long)warp * per_warp;
-  for (int i = lane; i < 256; i += 32) wh[warp][i] = 0;
+  constexpr int kPerWarp = kSortTile / kSortWarps;
+  constexpr int kPerLane = kPerWarp / 32;
+  const long long wbase = base + (long long)warp * kPerWarp;
+  unsigned long long kr[kPerLane];
+  int vr[kPerLane];
+  for (int i = lane; i < 256; i += 32) S.wh[warp][i] = 0;
   __syncwarp();
-  for (int i = lane; i < per_warp; i += 32) {
-    const long long k = wbase + i;
-    if (k < n) atomicAdd(&wh[warp][(kin[k] >> shift) & 255u], 1u);
+#pragma unroll
+  for (int j = 0; j < kPerLane; ++j) {
+    const long long k = wbase + j * 32 + lane;
+    const bool valid = k < n;
+    kr[j] = valid ? kin[k] : 0ull;
+    vr[j] = valid ? vin[k] : 0;
+    if (valid) atomicAdd(&S.wh[warp][(kr[j] >> shift) & 255u], 1u);
   }
   __syncthreads();
-  for (int dgt = threadIdx.x; dgt < 256; dgt += blockDim.x) {
-    unsigned run = (unsigned)offs[(long long)dgt * n_tiles + blockIdx.x];
+  {
+    // digit d = threadIdx.x: warp prefix within the digit, tile-wide digit starts
+    const int d = threadIdx.x;
+    unsigned run = 0;
     for (int w = 0; w < kSortWarps; ++w) {
-      const unsigned c = wh[w][dgt];
-      wh[w][dgt] = run;
+      const unsigned c = S.wh[w][d];
+      S.wh[w][d] = run;
       run += c;
     }
+    unsigned incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) S.wsum[warp] = incl;
+    __syncthreads();
+    unsigned before = 0;
+    for (int w = 0; w < warp; ++w) before += S.wsum[w];
+    const unsigned ls = before + incl - run;
+    S.lstart[d] = ls;
+    for (int w = 0; w < kSortWarps; ++w) S.wh[w][d] += ls;
+    S.goff[d] = offs[(long long)d * n_tiles + blockIdx.x];
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
-  for (int i0 = 0; i0 < per_warp; i0 += 32) {
-    const long long k = wbase + i0 + lane;
+#pragma unroll
+  for (int j = 0; j < kPerLane; ++j) {
+    const long long k = wbase + j * 32 + lane;
     const bool valid = k < n;
-    const unsigned long long key = valid ? kin[k] : 0ull;
-    const int val = valid ? vin[k] : 0;
-    const unsigned dgt = valid ? (unsigned)((key >> shift) & 255u) : 256u + lane;
+    const unsigned dgt = valid ? (unsigned)((kr[j] >> shift) & 255u) : 256u + lane;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, dgt);
     const unsigned rank = __popc(peers & lt);
     if (valid) {
-      const unsigned pos = wh[warp][dgt] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      const unsigned pos = S.wh[warp][dgt] + rank;
+      S.key[pos] = kr[j];
+      S.val[pos] = vr[j];
     }
     __syncwarp();
-    if (valid && rank == 0) wh[warp][dgt] += __popc(peers);
+    if (valid && rank == 0) S.wh[warp][dgt] += __popc(peers);
     __syncwarp();
+  }
+  __syncthreads();
+  const long long in_tile = n - base < kSortTile ? n - base : kSortTile;
+  for (int i = threadIdx.x; i < in_tile; i += kSortThreads) {
+    const unsigned long long key = S.key[i];
+    const unsigned dgt = (unsigned)((key >> shift) & 255u);
+    const long long pos = S.goff[dgt] + (i - (long long)S.lstart[dgt]);
+    kout[pos] = key;
+    vout[pos] = S.val[i];
   }
 }
 
@@ -260,6 +304,11 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
                        const int* flags, cudaStream_t st) {
   const long long n_tiles = (cap + kSortTile - 1) / kSortTile;
   const unsigned grid = (unsigned)(ws.num_sms * 8);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
+    attr = true;
+  }
   unsigned long long* kin = k0;
   unsigned long long* kout = k1;
   int* vin = v0;
@@ -268,7 +317,8 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
     k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n_p, cap, shift, ws.m_hist, n_tiles, flags);
     k_u32_to_i64<<<grid, 256, 0, st>>>(ws.m_hist, 256 * n_tiles, offs + 256 * n_tiles + 1);
     exclusive_scan<long long>(offs + 256 * n_tiles + 1, 256 * n_tiles, offs, ws.scan_tiles, st);
-    k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_p, cap, shift, offs, n_tiles, flags);
+    k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, sizeof(ScatterSmem), st>>>(kin, vin, kout, vout, n_p, cap,
+                                                                                   shift, offs, n_tiles, flags);
     unsigned long long* tk = kin; kin = kout; kout = tk;
     int* tv = vin; vin = vout; vout = tv;
   }
@@ -830,8 +880,7 @@ __global__ void __launch_bounds__(1024) k_mexact_greedy(const double* eX, const 
 
 // ------------------------------------------------------------------ ids, map, dictionary
 __global__ void k_mids(const int* lab, const long long* start_off, const int* sidx, const long long* n_p, long long cap,
-                       long long dict_capacity, int* l2g, int* gid_c, long long* k_out, unsigned* status,
-                       const int* flags) {
+                       long long dict_capacity, int* l2g, long long* k_out, unsigned* status, const int* flags) {
   if (flags[1]) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *k_out = 0;
     return;
@@ -846,7 +895,6 @@ __global__ void k_mids(const int* lab, const long long* start_off, const int* si
     const int gid = (int)start_off[la];
     const int c = sidx[a];
     l2g[c] = gid;
-    gid_c[c] = gid;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const long long K = start_off[n];
@@ -855,27 +903,70 @@ __global__ void k_mids(const int* lab, const long long* start_off, const int* si
   }
 }
 
-__global__ void k_dict_accumulate(const jabba_group* groups, const int* rec_of, const int* gid_c, const long long* n_p,
-                                  long long cap, const long long* k_p, long long dict_capacity, long long* acc,
-                                  const int* flags) {
+// Dictionary sums.  Items are visited in cell order, where neighbours mostly
+// share their global group: each warp sums runs of equal ids with a segmented
+// scan (count, length sum and the six 32-bit limbs of the increment sum) and
+// the last lane of each run adds them to the entry with 64-bit atomics, so
+// popular entries see a few atomics per cell instead of one per item.
+__global__ void k_dict_clear(const long long* k_p, long long dict_capacity, long long* acc) {
+  long long K = *k_p;
+  if (K > dict_capacity) K = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < K * 8; i += (long long)gridDim.x * blockDim.x)
+    acc[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_dict_accumulate(const jabba_group* groups, const int* rec_of,
+                                                         const int* sidx, const int* cord, const int* lab,
+                                                         const long long* start_off, const long long* n_p,
+                                                         long long cap, const long long* k_p,
+                                                         long long dict_capacity, long long* acc,
+                                                         const int* flags) {
   if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
   const long long K = *k_p;
   if (K > dict_capacity) return;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < G; c += (long long)gridDim.x * blockDim.x) {
-    const int gid = gid_c[c];
-    const jabba_group g = groups[rec_of[c]];
-    long long* a = acc + (long long)gid * 8;
-    atomicAdd((unsigned long long*)&a[0], (unsigned long long)g.count);
-    atomicAdd((unsigned long long*)&a[1], (unsigned long long)g.lensum);
-    I192 v;
-    v.w0 = g.inc[0];
-    v.w1 = g.inc[1];
-    v.w2 = g.inc[2];
-    i64 L[6];
-    limbs6(v, L);
-    for (int i = 0; i < 6; ++i)
-      if (L[i]) atomicAdd((unsigned long long*)&a[2 + i], (unsigned long long)L[i]);
+  const int lane = threadIdx.x & 31;
+  const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp_g * 32; base < G; base += n_warps * 32) {
+    const long long t = base + lane;
+    const bool valid = t < G;
+    int gid = -1;
+    long long v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (valid) {
+      const int a = cord[t];
+      int la = lab[a];
+      if (la < 0 || la >= G) la = 0;  // unresolved (status already set), as in k_mids
+      gid = (int)start_off[la];
+      const jabba_group g = groups[rec_of[sidx[a]]];
+      v[0] = g.count;
+      v[1] = g.lensum;
+      I192 w;
+      w.w0 = g.inc[0];
+      w.w1 = g.inc[1];
+      w.w2 = g.inc[2];
+      limbs6(w, v + 2);
+    }
+    const int gprev = __shfl_up_sync(0xFFFFFFFFu, gid, 1);
+    const bool head = lane == 0 || gprev != gid;
+    bool f = head;
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool fu = __shfl_up_sync(0xFFFFFFFFu, f, o);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const long long vu = __shfl_up_sync(0xFFFFFFFFu, v[i], o);
+        if (lane >= o && !f) v[i] += vu;
+      }
+      if (lane >= o) f = f || fu;
+    }
+    const bool next_head = __shfl_down_sync(0xFFFFFFFFu, head, 1);
+    const bool tail = valid && (lane == 31 || next_head);
+    if (tail && gid >= 0 && gid < K) {
+      long long* e = acc + (long long)gid * 8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (v[i]) atomicAdd((unsigned long long*)&e[i], (unsigned long long)v[i]);
+    }
   }
 }
 
@@ -948,7 +1039,8 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   k_msorted<<<grid, 256, 0, st>>>(sidx, ws.m_X32, ws.m_Y32, n_groups, cap, B.geom, B.flags, B.sX, B.sY, ck0, cv0);
   unsigned long long* ckey;
   int* cord;
-  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 32, ws, offs, &ckey, &cord, B.flags, st);
+  // cell ids are below cap_cells = 2^23: three 8-bit passes order them
+  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws, offs, &ckey, &cord, B.flags, st);
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
@@ -1022,10 +1114,10 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   k_mexact_prep<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, n_groups, cap, sigma, scl, B.flags, B.eX, B.eY, B.ekey);
   k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, B.flags, B.lab, B.is_start);
   exclusive_scan<int>(B.is_start, cap, B.start_off, ws.scan_tiles, st);
-  k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, n_groups, cap, dict_capacity, l2g, B.gid_c, k, status,
-                               B.flags);
-  cudaMemsetAsync(ws.d_acc, 0, sizeof(long long) * 8 * (size_t)(cap > 0 ? cap : 1), st);
-  k_dict_accumulate<<<grid, 256, 0, st>>>(groups, ws.m_rec, B.gid_c, n_groups, cap, k, dict_capacity, ws.d_acc, B.flags);
+  k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, n_groups, cap, dict_capacity, l2g, k, status, B.flags);
+  k_dict_clear<<<grid, 256, 0, st>>>(k, dict_capacity, ws.d_acc);
+  k_dict_accumulate<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, cord, B.lab, B.start_off, n_groups, cap, k,
+                                          dict_capacity, ws.d_acc, B.flags);
   k_dict_finalize<<<grid, 256, 0, st>>>(ws.d_acc, k, dict_capacity, dict_len, dict_inc, dict_count);
 }
 
