@@ -223,6 +223,10 @@ def run_ours(args, ws, rank, local):
         pl.x.copy_(x_host, non_blocking=True)
     st = torch.cuda.current_stream()
 
+    # ---- autotuned launch configuration (native autotuner: each stage times
+    # its candidate configurations on this collection)
+    tuning = pl.tune() if not args.no_tune else ctx.tuning()
+
     # ---- batched: graph capture of the whole step; one graph per timed step
     # so each keeps its own event pair around the compression kernel
     pl.enqueue()
@@ -343,7 +347,7 @@ def run_ours(args, ws, rank, local):
                     config=dict(workload=WORKLOAD_DESC[args.workload], n_series=S, n_points=n, pieces=N,
                                 local_groups=G, dictionary=k, parallelism=f"replicas x{ws}",
                                 l2="input 8 B/point >> L2 (no flush needed)" if 8 * n > 2e9 else "input fits L2",
-                                form="batched: CUDA-graph replay of the whole step"),
+                                form="batched: CUDA-graph replay of the whole step", tuning=tuning),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, plain=plain, clocks=clocks,
                     gpu_launches=kernels_per_step * args.steps,
                     stage_ms=dict(compress=float(np.mean(comp_ms)), finish=float(np.mean(fin_ms)),
@@ -391,6 +395,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--verify", type=int, default=0, help="oracle-check this many sampled domains")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

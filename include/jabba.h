@@ -229,6 +229,36 @@ jabba_status jabba_diagnostics(jabba_ctx* ctx, int64_t* out, int n);
 jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int64_t n_points, double* out,
                        jabba_stream stream);
 
+/* ---------------------------------------------------------------- launch tuning
+ * (No counterpart in the paper.)  Launch configuration of the batched
+ * kernels.  Every configuration computes the same results (bit for bit); only
+ * the speed differs.  Defaults: {3, 1, 4, 4, 4}. */
+typedef struct {
+  int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
+  int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
+  int32_t local_mid_warps;      /* warps that aggregate one domain of 257..2048 pieces together: 2, 4 or 8     */
+  int32_t local_big_warps;      /* warps that aggregate one domain of 2049..4096 pieces together: 4 or 8       */
+  int32_t merge_ctas_per_sm;    /* CTAs per SM of the cooperative merge-rounds kernel: 1, 2 or 4 (capped by the
+                                   kernel's occupancy so that the grid stays co-resident)                     */
+  int32_t reserved[3];          /* zero                                                                      */
+} jabba_tuning;
+
+/* Autotuning mode.  While enabled (enable = 1), each call of jabba_compress,
+ * jabba_digitize_local and jabba_merge_global runs its kernels once per
+ * candidate configuration on the call's own inputs, times them with CUDA
+ * events, keeps the fastest in the context and returns after synchronizing
+ * `stream` (the outputs are those of the call, as without tuning).  Candidates:
+ * compression {1, 2, 3} CTAs per SM x {packed, in order}; local aggregation
+ * {2, 4, 8} warps per mid-size domain and {4, 8} per large domain; merge
+ * {1, 2, 4} CTAs per SM.  Tuning calls must not be captured in a CUDA graph
+ * (JABBA_ERR_STATE).  enable = 0 ends the mode; the choice stays in effect. */
+jabba_status jabba_autotune(jabba_ctx* ctx, int enable);
+/* Current configuration of the context. */
+jabba_status jabba_get_tuning(jabba_ctx* ctx, jabba_tuning* out);
+/* Set a configuration (e.g. one cached from an earlier autotuning run);
+ * out-of-range fields -> JABBA_ERR_INVALID_ARG and nothing changes. */
+jabba_status jabba_set_tuning(jabba_ctx* ctx, const jabba_tuning* in);
+
 /* ---------------------------------------------------------------- allocation-free reconstruction
  * (No counterpart in the paper.)  The same result as jabba_reconstruct, for
  * callers that cannot allocate device memory -- code that runs where

@@ -61,6 +61,13 @@ class Params:
                        int(self.round_mode), int(self.domain_value))
 
 
+class _Tuning(C.Structure):
+    _fields_ = [("compress_ctas_per_sm", C.c_int32), ("compress_pack", C.c_int32), ("local_mid_warps", C.c_int32),
+                ("local_big_warps", C.c_int32), ("merge_ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+TUNING_FIELDS = ("compress_ctas_per_sm", "compress_pack", "local_mid_warps", "local_big_warps", "merge_ctas_per_sm")
+
 JABBA_GROUP_BYTES = 48
 PIECE_STATS_BYTES = 256
 
@@ -103,6 +110,9 @@ def load():
                 "jabba_diagnostics": (C.c_int, [V, C.POINTER(C.c_int64), C.c_int]),
                 "jabba_reconstruct_noalloc": (C.c_int, [V, I64, V, I64, V, V, I64, V, V, V, C.c_int32, V, V, V]),
                 "jabba_profile_elapsed": (C.c_int, [V, C.c_int, C.c_int, C.POINTER(C.c_float)]),
+                "jabba_autotune": (C.c_int, [V, C.c_int]),
+                "jabba_get_tuning": (C.c_int, [V, C.POINTER(_Tuning)]),
+                "jabba_set_tuning": (C.c_int, [V, C.POINTER(_Tuning)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -301,6 +311,25 @@ class Context:
             self._stream(stream)), "jabba_reconstruct_backward")
         return grad[:k]
 
+    def autotune(self, enable: bool):
+        """Autotuning mode: while on, every compress / local digitization /
+        merge call times each candidate launch configuration on its own
+        inputs and keeps the fastest (jabba_autotune)."""
+        _check(self.lib.jabba_autotune(self.h, 1 if enable else 0), "jabba_autotune")
+
+    def tuning(self) -> dict:
+        t = _Tuning()
+        _check(self.lib.jabba_get_tuning(self.h, C.byref(t)), "jabba_get_tuning")
+        return {f: int(getattr(t, f)) for f in TUNING_FIELDS}
+
+    def set_tuning(self, cfg: dict):
+        t = _Tuning()
+        cur = self.tuning()
+        cur.update(cfg)
+        for f in TUNING_FIELDS:
+            setattr(t, f, int(cur[f]))
+        _check(self.lib.jabba_set_tuning(self.h, C.byref(t)), "jabba_set_tuning")
+
     def diagnostics(self):
         """Counters of the last calls: exact compression decisions, merge rounds."""
         out = (C.c_int64 * 2)()
@@ -448,6 +477,18 @@ class Pipeline:
         _check(L.jabba_symbolize(h, P(b["local_label"]), P(b["dom_slot_off"]), P(b["dom_piece_cnt"]),
                                  P(b["dom_piece_off"]), P(b["dom_group_off"]), self.D, P(b["l2g"]), P(b["symbol"]), st),
                "jabba_symbolize")
+
+    def tune(self, stream=None) -> dict:
+        """Autotune the launch configuration on this collection: one eager
+        step in tuning mode (each stage times its candidates on its own
+        inputs).  Returns the configuration chosen."""
+        self.ctx.autotune(True)
+        try:
+            self.enqueue(stream)
+            self.ctx.sync_status(stream, "autotuning step")
+        finally:
+            self.ctx.autotune(False)
+        return self.ctx.tuning()
 
     def capture(self, keep_graph: bool = False):
         """Capture one step into a CUDA graph (call after one eager step).

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/jabba.h): argument checks, the context and its
 // scratch, and the stream-ordered launches of each step.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -20,6 +21,7 @@ struct jabba_ctx {
   Scratch ws;
   void* pool = nullptr;        // one allocation backing the scratch
   size_t pool_bytes = 0;
+  bool tuning = false;         // autotuning mode (jabba_autotune)
 };
 
 namespace {
@@ -192,6 +194,31 @@ jabba_status ensure(jabba_ctx* c, long long S, long long D, long long slots, lon
   return JABBA_OK;
 }
 
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Milliseconds between two events already recorded on a stream (synchronizes).
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 3.0e38f;
+  return ms;
+}
+
+bool tuning_ok(const jabba_tuning* t) {
+  if (!t) return false;
+  if (t->compress_ctas_per_sm < 1 || t->compress_ctas_per_sm > 3) return false;
+  if (t->compress_pack != 0 && t->compress_pack != 1) return false;
+  if (t->local_mid_warps != 2 && t->local_mid_warps != 4 && t->local_mid_warps != 8) return false;
+  if (t->local_big_warps != 4 && t->local_big_warps != 8) return false;
+  if (t->merge_ctas_per_sm != 1 && t->merge_ctas_per_sm != 2 && t->merge_ctas_per_sm != 4) return false;
+  for (int i = 0; i < 3; ++i)
+    if (t->reserved[i] != 0) return false;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -314,9 +341,39 @@ jabba_status jabba_compress(jabba_ctx* c, const double* x, int64_t n_points, con
   mk.a1 = prof_event(c, 0, 1);
   mk.b0 = prof_event(c, 1, 0);
   mk.b1 = prof_event(c, 1, 1);
-  launch_compress(x, n_points, (const long long*)dom_begin, (const long long*)dom_end,
-                  (const long long*)dom_slot_off, n_domains, p->tol, piece_len, piece_inc, dom_piece_cnt,
-                  (long long*)dom_piece_off, (long long*)piece_stats, c->ws, c->status, st, mk);
+  auto run = [&](const Marks& m) {
+    launch_compress(x, n_points, (const long long*)dom_begin, (const long long*)dom_end,
+                    (const long long*)dom_slot_off, n_domains, p->tol, piece_len, piece_inc, dom_piece_cnt,
+                    (long long*)dom_piece_off, (long long*)piece_stats, c->ws, c->status, st, m);
+  };
+  if (c->tuning) {
+    // every candidate once on these inputs; the packing and the kernel are timed together
+    if (capturing(st)) return JABBA_ERR_STATE;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return JABBA_ERR_CUDA;
+    Tuning best = c->ws.tune;
+    float best_ms = 3.0e38f;
+    for (int pack = 0; pack <= 1; ++pack) {
+      for (int per_sm = 1; per_sm <= 3; ++per_sm) {
+        c->ws.tune.compress_pack = pack;
+        c->ws.tune.compress_ctas_per_sm = per_sm;
+        Marks m;
+        m.a0 = e0;
+        m.a1 = e1;
+        run(m);
+        const float ms = elapsed_ms(e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c->ws.tune;
+        }
+      }
+    }
+    c->ws.tune = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_ok(cudaGetLastError());
+  }
+  run(mk);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -336,11 +393,41 @@ jabba_status jabba_digitize_local(jabba_ctx* c, const int32_t* piece_len, const 
   // domains above the shared-memory tile use the scratch sized by jabba_reserve
   jabba_status r = ensure(c, c->ws.cap_series, n_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
   if (r != JABBA_OK) return r;
+  auto run = [&]() {
+    launch_sigma((const long long*)piece_stats, sigma, st);
+    launch_local(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt, n_domains, sigma, p->alpha,
+                 p->scl, local_label, dom_group_cnt, (long long*)dom_group_off, groups, group_capacity,
+                 (long long*)n_groups, c->ws, c->status, st);
+  };
+  if (c->tuning) {
+    // three runs cover every tile variant: (mid, big) = (2, 4), (4, 8), (8, 4); each tile kernel is timed
+    if (capturing(st)) return JABBA_ERR_STATE;
+    TierEvents te;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (cudaEventCreate(&te.ev[i][j]) != cudaSuccess) return JABBA_ERR_CUDA;
+    const int mids[3] = {2, 4, 8}, bigs[3] = {4, 8, 4};
+    float mid_ms[3], big_ms[3];
+    c->ws.tier_ev = &te;
+    for (int r = 0; r < 3; ++r) {
+      c->ws.tune.local_mid_warps = mids[r];
+      c->ws.tune.local_big_warps = bigs[r];
+      run();
+      mid_ms[r] = elapsed_ms(te.ev[1][0], te.ev[1][1]);
+      big_ms[r] = elapsed_ms(te.ev[2][0], te.ev[2][1]);
+    }
+    c->ws.tier_ev = nullptr;
+    int bm = 0;
+    for (int r = 1; r < 3; ++r)
+      if (mid_ms[r] < mid_ms[bm]) bm = r;
+    c->ws.tune.local_mid_warps = mids[bm];
+    c->ws.tune.local_big_warps = big_ms[1] < fminf(big_ms[0], big_ms[2]) ? 8 : 4;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 2; ++j) cudaEventDestroy(te.ev[i][j]);
+    return cuda_ok(cudaGetLastError());
+  }
   mark(prof_event(c, 2, 0), st);
-  launch_sigma((const long long*)piece_stats, sigma, st);
-  launch_local(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt, n_domains, sigma, p->alpha,
-               p->scl, local_label, dom_group_cnt, (long long*)dom_group_off, groups, group_capacity,
-               (long long*)n_groups, c->ws, c->status, st);
+  run();
   mark(prof_event(c, 2, 1), st);
   return cuda_ok(cudaGetLastError());
 }
@@ -358,10 +445,36 @@ jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const i
   cudaStream_t st = (cudaStream_t)stream;
   jabba_status r = ensure(c, c->ws.cap_series, c->ws.cap_domains, c->ws.cap_slots, group_capacity, c->ws.cap_big, st);
   if (r != JABBA_OK) return r;
+  auto run = [&]() {
+    launch_merge(groups, (const long long*)n_groups, group_capacity, (const long long*)dom_group_off, sigma,
+                 p->alpha, p->scl, l2g, dict_len, dict_inc, (long long*)dict_count, dict_capacity, (long long*)k,
+                 c->ws, c->status, st);
+  };
+  if (c->tuning) {
+    if (capturing(st)) return JABBA_ERR_STATE;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return JABBA_ERR_CUDA;
+    const int cand[3] = {1, 2, 4};
+    int best = c->ws.tune.merge_ctas_per_sm;
+    float best_ms = 3.0e38f;
+    for (int r = 0; r < 3; ++r) {
+      c->ws.tune.merge_ctas_per_sm = cand[r];
+      cudaEventRecord(e0, st);
+      run();
+      cudaEventRecord(e1, st);
+      const float ms = elapsed_ms(e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand[r];
+      }
+    }
+    c->ws.tune.merge_ctas_per_sm = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_ok(cudaGetLastError());
+  }
   mark(prof_event(c, 3, 0), st);
-  launch_merge(groups, (const long long*)n_groups, group_capacity, (const long long*)dom_group_off, sigma, p->alpha,
-               p->scl, l2g, dict_len, dict_inc, (long long*)dict_count, dict_capacity, (long long*)k, c->ws,
-               c->status, st);
+  run();
   mark(prof_event(c, 3, 1), st);
   return cuda_ok(cudaGetLastError());
 }
@@ -446,6 +559,35 @@ jabba_status jabba_profile_elapsed(jabba_ctx* c, int slot, int stage, float* ms)
   cudaSetDevice(c->device);
   if (cudaEventSynchronize(b) != cudaSuccess) return JABBA_ERR_CUDA;
   return cuda_ok(cudaEventElapsedTime(ms, a, b));
+}
+
+jabba_status jabba_autotune(jabba_ctx* c, int enable) {
+  if (!c || (enable != 0 && enable != 1)) return JABBA_ERR_INVALID_ARG;
+  c->tuning = enable != 0;
+  return JABBA_OK;
+}
+
+jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
+  if (!c || !out) return JABBA_ERR_INVALID_ARG;
+  const Tuning& t = c->ws.tune;
+  out->compress_ctas_per_sm = t.compress_ctas_per_sm;
+  out->compress_pack = t.compress_pack;
+  out->local_mid_warps = t.local_mid_warps;
+  out->local_big_warps = t.local_big_warps;
+  out->merge_ctas_per_sm = t.merge_ctas_per_sm;
+  out->reserved[0] = out->reserved[1] = out->reserved[2] = 0;
+  return JABBA_OK;
+}
+
+jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
+  if (!c || !tuning_ok(in)) return JABBA_ERR_INVALID_ARG;
+  Tuning& t = c->ws.tune;
+  t.compress_ctas_per_sm = in->compress_ctas_per_sm;
+  t.compress_pack = in->compress_pack;
+  t.local_mid_warps = in->local_mid_warps;
+  t.local_big_warps = in->local_big_warps;
+  t.merge_ctas_per_sm = in->merge_ctas_per_sm;
+  return JABBA_OK;
 }
 
 jabba_status jabba_mse(jabba_ctx* c, const double* x, const double* xhat, int64_t n_points, double* out,

@@ -481,6 +481,12 @@ void launch_pack_domains(const long long* dom_begin, const long long* dom_end, l
 
 long long pack_buckets() { return kLenBuckets; }
 
+// Natural order (no packing): domain d goes to lane d % 32 of task d / 32.
+__global__ void k_dom_iota(long long n_domains, int* order) {
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n_domains; d += (long long)gridDim.x * blockDim.x)
+    order[d] = (int)d;
+}
+
 // ------------------------------------------------------------------ increments + statistics
 // One warp per domain (grid-stride): turns the end values written by
 // k_compress into increments inc_j = x_{e_j} - x_{s_j} (binary64, full-warp
@@ -616,11 +622,18 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   cudaMemsetAsync(ws.counters, 0, 4 * sizeof(unsigned), st);
   cudaMemsetAsync(stats, 0, JABBA_PIECE_STATS_BYTES, st);
   const long long n_tasks = (n_domains + 31) / 32;
-  long long ctas = (long long)ws.num_sms * 3;
+  int per_sm = ws.tune.compress_ctas_per_sm;
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 3) per_sm = 3;                      // the launch bounds allow 3 resident CTAs
+  long long ctas = (long long)ws.num_sms * per_sm;
   const long long need = (n_tasks + kWarpsPerCta - 1) / kWarpsPerCta;
   if (ctas > need) ctas = need;
-  launch_pack_domains(dom_begin, dom_end, n_domains, ws, st);
-  mark(mk.a0, st);
+  mark(mk.a0, st);  // the compression time includes the domain packing
+  if (ws.tune.compress_pack) {
+    launch_pack_domains(dom_begin, dom_end, n_domains, ws, st);
+  } else if (n_domains > 0) {
+    k_dom_iota<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(n_domains, ws.dom_order);
+  }
   if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, 0, st>>>(P);
   mark(mk.a1, st);
   mark(mk.b0, st);

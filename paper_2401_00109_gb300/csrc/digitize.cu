@@ -388,69 +388,26 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
 }
 
 // ------------------------------------------------------------------ shared-memory tiles
-// Domains of at most CAP pieces: W warps (one warp, or a whole CTA) own one
-// domain at a time with every per-piece array in shared memory.  Domains are
-// routed to the tile size that holds them (k_local_classify), so that small
-// domains run many warps per SM and large ones spread their sort, greedy and
-// sums over a CTA.
+// Domains of at most CAP pieces: W warps own one domain at a time with every
+// per-piece array in shared memory (W = 1: several independent warps per CTA).
+// The W warps share the sort and the sums; the greedy, which walks the starts
+// one after another, runs on the tile's first warp (one ballot pass per start
+// in the common case of a window shorter than 32 pieces).  Domains are routed
+// to the smallest tile that holds them (k_local_classify), so small domains
+// run many warps per SM.
 //
-// Per-domain shared memory (bytes): W * 1024 histograms, 4 CAP keys, 4 CAP X
-// (later sY), 4 CAP Y, 4 CAP sort temp (later sX), 2 CAP positions, 2 CAP sort
-// temp (later labels by position), 2 CAP labels by sorted index, 128 misc.
-// After the greedy, the 16 CAP bytes of keys and coordinates hold the group
-// accumulators (32 B per group), so CAP / 2 groups are summed per pass.
-// Stable LSD radix sort of (key, 16-bit val) by key, one warp (8-bit digits).
-__device__ void warp_radix_sort16(unsigned* key, unsigned short* val, unsigned* tk, unsigned short* tv, int n,
-                                  unsigned* hist) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  unsigned* kin = key;
-  unsigned short* vin = val;
-  unsigned* kout = tk;
-  unsigned short* vout = tv;
-  for (int shift = 0; shift < 32; shift += 8) {
-    for (int i = lane; i < 256; i += 32) hist[i] = 0;
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) atomicAdd(&hist[(kin[i] >> shift) & 255u], 1u);
-    __syncwarp();
-    unsigned loc[8], sum = 0;
-    for (int j = 0; j < 8; ++j) { loc[j] = hist[lane * 8 + j]; sum += loc[j]; }
-    unsigned incl = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    unsigned run = incl - sum;
-    __syncwarp();
-    for (int j = 0; j < 8; ++j) { hist[lane * 8 + j] = run; run += loc[j]; }
-    __syncwarp();
-    for (int i0 = 0; i0 < n; i0 += 32) {
-      const int i = i0 + lane;
-      const bool v = i < n;
-      const unsigned k = v ? kin[i] : 0u;
-      const unsigned short vv = v ? vin[i] : 0;
-      const unsigned d = v ? ((k >> shift) & 255u) : 256u + lane;
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-      const unsigned r = __popc(peers & lt);
-      if (v) {
-        const unsigned pos = hist[d] + r;
-        kout[pos] = k;
-        vout[pos] = vv;
-      }
-      __syncwarp();
-      if (v && r == 0) hist[d] += __popc(peers);
-      __syncwarp();
-    }
-    unsigned* t = kin; kin = kout; kout = t;
-    unsigned short* tt = vin; vin = vout; vout = tt;
-  }
-}
-
+// Per-tile shared memory: W * 1024 histogram bytes, then per piece 4 B key
+// (later sY), 4 B sort temp (later sX), 2 B position, 2 B sort temp (later
+// labels by position), 2 B label by sorted index, and 128 misc bytes.  The
+// FP32 key of a piece is recomputed from (sX, sY) by the same expression that
+// produced the sorted key, so it is not kept; after the greedy the 8 CAP bytes
+// of sX/sY hold the group accumulators (32 B per group, CAP / 4 per pass).
 template <int W, int CAP>
 struct TileCfg {
   static constexpr int kThreads = 32 * W;
-  static constexpr size_t kBytes = (size_t)W * 1024 + (size_t)CAP * 22 + 128;
-  static constexpr int kGroupsPerPass = CAP / 2;
+  static constexpr int kBlock = W == 1 ? 256 : 32 * W;
+  static constexpr size_t kBytes = (size_t)W * 1024 + (size_t)CAP * 14 + 128;
+  static constexpr int kGroupsPerPass = CAP / 4;
 };
 
 // Accumulator of one group during the sums: three 32-bit limbs of the
@@ -476,16 +433,22 @@ __device__ __forceinline__ bool tile_sync_or(bool p) {
   return __syncthreads_or(p) != 0;
 }
 
+__device__ __forceinline__ unsigned key32_of(float x, float y) { return __float_as_uint(fmaf(x, x, y * y)); }
+
 // Stable LSD radix sort of (key, val) by key with 8-bit digits over the W
-// warps of a tile: warp w sorts the contiguous segment [w seg, (w+1) seg) of
+// warps of a tile: warp w ranks the contiguous segment [w seg, (w+1) seg) of
 // the input into digit-major, warp-minor positions, so equal digits keep
-// their input order.  hist holds W x 256 counters; wsum W words.
+// their input order.  Thread t owns the 256 / (32 W) consecutive digits
+// starting at t * 256 / (32 W) for the offset scan.  hist: W x 256 counters;
+// wsum: W words.  The result is back in (key, val) after four passes.
 template <int W>
 __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* tk, unsigned short* tv, int n,
                                   unsigned* hist, unsigned* wsum) {
-  static_assert(W == 8, "one digit per thread: 256 threads");
+  constexpr int T = 32 * W;
+  constexpr int PER = 256 / T;
+  static_assert(PER * T == 256, "W must divide 8");
   const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) % W;
-  const int t = (threadIdx.x) % (32 * W);
+  const int t = threadIdx.x % T;
   const unsigned lt = (1u << lane) - 1u;
   const int seg = (((n + W - 1) / W) + 31) & ~31;
   const int lo = w * seg;
@@ -499,30 +462,41 @@ __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
     for (int i = lane; i < 256; i += 32) h[i] = 0;
     __syncwarp();
     for (int i = lo + lane; i < hi; i += 32) atomicAdd(&h[(kin[i] >> shift) & 255u], 1u);
-    __syncthreads();
-    // digit d = t (W = 8: one digit per thread): prefix over warps, then an
-    // exclusive scan of the digit totals over the CTA
+    tile_sync<W>();
     {
-      const int d = t;
-      unsigned run = 0;
-      for (int v = 0; v < W; ++v) {
-        const unsigned c = hist[v * 256 + d];
-        hist[v * 256 + d] = run;
-        run += c;
+      const int d0 = t * PER;
+      unsigned tot[PER];
+      unsigned sum = 0;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        unsigned run = 0;
+        for (int v = 0; v < W; ++v) {
+          const unsigned c = hist[v * 256 + d0 + k];
+          hist[v * 256 + d0 + k] = run;
+          run += c;
+        }
+        tot[k] = run;
+        sum += run;
       }
-      unsigned incl = run;
+      unsigned incl = sum;
       for (int o = 1; o < 32; o <<= 1) {
         const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += y;
       }
-      if (lane == 31) wsum[w] = incl;
-      __syncthreads();
       unsigned before = 0;
-      for (int v = 0; v < w; ++v) before += wsum[v];
-      const unsigned base = before + incl - run;
-      for (int v = 0; v < W; ++v) hist[v * 256 + d] += base;
+      if (W > 1) {
+        if (lane == 31) wsum[w] = incl;
+        tile_sync<W>();
+        for (int v = 0; v < w; ++v) before += wsum[v];
+      }
+      unsigned ex = before + incl - sum;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        for (int v = 0; v < W; ++v) hist[v * 256 + d0 + k] += ex;
+        ex += tot[k];
+      }
     }
-    __syncthreads();
+    tile_sync<W>();
     for (int i0 = lo; i0 < hi; i0 += 32) {
       const int i = i0 + lane;
       const bool v = i < hi;
@@ -540,37 +514,34 @@ __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
       if (v && r == 0) h[d] += __popc(peers);
       __syncwarp();
     }
-    __syncthreads();
+    tile_sync<W>();
     unsigned* tt = kin; kin = kout; kout = tt;
     unsigned short* tq = vin; vin = vout; vout = tq;
   }
-  // four passes: the result is back in (key, val)
 }
 
 template <int W, int CAP>
-__global__ void __launch_bounds__(W == 1 ? 256 : 32 * W) k_local_tile(LocalParams P, const int* list,
-                                                                       const unsigned* list_count,
-                                                                       unsigned* task_counter) {
+__global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalParams P, const int* list,
+                                                                        const unsigned* list_count,
+                                                                        unsigned* task_counter) {
   using Cfg = TileCfg<W, CAP>;
   constexpr int T = Cfg::kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
   const int tile = threadIdx.x / T;          // W == 1: one tile per warp
   const int t = threadIdx.x % T;
   unsigned char* base = smem_raw + (size_t)tile * Cfg::kBytes;
   unsigned* hist = (unsigned*)base;                                  // W * 256 words
-  unsigned* key = (unsigned*)(base + W * 1024);                      // [CAP] sorted keys
-  float* X = (float*)(key + CAP);                                    // [CAP] by position, then sY
-  float* Y = X + CAP;                                                // [CAP] by position
-  unsigned* tk = (unsigned*)(Y + CAP);                               // [CAP] sort temp, then sX
+  unsigned* key = (unsigned*)(base + W * 1024);                      // [CAP] sorted keys, then sY
+  unsigned* tk = key + CAP;                                          // [CAP] sort temp, then sX
   unsigned short* idx = (unsigned short*)(tk + CAP);                 // [CAP] sorted index -> position
   unsigned short* tv = idx + CAP;                                    // [CAP] sort temp, then labels by position
   short* lab = (short*)(tv + CAP);                                   // [CAP] label by sorted index
   int* misc = (int*)(lab + CAP);                                     // 32 words
   float* sX = (float*)tk;
-  float* sY = X;
+  float* sY = (float*)key;
   short* plab = (short*)tv;
-  GroupAcc* acc = (GroupAcc*)key;                                    // after the greedy: CAP / 2 groups
-  int* nx = misc;                                                    // [3] next-start candidates
+  GroupAcc* acc = (GroupAcc*)key;                                    // after the greedy: CAP / 4 groups
   unsigned* wsum = (unsigned*)(misc + 4);                            // [W] sort scan
   long long* gbase_s = (long long*)(misc + 16);                      // group record base
   const double a2 = __dmul_rn(P.alpha, P.alpha);
@@ -593,64 +564,58 @@ __global__ void __launch_bounds__(W == 1 ? 256 : 32 * W) k_local_tile(LocalParam
     const long long slot = P.dom_slot_off[d];
     const int* plen = P.piece_len + slot;
     const double* pinc = P.piece_inc + slot;
-    // 1. FP32 coordinates and keys by position
+    // 1. FP32 keys by position
     for (int i = t; i < n; i += T) {
       unsigned mh;
       const float x = x32_of(P, plen[i]);
       const float y = f64_to_f32_trunc(pinc[i], mh) * rinv;
-      X[i] = x;
-      Y[i] = y;
-      key[i] = __float_as_uint(fmaf(x, x, y * y));
+      key[i] = key32_of(x, y);
       idx[i] = (unsigned short)i;
     }
     tile_sync<W>();
     // 2. sort by (key32, position)
-    if (n > 1) {
-      if constexpr (W == 1) warp_radix_sort16(key, idx, tk, tv, n, hist);
-      else tile_radix_sort16<W>(key, idx, tk, tv, n, hist, wsum);
+    if (n > 1) tile_radix_sort16<W>(key, idx, tk, tv, n, hist, wsum);
+    tile_sync<W>();
+    // 3. runs of overlapping key intervals: re-sort by the binary64 keys (rare;
+    // the whole tile first checks whether any neighbouring pair overlaps)
+    {
+      bool ov = false;
+      for (int a = t; a + 1 < n; a += T) ov = ov || keys_overlap32(key[a], key[a + 1]);
+      if (tile_sync_or<W>(ov)) {
+        if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n);
+        tile_sync<W>();
+      }
     }
-    tile_sync<W>();
-    // 3. runs of overlapping key intervals: re-sort by the binary64 keys (rare)
-    if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n);
-    tile_sync<W>();
-    // 4. coordinates in key order: sX into the sort temp, then sY into X's slot
-    for (int a = t; a < n; a += T) sX[a] = X[idx[a]];
-    tile_sync<W>();
+    // 4. coordinates in key order (gathered again from the pieces, which are
+    // in L1/L2), over the keys and the sort temp
     for (int a = t; a < n; a += T) {
-      sY[a] = Y[idx[a]];
+      const int p = idx[a];
+      unsigned mh;
+      sX[a] = x32_of(P, plen[p]);
+      sY[a] = f64_to_f32_trunc(pinc[p], mh) * rinv;
       lab[a] = -1;
     }
-    if (t == 0) {
-      nx[0] = 0x7FFFFFFF;
-      nx[1] = 0x7FFFFFFF;
-      nx[2] = 0x7FFFFFFF;
-    }
     tile_sync<W>();
-    // 5. greedy in key order.  Item a is a start; one pass over (a, n) in
-    // chunks of T tests the window of a (members join), and the first item
-    // left free in the chunks passed is the next start (atomicMin into a
-    // triple-buffered slot: buffer it % 3 is written in pass it, reset in pass
-    // it - 1 and last read in pass it - 2).
-    int G = 0;
-    {
-      int a = 0, it = 0;
+    // 5. greedy in key order on the first warp: each start's window pass also
+    // finds the first piece left free behind the start (the next start)
+    if (t < 32) {
+      int G = 0, a = 0;
       while (a < n) {
-        if (t == 0) lab[a] = (short)G;
         const float xs = sX[a], ys = sY[a];
-        const float Tk = key_stop(__uint_as_float(key[a]), P.alpha_up);
+        const float Tk = key_stop(__uint_as_float(key32_of(xs, ys)), P.alpha_up);
+        if (lane == 0) lab[a] = (short)G;
         int next = n;
         int b0 = a + 1;
-        for (;;) {
-          int* slotp = &nx[it % 3];
-          if (t == 0) nx[(it + 1) % 3] = 0x7FFFFFFF;
-          const int b = b0 + t;
-          bool past = true;
+        for (; b0 < n; b0 += 32) {
+          const int b = b0 + lane;
+          bool stop = true, fr = false;
           if (b < n) {
-            past = __uint_as_float(key[b]) * (1.0f - kKeyRel) > Tk;
+            const float xb = sX[b], yb = sY[b];
+            stop = __uint_as_float(key32_of(xb, yb)) * (1.0f - kKeyRel) > Tk;
             if (lab[b] < 0) {
               bool join = false;
-              if (!past) {
-                int w = filter_within(xs, ys, sX[b], sY[b], P.a2lo, P.a2hi);
+              if (!stop) {
+                int w = filter_within(xs, ys, xb, yb, P.a2lo, P.a2hi);
                 if (w == 2) {
                   const int ps = idx[a], pb = idx[b];
                   w = exact_within(P, plen[ps], pinc[ps], plen[pb], pinc[pb], a2) ? 1 : 0;
@@ -658,34 +623,32 @@ __global__ void __launch_bounds__(W == 1 ? 256 : 32 * W) k_local_tile(LocalParam
                 join = w != 0;
               }
               if (join) lab[b] = (short)G;
-              else atomicMin(slotp, b);
+              else fr = true;
             }
           }
-          const bool any_past = tile_sync_or<W>(past);
-          const int m = *slotp;
-          ++it;
-          if (m < next) next = m;
-          if (any_past) break;
-          b0 += T;
+          const unsigned mf = __ballot_sync(0xFFFFFFFFu, fr);
+          if (mf && next == n) next = b0 + __ffs(mf) - 1;
+          if (__any_sync(0xFFFFFFFFu, stop)) break;
         }
         // nothing left free up to the window's last chunk: search on
-        while (next == n) {
-          b0 += T;
-          if (b0 >= n) break;
-          int* slotp = &nx[it % 3];
-          if (t == 0) nx[(it + 1) % 3] = 0x7FFFFFFF;
-          const int b = b0 + t;
-          if (b < n && lab[b] < 0) atomicMin(slotp, b);
-          tile_sync<W>();
-          const int m = *slotp;
-          ++it;
-          if (m < next) next = m;
+        if (next == n) {
+          for (b0 += 32; b0 < n; b0 += 32) {
+            const int b = b0 + lane;
+            const unsigned mf = __ballot_sync(0xFFFFFFFFu, b < n && lab[b] < 0);
+            if (mf) {
+              next = b0 + __ffs(mf) - 1;
+              break;
+            }
+          }
         }
+        __syncwarp();
         ++G;
         a = next;
       }
+      if (lane == 0) misc[13] = G;
     }
     tile_sync<W>();
+    const int G = misc[13];
     // 6. labels by position, written out coalesced
     for (int a = t; a < n; a += T) plab[idx[a]] = lab[a];
     tile_sync<W>();
@@ -805,7 +768,7 @@ template <int W, int CAP>
 static void launch_tile(const LocalParams& P, const int* list, const unsigned* cnt, unsigned* ctr, int num_sms,
                         cudaStream_t st) {
   using Cfg = TileCfg<W, CAP>;
-  constexpr int kBlock = 256;
+  constexpr int kBlock = Cfg::kBlock;
   constexpr size_t kSmem = (size_t)(kBlock / Cfg::kThreads) * Cfg::kBytes;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
@@ -859,9 +822,21 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
     const unsigned g = (unsigned)(ws.num_sms * 4);
     k_local_classify<<<g, 256, 0, st>>>(dom_piece_cnt, n_domains, dom_group_cnt, ws.loc_list, ws.loc_stride,
                                         list_cnt);
+    TierEvents* te = ws.tier_ev;
+    if (te) cudaEventRecord(te->ev[0][0], st);
     launch_tile<1, kTierCap0>(P, ws.loc_list, list_cnt + 0, task_ctr + 0, ws.num_sms, st);
-    launch_tile<8, kTierCap1>(P, ws.loc_list + ws.loc_stride, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
-    launch_tile<8, kTierCap2>(P, ws.loc_list + 2 * ws.loc_stride, list_cnt + 2, task_ctr + 2, ws.num_sms, st);
+    if (te) cudaEventRecord(te->ev[0][1], st);
+    const int* l1 = ws.loc_list + ws.loc_stride;
+    if (te) cudaEventRecord(te->ev[1][0], st);
+    if (ws.tune.local_mid_warps == 2) launch_tile<2, kTierCap1>(P, l1, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
+    else if (ws.tune.local_mid_warps == 8) launch_tile<8, kTierCap1>(P, l1, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
+    else launch_tile<4, kTierCap1>(P, l1, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
+    if (te) cudaEventRecord(te->ev[1][1], st);
+    const int* l2 = ws.loc_list + 2 * ws.loc_stride;
+    if (te) cudaEventRecord(te->ev[2][0], st);
+    if (ws.tune.local_big_warps == 8) launch_tile<8, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ws.num_sms, st);
+    else launch_tile<4, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ws.num_sms, st);
+    if (te) cudaEventRecord(te->ev[2][1], st);
     k_local_warp<<<(unsigned)ws.loc_ctas, kLocWarps * 32, 0, st>>>(P);
   }
   exclusive_scan<int>(dom_group_cnt, n_domains, dom_group_off, ws.scan_tiles, st);

@@ -43,9 +43,26 @@ struct MergeBufs {
   double* ekey = nullptr;
 };
 
+// Launch configuration of the batched kernels (chosen by the autotuner of
+// api.cu, or set by the caller).  Every choice computes the same result.
+struct Tuning {
+  int compress_ctas_per_sm = 3;  // resident CTAs per SM of the persistent compression kernel (1..3)
+  int compress_pack = 1;         // 1: domains handed to warps longest first; 0: natural order
+  int local_mid_warps = 4;       // warps per domain of 257..2048 pieces (2, 4 or 8)
+  int local_big_warps = 4;       // warps per domain of 2049..4096 pieces (4 or 8)
+  int merge_ctas_per_sm = 4;     // CTAs per SM of the cooperative merge-rounds kernel (1, 2 or 4)
+};
+
+// Events around the local-aggregation kernels of the tiles (tuning only).
+struct TierEvents {
+  cudaEvent_t ev[3][2] = {};
+};
+
 // Scratch owned by a context (device memory).  Sized by jabba_reserve().
 struct Scratch {
   int num_sms = 0;
+  Tuning tune;
+  TierEvents* tier_ev = nullptr;  // non-null while the autotuner times the tiles
   long long cap_series = 0, cap_domains = 0, cap_slots = 0, cap_groups = 0, cap_points = 0;
   long long cap_big = 0;          // elements of the big-domain aggregation scratch
   long long* series_a = nullptr;  // [cap_series + 1]

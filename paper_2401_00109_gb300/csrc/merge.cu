@@ -1089,12 +1089,14 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   R.max_rounds = 1u << 22;
   {
     // cooperative launch: every block resident, so the bounded grid barrier can complete
-    static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_mrounds, 256, 0);
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
-      if (blocks_per_sm > 4) blocks_per_sm = 4;
+    static int max_per_sm = -1;
+    if (max_per_sm < 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm, k_mrounds, 256, 0);
+      if (max_per_sm < 1) max_per_sm = 1;
     }
+    int blocks_per_sm = ws.tune.merge_ctas_per_sm;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    if (blocks_per_sm > max_per_sm) blocks_per_sm = max_per_sm;  // co-residency of the cooperative grid
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ws.num_sms * blocks_per_sm));
     cfg.blockDim = dim3(256);
