@@ -10,8 +10,10 @@ log-uniform lengths in [100, 100,000], ~1.44e9 points, 11.5 GB of float64 --
 far larger than L2, so no flush is needed between steps).
 
 Forms timed: "batched" = the whole step captured once in a CUDA graph and
-replayed (persistent work-stealing kernels); "plain" = the same C-ABI calls
-issued eagerly.  The CPU oracle is timed on a bounded sample of the same
+replayed (persistent work-stealing kernels, autotuned launch configuration);
+"plain" = the unbatched form, one compression launch and one Stage I launch
+per domain issued eagerly, timed on a bounded sample of the same workload
+(the first --plain-series series) next to the batched form on that sample.  The CPU oracle is timed on a bounded sample of the same
 workload on the host cores (`cpu_baseline`); `--impl reference` times only
 that oracle, as the reference arm.
 
@@ -266,20 +268,12 @@ def run_ours(args, ws, rank, local):
     N, G, k = res["n_pieces"], res["n_groups"], res["k"]
     value = ws * n / (ms_all * 1e-3) / 1e9
 
-    # ---- plain: the same calls issued eagerly, no graph
+    # ---- plain: the unbatched form (one compression launch and one Stage I
+    # launch per domain, eager, no graph) on a bounded sample of the same
+    # workload, next to the batched form on that sample
     plain = None
     if not args.no_plain:
-        for _ in range(2):
-            pl.enqueue()
-        torch.cuda.synchronize()
-        e0.record(st)
-        for _ in range(args.steps):
-            pl.enqueue()
-        e1.record(st)
-        torch.cuda.synchronize()
-        pms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
-        plain = dict(value=ws * n / (pms * 1e-3) / 1e9, unit="Gpts/s", ms_per_step=pms,
-                     form="same C-ABI calls issued eagerly per step (no CUDA graph)")
+        plain = plain_form(jb, synth, args, local, ws)
 
     # ---- e2e: H2D of the series from pinned memory, the step, D2H of the
     # symbols and dictionary, all inside the timed region
@@ -357,6 +351,52 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def plain_form(jb, synth, args, local, ws):
+    import torch
+    xs, offs, cfgs = synth.make(args.workload, max_series=args.plain_series)
+    p = jb.Params(tol=cfgs["tol"], alpha=cfgs["alpha"], scl=cfgs["scl"], domain_mode=cfgs["domain_mode"],
+                  domain_value=cfgs["domain_value"])
+    n = len(xs)
+    out = {}
+    for form in ("plain", "batched"):
+        c = jb.Context(local)
+        c.set_tuning(dict(per_domain_launch=1 if form == "plain" else 0))
+        pl = jb.Pipeline(c, offs, n, p, group_capacity=max(1 << 12, n // 4))
+        pl.x.copy_(torch.from_numpy(xs))
+        pl.enqueue()
+        c.sync_status(where=form + " sample")
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if form == "plain":
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(args.plain_steps):
+                pl.enqueue()
+            e1.record(st)
+        else:
+            g = pl.capture()
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(args.plain_steps):
+                g.replay()
+            e1.record(st)
+        torch.cuda.synchronize()
+        c.sync_status(where=form + " sample steps")
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.plain_steps, ws)
+        out[form] = dict(value=ws * n / (ms * 1e-3) / 1e9, ms_per_step=ms)
+        del pl, c
+    pl_ = out["plain"]
+    return dict(value=pl_["value"], unit="Gpts/s", ms_per_step=pl_["ms_per_step"],
+                sample=f"first {args.plain_series} series of the workload ({n} points, "
+                       f"{jb.Context.plan(offs, p)[0]} domains)",
+                form="per-domain launches: one compression launch and one Stage I launch per domain, "
+                     "issued eagerly (no CUDA graph); normalisation, merge and label propagation as single launches",
+                batched_same_sample=dict(value=out["batched"]["value"], unit="Gpts/s",
+                                         ms_per_step=out["batched"]["ms_per_step"]))
+
+
 def verify_sample(pl, x, off, cfg, n_dom):
     """Full-size parity on a sample: the oracle compresses n_dom domains drawn
     at random and must reproduce their pieces bit for bit."""
@@ -393,6 +433,8 @@ def main():
     ap.add_argument("--max-series", type=int, default=None)
     ap.add_argument("--cpu-series", type=int, default=2000)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-series", type=int, default=300, help="series in the plain-form sample")
+    ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")

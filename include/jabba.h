@@ -232,7 +232,7 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
 /* ---------------------------------------------------------------- launch tuning
  * (No counterpart in the paper.)  Launch configuration of the batched
  * kernels.  Every configuration computes the same results (bit for bit); only
- * the speed differs.  Defaults: {3, 1, 4, 4, 4}. */
+ * the speed differs.  Defaults: {3, 1, 4, 4, 4, 0}. */
 typedef struct {
   int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
@@ -240,7 +240,11 @@ typedef struct {
   int32_t local_big_warps;      /* warps that aggregate one domain of 2049..4096 pieces together: 4 or 8       */
   int32_t merge_ctas_per_sm;    /* CTAs per SM of the cooperative merge-rounds kernel: 1, 2 or 4 (capped by the
                                    kernel's occupancy so that the grid stays co-resident)                     */
-  int32_t reserved[3];          /* zero                                                                      */
+  int32_t per_domain_launch;    /* 1 = the plain (unbatched) form: jabba_compress and jabba_digitize_local
+                                   issue one kernel launch per domain, eagerly (they read the piece counts
+                                   back to the host); refused during graph capture and autotuning
+                                   (JABBA_ERR_STATE).  0 = the batched persistent launches (default)         */
+  int32_t reserved[2];          /* zero                                                                      */
 } jabba_tuning;
 
 /* Autotuning mode.  While enabled (enable = 1), each call of jabba_compress,

@@ -63,10 +63,12 @@ class Params:
 
 class _Tuning(C.Structure):
     _fields_ = [("compress_ctas_per_sm", C.c_int32), ("compress_pack", C.c_int32), ("local_mid_warps", C.c_int32),
-                ("local_big_warps", C.c_int32), ("merge_ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("local_big_warps", C.c_int32), ("merge_ctas_per_sm", C.c_int32), ("per_domain_launch", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
-TUNING_FIELDS = ("compress_ctas_per_sm", "compress_pack", "local_mid_warps", "local_big_warps", "merge_ctas_per_sm")
+TUNING_FIELDS = ("compress_ctas_per_sm", "compress_pack", "local_mid_warps", "local_big_warps", "merge_ctas_per_sm",
+                 "per_domain_launch")
 
 JABBA_GROUP_BYTES = 48
 PIECE_STATS_BYTES = 256

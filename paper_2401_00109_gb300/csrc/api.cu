@@ -83,6 +83,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.counters = (unsigned*)take(64);
   w.dom_order = (int*)take(4 * (D > 0 ? D : 1));
   w.loc_list = (int*)take(16 * (D > 0 ? D : 1));
+  w.plain_ctr = (unsigned*)take(4 * (D > 0 ? D : 1) + 16);
   if (base) w.loc_stride = D > 0 ? D : 1;
   w.pack_hist = (int*)take(4 * pack_buckets());
   w.pack_off = (long long*)take(8 * (pack_buckets() + 1));
@@ -214,7 +215,8 @@ bool tuning_ok(const jabba_tuning* t) {
   if (t->local_mid_warps != 2 && t->local_mid_warps != 4 && t->local_mid_warps != 8) return false;
   if (t->local_big_warps != 4 && t->local_big_warps != 8) return false;
   if (t->merge_ctas_per_sm != 1 && t->merge_ctas_per_sm != 2 && t->merge_ctas_per_sm != 4) return false;
-  for (int i = 0; i < 3; ++i)
+  if (t->per_domain_launch != 0 && t->per_domain_launch != 1) return false;
+  for (int i = 0; i < 2; ++i)
     if (t->reserved[i] != 0) return false;
   return true;
 }
@@ -346,6 +348,7 @@ jabba_status jabba_compress(jabba_ctx* c, const double* x, int64_t n_points, con
                     (const long long*)dom_slot_off, n_domains, p->tol, piece_len, piece_inc, dom_piece_cnt,
                     (long long*)dom_piece_off, (long long*)piece_stats, c->ws, c->status, st, m);
   };
+  if (c->ws.tune.per_domain_launch && (capturing(st) || c->tuning)) return JABBA_ERR_STATE;
   if (c->tuning) {
     // every candidate once on these inputs; the packing and the kernel are timed together
     if (capturing(st)) return JABBA_ERR_STATE;
@@ -399,6 +402,7 @@ jabba_status jabba_digitize_local(jabba_ctx* c, const int32_t* piece_len, const 
                  p->scl, local_label, dom_group_cnt, (long long*)dom_group_off, groups, group_capacity,
                  (long long*)n_groups, c->ws, c->status, st);
   };
+  if (c->ws.tune.per_domain_launch && (capturing(st) || c->tuning)) return JABBA_ERR_STATE;
   if (c->tuning) {
     // three runs cover every tile variant: (mid, big) = (2, 4), (4, 8), (8, 4); each tile kernel is timed
     if (capturing(st)) return JABBA_ERR_STATE;
@@ -575,7 +579,8 @@ jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
   out->local_mid_warps = t.local_mid_warps;
   out->local_big_warps = t.local_big_warps;
   out->merge_ctas_per_sm = t.merge_ctas_per_sm;
-  out->reserved[0] = out->reserved[1] = out->reserved[2] = 0;
+  out->per_domain_launch = t.per_domain_launch;
+  out->reserved[0] = out->reserved[1] = 0;
   return JABBA_OK;
 }
 
@@ -587,6 +592,7 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.local_mid_warps = in->local_mid_warps;
   t.local_big_warps = in->local_big_warps;
   t.merge_ctas_per_sm = in->merge_ctas_per_sm;
+  t.per_domain_launch = in->per_domain_launch;
   return JABBA_OK;
 }
 

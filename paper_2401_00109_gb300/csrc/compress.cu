@@ -108,6 +108,7 @@ struct CompressParams {
   const long long* dom_end;
   const long long* dom_slot_off;
   const int* dom_order;  // domains, longest first
+  long long n_order;     // entries of dom_order this launch processes
   long long n_domains;
   double tol2;        // tol * tol, binary64
   float tol_lo;       // tol (1 - 2^-18) rounded down
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
   unsigned phase0 = 0, phase1 = 0;
   const unsigned bar0 = smem_u32(&bars[warp][0]);
   const unsigned bar1 = smem_u32(&bars[warp][1]);
-  const long long n_tasks = (P.n_domains + 31) / 32;
+  const long long n_tasks = (P.n_order + 31) / 32;
   LaneState L;
   L.amax = 0;
 
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
     task = __shfl_sync(0xFFFFFFFFu, task, 0);
     if (task >= n_tasks) break;
     const long long dt = task * 32 + lane;
-    const long long d = dt < P.n_domains ? (long long)P.dom_order[dt] : P.n_domains;
+    const long long d = dt < P.n_order ? (long long)P.dom_order[dt] : P.n_domains;
     LaneDomain D;
     long long slot = 0;
     D.b = 0;
@@ -602,6 +603,7 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   P.dom_slot_off = dom_slot_off;
   P.dom_order = ws.dom_order;
   P.n_domains = n_domains;
+  P.n_order = n_domains;
   P.tol2 = tol * tol;
   {
     // tau also carries an absolute 2^-100 (conversion of |x| < 2^-126), so the
@@ -629,12 +631,27 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   const long long need = (n_tasks + kWarpsPerCta - 1) / kWarpsPerCta;
   if (ctas > need) ctas = need;
   mark(mk.a0, st);  // the compression time includes the domain packing
-  if (ws.tune.compress_pack) {
-    launch_pack_domains(dom_begin, dom_end, n_domains, ws, st);
-  } else if (n_domains > 0) {
-    k_dom_iota<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(n_domains, ws.dom_order);
+  if (ws.tune.per_domain_launch) {
+    // the plain form: one launch (one CTA, one active lane) per domain, in order
+    if (n_domains > 0) {
+      k_dom_iota<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(n_domains, ws.dom_order);
+      cudaMemsetAsync(ws.plain_ctr, 0, sizeof(unsigned) * (size_t)n_domains, st);
+    }
+    CompressParams Q = P;
+    Q.n_order = 1;
+    for (long long d = 0; d < n_domains; ++d) {
+      Q.dom_order = ws.dom_order + d;
+      Q.task_counter = ws.plain_ctr + d;
+      k_compress<<<1, kWarpsPerCta * 32, 0, st>>>(Q);
+    }
+  } else {
+    if (ws.tune.compress_pack) {
+      launch_pack_domains(dom_begin, dom_end, n_domains, ws, st);
+    } else if (n_domains > 0) {
+      k_dom_iota<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(n_domains, ws.dom_order);
+    }
+    if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, 0, st>>>(P);
   }
-  if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, 0, st>>>(P);
   mark(mk.a1, st);
   mark(mk.b0, st);
   if (n_domains > 0) {

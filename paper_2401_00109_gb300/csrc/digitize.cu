@@ -764,6 +764,32 @@ static float round_up_f(double v) {
   return f;
 }
 
+__global__ void k_set_one(unsigned* p) { *p = 1u; }
+
+// Plain form: list[d] = d, and no groups for empty domains.
+__global__ void k_local_plain_prep(const int* dom_piece_cnt, long long n_domains, int* dom_group_cnt, int* list) {
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n_domains; d += (long long)gridDim.x * blockDim.x) {
+    list[d] = (int)d;
+    if (dom_piece_cnt[d] == 0) dom_group_cnt[d] = 0;
+  }
+}
+__global__ void k_set_status(unsigned* status, unsigned code) { set_status(status, code); }
+
+// One launch of a tile kernel for a single domain (the plain form): one CTA
+// holding one tile.
+template <int W, int CAP>
+static void launch_tile_one(const LocalParams& P, const int* list, const unsigned* one, unsigned* ctr,
+                            cudaStream_t st) {
+  using Cfg = TileCfg<W, CAP>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_local_tile<W, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((Cfg::kBlock / Cfg::kThreads) * Cfg::kBytes));
+    attr = true;
+  }
+  k_local_tile<W, CAP><<<1, Cfg::kThreads, Cfg::kBytes, st>>>(P, list, one, ctr);
+}
+
 template <int W, int CAP>
 static void launch_tile(const LocalParams& P, const int* list, const unsigned* cnt, unsigned* ctr, int num_sms,
                         cudaStream_t st) {
@@ -820,6 +846,40 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
   P.cap_items = ws.cap_items;
   if (n_domains > 0) {
     const unsigned g = (unsigned)(ws.num_sms * 4);
+    if (ws.tune.per_domain_launch) {
+      // the plain form: one launch per domain, its tile chosen on the host from
+      // the piece count (read back); the list entries are 0..D-1
+      unsigned* one = ws.counters + 15;
+      k_local_plain_prep<<<g, 256, 0, st>>>(dom_piece_cnt, n_domains, dom_group_cnt, ws.loc_list);
+      k_set_one<<<1, 1, 0, st>>>(one);
+      cudaMemsetAsync(ws.plain_ctr, 0, sizeof(unsigned) * (size_t)n_domains, st);
+      int* cnt_h = (int*)malloc(sizeof(int) * (size_t)n_domains);
+      if (!cnt_h) {
+        k_set_status<<<1, 1, 0, st>>>(status, JABBA_ERR_CUDA);
+      } else {
+        cudaMemcpyAsync(cnt_h, dom_piece_cnt, sizeof(int) * (size_t)n_domains, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        for (long long dd = 0; dd < n_domains; ++dd) {
+          const int n = cnt_h[dd];
+          if (n == 0) continue;
+          const int* l = ws.loc_list + dd;
+          unsigned* c = ws.plain_ctr + dd;
+          if (n <= kTierCap0) launch_tile_one<1, kTierCap0>(P, l, one, c, st);
+          else if (n <= kTierCap1) launch_tile_one<4, kTierCap1>(P, l, one, c, st);
+          else if (n <= kTierCap2) launch_tile_one<8, kTierCap2>(P, l, one, c, st);
+          else {
+            LocalParams Q = P;
+            Q.list = l;
+            Q.list_count = one;
+            Q.task_counter = c;
+            k_local_warp<<<1, 32 * kLocWarps, 0, st>>>(Q);
+          }
+        }
+        free(cnt_h);
+      }
+      exclusive_scan<int>(dom_group_cnt, n_domains, dom_group_off, ws.scan_tiles, st);
+      return;
+    }
     k_local_classify<<<g, 256, 0, st>>>(dom_piece_cnt, n_domains, dom_group_cnt, ws.loc_list, ws.loc_stride,
                                         list_cnt);
     TierEvents* te = ws.tier_ev;

@@ -51,6 +51,7 @@ struct Tuning {
   int local_mid_warps = 4;       // warps per domain of 257..2048 pieces (2, 4 or 8)
   int local_big_warps = 4;       // warps per domain of 2049..4096 pieces (4 or 8)
   int merge_ctas_per_sm = 4;     // CTAs per SM of the cooperative merge-rounds kernel (1, 2 or 4)
+  int per_domain_launch = 0;     // 1: the plain form, one launch per domain for compression and Stage I
 };
 
 // Events around the local-aggregation kernels of the tiles (tuning only).
@@ -71,6 +72,7 @@ struct Scratch {
   long long* scan_tiles = nullptr;
   unsigned* counters = nullptr;   // [16]: task counters, diagnostics
   int* dom_order = nullptr;       // [cap_domains] domains, longest first
+  unsigned* plain_ctr = nullptr;  // [cap_domains] task counters of the per-domain launches (plain form)
   int* pack_hist = nullptr;       // [65536] length buckets
   long long* pack_off = nullptr;  // [65537]
   // local aggregation: per-warp arenas and the FP32 normalisation tables

@@ -24,9 +24,15 @@ def sample():
 
 
 CONFIGS = [
-    dict(compress_ctas_per_sm=1, compress_pack=0, local_mid_warps=2, local_big_warps=4, merge_ctas_per_sm=1),
-    dict(compress_ctas_per_sm=2, compress_pack=1, local_mid_warps=8, local_big_warps=8, merge_ctas_per_sm=2),
-    dict(compress_ctas_per_sm=3, compress_pack=1, local_mid_warps=4, local_big_warps=4, merge_ctas_per_sm=4),
+    dict(compress_ctas_per_sm=1, compress_pack=0, local_mid_warps=2, local_big_warps=4, merge_ctas_per_sm=1,
+         per_domain_launch=0),
+    dict(compress_ctas_per_sm=2, compress_pack=1, local_mid_warps=8, local_big_warps=8, merge_ctas_per_sm=2,
+         per_domain_launch=0),
+    dict(compress_ctas_per_sm=3, compress_pack=1, local_mid_warps=4, local_big_warps=4, merge_ctas_per_sm=4,
+         per_domain_launch=0),
+    # the plain form: one launch per domain for compression and Stage I
+    dict(compress_ctas_per_sm=3, compress_pack=1, local_mid_warps=4, local_big_warps=4, merge_ctas_per_sm=4,
+         per_domain_launch=1),
 ]
 
 
@@ -42,6 +48,7 @@ def test_every_configuration_matches_oracle(C, sample, cfg_t):
 def test_autotune_picks_valid_configuration(C, sample):
     import paper_2401_00109_gb300 as jb
     x, off, cfg, r = sample
+    C.set_tuning(dict(per_domain_launch=0))
     C.autotune(True)
     try:
         g, *_ = run_gpu(C, x, off, cfg, recon=False)
@@ -51,11 +58,25 @@ def test_autotune_picks_valid_configuration(C, sample):
     t = C.tuning()
     assert t["compress_ctas_per_sm"] in (1, 2, 3) and t["compress_pack"] in (0, 1)
     assert t["local_mid_warps"] in (2, 4, 8) and t["local_big_warps"] in (4, 8)
-    assert t["merge_ctas_per_sm"] in (1, 2, 4)
+    assert t["merge_ctas_per_sm"] in (1, 2, 4) and t["per_domain_launch"] == 0
     # the configuration chosen keeps producing the oracle's result
     g, *_ = run_gpu(C, x, off, cfg, recon=False)
     assert_parity(g, r, recon=False)
-    for bad in (dict(compress_ctas_per_sm=4), dict(local_mid_warps=3), dict(merge_ctas_per_sm=0)):
+    for bad in (dict(compress_ctas_per_sm=4), dict(local_mid_warps=3), dict(merge_ctas_per_sm=0),
+                dict(per_domain_launch=2)):
         with pytest.raises(jb.JabbaError):
             C.set_tuning(bad)
     assert C.tuning() == t
+
+
+def test_plain_form_refused_while_tuning(C, sample):
+    import paper_2401_00109_gb300 as jb
+    x, off, cfg, r = sample
+    C.set_tuning(dict(per_domain_launch=1))
+    C.autotune(True)
+    try:
+        with pytest.raises(jb.JabbaError):
+            run_gpu(C, x, off, cfg, recon=False)
+    finally:
+        C.autotune(False)
+        C.set_tuning(dict(per_domain_launch=0))
