@@ -232,11 +232,13 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
 /* ---------------------------------------------------------------- launch tuning
  * (No counterpart in the paper.)  Launch configuration of the batched
  * kernels.  Every configuration computes the same results (bit for bit); only
- * the speed differs.  Defaults: {3, 1, 4, 4, 4, 0}. */
+ * the speed differs.  Domains of up to 512 pieces are aggregated by one warp
+ * each; larger domains by the number of warps chosen here.
+ * Defaults: {3, 1, 4, 4, 4, 0, 1}. */
 typedef struct {
   int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
-  int32_t local_mid_warps;      /* warps that aggregate one domain of 257..2048 pieces together: 2, 4 or 8     */
+  int32_t local_mid_warps;      /* warps that aggregate one domain of 1025..2048 pieces together: 1, 2, 4, 8   */
   int32_t local_big_warps;      /* warps that aggregate one domain of 2049..4096 pieces together: 4 or 8       */
   int32_t merge_ctas_per_sm;    /* CTAs per SM of the cooperative merge-rounds kernel: 1, 2 or 4 (capped by the
                                    kernel's occupancy so that the grid stays co-resident)                     */
@@ -244,7 +246,8 @@ typedef struct {
                                    issue one kernel launch per domain, eagerly (they read the piece counts
                                    back to the host); refused during graph capture and autotuning
                                    (JABBA_ERR_STATE).  0 = the batched persistent launches (default)         */
-  int32_t reserved[2];          /* zero                                                                      */
+  int32_t local_k_warps;        /* warps that aggregate one domain of 513..1024 pieces together: 1 or 4        */
+  int32_t reserved;             /* zero                                                                      */
 } jabba_tuning;
 
 /* Autotuning mode.  While enabled (enable = 1), each call of jabba_compress,
@@ -253,8 +256,8 @@ typedef struct {
  * events, keeps the fastest in the context and returns after synchronizing
  * `stream` (the outputs are those of the call, as without tuning).  Candidates:
  * compression {1, 2, 3} CTAs per SM x {packed, in order}; local aggregation
- * {2, 4, 8} warps per mid-size domain and {4, 8} per large domain; merge
- * {1, 2, 4} CTAs per SM.  Tuning calls must not be captured in a CUDA graph
+ * {1, 4} warps per domain of 513..1024 pieces, {1, 2, 4, 8} of 1025..2048 and
+ * {4, 8} of 2049..4096; merge {1, 2, 4} CTAs per SM.  Tuning calls must not be captured in a CUDA graph
  * (JABBA_ERR_STATE).  enable = 0 ends the mode; the choice stays in effect. */
 jabba_status jabba_autotune(jabba_ctx* ctx, int enable);
 /* Current configuration of the context. */

@@ -82,7 +82,8 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.scan_tiles = (long long*)take(8 * scan_n);
   w.counters = (unsigned*)take(64);
   w.dom_order = (int*)take(4 * (D > 0 ? D : 1));
-  w.loc_list = (int*)take(16 * (D > 0 ? D : 1));
+  w.loc_list = (int*)take(24 * (D > 0 ? D : 1));
+  w.loc_ctr = (unsigned*)take(64);
   w.plain_ctr = (unsigned*)take(4 * (D > 0 ? D : 1) + 16);
   if (base) w.loc_stride = D > 0 ? D : 1;
   w.pack_hist = (int*)take(4 * pack_buckets());
@@ -101,7 +102,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.m_v0 = (int*)take(4 * G);
   w.m_v1 = (int*)take(4 * G);
   w.m_rec = (int*)take(4 * G);
-  w.m_hist = (unsigned*)take(4 * 256 * ((G + 4095) / 4096 + 1));
+  w.m_hist = (unsigned*)take(4 * (size_t)rs_hist_words(G));
   w.m_X32 = (float*)take(4 * G);
   w.m_Y32 = (float*)take(4 * G);
   {
@@ -110,6 +111,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     MergeBufs& B = w.mb;
     B.bounds = (int*)take(16);
     B.bar = (unsigned*)take(64);
+    B.bar_sub = (unsigned*)take(4 * 32 * 17);
     B.rinv = (float*)take(16);
     B.geom = (struct GridGeom*)take(64);
     B.flags = (int*)take(16);
@@ -212,12 +214,13 @@ bool tuning_ok(const jabba_tuning* t) {
   if (!t) return false;
   if (t->compress_ctas_per_sm < 1 || t->compress_ctas_per_sm > 3) return false;
   if (t->compress_pack != 0 && t->compress_pack != 1) return false;
-  if (t->local_mid_warps != 2 && t->local_mid_warps != 4 && t->local_mid_warps != 8) return false;
+  if (t->local_k_warps != 1 && t->local_k_warps != 4) return false;
+  if (t->local_mid_warps != 1 && t->local_mid_warps != 2 && t->local_mid_warps != 4 && t->local_mid_warps != 8)
+    return false;
   if (t->local_big_warps != 4 && t->local_big_warps != 8) return false;
   if (t->merge_ctas_per_sm != 1 && t->merge_ctas_per_sm != 2 && t->merge_ctas_per_sm != 4) return false;
   if (t->per_domain_launch != 0 && t->per_domain_launch != 1) return false;
-  for (int i = 0; i < 2; ++i)
-    if (t->reserved[i] != 0) return false;
+  if (t->reserved != 0) return false;
   return true;
 }
 
@@ -404,28 +407,32 @@ jabba_status jabba_digitize_local(jabba_ctx* c, const int32_t* piece_len, const 
   };
   if (c->ws.tune.per_domain_launch && (capturing(st) || c->tuning)) return JABBA_ERR_STATE;
   if (c->tuning) {
-    // three runs cover every tile variant: (mid, big) = (2, 4), (4, 8), (8, 4); each tile kernel is timed
+    // four runs cover every tile variant: (k, mid, big) warps = (1, 1, 4), (4, 2, 8), (1, 4, 4), (4, 8, 8);
+    // each variable tile kernel is timed on its own
     if (capturing(st)) return JABBA_ERR_STATE;
     TierEvents te;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 2; ++j)
         if (cudaEventCreate(&te.ev[i][j]) != cudaSuccess) return JABBA_ERR_CUDA;
-    const int mids[3] = {2, 4, 8}, bigs[3] = {4, 8, 4};
-    float mid_ms[3], big_ms[3];
+    const int ks[4] = {1, 4, 1, 4}, mids[4] = {1, 2, 4, 8}, bigs[4] = {4, 8, 4, 8};
+    float k_ms[4], mid_ms[4], big_ms[4];
     c->ws.tier_ev = &te;
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 4; ++r) {
+      c->ws.tune.local_k_warps = ks[r];
       c->ws.tune.local_mid_warps = mids[r];
       c->ws.tune.local_big_warps = bigs[r];
       run();
+      k_ms[r] = elapsed_ms(te.ev[0][0], te.ev[0][1]);
       mid_ms[r] = elapsed_ms(te.ev[1][0], te.ev[1][1]);
       big_ms[r] = elapsed_ms(te.ev[2][0], te.ev[2][1]);
     }
     c->ws.tier_ev = nullptr;
     int bm = 0;
-    for (int r = 1; r < 3; ++r)
+    for (int r = 1; r < 4; ++r)
       if (mid_ms[r] < mid_ms[bm]) bm = r;
     c->ws.tune.local_mid_warps = mids[bm];
-    c->ws.tune.local_big_warps = big_ms[1] < fminf(big_ms[0], big_ms[2]) ? 8 : 4;
+    c->ws.tune.local_k_warps = fminf(k_ms[1], k_ms[3]) < fminf(k_ms[0], k_ms[2]) ? 4 : 1;
+    c->ws.tune.local_big_warps = fminf(big_ms[1], big_ms[3]) < fminf(big_ms[0], big_ms[2]) ? 8 : 4;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 2; ++j) cudaEventDestroy(te.ev[i][j]);
     return cuda_ok(cudaGetLastError());
@@ -580,7 +587,8 @@ jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
   out->local_big_warps = t.local_big_warps;
   out->merge_ctas_per_sm = t.merge_ctas_per_sm;
   out->per_domain_launch = t.per_domain_launch;
-  out->reserved[0] = out->reserved[1] = 0;
+  out->local_k_warps = t.local_k_warps;
+  out->reserved = 0;
   return JABBA_OK;
 }
 
@@ -593,6 +601,7 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.local_big_warps = in->local_big_warps;
   t.merge_ctas_per_sm = in->merge_ctas_per_sm;
   t.per_domain_launch = in->per_domain_launch;
+  t.local_k_warps = in->local_k_warps;
   return JABBA_OK;
 }
 

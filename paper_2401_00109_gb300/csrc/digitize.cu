@@ -405,8 +405,10 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
 template <int W, int CAP>
 struct TileCfg {
   static constexpr int kThreads = 32 * W;
-  static constexpr int kBlock = W == 1 ? 256 : 32 * W;
   static constexpr size_t kBytes = (size_t)W * 1024 + (size_t)CAP * 14 + 128;
+  // W = 1: independent warps per CTA, as many as fit in ~56 KB (at most 8)
+  static constexpr int kTilesPerCta = W > 1 ? 1 : (57344 / (int)kBytes < 1 ? 1 : (57344 / (int)kBytes > 8 ? 8 : 57344 / (int)kBytes));
+  static constexpr int kBlock = kThreads * kTilesPerCta;
   static constexpr int kGroupsPerPass = CAP / 4;
 };
 
@@ -713,10 +715,12 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
   }
 }
 
-// Routes every domain to the kernel whose tile holds it: list 0 (<= 256
-// pieces, a warp per domain), 1 (<= 2048, a CTA), 2 (<= 4096, a CTA), 3
-// (larger: the global-memory arena kernel).  Empty domains get no groups here.
-constexpr int kTierCap0 = 256, kTierCap1 = 2048, kTierCap2 = 4096;
+// Routes every domain to the kernel whose tile holds it: list k < kTiers
+// holds the domains with kTierCap[k-1] < pieces <= kTierCap[k]; list kTiers
+// the larger ones (the global-memory arena kernel).  Empty domains get no
+// groups here.
+constexpr int kTiers = 5;
+constexpr int kTierCap0 = 256, kTierCap1 = 512, kTierCap2 = 1024, kTierCap3 = 2048, kTierCap4 = 4096;
 
 __global__ void k_local_classify(const int* dom_piece_cnt, long long n_domains, int* dom_group_cnt, int* lists,
                                  long long list_stride, unsigned* list_count) {
@@ -727,9 +731,9 @@ __global__ void k_local_classify(const int* dom_piece_cnt, long long n_domains, 
     if (d < n_domains) {
       const int n = dom_piece_cnt[d];
       if (n == 0) dom_group_cnt[d] = 0;
-      else tier = n <= kTierCap0 ? 0 : n <= kTierCap1 ? 1 : n <= kTierCap2 ? 2 : 3;
+      else tier = n <= kTierCap0 ? 0 : n <= kTierCap1 ? 1 : n <= kTierCap2 ? 2 : n <= kTierCap3 ? 3 : n <= kTierCap4 ? 4 : 5;
     }
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k <= kTiers; ++k) {
       const unsigned m = __ballot_sync(0xFFFFFFFFu, tier == k);
       if (!m) continue;
       const int leader = __ffs(m) - 1;
@@ -809,11 +813,11 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
                   const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
                   int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
                   long long group_capacity, long long* n_groups, Scratch& ws, unsigned* status, cudaStream_t st) {
-  // counters[4..5] unused here; [6..9] list sizes of the four tiers, [10..13] their task counters
-  unsigned* list_cnt = ws.counters + 6;
-  unsigned* task_ctr = ws.counters + 10;
+  // loc_ctr[0..5]: list sizes of the tiers and the arena; [8..13]: their task counters
+  unsigned* list_cnt = ws.loc_ctr;
+  unsigned* task_ctr = ws.loc_ctr + 8;
   cudaMemsetAsync(n_groups, 0, sizeof(long long), st);
-  cudaMemsetAsync(ws.counters + 4, 0, 10 * sizeof(unsigned), st);
+  cudaMemsetAsync(ws.loc_ctr, 0, 16 * sizeof(unsigned), st);
   k_norm_tables<<<(unsigned)((ws.cap_len + 256) / 256), 256, 0, st>>>(sigma, scl, ws.cap_len, ws.xtab64, ws.xtab32,
                                                                         ws.rinv32);
   LocalParams P;
@@ -839,9 +843,9 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
   P.group_capacity = group_capacity;
   P.n_groups = n_groups;
   P.status = status;
-  P.task_counter = task_ctr + 3;
-  P.list = ws.loc_list + 3 * ws.loc_stride;
-  P.list_count = list_cnt + 3;
+  P.task_counter = task_ctr + kTiers;
+  P.list = ws.loc_list + kTiers * ws.loc_stride;
+  P.list_count = list_cnt + kTiers;
   P.arena = ws.arena;
   P.cap_items = ws.cap_items;
   if (n_domains > 0) {
@@ -865,8 +869,10 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
           const int* l = ws.loc_list + dd;
           unsigned* c = ws.plain_ctr + dd;
           if (n <= kTierCap0) launch_tile_one<1, kTierCap0>(P, l, one, c, st);
-          else if (n <= kTierCap1) launch_tile_one<4, kTierCap1>(P, l, one, c, st);
-          else if (n <= kTierCap2) launch_tile_one<8, kTierCap2>(P, l, one, c, st);
+          else if (n <= kTierCap1) launch_tile_one<1, kTierCap1>(P, l, one, c, st);
+          else if (n <= kTierCap2) launch_tile_one<4, kTierCap2>(P, l, one, c, st);
+          else if (n <= kTierCap3) launch_tile_one<4, kTierCap3>(P, l, one, c, st);
+          else if (n <= kTierCap4) launch_tile_one<8, kTierCap4>(P, l, one, c, st);
           else {
             LocalParams Q = P;
             Q.list = l;
@@ -883,19 +889,34 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
     k_local_classify<<<g, 256, 0, st>>>(dom_piece_cnt, n_domains, dom_group_cnt, ws.loc_list, ws.loc_stride,
                                         list_cnt);
     TierEvents* te = ws.tier_ev;
+    const long long L = ws.loc_stride;
+    const int ns = ws.num_sms;
+    launch_tile<1, kTierCap0>(P, ws.loc_list, list_cnt + 0, task_ctr + 0, ns, st);
+    launch_tile<1, kTierCap1>(P, ws.loc_list + L, list_cnt + 1, task_ctr + 1, ns, st);
     if (te) cudaEventRecord(te->ev[0][0], st);
-    launch_tile<1, kTierCap0>(P, ws.loc_list, list_cnt + 0, task_ctr + 0, ws.num_sms, st);
+    {
+      const int* l2 = ws.loc_list + 2 * L;
+      if (ws.tune.local_k_warps == 4) launch_tile<4, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ns, st);
+      else launch_tile<1, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ns, st);
+    }
     if (te) cudaEventRecord(te->ev[0][1], st);
-    const int* l1 = ws.loc_list + ws.loc_stride;
     if (te) cudaEventRecord(te->ev[1][0], st);
-    if (ws.tune.local_mid_warps == 2) launch_tile<2, kTierCap1>(P, l1, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
-    else if (ws.tune.local_mid_warps == 8) launch_tile<8, kTierCap1>(P, l1, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
-    else launch_tile<4, kTierCap1>(P, l1, list_cnt + 1, task_ctr + 1, ws.num_sms, st);
+    {
+      const int* l3 = ws.loc_list + 3 * L;
+      switch (ws.tune.local_mid_warps) {
+        case 1: launch_tile<1, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
+        case 2: launch_tile<2, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
+        case 8: launch_tile<8, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
+        default: launch_tile<4, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
+      }
+    }
     if (te) cudaEventRecord(te->ev[1][1], st);
-    const int* l2 = ws.loc_list + 2 * ws.loc_stride;
     if (te) cudaEventRecord(te->ev[2][0], st);
-    if (ws.tune.local_big_warps == 8) launch_tile<8, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ws.num_sms, st);
-    else launch_tile<4, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ws.num_sms, st);
+    {
+      const int* l4 = ws.loc_list + 4 * L;
+      if (ws.tune.local_big_warps == 8) launch_tile<8, kTierCap4>(P, l4, list_cnt + 4, task_ctr + 4, ns, st);
+      else launch_tile<4, kTierCap4>(P, l4, list_cnt + 4, task_ctr + 4, ns, st);
+    }
     if (te) cudaEventRecord(te->ev[2][1], st);
     k_local_warp<<<(unsigned)ws.loc_ctas, kLocWarps * 32, 0, st>>>(P);
   }

@@ -9,7 +9,8 @@ namespace jabba {
 // Buffers of the global merge (sizes: cap = group capacity, cells = grid cells).
 struct MergeBufs {
   int* bounds = nullptr;             // [4] ordered-int min/max of the FP32 coordinates
-  unsigned* bar = nullptr;           // [8] grid barrier and round counters
+  unsigned* bar = nullptr;           // [16] grid barrier generation and round counters
+  unsigned* bar_sub = nullptr;       // [32 * 17] grid barrier arrival counters
   float* rinv = nullptr;             // [2] 1/sigma in FP32
   struct GridGeom* geom = nullptr;   // grid geometry (device)
   int* flags = nullptr;              // [4] [0] = sequential fallback
@@ -48,7 +49,8 @@ struct MergeBufs {
 struct Tuning {
   int compress_ctas_per_sm = 3;  // resident CTAs per SM of the persistent compression kernel (1..3)
   int compress_pack = 1;         // 1: domains handed to warps longest first; 0: natural order
-  int local_mid_warps = 4;       // warps per domain of 257..2048 pieces (2, 4 or 8)
+  int local_k_warps = 1;         // warps per domain of 513..1024 pieces (1 or 4)
+  int local_mid_warps = 4;       // warps per domain of 1025..2048 pieces (1, 2, 4 or 8)
   int local_big_warps = 4;       // warps per domain of 2049..4096 pieces (4 or 8)
   int merge_ctas_per_sm = 4;     // CTAs per SM of the cooperative merge-rounds kernel (1, 2 or 4)
   int per_domain_launch = 0;     // 1: the plain form, one launch per domain for compression and Stage I
@@ -79,7 +81,8 @@ struct Scratch {
   long long cap_len = 0;          // largest piece length covered by the X table
   long long cap_items = 0;        // largest domain (pieces) an arena holds
   int loc_ctas = 0;               // CTAs of the arena local-aggregation kernel
-  int* loc_list = nullptr;        // [4 * loc_stride] domains routed to each local-aggregation tier
+  int* loc_list = nullptr;        // [6 * loc_stride] domains routed to each local-aggregation tier
+  unsigned* loc_ctr = nullptr;    // [16] list sizes and task counters of the tiers
   long long loc_stride = 0;
   unsigned* arena = nullptr;
   double* xtab64 = nullptr;
@@ -146,6 +149,8 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
                   const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
                   int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
                   long long group_capacity, long long* n_groups, Scratch& ws, unsigned* status, cudaStream_t st);
+
+long long rs_hist_words(long long cap);  // radix-sort histogram words for cap items
 
 void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
                   const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,

@@ -180,97 +180,163 @@ __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long lo
 }
 
 // ------------------------------------------------------------------ LSD radix sort (stable)
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kSortWarps = kSortThreads / 32;
+// 8-bit digits over tiles of kRsTile items.  Per pass: k_rs_hist counts the
+// digits of every tile (column d of hist holds digit d over the tiles),
+// k_rs_scan turns each column into exclusive offsets (one CTA per digit) and
+// the digit totals, and k_rs_scatter ranks the tile's items stably (warp w owns
+// the contiguous items [w 256, (w+1) 256) of the tile; ranks from ballots on
+// the digit bits), reorders the tile by digit in shared memory and writes each
+// digit's run to its global position with consecutive threads on consecutive
+// addresses.
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsPerLane = 8;
+constexpr int kRsPerWarp = 32 * kRsPerLane;
+constexpr int kRsTile = kRsWarps * kRsPerWarp;  // 2048
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long long* keys, const long long* n_p,
-                                                            long long cap, int shift, unsigned* hist,
-                                                            long long n_tiles, const int* flags) {
-  __shared__ unsigned h[256];
-  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * kSortTile;
-  for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
-    const long long k = base + i;
-    if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * n_tiles + blockIdx.x] = h[i];
-}
-
-// One tile of kSortTile items: every warp ranks its contiguous 512 items (in
-// input order, so the sort is stable), the tile is reordered by digit in
-// shared memory, and each digit's run is then written to its global offset
-// with consecutive threads writing consecutive addresses.
-struct ScatterSmem {
-  unsigned long long key[kSortTile];
-  int val[kSortTile];
-  unsigned wh[kSortWarps][256];
-  unsigned lstart[256];      // first local position of each digit
-  long long goff[256];       // global position of the tile's first item of each digit
-  unsigned wsum[kSortWarps];
-};
-
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned long long* kin, const int* vin,
-                                                               unsigned long long* kout, int* vout,
-                                                               const long long* n_p, long long cap, int shift,
-                                                               const long long* offs, long long n_tiles,
-                                                               const int* flags) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ScatterSmem& S = *(ScatterSmem*)smem_raw;
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* keys, const long long* n_p,
+                                                       long long cap, int shift, unsigned* hist, long long n_tiles,
+                                                       const int* flags) {
+  __shared__ unsigned h[kRsWarps][256];
   const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long base = (long long)blockIdx.x * kSortTile;
-  constexpr int kPerWarp = kSortTile / kSortWarps;
-  constexpr int kPerLane = kPerWarp / 32;
-  const long long wbase = base + (long long)warp * kPerWarp;
-  unsigned long long kr[kPerLane];
-  int vr[kPerLane];
+  for (int i = lane; i < 256; i += 32) h[warp][i] = 0;
+  __syncwarp();
+  const long long wbase = (long long)blockIdx.x * kRsTile + (long long)warp * kRsPerWarp;
+#pragma unroll
+  for (int j = 0; j < kRsPerLane; ++j) {
+    const long long k = wbase + j * 32 + lane;
+    if (k < n) atomicAdd(&h[warp][(unsigned)(keys[k] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  const int d = threadIdx.x;
+  unsigned sum = 0;
+#pragma unroll
+  for (int w = 0; w < kRsWarps; ++w) sum += h[w][d];
+  hist[(long long)d * n_tiles + blockIdx.x] = sum;
+}
+
+// Exclusive scan of column d (blockIdx.x) over the tiles, in place; dtot[d] =
+// the column total.
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* hist, long long n_tiles, unsigned* dtot) {
+  __shared__ unsigned ws[32];
+  unsigned* col = hist + (long long)blockIdx.x * n_tiles;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const long long per = (n_tiles + 1023) / 1024;
+  const long long lo = (long long)t * per;
+  const long long hi = lo + per < n_tiles ? lo + per : n_tiles;
+  unsigned sum = 0;
+  for (long long i = lo; i < hi; ++i) sum += col[i];
+  unsigned incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    ws[lane] = w;
+  }
+  __syncthreads();
+  unsigned run = (warp ? ws[warp - 1] : 0u) + incl - sum;
+  for (long long i = lo; i < hi; ++i) {
+    const unsigned c = col[i];
+    col[i] = run;
+    run += c;
+  }
+  if (t == 1023) dtot[blockIdx.x] = ws[31];
+}
+
+struct RsSmem {
+  unsigned long long key[kRsTile];
+  int val[kRsTile];
+  unsigned wh[kRsWarps][256];
+  unsigned lstart[256];      // first local position of each digit
+  long long gpos[256];       // global position of the tile's first item of each digit
+  unsigned wsum[kRsWarps];
+};
+
+__global__ void __launch_bounds__(kRsThreads, 4) k_rs_scatter(const unsigned long long* kin, const int* vin,
+                                                             unsigned long long* kout, int* vout,
+                                                             const long long* n_p, long long cap, int shift,
+                                                             const unsigned* hist, const unsigned* dtot,
+                                                             long long n_tiles, const int* flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RsSmem& S = *(RsSmem*)smem_raw;
+  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = (long long)blockIdx.x * kRsTile;
+  if (base >= n) return;
+  const long long wbase = base + (long long)warp * kRsPerWarp;
+  unsigned long long kr[kRsPerLane];
+  int vr[kRsPerLane];
   for (int i = lane; i < 256; i += 32) S.wh[warp][i] = 0;
   __syncwarp();
 #pragma unroll
-  for (int j = 0; j < kPerLane; ++j) {
+  for (int j = 0; j < kRsPerLane; ++j) {
     const long long k = wbase + j * 32 + lane;
     const bool valid = k < n;
     kr[j] = valid ? kin[k] : 0ull;
     vr[j] = valid ? vin[k] : 0;
-    if (valid) atomicAdd(&S.wh[warp][(kr[j] >> shift) & 255u], 1u);
+    if (valid) atomicAdd(&S.wh[warp][(unsigned)(kr[j] >> shift) & 255u], 1u);
   }
   __syncthreads();
   {
-    // digit d = threadIdx.x: warp prefix within the digit, tile-wide digit starts
+    // digit d = threadIdx.x: warp prefix within the digit; tile-wide digit
+    // starts; global digit bases from the totals of all tiles
     const int d = threadIdx.x;
     unsigned run = 0;
-    for (int w = 0; w < kSortWarps; ++w) {
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
       const unsigned c = S.wh[w][d];
       S.wh[w][d] = run;
       run += c;
     }
-    unsigned incl = run;
+    const unsigned tot = dtot[d];
+    unsigned incl = run, gincl = tot;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += y;
+      const unsigned z = __shfl_up_sync(0xFFFFFFFFu, gincl, o);
+      if (lane >= o) {
+        incl += y;
+        gincl += z;
+      }
     }
-    if (lane == 31) S.wsum[warp] = incl;
+    __shared__ unsigned gsum[kRsWarps];
+    if (lane == 31) {
+      S.wsum[warp] = incl;
+      gsum[warp] = gincl;
+    }
     __syncthreads();
-    unsigned before = 0;
-    for (int w = 0; w < warp; ++w) before += S.wsum[w];
+    unsigned before = 0, gbefore = 0;
+    for (int w = 0; w < warp; ++w) {
+      before += S.wsum[w];
+      gbefore += gsum[w];
+    }
     const unsigned ls = before + incl - run;
     S.lstart[d] = ls;
-    for (int w = 0; w < kSortWarps; ++w) S.wh[w][d] += ls;
-    S.goff[d] = offs[(long long)d * n_tiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) S.wh[w][d] += ls;
+    S.gpos[d] = (long long)(gbefore + gincl - tot) + (long long)hist[(long long)d * n_tiles + blockIdx.x];
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int j = 0; j < kPerLane; ++j) {
+  for (int j = 0; j < kRsPerLane; ++j) {
     const long long k = wbase + j * 32 + lane;
     const bool valid = k < n;
-    const unsigned dgt = valid ? (unsigned)((kr[j] >> shift) & 255u) : 256u + lane;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, dgt);
+    const unsigned dgt = (unsigned)(kr[j] >> shift) & 255u;
+    unsigned peers = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, (dgt >> b) & 1u);
+      peers &= ((dgt >> b) & 1u) ? m : ~m;
+    }
     const unsigned rank = __popc(peers & lt);
     if (valid) {
       const unsigned pos = S.wh[warp][dgt] + rank;
@@ -282,43 +348,40 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned l
     __syncwarp();
   }
   __syncthreads();
-  const long long in_tile = n - base < kSortTile ? n - base : kSortTile;
-  for (int i = threadIdx.x; i < in_tile; i += kSortThreads) {
+  const int in_tile = (int)(n - base < kRsTile ? n - base : kRsTile);
+  for (int i = threadIdx.x; i < in_tile; i += kRsThreads) {
     const unsigned long long key = S.key[i];
-    const unsigned dgt = (unsigned)((key >> shift) & 255u);
-    const long long pos = S.goff[dgt] + (i - (long long)S.lstart[dgt]);
+    const unsigned dgt = (unsigned)(key >> shift) & 255u;
+    const long long pos = S.gpos[dgt] + (i - (long long)S.lstart[dgt]);
     kout[pos] = key;
     vout[pos] = S.val[i];
   }
 }
 
-__global__ void k_u32_to_i64(const unsigned* in, long long n, long long* out) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = in[i];
-}
+long long rs_hist_words(long long cap) { return 256 * ((cap + kRsTile - 1) / kRsTile + 1) + 256; }
 
 // Stable sort of (keys, vals) by the low `bits` bits of the keys; the result
 // ends in the buffers returned through kres/vres.
 static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, const long long* n_p,
-                       long long cap, int bits, Scratch& ws, long long* offs, unsigned long long** kres, int** vres,
+                       long long cap, int bits, Scratch& ws, unsigned long long** kres, int** vres,
                        const int* flags, cudaStream_t st) {
-  const long long n_tiles = (cap + kSortTile - 1) / kSortTile;
-  const unsigned grid = (unsigned)(ws.num_sms * 8);
+  const long long n_tiles = (cap + kRsTile - 1) / kRsTile;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem));
     attr = true;
   }
+  unsigned* hist = ws.m_hist;
+  unsigned* dtot = ws.m_hist + 256 * (n_tiles + 1);
   unsigned long long* kin = k0;
   unsigned long long* kout = k1;
   int* vin = v0;
   int* vout = v1;
   for (int shift = 0; shift < bits && n_tiles > 0; shift += 8) {
-    k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n_p, cap, shift, ws.m_hist, n_tiles, flags);
-    k_u32_to_i64<<<grid, 256, 0, st>>>(ws.m_hist, 256 * n_tiles, offs + 256 * n_tiles + 1);
-    exclusive_scan<long long>(offs + 256 * n_tiles + 1, 256 * n_tiles, offs, ws.scan_tiles, st);
-    k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, sizeof(ScatterSmem), st>>>(kin, vin, kout, vout, n_p, cap,
-                                                                                   shift, offs, n_tiles, flags);
+    k_rs_hist<<<(unsigned)n_tiles, kRsThreads, 0, st>>>(kin, n_p, cap, shift, hist, n_tiles, flags);
+    k_rs_scan<<<256, 1024, 0, st>>>(hist, n_tiles, dtot);
+    k_rs_scatter<<<(unsigned)n_tiles, kRsThreads, sizeof(RsSmem), st>>>(kin, vin, kout, vout, n_p, cap, shift, hist,
+                                                                        dtot, n_tiles, flags);
     unsigned long long* tk = kin; kin = kout; kout = tk;
     int* tv = vin; vin = vout; vout = tv;
   }
@@ -458,7 +521,8 @@ struct RoundArgs {
   const long long* n_cells_p;
   const GridGeom* geom;
   const int* flags;
-  unsigned* bar;            // [0] arrival counter, [1] generation, [2] rounds used
+  unsigned* bar;            // [1] barrier generation, [2] rounds used
+  unsigned* bar_sub;        // [32 * (kBarGroups + 1)] barrier arrival counters (one per 128-byte line)
   unsigned* status;
   unsigned max_rounds;
 };
@@ -467,8 +531,15 @@ __device__ __forceinline__ unsigned long long ld_state(const unsigned long long*
   return *((volatile const unsigned long long*)p);
 }
 
-// Bounded grid-wide barrier for a co-resident (cooperative) grid.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+// Bounded grid-wide barrier for a co-resident (cooperative) grid, two-level:
+// the CTAs arrive on kBarGroups counters (CTA b on counter b % kBarGroups,
+// each on its own 128-byte line); the last arrival of a group arrives on the
+// top counter, and the last of those advances the generation that every CTA
+// waits on.  bar[1] is the generation; sub[32 g] the group counters and
+// sub[32 kBarGroups] the top counter.
+constexpr unsigned kBarGroups = 16;
+
+__device__ bool grid_barrier(unsigned* bar, unsigned* sub, unsigned nblocks, unsigned* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -476,11 +547,20 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) 
     const unsigned g = *gen;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
-      atomicExch(&bar[0], 0u);
-      __threadfence();
-      atomicAdd(&bar[1], 1u);
-    } else {
+    const unsigned grp = blockIdx.x % kBarGroups;
+    const unsigned gsz = nblocks / kBarGroups + (grp < nblocks % kBarGroups ? 1u : 0u);
+    const unsigned ngrp = nblocks < kBarGroups ? nblocks : kBarGroups;
+    bool released = false;
+    if (atomicAdd(&sub[32 * grp], 1u) == gsz - 1) {
+      atomicExch(&sub[32 * grp], 0u);
+      if (atomicAdd(&sub[32 * kBarGroups], 1u) == ngrp - 1) {
+        atomicExch(&sub[32 * kBarGroups], 0u);
+        __threadfence();
+        atomicAdd(&bar[1], 1u);
+        released = true;
+      }
+    }
+    if (!released) {
       unsigned spins = 0;
       while (*gen == g) {
         if (++spins > kSpinLimit) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
@@ -649,10 +729,20 @@ __device__ __forceinline__ void cover_units(const RoundArgs& R, unsigned u, unsi
                                            unsigned round, int* chg, unsigned* n_chg) {
   const int lane = threadIdx.x & 31;
   // the slot holding u: the last one whose first unit is <= u
-  int lo = 0, hi = (int)n_new - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldcg(&R.s_base[mid]) <= u) lo = mid; else hi = mid - 1;
+  // warp-parallel search (s_base is non-decreasing and s_base[0] = 0): each
+  // step narrows the range to one of 32 equal parts with one load per lane
+  int lo = 0, len = (int)n_new;
+  while (len > 32) {
+    const int step = (len + 31) / 32;
+    const int i = lo + lane * step;
+    const unsigned v = lane * step < len ? __ldcg(&R.s_base[i]) : 0xFFFFFFFFu;
+    const int k = 31 - __clz(__ballot_sync(0xFFFFFFFFu, v <= u));
+    lo += k * step;
+    len = min(step, len - k * step);
+  }
+  {
+    const unsigned v = lane < len ? __ldcg(&R.s_base[lo + lane]) : 0xFFFFFFFFu;
+    lo += 31 - __clz(__ballot_sync(0xFFFFFFFFu, v <= u));
   }
   int s = lo;
   for (;;) {
@@ -743,7 +833,7 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
         if (eval_cell(R, g, q, nctr) && lane == 0) mark_changed(R, q, round, chg, n_chg);
       }
     }
-    if (!grid_barrier(R.bar, nblocks, R.status)) return;
+    if (!grid_barrier(R.bar, R.bar_sub, nblocks, R.status)) return;
     // ---- phase B
     // every read of the other parity's counters (n_prev, the previous
     // round's new starts) happened before the barrier; they are written
@@ -760,7 +850,7 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
       const unsigned u0 = (unsigned)(warp_g * per);
       if (per && u0 < total) cover_units(R, u0, min(total, u0 + per), n_new, round, chg, n_chg);
     }
-    if (!grid_barrier(R.bar, nblocks, R.status)) return;
+    if (!grid_barrier(R.bar, R.bar_sub, nblocks, R.status)) return;
     // nothing changed: a fixed point, where every cell is decided (the
     // earliest undecided candidate always progresses); k_mcheck verifies it
     if (*((volatile unsigned*)n_chg) == 0) {
@@ -781,15 +871,19 @@ __global__ void k_mcheck(const unsigned long long* state, const long long* n_cel
 }
 
 // ------------------------------------------------------------------ 5. labels
-// lab[a] = sorted position of the earliest start within alpha (a itself for a start).
-__global__ void __launch_bounds__(256) k_mlabel(MergeView V, const unsigned long long* ckey, const int* cell_of_id,
-                         const unsigned long long* state, const GridGeom* geom, const int* flags,
-                         const long long* n_p, long long cap, int* lab, int* is_start) {
+// lab[a] = sorted position of the earliest start within alpha (a itself for a
+// start).  Items are visited in cell order, so the lanes of a warp mostly
+// share one cell and its 5 x 5 neighbourhood (broadcast loads).
+__global__ void __launch_bounds__(256) k_mlabel(MergeView V, const int* cord, const float* cX, const float* cY,
+                                               const int* cell_of_id, const unsigned long long* state,
+                                               const GridGeom* geom, const int* flags, const long long* n_p,
+                                               long long cap, int* lab, int* is_start) {
   if (flags[0] || flags[1]) return;
   const long long n = clamp_groups(n_p, cap);
   const GridGeom g = *geom;
-  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
-    const int id = cell_of(g, V.sX[a], V.sY[a]);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int a = cord[t];
+    const int id = cell_of(g, cX[t], cY[t]);
     const int cx = id % g.ncx, cy = id / g.ncx;
     int best = 0x7FFFFFFF;
     for (int dy = -2; dy <= 2; ++dy) {
@@ -801,13 +895,12 @@ __global__ void __launch_bounds__(256) k_mlabel(MergeView V, const unsigned long
         const int q = cell_of_id[yy * g.ncx + xx];
         if (q < 0) continue;
         const unsigned s = (unsigned)state[q];
-        if (s >= kNoStart || (int)s > (int)a || (int)s >= best) continue;
-        if ((int)s == (int)a || within_sorted(V, (int)s, (int)a)) best = (int)s;
+        if (s >= kNoStart || (int)s > a || (int)s >= best) continue;
+        if ((int)s == a || within_sorted(V, (int)s, a)) best = (int)s;
       }
     }
     lab[a] = best;
-    is_start[a] = best == (int)a ? 1 : 0;
-    (void)ckey;
+    is_start[a] = best == a ? 1 : 0;
   }
 }
 
@@ -985,8 +1078,9 @@ __global__ void k_dict_finalize(const long long* acc, const long long* k_p, long
   }
 }
 
-__global__ void k_minit(int* bounds, unsigned* bar, int* flags, const unsigned* status, const long long* n_p,
-                        long long cap) {
+__global__ void k_minit(int* bounds, unsigned* bar, unsigned* bar_sub, int* flags, const unsigned* status,
+                        const long long* n_p, long long cap) {
+  for (unsigned i = 0; i <= kBarGroups; ++i) bar_sub[32 * i] = 0;
   for (int i = 3; i < 16; ++i) bar[i] = 0;  // [2] rounds used, [4..5] changed cells, [8..11] new starts
   flags[0] = 0;
   flags[1] = (*status != 0u || *n_p > cap) ? 1 : 0;  // earlier error: leave the merge outputs alone
@@ -1022,8 +1116,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   const long long cap = group_capacity;
   const unsigned grid = (unsigned)(ws.num_sms * 8);
   MergeBufs& B = ws.mb;
-  long long* offs = (long long*)ws.d_acc;  // reused before the dictionary accumulation
-  k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.flags, status, n_groups, cap);
+  k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.bar_sub, B.flags, status, n_groups, cap);
   k_mrinv<<<1, 1, 0, st>>>(sigma, B.rinv);
   k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, B.rinv, sigma, scl, ws.m_k0, ws.m_v0, ws.m_rec,
                                 ws.m_X32, ws.m_Y32, B.bounds, B.flags);
@@ -1031,7 +1124,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   int* sidx;
   // keys are non-negative binary64: their bit patterns order as the values;
   // the sort is stable and starts in compact-index order, so ties keep it
-  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws, offs, &skey, &sidx, B.flags, st);
+  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws, &skey, &sidx, B.flags, st);
   k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
   // the cell sort ping-pongs in the buffers the key sort left free
   unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
@@ -1040,7 +1133,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   unsigned long long* ckey;
   int* cord;
   // cell ids are below cap_cells = 2^23: three 8-bit passes order them
-  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws, offs, &ckey, &cord, B.flags, st);
+  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws, &ckey, &cord, B.flags, st);
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
@@ -1085,6 +1178,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   R.geom = B.geom;
   R.flags = B.flags;
   R.bar = B.bar;
+  R.bar_sub = B.bar_sub;
   R.status = status;
   R.max_rounds = 1u << 22;
   {
@@ -1111,7 +1205,8 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   }
   k_mcheck<<<grid, 256, 0, st>>>(B.state, B.head_off + cap, B.flags, status);
   k_clear_i32<<<grid, 256, 0, st>>>(B.is_start, cap, 0);
-  k_mlabel<<<grid, 256, 0, st>>>(V, ckey, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab, B.is_start);
+  k_mlabel<<<grid, 256, 0, st>>>(V, cord, B.cX, B.cY, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab,
+                                 B.is_start);
   // sequential fallback (only acts when flags[0] is set)
   k_mexact_prep<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, n_groups, cap, sigma, scl, B.flags, B.eX, B.eY, B.ekey);
   k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, B.flags, B.lab, B.is_start);

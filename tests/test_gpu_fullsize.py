@@ -176,3 +176,49 @@ def test_scale_full_sampled():
         n = h["cnt"][d]
         assert np.array_equal(ln, h["piece_len"][s0:s0 + n]) and np.array_equal(inc, h["piece_inc"][s0:s0 + n]), d
     assert h["dict_count"].sum() == h["dom_piece_off"][-1]
+
+
+def test_diff_full_adjoint_and_refinement():
+    """The dictionary-refinement workload at full size (1,024 series x 10,000
+    points): the whole forward path and the reconstruction equal the oracle's,
+    the adjoint equals the oracle's gradient and FP64 central differences
+    (h = 1e-6), and 50 Adam steps (lr 1e-3) through the autograd.Function
+    end below the starting reconstruction MSE."""
+    import torch
+    import paper_2401_00109_gb300 as jb
+    from _gpu import assert_parity, ctx, params, run_gpu, run_oracle
+    x_np, off_np, cfg = synth.make("diff")
+    C = ctx()
+    g, out, x, off = run_gpu(C, x_np, off_np, cfg)
+    r = run_oracle(x_np, off_np, cfg, threads=16)
+    assert_parity(g, r)
+    p = params(cfg)
+    qlen = torch.from_numpy(g["qlen"]).cuda()
+    di = out["dict_inc"].clone()
+    grad = C.reconstruct_backward(x, off, out, qlen, di).cpu().numpy()
+    k = len(r["dict_inc"])
+    gr = oracle.reconstruct_grad(x_np, r["xhat"], r["symbol"], r["qlen"], r["series_piece_off"], off_np, k)
+    np.testing.assert_allclose(grad, gr, rtol=1e-9, atol=1e-9 * np.abs(gr).max())
+    rng = np.random.default_rng(5)
+    for c in rng.choice(k, 8, replace=False):
+        h = 1e-6
+        dp = di.clone()
+        dp[c] += h
+        dm = di.clone()
+        dm[c] -= h
+        _, xp = C.reconstruct(x, off, out, p, dict_inc=dp)
+        _, xm = C.reconstruct(x, off, out, p, dict_inc=dm)
+        fd = (C.mse(x, xp).item() - C.mse(x, xm).item()) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * max(abs(grad[c]), 1e-7), (c, fd, grad[c])
+    w = di.clone().requires_grad_(True)
+    opt = torch.optim.Adam([w], lr=1e-3, betas=(0.9, 0.999))
+    F = jb.JabbaMSE()
+    losses = []
+    for _ in range(50):
+        opt.zero_grad()
+        loss = F.apply(w, C, x, off, out, qlen, p)
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert abs(losses[0] - r["mse"]) <= 1e-9 * r["mse"]
+    assert losses[-1] < losses[0]
