@@ -213,8 +213,9 @@ jabba_status jabba_reconstruct_backward(jabba_ctx* ctx, const double* x, int64_t
  * use cudaEventRecordExternal, so a graph captured meanwhile keeps them.
  * slot = -1 stops recording.  jabba_profile_elapsed synchronizes the events
  * of (slot, stage) and returns the milliseconds between them.  Stages:
- * 0 = compression kernel, 1 = increments + exact sums, 2 = local aggregation,
- * 3 = global merge (whole call), 4 = label propagation. */
+ * 0 = compression kernel (with the domain packing), 1 = increments + exact
+ * sums, 2 = local aggregation, 3 = global merge (whole call), 4 = label
+ * propagation, 5 = the merge-rounds kernel alone. */
 jabba_status jabba_profile_slot(jabba_ctx* ctx, int slot);
 jabba_status jabba_profile_elapsed(jabba_ctx* ctx, int slot, int stage, float* ms);
 

@@ -11,7 +11,7 @@
 using namespace jabba;
 
 constexpr int kProfSlots = 256;
-constexpr int kProfStages = 5;
+constexpr int kProfStages = 6;
 
 struct jabba_ctx {
   int device = 0;
@@ -457,9 +457,14 @@ jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const i
   jabba_status r = ensure(c, c->ws.cap_series, c->ws.cap_domains, c->ws.cap_slots, group_capacity, c->ws.cap_big, st);
   if (r != JABBA_OK) return r;
   auto run = [&]() {
+    Marks mk;
+    if (!c->tuning) {
+      mk.a0 = prof_event(c, 5, 0);
+      mk.a1 = prof_event(c, 5, 1);
+    }
     launch_merge(groups, (const long long*)n_groups, group_capacity, (const long long*)dom_group_off, sigma,
                  p->alpha, p->scl, l2g, dict_len, dict_inc, (long long*)dict_count, dict_capacity, (long long*)k,
-                 c->ws, c->status, st);
+                 c->ws, c->status, st, mk);
   };
   if (c->tuning) {
     if (capturing(st)) return JABBA_ERR_STATE;

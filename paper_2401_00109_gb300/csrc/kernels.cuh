@@ -155,7 +155,8 @@ long long rs_hist_words(long long cap);  // radix-sort histogram words for cap i
 void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
                   const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
                   double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,
-                  Scratch& ws, unsigned* status, cudaStream_t st);
+                  Scratch& ws, unsigned* status, cudaStream_t st,
+                  const Marks& mk);
 
 void launch_symbolize(const int* local_label, const long long* dom_slot_off, const int* dom_piece_cnt,
                       const long long* dom_piece_off, const long long* dom_group_off, long long n_domains,

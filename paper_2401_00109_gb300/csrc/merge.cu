@@ -1112,7 +1112,8 @@ static float rup(double v) {
 void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
                   const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
                   double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,
-                  Scratch& ws, unsigned* status, cudaStream_t st) {
+                  Scratch& ws, unsigned* status, cudaStream_t st,
+                  const Marks& mk) {
   const long long cap = group_capacity;
   const unsigned grid = (unsigned)(ws.num_sms * 8);
   MergeBufs& B = ws.mb;
@@ -1201,7 +1202,9 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    mark(mk.a0, st);
     cudaLaunchKernelEx(&cfg, k_mrounds, R);
+    mark(mk.a1, st);
   }
   k_mcheck<<<grid, 256, 0, st>>>(B.state, B.head_off + cap, B.flags, status);
   k_clear_i32<<<grid, 256, 0, st>>>(B.is_start, cap, 0);
