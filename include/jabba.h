@@ -235,7 +235,7 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
  * kernels.  Every configuration computes the same results (bit for bit); only
  * the speed differs.  Domains of up to 512 pieces are aggregated by one warp
  * each; larger domains by the number of warps chosen here.
- * Defaults: {3, 1, 4, 4, 4, 0, 1}. */
+ * Defaults: {2, 1, 4, 4, 4, 0, 1}. */
 typedef struct {
   int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */

@@ -232,7 +232,8 @@ struct LaneState {
   double prevd;                 // x at the previous point (end value of a piece)
   float xs, prevf, S2, SK, K2, Lf, M;
   int s;                        // start of the open piece (domain-local index)
-  int* out_len;                 // next output slot
+  int cnt;                      // pieces written so far
+  int* out_len;                 // the domain's first output slot
   double* out_end;
   float tlo, thi;               // tol (1 -+ 2^-18) -+ 2^-99; (-1, inf) forces the exact path
   unsigned amax;
@@ -279,36 +280,34 @@ __device__ __forceinline__ void step(const CompressParams& P, LaneState& L, cons
     }
     if (lane == 0) atomicAdd(n_exact, (unsigned long long)__popc(amb));
   }
-  if (act) {
-    if (feas) {
-      L.S2 = fmaf(dd, dd, L.S2);
-      L.SK = fmaf(Ln, dd, L.SK);
-      L.K2 = fmaf(Ln, Ln, L.K2);
-      L.Lf = Ln;
-      L.M = Mx;
-    } else {
-      // piece (s, p - 1) ends; restart at p - 1 with p as its first candidate
-      *L.out_len++ = (p - 1) - L.s;
-      *L.out_end++ = L.prevd;
-      L.s = p - 1;
-      L.xs = L.prevf;
-      dd = v - L.xs;
-      L.S2 = dd * dd;
-      L.SK = dd;
-      L.K2 = 1.0f;
-      L.Lf = 1.0f;
-      L.M = fmaxf(fabsf(L.prevf), fabsf(v));
-    }
-    L.prevf = v;
-    L.prevd = vd;
-    if (TAIL && p == D.n_int) {  // domain end: the open piece ends here
-      *L.out_len++ = p - L.s;
-      *L.out_end++ = vd;
-    }
+  // Branch-free update: on a break (piece (s, p - 1) ends) the open piece
+  // restarts at p - 1 with p as its first candidate; otherwise p extends it.
+  const bool brk = act && !feas;
+  if (brk) {
+    L.out_len[L.cnt] = (p - 1) - L.s;
+    L.out_end[L.cnt] = L.prevd;
+  }
+  L.cnt += brk ? 1 : 0;
+  L.s = brk ? p - 1 : L.s;
+  const float xs_n = brk ? L.prevf : L.xs;
+  dd = v - xs_n;
+  const float Ln_n = brk ? 1.0f : Ln;
+  L.S2 = fmaf(dd, dd, brk ? 0.0f : L.S2);
+  L.SK = fmaf(Ln_n, dd, brk ? 0.0f : L.SK);
+  L.K2 = fmaf(Ln_n, Ln_n, brk ? 0.0f : L.K2);
+  L.Lf = Ln_n;
+  L.M = brk ? fmaxf(fabsf(L.prevf), fabsf(v)) : Mx;
+  L.xs = xs_n;
+  L.prevf = v;
+  L.prevd = vd;
+  if (TAIL && act && p == D.n_int) {  // domain end: the open piece ends here
+    L.out_len[L.cnt] = p - L.s;
+    L.out_end[L.cnt] = vd;
+    L.cnt += 1;
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParams P) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_compress(CompressParams P) {
   __shared__ __align__(16) double stage[kWarpsPerCta][kStages][32][kRow];
   __shared__ __align__(8) unsigned long long bars[kWarpsPerCta][kStages];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -348,6 +347,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
 
     L.out_len = P.piece_len + slot;
     L.out_end = P.piece_end + slot;
+    L.cnt = 0;
     // FP32 lengths are exact below 2^24: longer domains take the exact path throughout
     L.tlo = D.n_int < (1 << 24) ? P.tol_lo : -1.0f;
     L.thi = D.n_int < (1 << 24) ? P.tol_hi : INFINITY;
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_compress(CompressParam
         for (int j = 0; j < kChunk; ++j) step<true>(P, L, D, p0 + j, row[j], n_exact);
       }
     }
-    if (d < P.n_domains) P.dom_piece_cnt[d] = (int)(L.out_len - (P.piece_len + slot));
+    if (d < P.n_domains) P.dom_piece_cnt[d] = L.cnt;
   }
   // range / finiteness of every value this lane read
   if (L.amax >= 0x7FF00000u) set_status(P.status, JABBA_ERR_NONFINITE);
@@ -626,7 +626,7 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   const long long n_tasks = (n_domains + 31) / 32;
   int per_sm = ws.tune.compress_ctas_per_sm;
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 3) per_sm = 3;                      // the launch bounds allow 3 resident CTAs
+  if (per_sm > 3) per_sm = 3;  // 2 are resident at the kernel's register count; a third CTA per SM waits for a slot
   long long ctas = (long long)ws.num_sms * per_sm;
   const long long need = (n_tasks + kWarpsPerCta - 1) / kWarpsPerCta;
   if (ctas > need) ctas = need;

@@ -47,7 +47,7 @@ struct MergeBufs {
 // Launch configuration of the batched kernels (chosen by the autotuner of
 // api.cu, or set by the caller).  Every choice computes the same result.
 struct Tuning {
-  int compress_ctas_per_sm = 3;  // resident CTAs per SM of the persistent compression kernel (1..3)
+  int compress_ctas_per_sm = 2;  // resident CTAs per SM of the persistent compression kernel (1..3)
   int compress_pack = 1;         // 1: domains handed to warps longest first; 0: natural order
   int local_k_warps = 1;         // warps per domain of 513..1024 pieces (1 or 4)
   int local_mid_warps = 4;       // warps per domain of 1025..2048 pieces (1, 2, 4 or 8)
