@@ -64,11 +64,11 @@ class Params:
 class _Tuning(C.Structure):
     _fields_ = [("compress_ctas_per_sm", C.c_int32), ("compress_pack", C.c_int32), ("local_mid_warps", C.c_int32),
                 ("local_big_warps", C.c_int32), ("merge_ctas_per_sm", C.c_int32), ("per_domain_launch", C.c_int32),
-                ("local_k_warps", C.c_int32), ("reserved", C.c_int32)]
+                ("local_k_warps", C.c_int32), ("local_ctas_cap", C.c_int32)]
 
 
 TUNING_FIELDS = ("compress_ctas_per_sm", "compress_pack", "local_mid_warps", "local_big_warps", "merge_ctas_per_sm",
-                 "per_domain_launch", "local_k_warps")
+                 "per_domain_launch", "local_k_warps", "local_ctas_cap")
 
 JABBA_GROUP_BYTES = 48
 PIECE_STATS_BYTES = 256
@@ -461,6 +461,11 @@ class Pipeline:
 
     def enqueue(self, stream=None):
         """Enqueue one forward step on `stream` (default: current stream)."""
+        self.enqueue_front(stream)
+        self.enqueue_back(stream)
+
+    def enqueue_front(self, stream=None):
+        """The per-domain half of a step: compression and Stage I."""
         L, h, b, pc = self.ctx.lib, self.ctx.h, self.b, self.pc
         st = self.ctx._stream(stream)
         P = _ptr
@@ -473,6 +478,12 @@ class Pipeline:
                                       P(b["dom_piece_cnt"]), self.D, P(b["piece_stats"]), C.byref(pc), P(b["sigma"]),
                                       P(b["local_label"]), P(b["dom_group_cnt"]), P(b["dom_group_off"]),
                                       P(b["groups"]), self.gcap, P(b["n_groups"]), st), "jabba_digitize_local")
+
+    def enqueue_back(self, stream=None):
+        """The global half of a step: Stage II merge and label propagation."""
+        L, h, b, pc = self.ctx.lib, self.ctx.h, self.b, self.pc
+        st = self.ctx._stream(stream)
+        P = _ptr
         _check(L.jabba_merge_global(h, P(b["groups"]), P(b["n_groups"]), self.gcap, P(b["dom_group_off"]),
                                     P(b["sigma"]), C.byref(pc), P(b["l2g"]), P(b["dict_len"]), P(b["dict_inc"]),
                                     P(b["dict_count"]), self.kcap, P(b["k"]), st), "jabba_merge_global")
@@ -506,6 +517,21 @@ class Pipeline:
         self.graph = g
         return g
 
+    def capture_halves(self, stream):
+        """Capture the two halves of a step (front: compression + Stage I;
+        back: merge + label propagation) as two CUDA graphs on `stream`, so
+        that consecutive steps of two pipelines can overlap (see
+        InFlight)."""
+        torch = _torch()
+        graphs = []
+        for fn in (self.enqueue_front, self.enqueue_back):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(stream):
+                with torch.cuda.graph(g, stream=stream):
+                    fn(stream)
+            graphs.append(g)
+        return graphs
+
     def results(self):
         """Host copies of the symbols and dictionary of the last step."""
         b = self.b
@@ -514,6 +540,99 @@ class Pipeline:
         return dict(symbol=b["symbol"][:N].cpu().numpy(), dict_len=b["dict_len"][:k].cpu().numpy(),
                     dict_inc=b["dict_inc"][:k].cpu().numpy(), dict_count=b["dict_count"][:k].cpu().numpy(),
                     n_pieces=N, k=k, n_groups=int(b["n_groups"][0].item()))
+
+
+class InFlight:
+    """Two batches in flight: two pipelines (each with its own context and
+    buffers) on two streams.  Step i runs on pipeline i % 2: its front half
+    (compression, Stage I) may overlap the other pipeline's back half, whose
+    merge-rounds kernel leaves most of the GPU idle; the back halves of the
+    two pipelines are ordered one after the other (the merge's cooperative
+    kernels never run concurrently)."""
+
+    def __init__(self, pipelines):
+        torch = _torch()
+        self.pl = list(pipelines)
+        self.streams = [torch.cuda.Stream(device=p.x.device) for p in self.pl]
+        for s in self.streams:
+            s.wait_stream(torch.cuda.current_stream())
+        self.halves = [p.capture_halves(s) for p, s in zip(self.pl, self.streams)]
+        self.back_done = [torch.cuda.Event() for _ in self.pl]
+        self.count = 0
+
+    def step(self, before=None, after=None):
+        """Issue one step on the next pipeline.  before(i, stream) and
+        after(i, stream), if given, enqueue work on that pipeline's stream
+        around the step (e.g. the host->device copy of its input and the
+        device->host copy of its symbols)."""
+        torch = _torch()
+        i = self.count % len(self.pl)
+        j = (i + len(self.pl) - 1) % len(self.pl)
+        s = self.streams[i]
+        front, back = self.halves[i]
+        with torch.cuda.stream(s):
+            if before is not None:
+                before(i, s)
+            front.replay()
+            s.wait_event(self.back_done[j])
+            back.replay()
+            self.back_done[i].record(s)
+            if after is not None:
+                after(i, s)
+        self.count += 1
+
+    def join(self, stream=None):
+        """Make `stream` (default: current) wait for every step issued so far."""
+        torch = _torch()
+        cur = torch.cuda.current_stream() if stream is None else stream
+        for s in self.streams:
+            cur.wait_stream(s)
+
+    def fork(self, stream=None):
+        """Make the pipelines' streams wait for `stream` (default: current)."""
+        torch = _torch()
+        cur = torch.cuda.current_stream() if stream is None else stream
+        for s in self.streams:
+            s.wait_stream(cur)
+
+
+def tune_inflight(pipelines, base: dict, steps: int = 4):
+    """Pick the launch configuration of two batches in flight: the front
+    half's kernels must leave room on every SM for the other batch's
+    cooperative merge, so the resident CTAs per SM of compression, of the
+    local-aggregation kernels and of the merge rounds are searched around
+    `base` (the single-batch autotuned configuration), timing a few steps of
+    each candidate with CUDA events.  Returns (best configuration, its ms per
+    step, an InFlight runner captured with it)."""
+    torch = _torch()
+    best = None
+    for c_sm in (1, 2):
+        for cap in (2, 3, 4):
+            for m_sm in (1, 2):
+                cfg = dict(base, compress_ctas_per_sm=c_sm, local_ctas_cap=cap, merge_ctas_per_sm=m_sm)
+                for pl in pipelines:
+                    pl.ctx.set_tuning(cfg)
+                fl = InFlight(pipelines)
+                for _ in range(2):
+                    fl.step()
+                fl.join()
+                torch.cuda.synchronize()
+                st = torch.cuda.current_stream()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fl.fork(st)
+                for _ in range(steps):
+                    fl.step()
+                fl.join(st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                if best is None or ms < best[1]:
+                    best = (cfg, ms, fl)
+    for pl in pipelines:
+        pl.ctx.set_tuning(best[0])
+        pl.ctx.sync_status(where="in-flight tuning")
+    return best
 
 
 def graph_kernel_nodes(graph) -> int:

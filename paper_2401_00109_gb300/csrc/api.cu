@@ -21,6 +21,8 @@ struct jabba_ctx {
   Scratch ws;
   void* pool = nullptr;        // one allocation backing the scratch
   size_t pool_bytes = 0;
+  void* rpool = nullptr;       // per-piece scratch of the reconstruction (allocated on its first use)
+  long long cap_recon = 0;
   bool tuning = false;         // autotuning mode (jabba_autotune)
 };
 
@@ -152,10 +154,6 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     const long long off_elems = 512 * tiles + 2;
     w.d_acc = (long long*)take(8 * (acc_elems > off_elems ? acc_elems : off_elems) + 64);
   }
-  w.r_level = (double*)take(8 * slots);
-  w.r_pos = (long long*)take(8 * slots);
-  w.r_tsum = (double*)take(8 * slots);
-  w.r_wsum = (double*)take(8 * slots);
   w.r_tail = (double*)take(8 * (S + 1 > 512 ? S + 1 : 512));
   w.r_tailpos = (long long*)take(8 * (S + 1));
   w.r_tail_level = (double*)take(8 * (S + 1));
@@ -220,8 +218,30 @@ bool tuning_ok(const jabba_tuning* t) {
   if (t->local_big_warps != 4 && t->local_big_warps != 8) return false;
   if (t->merge_ctas_per_sm != 1 && t->merge_ctas_per_sm != 2 && t->merge_ctas_per_sm != 4) return false;
   if (t->per_domain_launch != 0 && t->per_domain_launch != 1) return false;
-  if (t->reserved != 0) return false;
+  if (t->local_ctas_cap < 0 || t->local_ctas_cap > 16) return false;
   return true;
+}
+
+// Per-piece scratch of the reconstruction and its adjoint (level, position,
+// two residual sums per piece), kept apart from the forward path's pool and
+// allocated by the first reconstruction call that needs it (never during
+// graph capture).
+jabba_status ensure_recon(jabba_ctx* c, long long pieces, cudaStream_t st) {
+  if (pieces <= c->cap_recon) return JABBA_OK;
+  if (st && capturing(st)) return JABBA_ERR_STATE;
+  if (cudaDeviceSynchronize() != cudaSuccess) return JABBA_ERR_CUDA;
+  if (c->rpool) cudaFree(c->rpool);
+  c->rpool = nullptr;
+  c->cap_recon = 0;
+  const size_t per = align_up(8 * (size_t)(pieces > 0 ? pieces : 1));
+  if (cudaMalloc(&c->rpool, 4 * per) != cudaSuccess) return JABBA_ERR_CUDA;
+  unsigned char* b = (unsigned char*)c->rpool;
+  c->ws.r_level = (double*)b;
+  c->ws.r_pos = (long long*)(b + per);
+  c->ws.r_tsum = (double*)(b + 2 * per);
+  c->ws.r_wsum = (double*)(b + 3 * per);
+  c->cap_recon = pieces;
+  return JABBA_OK;
 }
 
 }  // namespace
@@ -273,6 +293,7 @@ void jabba_destroy(jabba_ctx* c) {
       for (int k = 0; k < 2; ++k)
         if (c->prof[i][j][k]) cudaEventDestroy(c->prof[i][j][k]);
   if (c->pool) cudaFree(c->pool);
+  if (c->rpool) cudaFree(c->rpool);
   if (c->status) cudaFree(c->status);
   delete c;
 }
@@ -519,8 +540,10 @@ jabba_status jabba_reconstruct(jabba_ctx* c, const double* x, int64_t n_points, 
   if (n_series > 0 && (!x || !series_off || !series_dom_off || !dom_piece_off || !xhat)) return JABBA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   cudaStream_t st = (cudaStream_t)stream;
-  // pieces never outnumber the slots (intervals)
-  jabba_status r = ensure(c, n_series, c->ws.cap_domains, n_points, c->ws.cap_groups, c->ws.cap_big, st);
+  // pieces never outnumber the slots (intervals), which are fewer than the points
+  jabba_status r = ensure(c, n_series, c->ws.cap_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  r = ensure_recon(c, n_points, st);
   if (r != JABBA_OK) return r;
   launch_reconstruct(x, n_points, (const long long*)series_off, n_series, (const long long*)series_dom_off,
                      (const long long*)dom_piece_off, symbol, dict_len, dict_inc, p->round_mode, qlen, xhat, c->ws,
@@ -538,7 +561,9 @@ jabba_status jabba_reconstruct_backward(jabba_ctx* c, const double* x, int64_t n
   if (n_series > 0 && (!x || !series_off || !series_dom_off || !dom_piece_off)) return JABBA_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   cudaStream_t st = (cudaStream_t)stream;
-  jabba_status r = ensure(c, n_series, c->ws.cap_domains, n_points, c->ws.cap_groups, c->ws.cap_big, st);
+  jabba_status r = ensure(c, n_series, c->ws.cap_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  r = ensure_recon(c, n_points, st);
   if (r != JABBA_OK) return r;
   launch_reconstruct_backward(x, n_points, (const long long*)series_off, n_series, (const long long*)series_dom_off,
                               (const long long*)dom_piece_off, symbol, qlen, dict_inc, k, grad_dict_inc, c->ws, st);
@@ -593,7 +618,7 @@ jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
   out->merge_ctas_per_sm = t.merge_ctas_per_sm;
   out->per_domain_launch = t.per_domain_launch;
   out->local_k_warps = t.local_k_warps;
-  out->reserved = 0;
+  out->local_ctas_cap = t.local_ctas_cap;
   return JABBA_OK;
 }
 
@@ -607,6 +632,7 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.merge_ctas_per_sm = in->merge_ctas_per_sm;
   t.per_domain_launch = in->per_domain_launch;
   t.local_k_warps = in->local_k_warps;
+  t.local_ctas_cap = in->local_ctas_cap;
   return JABBA_OK;
 }
 

@@ -796,7 +796,7 @@ static void launch_tile_one(const LocalParams& P, const int* list, const unsigne
 
 template <int W, int CAP>
 static void launch_tile(const LocalParams& P, const int* list, const unsigned* cnt, unsigned* ctr, int num_sms,
-                        cudaStream_t st) {
+                        int cap_per_sm, cudaStream_t st) {
   using Cfg = TileCfg<W, CAP>;
   constexpr int kBlock = Cfg::kBlock;
   constexpr size_t kSmem = (size_t)(kBlock / Cfg::kThreads) * Cfg::kBytes;
@@ -806,7 +806,8 @@ static void launch_tile(const LocalParams& P, const int* list, const unsigned* c
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_local_tile<W, CAP>, kBlock, kSmem);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
-  k_local_tile<W, CAP><<<(unsigned)(num_sms * blocks_per_sm), kBlock, kSmem, st>>>(P, list, cnt, ctr);
+  const int per_sm = cap_per_sm > 0 && cap_per_sm < blocks_per_sm ? cap_per_sm : blocks_per_sm;
+  k_local_tile<W, CAP><<<(unsigned)(num_sms * per_sm), kBlock, kSmem, st>>>(P, list, cnt, ctr);
 }
 
 void launch_local(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
@@ -891,31 +892,31 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
     TierEvents* te = ws.tier_ev;
     const long long L = ws.loc_stride;
     const int ns = ws.num_sms;
-    launch_tile<1, kTierCap0>(P, ws.loc_list, list_cnt + 0, task_ctr + 0, ns, st);
-    launch_tile<1, kTierCap1>(P, ws.loc_list + L, list_cnt + 1, task_ctr + 1, ns, st);
+    launch_tile<1, kTierCap0>(P, ws.loc_list, list_cnt + 0, task_ctr + 0, ns, ws.tune.local_ctas_cap, st);
+    launch_tile<1, kTierCap1>(P, ws.loc_list + L, list_cnt + 1, task_ctr + 1, ns, ws.tune.local_ctas_cap, st);
     if (te) cudaEventRecord(te->ev[0][0], st);
     {
       const int* l2 = ws.loc_list + 2 * L;
-      if (ws.tune.local_k_warps == 4) launch_tile<4, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ns, st);
-      else launch_tile<1, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ns, st);
+      if (ws.tune.local_k_warps == 4) launch_tile<4, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ns, ws.tune.local_ctas_cap, st);
+      else launch_tile<1, kTierCap2>(P, l2, list_cnt + 2, task_ctr + 2, ns, ws.tune.local_ctas_cap, st);
     }
     if (te) cudaEventRecord(te->ev[0][1], st);
     if (te) cudaEventRecord(te->ev[1][0], st);
     {
       const int* l3 = ws.loc_list + 3 * L;
       switch (ws.tune.local_mid_warps) {
-        case 1: launch_tile<1, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
-        case 2: launch_tile<2, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
-        case 8: launch_tile<8, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
-        default: launch_tile<4, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, st); break;
+        case 1: launch_tile<1, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, ws.tune.local_ctas_cap, st); break;
+        case 2: launch_tile<2, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, ws.tune.local_ctas_cap, st); break;
+        case 8: launch_tile<8, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, ws.tune.local_ctas_cap, st); break;
+        default: launch_tile<4, kTierCap3>(P, l3, list_cnt + 3, task_ctr + 3, ns, ws.tune.local_ctas_cap, st); break;
       }
     }
     if (te) cudaEventRecord(te->ev[1][1], st);
     if (te) cudaEventRecord(te->ev[2][0], st);
     {
       const int* l4 = ws.loc_list + 4 * L;
-      if (ws.tune.local_big_warps == 8) launch_tile<8, kTierCap4>(P, l4, list_cnt + 4, task_ctr + 4, ns, st);
-      else launch_tile<4, kTierCap4>(P, l4, list_cnt + 4, task_ctr + 4, ns, st);
+      if (ws.tune.local_big_warps == 8) launch_tile<8, kTierCap4>(P, l4, list_cnt + 4, task_ctr + 4, ns, ws.tune.local_ctas_cap, st);
+      else launch_tile<4, kTierCap4>(P, l4, list_cnt + 4, task_ctr + 4, ns, ws.tune.local_ctas_cap, st);
     }
     if (te) cudaEventRecord(te->ev[2][1], st);
     k_local_warp<<<(unsigned)ws.loc_ctas, kLocWarps * 32, 0, st>>>(P);

@@ -54,6 +54,7 @@ struct Tuning {
   int local_big_warps = 4;       // warps per domain of 2049..4096 pieces (4 or 8)
   int merge_ctas_per_sm = 4;     // CTAs per SM of the cooperative merge-rounds kernel (1, 2 or 4)
   int per_domain_launch = 0;     // 1: the plain form, one launch per domain for compression and Stage I
+  int local_ctas_cap = 0;        // at most this many resident CTAs per SM per local kernel (0: all that fit)
 };
 
 // Events around the local-aggregation kernels of the tiles (tuning only).
