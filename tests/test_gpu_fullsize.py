@@ -222,3 +222,59 @@ def test_diff_full_adjoint_and_refinement():
         losses.append(loss.item())
     assert abs(losses[0] - r["mse"]) <= 1e-9 * r["mse"]
     assert losses[-1] < losses[0]
+
+
+def test_scale_full_two_in_flight():
+    """The benchmark's launch configuration: two pipelines with a batch each
+    in flight (front and back halves on two streams, front kernels capped so
+    the other batch's merge fits beside them).  After several interleaved
+    steps both pipelines hold exactly the result of one pipeline run alone
+    with the default configuration, and sampled domains match the oracle."""
+    import torch
+    import paper_2401_00109_gb300 as jb
+    x, off, cfg, pl = _pipeline("scale")
+    D = pl.D
+
+    def compact(q, key):
+        # the valid slots of every domain, in domain order (slots past a
+        # domain's count hold nothing)
+        b = q.b
+        cnt = b["dom_piece_cnt"][:D].long()
+        first = torch.repeat_interleave(b["dom_slot_off"][:D], cnt)
+        within = torch.arange(first.numel(), device=first.device) - torch.repeat_interleave(b["dom_piece_off"][:D], cnt)
+        return b[key][first + within]
+
+    ref = {k: pl.b[k].clone() for k in ("symbol", "dict_len", "dict_inc", "dict_count", "k", "n_groups",
+                                        "dom_piece_off", "dom_piece_cnt")}
+    for key in ("piece_len", "piece_inc", "local_label"):
+        ref[key] = compact(pl, key)
+    ctx2 = jb.Context()
+    pl2 = jb.Pipeline(ctx2, off, len(x), pl.p, group_capacity=pl.gcap)
+    pl2.x.copy_(torch.from_numpy(x))
+    prof = dict(pl.ctx.tuning(), compress_ctas_per_sm=1, local_ctas_cap=3, merge_ctas_per_sm=1)
+    for c in (pl.ctx, ctx2):
+        c.set_tuning(prof)
+    fl = jb.InFlight([pl, pl2])
+    for _ in range(5):
+        fl.step()
+    fl.join()
+    torch.cuda.synchronize()
+    pl.ctx.sync_status(where="in flight A")
+    ctx2.sync_status(where="in flight B")
+    N = int(ref["dom_piece_off"][-1].item())
+    k = int(ref["k"][0].item())
+    for q in (pl, pl2):
+        assert int(q.b["k"][0].item()) == k and int(q.b["n_groups"][0].item()) == int(ref["n_groups"][0].item())
+        assert torch.equal(q.b["symbol"][:N], ref["symbol"][:N])
+        for key in ("dict_len", "dict_inc", "dict_count"):
+            assert torch.equal(q.b[key][:k], ref[key][:k]), key
+        assert torch.equal(q.b["dom_piece_cnt"][:D], ref["dom_piece_cnt"][:D])
+        for key in ("piece_len", "piece_inc", "local_label"):
+            assert torch.equal(compact(q, key), ref[key]), key
+    h = _host(pl2)
+    rng = np.random.default_rng(2)
+    for d in rng.choice(len(h["cnt"]), 100, replace=False):
+        ln, inc, _ = oracle.compress(x, h["dom_begin"][d:d + 1], h["dom_end"][d:d + 1], cfg["tol"])
+        s0 = h["dom_slot_off"][d]
+        n = h["cnt"][d]
+        assert np.array_equal(ln, h["piece_len"][s0:s0 + n]) and np.array_equal(inc, h["piece_inc"][s0:s0 + n]), d
