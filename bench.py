@@ -422,6 +422,7 @@ def run_ours(args, ws, rank, local):
 
     if args.verify and rank == 0:
         verify_sample(pl, x_host.numpy(), off_np, cfg, args.verify)
+    sweep = partition_sweep(jb, synth, local) if args.partition_sweep and rank == 0 else None
 
     if rank == 0:
         single = dict(value=value, unit="Gpts/s", ms_per_step=ms_all, tuning=tuning,
@@ -444,6 +445,8 @@ def run_ours(args, ws, rank, local):
                                   local=float(np.mean(loc_ms)), merge=float(np.mean(mrg_ms)),
                                   merge_rounds_kernel=float(np.mean(rnd_ms)), symbolize=float(np.mean(sym_ms))),
                     diagnostics=diag, input_gen_s=t_gen)
+        if sweep is not None:
+            line["partition_sweep"] = sweep
         print(json.dumps(line), flush=True)
 
 
@@ -493,6 +496,50 @@ def plain_form(jb, synth, args, local, ws):
                                          ms_per_step=out["batched"]["ms_per_step"]))
 
 
+def partition_sweep(jb, synth, local, steps=20):
+    """Sec. 7.3's experiment on the GPU path: one series of 100,000 N(0, 1)
+    draws (tol = 0.01, alpha = 0.05) cut into M equal domains; per M the
+    pieces, local groups, dictionary size, reconstruction MSE and the
+    CUDA-event time of the whole forward step (median of graph replays), and
+    the oracle's single-thread time on the same input."""
+    import torch
+    import oracle
+    oracle.build()
+    x_np, off_np, cfg = synth.make("noise")
+    x = torch.from_numpy(x_np).cuda()
+    off = torch.from_numpy(off_np).cuda()
+    rows = []
+    for M in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+        p = jb.Params(tol=cfg["tol"], alpha=cfg["alpha"], scl=cfg["scl"], domain_mode=cfg["domain_mode"],
+                      domain_value=M)
+        c = jb.Context(local)
+        out = c.symbolize(x, off, p, series_off_host=off_np)
+        _, xhat = c.reconstruct(x, off, out, p)
+        mse = float(c.mse(x, xhat).item())
+        pl = jb.Pipeline(c, off_np, len(x_np), p, group_capacity=max(out["n_groups_host"] + 1024, 4096))
+        pl.x.copy_(x)
+        pl.enqueue()
+        c.sync_status(where=f"sweep M={M}")
+        g = pl.capture()
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        c.sync_status(where=f"sweep M={M} replays")
+        t0 = time.perf_counter()
+        oracle.pipeline(x_np, off_np, cfg["tol"], cfg["alpha"], cfg["scl"], cfg["domain_mode"], M, threads=1,
+                        with_reconstruct=False)
+        t_cpu = time.perf_counter() - t0
+        rows.append(dict(M=M, pieces=out["n_pieces"], local_groups=out["n_groups_host"], symbols=out["k_host"],
+                         mse=mse, gpu_ms=float(np.median(ts)), oracle_1thread_ms=1e3 * t_cpu))
+        del pl, g, c
+    return rows
+
+
 def verify_sample(pl, x, off, cfg, n_dom):
     """Full-size parity on a sample: the oracle compresses n_dom domains drawn
     at random and must reproduce their pieces bit for bit."""
@@ -531,6 +578,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--plain-series", type=int, default=300, help="series in the plain-form sample")
     ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--partition-sweep", action="store_true",
+                    help="add the Gaussian-noise partition sweep (Sec. 7.3) to the JSON line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")

@@ -27,6 +27,9 @@ Workloads (sizes, generators and parameters; paper section in brackets):
   scale     100,000 series, lengths log-uniform in [100, 100,000] (rounded);
             each series drawn uniformly from {walk, multivar channel, uneven
             level-shift walk}; domains of 4,096 intervals; tol = alpha = 0.1.
+  noise     one series of 100,000 N(0, 1) draws; tol = 0.01, alpha = 0.05;
+            the number of equal domains M is the variable of the partition
+            sweep [Sec. 7.3] (default 1).
 """
 from __future__ import annotations
 
@@ -45,6 +48,7 @@ CONFIGS = {
     "multivar": dict(index=2, tol=0.1,  alpha=0.2,  scl=1.0, domain_mode=EQUAL_COUNT, domain_value=1024, seed=2),
     "diff":     dict(index=3, tol=0.1,  alpha=0.1,  scl=1.0, domain_mode=EQUAL_COUNT, domain_value=4,    seed=3),
     "scale":    dict(index=4, tol=0.1,  alpha=0.1,  scl=1.0, domain_mode=FIXED_LEN,   domain_value=4096, seed=4),
+    "noise":    dict(index=5, tol=0.01, alpha=0.05, scl=1.0, domain_mode=EQUAL_COUNT, domain_value=1,    seed=5),
 }
 
 
@@ -116,6 +120,8 @@ def _lengths(name: str, rng: np.random.Generator) -> np.ndarray:
     if name == "scale":
         u = rng.uniform(math.log(100.0), math.log(100000.0), size=100000)
         return np.rint(np.exp(u)).astype(np.int64)
+    if name == "noise":
+        return np.full(1, 100000, dtype=np.int64)
     raise KeyError(name)
 
 
@@ -134,6 +140,8 @@ def _series(name: str, kind: int, rng: np.random.Generator, n: int) -> np.ndarra
         return sines_ar1(rng, n)
     if name == "scale":
         return (walk, sines_ar1, level_shift_walk)[kind](rng, n)
+    if name == "noise":
+        return rng.standard_normal(n)
     raise KeyError(name)
 
 

@@ -132,3 +132,16 @@ def test_merge_sequential_fallback(C):
     g, *_ = run_gpu(C, x, off, cfg)
     r = run_oracle(x, off, cfg)
     assert_parity(g, r)
+
+
+@pytest.mark.parametrize("M", [1, 8, 64])
+def test_noise_partition_parity(C, M):
+    """The Gaussian-noise workload of the partition sweep (one series of
+    100,000 N(0, 1) draws, tol = 0.01, alpha = 0.05) cut into M equal domains:
+    the whole path, reconstruction included, equals the oracle for each M
+    (M = 1 puts ~70,000 pieces in one domain: the global-memory arena)."""
+    x, off, cfg = synth.make("noise")
+    cfg = dict(cfg, domain_value=M)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert_parity(g, r)
