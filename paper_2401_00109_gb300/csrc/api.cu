@@ -187,6 +187,8 @@ jabba_status ensure(jabba_ctx* c, long long S, long long D, long long slots, lon
   }
   c->pool_bytes = bytes;
   layout(w, S, D, slots, G, big, (unsigned char*)c->pool);
+  // the merge sort's look-back status words must start without a valid tag
+  if (cudaMemset(w.m_hist, 0, 4 * (size_t)rs_hist_words(G)) != cudaSuccess) return JABBA_ERR_CUDA;
   w.cap_series = S;
   w.cap_domains = D;
   w.cap_slots = slots;

@@ -180,76 +180,74 @@ __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long lo
 }
 
 // ------------------------------------------------------------------ LSD radix sort (stable)
-// 8-bit digits over tiles of kRsTile items.  Per pass: k_rs_hist counts the
-// digits of every tile (column d of hist holds digit d over the tiles),
-// k_rs_scan turns each column into exclusive offsets (one CTA per digit) and
-// the digit totals, and k_rs_scatter ranks the tile's items stably (warp w owns
-// the contiguous items [w 256, (w+1) 256) of the tile; ranks from ballots on
-// the digit bits), reorders the tile by digit in shared memory and writes each
-// digit's run to its global position with consecutive threads on consecutive
-// addresses.
+// 8-bit digits over tiles of kRsTile items, one kernel per pass (the
+// decoupled look-back scheme): the CTAs take tiles in increasing order from a
+// counter; each counts its tile's digits, publishes the counts, and every
+// digit's thread walks back over the earlier tiles' published counts (or
+// their inclusive prefixes, once known) to find where the tile's run of that
+// digit starts; the global start of each digit comes from one histogram
+// kernel per sort that counts all passes' digits at once.  A tile waits only
+// on tiles taken before it, so the waits end; every wait is bounded.  The
+// tile's items are ranked stably (warp w owns items [w 256, (w+1) 256); ranks
+// from ballots on the digit bits), reordered by digit in shared memory and
+// written run by run with consecutive threads on consecutive addresses.
+//
+// Published words (64 bits): tag (31) | state (2: 1 = tile count, 2 =
+// inclusive prefix) | value (31; counts are below the group capacity, which
+// is below 2^31).  The tag is (sort epoch * 8 + pass), counted from 1: a
+// word left by an earlier sort or pass does not match, so the status array
+// (zeroed when allocated) needs no clearing between sorts.
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsPerLane = 8;
 constexpr int kRsPerWarp = 32 * kRsPerLane;
 constexpr int kRsTile = kRsWarps * kRsPerWarp;  // 2048
+constexpr int kRsPasses = 8;
 
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* keys, const long long* n_p,
-                                                       long long cap, int shift, unsigned* hist, long long n_tiles,
+struct RsScratch {
+  unsigned long long* status;  // [n_tiles][256]
+  unsigned* ghist;             // [kRsPasses][256] digit counts of all items
+  unsigned* gbase;             // [kRsPasses][256] exclusive digit starts
+  unsigned* tile_ctr;          // [kRsPasses]
+  unsigned* epoch;             // [1]
+};
+
+__global__ void __launch_bounds__(256) k_rs_global_hist(const unsigned long long* keys, const long long* n_p,
+                                                       long long cap, int passes, unsigned* ghist,
                                                        const int* flags) {
-  __shared__ unsigned h[kRsWarps][256];
+  __shared__ unsigned h[kRsPasses][256];
   const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = lane; i < 256; i += 32) h[warp][i] = 0;
-  __syncwarp();
-  const long long wbase = (long long)blockIdx.x * kRsTile + (long long)warp * kRsPerWarp;
-#pragma unroll
-  for (int j = 0; j < kRsPerLane; ++j) {
-    const long long k = wbase + j * 32 + lane;
-    if (k < n) atomicAdd(&h[warp][(unsigned)(keys[k] >> shift) & 255u], 1u);
+  for (int i = threadIdx.x; i < kRsPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
   }
   __syncthreads();
-  const int d = threadIdx.x;
-  unsigned sum = 0;
-#pragma unroll
-  for (int w = 0; w < kRsWarps; ++w) sum += h[w][d];
-  hist[(long long)d * n_tiles + blockIdx.x] = sum;
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    const unsigned v = (&h[0][0])[i];
+    if (v) atomicAdd(&ghist[i], v);
+  }
 }
 
-// Exclusive scan of column d (blockIdx.x) over the tiles, in place; dtot[d] =
-// the column total.
-__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* hist, long long n_tiles, unsigned* dtot) {
-  __shared__ unsigned ws[32];
-  unsigned* col = hist + (long long)blockIdx.x * n_tiles;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const long long per = (n_tiles + 1023) / 1024;
-  const long long lo = (long long)t * per;
-  const long long hi = lo + per < n_tiles ? lo + per : n_tiles;
-  unsigned sum = 0;
-  for (long long i = lo; i < hi; ++i) sum += col[i];
-  unsigned incl = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) ws[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned w = ws[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, w, o);
-      if (lane >= o) w += y;
+// Exclusive digit starts of every pass (one warp per pass); a new sort epoch.
+__global__ void k_rs_bases(const unsigned* ghist, int passes, unsigned* gbase, unsigned* tile_ctr, unsigned* epoch) {
+  const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
+  if (p < passes) {
+    unsigned carry = 0;
+    for (int d0 = 0; d0 < 256; d0 += 32) {
+      const unsigned v = ghist[p * 256 + d0 + lane];
+      unsigned incl = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      gbase[p * 256 + d0 + lane] = carry + incl - v;
+      carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
-    ws[lane] = w;
+    if (lane == 0) tile_ctr[p] = 0;
   }
-  __syncthreads();
-  unsigned run = (warp ? ws[warp - 1] : 0u) + incl - sum;
-  for (long long i = lo; i < hi; ++i) {
-    const unsigned c = col[i];
-    col[i] = run;
-    run += c;
-  }
-  if (t == 1023) dtot[blockIdx.x] = ws[31];
+  if (threadIdx.x == 0) *epoch += 1;
 }
 
 struct RsSmem {
@@ -259,19 +257,29 @@ struct RsSmem {
   unsigned lstart[256];      // first local position of each digit
   long long gpos[256];       // global position of the tile's first item of each digit
   unsigned wsum[kRsWarps];
+  unsigned tile;
+  int ok;
 };
 
-__global__ void __launch_bounds__(kRsThreads, 4) k_rs_scatter(const unsigned long long* kin, const int* vin,
-                                                             unsigned long long* kout, int* vout,
-                                                             const long long* n_p, long long cap, int shift,
-                                                             const unsigned* hist, const unsigned* dtot,
-                                                             long long n_tiles, const int* flags) {
+__device__ __forceinline__ unsigned long long rs_word(unsigned tag, unsigned state, unsigned long long v) {
+  return ((unsigned long long)tag << 33) | ((unsigned long long)state << 31) | v;
+}
+
+__global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long long* kin, const int* vin,
+                                                          unsigned long long* kout, int* vout, const long long* n_p,
+                                                          long long cap, int pass, RsScratch R, long long n_tiles,
+                                                          const int* flags, unsigned* status_word) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RsSmem& S = *(RsSmem*)smem_raw;
   const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
+  const int shift = 8 * pass;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long base = (long long)blockIdx.x * kRsTile;
-  if (base >= n) return;
+  if (threadIdx.x == 0) S.tile = atomicAdd(&R.tile_ctr[pass], 1u);
+  __syncthreads();
+  const unsigned tile = S.tile;
+  const long long base = (long long)tile * kRsTile;
+  if (base >= n) return;  // tiles are taken in order: every later tile is empty too
+  const unsigned tag = ((*R.epoch) * kRsPasses + (unsigned)pass) & 0x7FFFFFFFu;
   const long long wbase = base + (long long)warp * kRsPerWarp;
   unsigned long long kr[kRsPerLane];
   int vr[kRsPerLane];
@@ -287,8 +295,6 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_scatter(const unsigned lon
   }
   __syncthreads();
   {
-    // digit d = threadIdx.x: warp prefix within the digit; tile-wide digit
-    // starts; global digit bases from the totals of all tiles
     const int d = threadIdx.x;
     unsigned run = 0;
 #pragma unroll
@@ -297,32 +303,48 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_scatter(const unsigned lon
       S.wh[w][d] = run;
       run += c;
     }
-    const unsigned tot = dtot[d];
-    unsigned incl = run, gincl = tot;
+    // publish this tile's count of digit d, then look back for its prefix
+    unsigned long long* mine = R.status + (long long)tile * 256 + d;
+    volatile unsigned long long* vs = (volatile unsigned long long*)R.status;
+    unsigned long long excl = 0;
+    int ok = 1;
+    if (tile == 0) {
+      *(volatile unsigned long long*)mine = rs_word(tag, 2, run);
+    } else {
+      *(volatile unsigned long long*)mine = rs_word(tag, 1, run);
+      long long t = (long long)tile - 1;
+      unsigned spins = 0;
+      while (t >= 0) {
+        const unsigned long long w = vs[t * 256 + d];
+        const unsigned wt = (unsigned)(w >> 33), st = (unsigned)(w >> 31) & 3u;
+        if (wt != tag || st == 0) {
+          if (++spins > kSpinLimit) { ok = 0; break; }
+          if (spins > 64) __nanosleep(64);
+          continue;
+        }
+        excl += w & 0x7FFFFFFFull;
+        if (st == 2) break;
+        --t;
+      }
+      __threadfence();
+      *(volatile unsigned long long*)mine = rs_word(tag, 2, excl + run);
+    }
+    if (!ok) set_status(status_word, JABBA_ERR_TIMEOUT);
+    // tile-local digit starts
+    unsigned incl = run;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      const unsigned z = __shfl_up_sync(0xFFFFFFFFu, gincl, o);
-      if (lane >= o) {
-        incl += y;
-        gincl += z;
-      }
+      if (lane >= o) incl += y;
     }
-    __shared__ unsigned gsum[kRsWarps];
-    if (lane == 31) {
-      S.wsum[warp] = incl;
-      gsum[warp] = gincl;
-    }
+    if (lane == 31) S.wsum[warp] = incl;
     __syncthreads();
-    unsigned before = 0, gbefore = 0;
-    for (int w = 0; w < warp; ++w) {
-      before += S.wsum[w];
-      gbefore += gsum[w];
-    }
+    unsigned before = 0;
+    for (int w = 0; w < warp; ++w) before += S.wsum[w];
     const unsigned ls = before + incl - run;
     S.lstart[d] = ls;
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) S.wh[w][d] += ls;
-    S.gpos[d] = (long long)(gbefore + gincl - tot) + (long long)hist[(long long)d * n_tiles + blockIdx.x];
+    S.gpos[d] = (long long)R.gbase[pass * 256 + d] + (long long)excl;
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
@@ -358,30 +380,42 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_scatter(const unsigned lon
   }
 }
 
-long long rs_hist_words(long long cap) { return 256 * ((cap + kRsTile - 1) / kRsTile + 1) + 256; }
+// Scratch words (32-bit) of the sort for cap items.
+long long rs_hist_words(long long cap) {
+  const long long n_tiles = (cap + kRsTile - 1) / kRsTile + 1;
+  return 2 * 256 * n_tiles + 2 * kRsPasses * 256 + 64;
+}
 
 // Stable sort of (keys, vals) by the low `bits` bits of the keys; the result
 // ends in the buffers returned through kres/vres.
 static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, const long long* n_p,
-                       long long cap, int bits, Scratch& ws, unsigned long long** kres, int** vres,
-                       const int* flags, cudaStream_t st) {
+                       long long cap, int bits, Scratch& ws, unsigned* status_word, unsigned long long** kres,
+                       int** vres, const int* flags, cudaStream_t st) {
   const long long n_tiles = (cap + kRsTile - 1) / kRsTile;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem));
+    cudaFuncSetAttribute(k_rs_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem));
     attr = true;
   }
-  unsigned* hist = ws.m_hist;
-  unsigned* dtot = ws.m_hist + 256 * (n_tiles + 1);
+  RsScratch R;
+  R.status = (unsigned long long*)ws.m_hist;
+  R.ghist = ws.m_hist + 2 * 256 * (n_tiles + 1);
+  R.gbase = R.ghist + kRsPasses * 256;
+  R.tile_ctr = R.gbase + kRsPasses * 256;
+  R.epoch = R.tile_ctr + 16;
+  const int passes = (bits + 7) / 8;
   unsigned long long* kin = k0;
   unsigned long long* kout = k1;
   int* vin = v0;
   int* vout = v1;
-  for (int shift = 0; shift < bits && n_tiles > 0; shift += 8) {
-    k_rs_hist<<<(unsigned)n_tiles, kRsThreads, 0, st>>>(kin, n_p, cap, shift, hist, n_tiles, flags);
-    k_rs_scan<<<256, 1024, 0, st>>>(hist, n_tiles, dtot);
-    k_rs_scatter<<<(unsigned)n_tiles, kRsThreads, sizeof(RsSmem), st>>>(kin, vin, kout, vout, n_p, cap, shift, hist,
-                                                                        dtot, n_tiles, flags);
+  if (n_tiles > 0) {
+    cudaMemsetAsync(R.ghist, 0, sizeof(unsigned) * kRsPasses * 256, st);
+    k_rs_global_hist<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(k0, n_p, cap, passes, R.ghist, flags);
+    k_rs_bases<<<1, 32 * kRsPasses, 0, st>>>(R.ghist, passes, R.gbase, R.tile_ctr, R.epoch);
+  }
+  for (int pass = 0; pass < passes && n_tiles > 0; ++pass) {
+    k_rs_pass<<<(unsigned)n_tiles, kRsThreads, sizeof(RsSmem), st>>>(kin, vin, kout, vout, n_p, cap, pass, R,
+                                                                     n_tiles, flags, status_word);
     unsigned long long* tk = kin; kin = kout; kout = tk;
     int* tv = vin; vin = vout; vout = tv;
   }
@@ -1125,7 +1159,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   int* sidx;
   // keys are non-negative binary64: their bit patterns order as the values;
   // the sort is stable and starts in compact-index order, so ties keep it
-  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws, &skey, &sidx, B.flags, st);
+  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws, status, &skey, &sidx, B.flags, st);
   k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
   // the cell sort ping-pongs in the buffers the key sort left free
   unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
@@ -1134,7 +1168,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   unsigned long long* ckey;
   int* cord;
   // cell ids are below cap_cells = 2^23: three 8-bit passes order them
-  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws, &ckey, &cord, B.flags, st);
+  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws, status, &ckey, &cord, B.flags, st);
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
