@@ -72,6 +72,9 @@ def lib():
                 "jo_merge": (C.c_int64, [I64, I64, U64, C.c_int64, C.c_double, C.c_double, C.c_double,
                                          C.c_double, I32, F64, F64, I64]),
                 "jo_symbolize": (None, [I32, I64, I64, C.c_int64, I32, I32]),
+                "jo_reassign": (None, [I32, F64, C.c_int64, C.c_double, C.c_double, C.c_double, F64, F64,
+                                       C.c_int64, I32]),
+                "jo_sse": (C.c_double, [I32, F64, C.c_int64, C.c_double, C.c_double, C.c_double, F64, F64, I32]),
                 "jo_reconstruct_series": (None, [I32, C.c_int64, F64, F64, C.c_double, C.c_int64, C.c_int,
                                                  I32, F64]),
                 "jo_mse": (C.c_double, [F64, F64, C.c_int64]),
@@ -228,6 +231,32 @@ def symbolize(local_label, dom_piece_off, dom_group_off, l2g):
     out = np.empty(max(len(lab), 1), np.int32)
     lib().jo_symbolize(_p(lab, I32), _p(po, I64), _p(go, I64), len(po) - 1, _p(m, I32), _p(out, I32))
     return out[:len(lab)].copy()
+
+
+def reassign(piece_len, piece_inc, sigma_len, sigma_inc, scl, dict_len, dict_inc):
+    """Full-reassignment digitization (Alg. 1 Digitize; Sec. 3.2 argmin): the
+    index of the nearest dictionary entry of every piece, ties to the smaller
+    index."""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    dl = _c(dict_len, np.float64)
+    di = _c(dict_inc, np.float64)
+    out = np.empty(max(len(ln), 1), np.int32)
+    lib().jo_reassign(_p(ln, I32), _p(inc, F64), len(ln), float(sigma_len), float(sigma_inc), float(scl),
+                      _p(dl, F64), _p(di, F64), len(dl), _p(out, I32))
+    return out[:len(ln)].copy()
+
+
+def sse(piece_len, piece_inc, sigma_len, sigma_inc, scl, dict_len, dict_inc, symbol):
+    """Sum of squared normalised distances of the pieces to their entries,
+    summed exactly (2^-64 fixed point) and rounded once."""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    dl = _c(dict_len, np.float64)
+    di = _c(dict_inc, np.float64)
+    sym = _c(symbol, np.int32)
+    return lib().jo_sse(_p(ln, I32), _p(inc, F64), len(ln), float(sigma_len), float(sigma_inc), float(scl),
+                        _p(dl, F64), _p(di, F64), _p(sym, I32))
 
 
 # ---------------------------------------------------------------- inverse symbolization

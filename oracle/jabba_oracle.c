@@ -498,6 +498,58 @@ void jo_symbolize(const int32_t* local_label, const int64_t* dom_piece_off, cons
 }
 
 /* ------------------------------------------------------------------------ */
+/* Full-reassignment digitization (Alg. 1, Digitize(P^(m), D); the argmin of */
+/* Sec. 3.2): each piece takes the dictionary entry nearest to it in         */
+/* normalised coordinates, d2 = dx*dx + dy*dy with dx = X_p - X_c and        */
+/* dy = Y_p - Y_c (binary64, in that order), X = (scl len) / sigma_len and   */
+/* Y = inc / sigma_inc for pieces and entries alike; a tie goes to the       */
+/* smaller entry index.  Plain O(N k) scan.  The two-stage scheme of Sec. 5  */
+/* replaces this pass by label propagation.                                  */
+/* ------------------------------------------------------------------------ */
+void jo_reassign(const int32_t* len, const double* inc, int64_t n, double sigma_len, double sigma_inc, double scl,
+                 const double* dict_len, const double* dict_inc, int64_t k, int32_t* symbol) {
+  double* Xc = (double*)malloc(sizeof(double) * (size_t)(k ? k : 1));
+  double* Yc = (double*)malloc(sizeof(double) * (size_t)(k ? k : 1));
+  for (int64_t c = 0; c < k; ++c) {
+    Xc[c] = norm_len(dict_len[c], scl, sigma_len);
+    Yc[c] = norm_inc(dict_inc[c], sigma_inc);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const double X = norm_len((double)len[i], scl, sigma_len), Y = norm_inc(inc[i], sigma_inc);
+    double best = 0.0;
+    int64_t bi = -1;
+    for (int64_t c = 0; c < k; ++c) {
+      const double dx = X - Xc[c], dy = Y - Yc[c];
+      const double d2 = dx * dx + dy * dy;
+      if (bi < 0 || d2 < best) {
+        best = d2;
+        bi = c;
+      }
+    }
+    symbol[i] = (int32_t)bi;
+  }
+  free(Xc);
+  free(Yc);
+}
+
+/* Sum of squared errors of an assignment in normalised units (Sec. 3.2; the */
+/* quantity whose ratio Table 2 reports): sum over pieces of d2(piece, entry */
+/* of its symbol), d2 as in jo_reassign, summed exactly (fixed point 2^-64,  */
+/* each term truncated toward zero) and rounded once.                        */
+double jo_sse(const int32_t* len, const double* inc, int64_t n, double sigma_len, double sigma_inc, double scl,
+              const double* dict_len, const double* dict_inc, const int32_t* symbol) {
+  jo_fx acc;
+  fx_zero(&acc);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t c = symbol[i];
+    const double dx = norm_len((double)len[i], scl, sigma_len) - norm_len(dict_len[c], scl, sigma_len);
+    const double dy = norm_inc(inc[i], sigma_inc) - norm_inc(dict_inc[c], sigma_inc);
+    fx_add_double(&acc, dx * dx + dy * dy);
+  }
+  return fx_to_double(&acc);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Inverse symbolization of one series (Sec. 3.3).                          */
 /* inverse digitization: (l~, i~) = dictionary entry of each symbol;         */
 /* quantization: v = l~_j + e; l^_j = round(v); e = v - l^_j (e_0 = 0)        */

@@ -248,3 +248,46 @@ def test_merge_alpha0_merges_identical_only():
     assert l2g[0] == l2g[1] == l2g[2] != l2g[3]          # centres (5, 1) x3 identical; (3, 1/6) differs
     # the centre (3, 1/6) has the smaller norm, so its global group is created first
     assert l2g[3] == 0 and dc.tolist() == [3, 4]
+
+
+def test_reassign_hand():
+    """Full reassignment on the hand-derived fixture (nearest entry, ties to
+    the smaller index) and its exact SSE."""
+    from _golden import load
+    g = load("reassign_hand.txt")
+    ln = g["len"].astype(np.int32)
+    lab = oracle.reassign(ln, g["inc"], 1.0, 1.0, 1.0, g["dict_len"], g["dict_inc"])
+    assert np.array_equal(lab, g["labels"].astype(np.int32))
+    assert oracle.sse(ln, g["inc"], 1.0, 1.0, 1.0, g["dict_len"], g["dict_inc"], lab) == g["sse"][0]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_reassign_matches_vectorized_argmin_and_beats_two_stage(seed):
+    """The reassignment equals a vectorised argmin over all entries (same
+    binary64 operations; numpy's argmin keeps the first minimum); every piece
+    is at least as close to its reassigned entry as to its two-stage entry,
+    so the SSE cannot grow; the exact SSE is within n 2^-64 of math.fsum."""
+    import math
+    import synth
+    x, off, cfg = synth.make("small", max_series=6 + seed)
+    r = oracle.pipeline(x, off, cfg["tol"], cfg["alpha"], cfg["scl"], cfg["domain_mode"], cfg["domain_value"],
+                        with_reconstruct=False)
+    sl, si, scl = r["sigma_len"], r["sigma_inc"], cfg["scl"]
+    ln, inc = r["piece_len"], r["piece_inc"]
+    dl, di = r["dict_len"], r["dict_inc"]
+    lab = oracle.reassign(ln, inc, sl, si, scl, dl, di)
+    X = (scl * ln.astype(np.float64)) / sl
+    Y = inc / si
+    Xc = (scl * dl) / sl
+    Yc = di / si
+    dx = X[:, None] - Xc[None, :]
+    dy = Y[:, None] - Yc[None, :]
+    d2 = dx * dx + dy * dy
+    assert np.array_equal(lab, np.argmin(d2, axis=1).astype(np.int32))
+    rows = np.arange(len(ln))
+    assert np.all(d2[rows, lab] <= d2[rows, r["symbol"]])
+    s_re = oracle.sse(ln, inc, sl, si, scl, dl, di, lab)
+    s_two = oracle.sse(ln, inc, sl, si, scl, dl, di, r["symbol"])
+    assert s_re <= s_two
+    ref = math.fsum(d2[rows, lab])
+    assert abs(s_re - ref) <= len(ln) * 2.0**-64 + 2 * math.ulp(ref)
