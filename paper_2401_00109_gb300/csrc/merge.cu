@@ -194,9 +194,11 @@ __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long lo
 //
 // Published words (64 bits): tag (31) | state (2: 1 = tile count, 2 =
 // inclusive prefix) | value (31; counts are below the group capacity, which
-// is below 2^31).  The tag is (sort epoch * 8 + pass), counted from 1: a
-// word left by an earlier sort or pass does not match, so the status array
-// (zeroed when allocated) needs no clearing between sorts.
+// is below 2^31).  The tag is (sort epoch * 8 + pass), counted from 1, and the
+// epoch sits at a fixed place ahead of the status words: a word left by an
+// earlier sort or pass (of any size) does not match until the tags wrap after
+// 2^28 sorts, so the status array (zeroed when allocated) needs no clearing
+// between sorts.
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsPerLane = 8;
@@ -380,10 +382,12 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
   }
 }
 
-// Scratch words (32-bit) of the sort for cap items.
+// Scratch words (32-bit) of the sort for cap items: the fixed header
+// (2 x kRsPasses x 256 histogram words, 16 tile counters, the epoch, padding
+// to 64 words) and one 64-bit status word per (tile, digit).
 long long rs_hist_words(long long cap) {
   const long long n_tiles = (cap + kRsTile - 1) / kRsTile + 1;
-  return 2 * 256 * n_tiles + 2 * kRsPasses * 256 + 64;
+  return 2 * kRsPasses * 256 + 64 + 2 * 256 * n_tiles;
 }
 
 // Stable sort of (keys, vals) by the low `bits` bits of the keys; the result
@@ -397,12 +401,15 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
     cudaFuncSetAttribute(k_rs_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem));
     attr = true;
   }
+  // Fixed header (histograms, tile counters, epoch) first, status words after
+  // it: the layout does not depend on cap, so the epoch persists across sorts
+  // of any size and no status word left by an earlier sort carries a live tag.
   RsScratch R;
-  R.status = (unsigned long long*)ws.m_hist;
-  R.ghist = ws.m_hist + 2 * 256 * (n_tiles + 1);
+  R.ghist = ws.m_hist;
   R.gbase = R.ghist + kRsPasses * 256;
   R.tile_ctr = R.gbase + kRsPasses * 256;
   R.epoch = R.tile_ctr + 16;
+  R.status = (unsigned long long*)(ws.m_hist + 2 * kRsPasses * 256 + 64);
   const int passes = (bits + 7) / 8;
   unsigned long long* kin = k0;
   unsigned long long* kout = k1;
