@@ -424,6 +424,26 @@ def run_ours(args, ws, rank, local):
         verify_sample(pl, x_host.numpy(), off_np, cfg, args.verify)
     sweep = partition_sweep(jb, synth, local) if args.partition_sweep and rank == 0 else None
 
+    # ---- the full-reassignment variant (Alg. 1 Digitize, the O(N k) argmin
+    # pass that label propagation replaces): its time on this workload and the
+    # SSE of both assignments (Table 2's comparison)
+    reassign = None
+    if not args.no_reassign:
+        res = pl.as_result()
+        ctx.reassign(res, p)
+        ctx.sync_status(where="reassignment warm-up")
+        e0.record(st)
+        sym_re = ctx.reassign(res, p)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ra_ms = e0.elapsed_time(e1)
+        s_two = float(ctx.sse(res, p, res["symbol"]).item())
+        s_re = float(ctx.sse(res, p, sym_re).item())
+        changed = float((sym_re != res["symbol"]).double().mean().item())
+        ctx.sync_status(where="reassignment")
+        reassign = dict(ms=ra_ms, sse_label_propagation=s_two, sse_reassigned=s_re,
+                        sse_ratio=s_two / s_re if s_re > 0 else None, pieces_changed=changed)
+
     if rank == 0:
         single = dict(value=value, unit="Gpts/s", ms_per_step=ms_all, tuning=tuning,
                       form="one batch at a time: CUDA-graph replay of the whole step")
@@ -447,6 +467,8 @@ def run_ours(args, ws, rank, local):
                     diagnostics=diag, input_gen_s=t_gen)
         if sweep is not None:
             line["partition_sweep"] = sweep
+        if reassign is not None:
+            line["reassignment"] = reassign
         print(json.dumps(line), flush=True)
 
 
@@ -578,6 +600,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--plain-series", type=int, default=300, help="series in the plain-form sample")
     ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-reassign", action="store_true", help="skip the full-reassignment comparison")
     ap.add_argument("--partition-sweep", action="store_true",
                     help="add the Gaussian-noise partition sweep (Sec. 7.3) to the JSON line")
     ap.add_argument("--no-e2e", action="store_true")

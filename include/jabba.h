@@ -182,6 +182,34 @@ jabba_status jabba_symbolize(jabba_ctx* ctx, const int32_t* local_label, const i
                              const int64_t* dom_group_off, int64_t n_domains, const int32_t* l2g,
                              int32_t* symbol, jabba_stream stream);
 
+/* ---------------------------------------------------------------- full reassignment (variant)
+ * Alg. 1's Digitize(P^(m), D) with the argmin of Sec. 3.2: every piece is
+ * assigned the dictionary entry nearest to it in normalised coordinates,
+ *     c* = argmin_c d2,  d2 = dx*dx + dy*dy,  dx = X_p - X_c,  dy = Y_p - Y_c,
+ * X = (scl * len) / sigma_len and Y = inc / sigma_inc for pieces and entries
+ * (binary64 in that order, no fused operations); a tie goes to the smaller
+ * entry index.  This is the O(N k) pass that Sec. 5's label propagation
+ * (jabba_symbolize) replaces; it exists for comparing the two.  Pieces and
+ * domains as for jabba_symbolize; the dictionary is dict_len/dict_inc[*k]
+ * (k a device scalar, k <= dict_capacity).  Output: symbol (compact, one per
+ * piece, like jabba_symbolize's).  The first call allocates the call's
+ * scratch for dict_capacity entries (not during graph capture:
+ * JABBA_ERR_STATE). */
+jabba_status jabba_reassign(jabba_ctx* ctx, const int32_t* piece_len, const double* piece_inc,
+                            const int64_t* dom_slot_off, const int32_t* dom_piece_cnt, const int64_t* dom_piece_off,
+                            int64_t n_domains, const double* sigma, const double* dict_len, const double* dict_inc,
+                            const int64_t* k, int64_t dict_capacity, const jabba_params* p, int32_t* symbol,
+                            jabba_stream stream);
+
+/* Sum of squared errors of an assignment (Sec. 3.2; the quantity whose ratio
+ * Table 2 reports): sse (device scalar) = sum over pieces of d2(piece, entry
+ * symbol[piece]) with d2 as in jabba_reassign, each term truncated to 2^-64
+ * fixed point and the sum rounded once (independent of summation order). */
+jabba_status jabba_sse(jabba_ctx* ctx, const int32_t* piece_len, const double* piece_inc, const int64_t* dom_slot_off,
+                       const int32_t* dom_piece_cnt, const int64_t* dom_piece_off, int64_t n_domains,
+                       const double* sigma, const double* dict_len, const double* dict_inc, const int32_t* symbol,
+                       const jabba_params* p, double* sse, jabba_stream stream);
+
 /* ---------------------------------------------------------------- 6. reconstruct
  * Sec. 3.3, per series: inverse digitization (l~, i~) = dictionary entry of
  * each symbol; quantization v = l~ + e, l^ = round(v) (round_mode), e = v - l^,

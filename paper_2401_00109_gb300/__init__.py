@@ -113,6 +113,8 @@ def load():
                 "jabba_reconstruct_noalloc": (C.c_int, [V, I64, V, I64, V, V, I64, V, V, V, C.c_int32, V, V, V]),
                 "jabba_profile_elapsed": (C.c_int, [V, C.c_int, C.c_int, C.POINTER(C.c_float)]),
                 "jabba_autotune": (C.c_int, [V, C.c_int]),
+                "jabba_reassign": (C.c_int, [V, V, V, V, V, V, I64, V, V, V, V, I64, C.POINTER(_Params), V, V]),
+                "jabba_sse": (C.c_int, [V, V, V, V, V, V, I64, V, V, V, V, C.POINTER(_Params), V, V]),
                 "jabba_get_tuning": (C.c_int, [V, C.POINTER(_Tuning)]),
                 "jabba_set_tuning": (C.c_int, [V, C.POINTER(_Tuning)]),
             }
@@ -312,6 +314,32 @@ class Context:
             _ptr(out["dom_piece_off"]), _ptr(out["symbol"]), _ptr(qlen), _ptr(dict_inc), k, _ptr(grad),
             self._stream(stream)), "jabba_reconstruct_backward")
         return grad[:k]
+
+    def reassign(self, out: dict, p: Params, stream=None):
+        """Full-reassignment digitization (Alg. 1 Digitize; Sec. 3.2 argmin):
+        the nearest dictionary entry of every piece of a symbolize() result,
+        ties to the smaller entry index.  Returns the compact symbols."""
+        torch = _torch()
+        N = int(out["n_pieces"])
+        sym = torch.empty(max(N, 1), dtype=torch.int32, device=out["piece_len"].device)
+        cap = max(int(out["k_host"]), 1)
+        _check(self.lib.jabba_reassign(
+            self.h, _ptr(out["piece_len"]), _ptr(out["piece_inc"]), _ptr(out["dom_slot_off"]),
+            _ptr(out["dom_piece_cnt"]), _ptr(out["dom_piece_off"]), out["n_domains"], _ptr(out["sigma"]),
+            _ptr(out["dict_len"]), _ptr(out["dict_inc"]), _ptr(out["k"]), cap, C.byref(p.c()), _ptr(sym),
+            self._stream(stream)), "jabba_reassign")
+        return sym[:N]
+
+    def sse(self, out: dict, p: Params, symbol, stream=None):
+        """Exact sum of squared normalised errors of an assignment (device scalar)."""
+        torch = _torch()
+        res = torch.empty(1, dtype=torch.float64, device=out["piece_len"].device)
+        _check(self.lib.jabba_sse(
+            self.h, _ptr(out["piece_len"]), _ptr(out["piece_inc"]), _ptr(out["dom_slot_off"]),
+            _ptr(out["dom_piece_cnt"]), _ptr(out["dom_piece_off"]), out["n_domains"], _ptr(out["sigma"]),
+            _ptr(out["dict_len"]), _ptr(out["dict_inc"]), _ptr(symbol), C.byref(p.c()), _ptr(res),
+            self._stream(stream)), "jabba_sse")
+        return res
 
     def autotune(self, enable: bool):
         """Autotuning mode: while on, every compress / local digitization /
@@ -531,6 +559,18 @@ class Pipeline:
                     fn(stream)
             graphs.append(g)
         return graphs
+
+    def as_result(self) -> dict:
+        """The last step's outputs in the layout Context.symbolize() returns
+        (device tensors; reads the piece and dictionary counts)."""
+        b = self.b
+        N = int(b["dom_piece_off"][self.D].item())
+        k = int(b["k"][0].item())
+        out = {key: b[key] for key in ("piece_len", "piece_inc", "dom_slot_off", "dom_piece_cnt", "dom_piece_off",
+                                       "sigma", "k")}
+        out.update(n_domains=self.D, n_pieces=N, k_host=k, dict_len=b["dict_len"][:k], dict_inc=b["dict_inc"][:k],
+                   symbol=b["symbol"][:N])
+        return out
 
     def results(self):
         """Host copies of the symbols and dictionary of the last step."""

@@ -23,6 +23,9 @@ struct jabba_ctx {
   size_t pool_bytes = 0;
   void* rpool = nullptr;       // per-piece scratch of the reconstruction (allocated on its first use)
   long long cap_recon = 0;
+  void* rapool = nullptr;      // scratch of the full reassignment and the SSE (allocated on first use)
+  long long cap_ra = -1;
+  RaScratch ra;
   bool tuning = false;         // autotuning mode (jabba_autotune)
 };
 
@@ -246,6 +249,46 @@ jabba_status ensure_recon(jabba_ctx* c, long long pieces, cudaStream_t st) {
   return JABBA_OK;
 }
 
+// Scratch of jabba_reassign / jabba_sse for dictionaries of up to `entries`
+// entries (allocated by the first call that needs it, never during capture).
+jabba_status ensure_ra(jabba_ctx* c, long long entries, cudaStream_t st) {
+  if (entries <= c->cap_ra) return JABBA_OK;
+  if (st && capturing(st)) return JABBA_ERR_STATE;
+  if (cudaDeviceSynchronize() != cudaSuccess) return JABBA_ERR_CUDA;
+  if (c->rapool) cudaFree(c->rapool);
+  c->rapool = nullptr;
+  c->cap_ra = -1;
+  const long long e = entries > 0 ? entries : 1;
+  const long long cells = ra_cells_max() + 1;
+  size_t off = 0;
+  size_t sz[13] = {8 * (size_t)e, 8 * (size_t)e, 4 * (size_t)e, 4 * (size_t)e, 4 * (size_t)e, 4 * (size_t)e,
+                   4 * (size_t)e, 4 * (size_t)cells, 8 * (size_t)cells, 8 * (size_t)scan_scratch_elems(cells), 64,
+                   16, 64};
+  size_t at[13];
+  for (int i = 0; i < 13; ++i) {
+    at[i] = off;
+    off += align_up(sz[i]);
+  }
+  if (cudaMalloc(&c->rapool, off) != cudaSuccess) return JABBA_ERR_CUDA;
+  unsigned char* b = (unsigned char*)c->rapool;
+  RaScratch& R = c->ra;
+  R.X64 = (double*)(b + at[0]);
+  R.Y64 = (double*)(b + at[1]);
+  R.X32 = (float*)(b + at[2]);
+  R.Y32 = (float*)(b + at[3]);
+  R.eX = (float*)(b + at[4]);
+  R.eY = (float*)(b + at[5]);
+  R.ent = (int*)(b + at[6]);
+  R.cnt = (int*)(b + at[7]);
+  R.off = (long long*)(b + at[8]);
+  R.scan = (long long*)(b + at[9]);
+  R.geom = (struct RaGeom*)(b + at[10]);
+  R.bounds = (int*)(b + at[11]);
+  R.acc = (unsigned long long*)(b + at[12]);
+  c->cap_ra = entries;
+  return JABBA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -296,6 +339,7 @@ void jabba_destroy(jabba_ctx* c) {
         if (c->prof[i][j][k]) cudaEventDestroy(c->prof[i][j][k]);
   if (c->pool) cudaFree(c->pool);
   if (c->rpool) cudaFree(c->rpool);
+  if (c->rapool) cudaFree(c->rapool);
   if (c->status) cudaFree(c->status);
   delete c;
 }
@@ -602,6 +646,47 @@ jabba_status jabba_profile_elapsed(jabba_ctx* c, int slot, int stage, float* ms)
   cudaSetDevice(c->device);
   if (cudaEventSynchronize(b) != cudaSuccess) return JABBA_ERR_CUDA;
   return cuda_ok(cudaEventElapsedTime(ms, a, b));
+}
+
+jabba_status jabba_reassign(jabba_ctx* c, const int32_t* piece_len, const double* piece_inc,
+                            const int64_t* dom_slot_off, const int32_t* dom_piece_cnt, const int64_t* dom_piece_off,
+                            int64_t n_domains, const double* sigma, const double* dict_len, const double* dict_inc,
+                            const int64_t* k, int64_t dict_capacity, const jabba_params* p, int32_t* symbol,
+                            jabba_stream stream) {
+  if (!c || !params_ok(p) || n_domains < 0 || dict_capacity < 1 || dict_capacity >= 0x7FFFFFFFll)
+    return JABBA_ERR_INVALID_ARG;
+  if (!sigma || !dict_len || !dict_inc || !k) return JABBA_ERR_INVALID_ARG;
+  if (n_domains > 0 && (!piece_len || !piece_inc || !dom_slot_off || !dom_piece_cnt || !dom_piece_off || !symbol))
+    return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  jabba_status r = ensure(c, c->ws.cap_series, c->ws.cap_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  r = ensure_ra(c, dict_capacity, st);
+  if (r != JABBA_OK) return r;
+  launch_reassign(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt, (const long long*)dom_piece_off,
+                  n_domains, sigma, dict_len, dict_inc, (const long long*)k, dict_capacity, p->scl, p->alpha, symbol,
+                  c->ra, c->ws, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_sse(jabba_ctx* c, const int32_t* piece_len, const double* piece_inc, const int64_t* dom_slot_off,
+                       const int32_t* dom_piece_cnt, const int64_t* dom_piece_off, int64_t n_domains,
+                       const double* sigma, const double* dict_len, const double* dict_inc, const int32_t* symbol,
+                       const jabba_params* p, double* sse, jabba_stream stream) {
+  if (!c || !params_ok(p) || n_domains < 0 || !sigma || !sse) return JABBA_ERR_INVALID_ARG;
+  if (n_domains > 0 && (!piece_len || !piece_inc || !dom_slot_off || !dom_piece_cnt || !dom_piece_off || !symbol ||
+                        !dict_len || !dict_inc))
+    return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  jabba_status r = ensure(c, c->ws.cap_series, c->ws.cap_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
+  if (r != JABBA_OK) return r;
+  r = ensure_ra(c, c->cap_ra > 0 ? c->cap_ra : 1, st);
+  if (r != JABBA_OK) return r;
+  launch_sse(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt, (const long long*)dom_piece_off,
+             n_domains, sigma, dict_len, dict_inc, symbol, p->scl, sse, c->ra, c->ws, st);
+  return cuda_ok(cudaGetLastError());
 }
 
 jabba_status jabba_autotune(jabba_ctx* c, int enable) {

@@ -153,6 +153,35 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
 
 long long rs_hist_words(long long cap);  // radix-sort histogram words for cap items
 
+// Scratch of the full reassignment and of the SSE (reassign.cu), allocated
+// by their first call for a dictionary capacity.
+struct RaScratch {
+  double* X64 = nullptr;   // [cap] entry coordinates, binary64
+  double* Y64 = nullptr;
+  float* X32 = nullptr;    // [cap] FP32
+  float* Y32 = nullptr;
+  float* eX = nullptr;     // [cap] FP32 coordinates in cell order
+  float* eY = nullptr;
+  int* ent = nullptr;      // [cap] entry index in cell order
+  int* cnt = nullptr;      // [cells + 1]
+  long long* off = nullptr;  // [cells + 1]
+  long long* scan = nullptr; // scan scratch for cells + 1 elements
+  struct RaGeom* geom = nullptr;
+  int* bounds = nullptr;   // [4]
+  unsigned long long* acc = nullptr;  // [8]
+};
+long long ra_cells_max();
+
+void launch_reassign(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
+                     const int* dom_piece_cnt, const long long* dom_piece_off, long long n_domains,
+                     const double* sigma, const double* dict_len, const double* dict_inc, const long long* k,
+                     long long dict_capacity, double scl, double alpha, int* symbol, RaScratch& R, Scratch& ws,
+                     cudaStream_t st);
+void launch_sse(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
+                const int* dom_piece_cnt, const long long* dom_piece_off, long long n_domains, const double* sigma,
+                const double* dict_len, const double* dict_inc, const int* symbol, double scl, double* out,
+                RaScratch& R, Scratch& ws, cudaStream_t st);
+
 void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
                   const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
                   double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,

@@ -145,3 +145,58 @@ def test_noise_partition_parity(C, M):
     g, *_ = run_gpu(C, x, off, cfg)
     r = run_oracle(x, off, cfg)
     assert_parity(g, r)
+
+
+@pytest.mark.parametrize("name,max_series", [("small", None), ("uneven", 30), ("scale", 120), ("multivar", 1)])
+def test_reassign_and_sse_parity(C, name, max_series):
+    """Full-reassignment digitization (Alg. 1 Digitize) and the exact SSE of
+    both assignments equal the oracle's, bit for bit; the reassignment never
+    has a larger SSE than label propagation."""
+    import oracle
+    x, off, cfg = synth.make(name, max_series=max_series)
+    g, out, xg, offg = run_gpu(C, x, off, cfg, recon=False)
+    r = run_oracle(x, off, cfg, recon=False)
+    assert_parity(g, r, recon=False)
+    p = __import__("_gpu").params(cfg)
+    sym = C.reassign(out, p)
+    ref = oracle.reassign(r["piece_len"], r["piece_inc"], r["sigma_len"], r["sigma_inc"], cfg["scl"],
+                          r["dict_len"], r["dict_inc"])
+    assert np.array_equal(sym.cpu().numpy(), ref)
+    s_re = float(C.sse(out, p, sym).item())
+    s_two = float(C.sse(out, p, out["symbol"]).item())
+    C.sync_status(where="reassign")
+    o_re = oracle.sse(r["piece_len"], r["piece_inc"], r["sigma_len"], r["sigma_inc"], cfg["scl"], r["dict_len"],
+                      r["dict_inc"], ref)
+    o_two = oracle.sse(r["piece_len"], r["piece_inc"], r["sigma_len"], r["sigma_inc"], cfg["scl"], r["dict_len"],
+                       r["dict_inc"], r["symbol"])
+    assert s_re == o_re and s_two == o_two
+    assert s_re <= s_two
+
+
+def test_merge_group_capacity_changes(C):
+    """Stage II on one context with group capacities that grow and shrink
+    between calls (the merge sort's scratch is laid out for each call's
+    capacity): the dictionary, the local -> global map and the symbols equal
+    the oracle's every time."""
+    import torch
+    from _gpu import params
+    x, off, cfg = synth.make("small")
+    r = run_oracle(x, off, cfg, recon=False)
+    p = params(cfg)
+    c = C.compress(torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda(), p, series_off_host=off)
+    C.sync_status(where="compress")
+    D = c["n_domains"]
+    cnt = c["dom_piece_cnt"][:D].cpu().numpy().astype(np.int64)
+    G = len(r["l2g"])
+    for mult in (1, 64, 8, 1, 32, 2, 1):
+        l = C.digitize_local(c, p, group_capacity=G * mult)
+        m = C.merge_global(l, p)
+        C.sync_status(where="merge")
+        k = int(m["k"].item())
+        assert np.array_equal(m["l2g"][:G].cpu().numpy(), r["l2g"]), mult
+        assert np.array_equal(m["dict_len"][:k].cpu().numpy(), r["dict_len"]), mult
+        assert np.array_equal(m["dict_count"][:k].cpu().numpy(), r["dict_count"]), mult
+        N = int(cnt.sum())
+        sym = C.symbolize_step(c, l, m, N)
+        C.sync_status(where="symbolize")
+        assert np.array_equal(sym.cpu().numpy(), r["symbol"]), mult
