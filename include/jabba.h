@@ -263,7 +263,7 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
  * kernels.  Every configuration computes the same results (bit for bit); only
  * the speed differs.  Domains of up to 512 pieces are aggregated by one warp
  * each; larger domains by the number of warps chosen here.
- * Defaults: {2, 1, 4, 4, 4, 0, 1, 0}. */
+ * Defaults: {2, 1, 4, 4, 4, 0, 1, 0, 1}. */
 typedef struct {
   int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
@@ -278,6 +278,9 @@ typedef struct {
   int32_t local_k_warps;        /* warps that aggregate one domain of 513..1024 pieces together: 1 or 4        */
   int32_t local_ctas_cap;       /* resident CTAs per SM of each local-aggregation kernel: 0 = as many as fit,
                                    1..16 = at most that many (leaves room for a concurrent kernel)            */
+  int32_t merge_form;           /* merge rounds: 1 = one grid barrier per round, coverage by the decided
+                                   starts tested on the fly (default); 0 = two barriers per round, coverage
+                                   marked between them                                                       */
 } jabba_tuning;
 
 /* Autotuning mode.  While enabled (enable = 1), each call of jabba_compress,

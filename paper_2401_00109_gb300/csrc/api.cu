@@ -137,11 +137,13 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.cY = (float*)take(4 * G);
     B.cov = (unsigned char*)take((G > 0 ? G : 1) + 64);  // 16-byte loads read past the last item
     B.chg_list = (int*)take(8 * (G > 0 ? G : 1));
-    B.s_pos = (int*)take(4 * slots);
-    B.s_base = (unsigned*)take(4 * slots);
-    B.s_pre = (unsigned*)take(4 * 26 * slots);
-    B.s_q = (int*)take(4 * 25 * slots);
-    B.s_lo = (int*)take(4 * 25 * slots);
+    // two buffers: the one-phase rounds mark a round's starts in the next round
+    if (base) B.slots = slots;
+    B.s_pos = (int*)take(4 * 2 * slots);
+    B.s_base = (unsigned*)take(4 * 2 * slots);
+    B.s_pre = (unsigned*)take(4 * 2 * 26 * slots);
+    B.s_q = (int*)take(4 * 2 * 25 * slots);
+    B.s_lo = (int*)take(4 * 2 * 25 * slots);
     B.eval_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.chg_stamp = (unsigned*)take(4 * (G > 0 ? G : 1));
     B.lab = (int*)take(4 * G);
@@ -224,6 +226,7 @@ bool tuning_ok(const jabba_tuning* t) {
   if (t->merge_ctas_per_sm != 1 && t->merge_ctas_per_sm != 2 && t->merge_ctas_per_sm != 4) return false;
   if (t->per_domain_launch != 0 && t->per_domain_launch != 1) return false;
   if (t->local_ctas_cap < 0 || t->local_ctas_cap > 16) return false;
+  if (t->merge_form != 0 && t->merge_form != 1) return false;
   return true;
 }
 
@@ -706,6 +709,7 @@ jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
   out->per_domain_launch = t.per_domain_launch;
   out->local_k_warps = t.local_k_warps;
   out->local_ctas_cap = t.local_ctas_cap;
+  out->merge_form = t.merge_form;
   return JABBA_OK;
 }
 
@@ -720,6 +724,7 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.per_domain_launch = in->per_domain_launch;
   t.local_k_warps = in->local_k_warps;
   t.local_ctas_cap = in->local_ctas_cap;
+  t.merge_form = in->merge_form;
   return JABBA_OK;
 }
 

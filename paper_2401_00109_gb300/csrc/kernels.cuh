@@ -29,11 +29,12 @@ struct MergeBufs {
   float* cY = nullptr;
   unsigned char* cov = nullptr;      // [cap + 64] covered flags (cell order)
   int* chg_list = nullptr;           // [2 * cap] cells that changed (per round parity)
-  int* s_pos = nullptr;              // [slots] new starts of a round: sorted position
-  unsigned* s_base = nullptr;        // [slots] first coverage unit
-  unsigned* s_pre = nullptr;         // [26 * slots] coverage units per neighbour
-  int* s_q = nullptr;                // [25 * slots] neighbour cells to cover
-  int* s_lo = nullptr;               // [25 * slots] first item to test there
+  long long slots = 0;               // slots of one buffer of s_* (two buffers)
+  int* s_pos = nullptr;              // [2 * slots] new starts of a round: sorted position
+  unsigned* s_base = nullptr;        // [2 * slots] first coverage unit
+  unsigned* s_pre = nullptr;         // [2 * 26 * slots] coverage units per neighbour
+  int* s_q = nullptr;                // [2 * 25 * slots] neighbour cells to cover
+  int* s_lo = nullptr;               // [2 * 25 * slots] first item to test there
   unsigned* eval_stamp = nullptr;    // [cap]
   unsigned* chg_stamp = nullptr;     // [cap]
   int* lab = nullptr;                // [cap]
@@ -55,6 +56,7 @@ struct Tuning {
   int merge_ctas_per_sm = 4;     // CTAs per SM of the cooperative merge-rounds kernel (1, 2 or 4)
   int per_domain_launch = 0;     // 1: the plain form, one launch per domain for compression and Stage I
   int local_ctas_cap = 0;        // at most this many resident CTAs per SM per local kernel (0: all that fit)
+  int merge_form = 1;            // merge rounds: 1 = one barrier per round (coverage tested on the fly), 0 = two
 };
 
 // Events around the local-aggregation kernels of the tiles (tuning only).

@@ -566,6 +566,10 @@ struct RoundArgs {
   unsigned* bar_sub;        // [32 * (kBarGroups + 1)] barrier arrival counters (one per 128-byte line)
   unsigned* status;
   unsigned max_rounds;
+  // one-phase rounds (k_mrounds1)
+  unsigned* lcnt;            // [3] sizes of the evaluation lists (by round mod 3)
+  unsigned long long* uctr;  // [3] packed new starts << 40 | coverage units (by round mod 3)
+  long long slot_stride;     // slots per buffer of s_* (two buffers, by round parity)
 };
 
 __device__ __forceinline__ unsigned long long ld_state(const unsigned long long* p) {
@@ -766,9 +770,15 @@ __device__ __forceinline__ void mark_changed(const RoundArgs& R, long long q, un
 // Phase B: the coverage units [u, u_end) of this warp (whole warp).  Unit u of
 // start s, neighbour k, tests the items [lo + i * kCoverUnit, +kCoverUnit) of
 // cell q that follow the start in key order and are not yet covered.
-__device__ __forceinline__ void cover_units(const RoundArgs& R, unsigned u, unsigned u_end, unsigned n_new,
-                                           unsigned round, int* chg, unsigned* n_chg) {
+template <bool kMark>
+__device__ __forceinline__ void cover_units(const RoundArgs& R, long long soff, unsigned u, unsigned u_end,
+                                           unsigned n_new, unsigned round, int* chg, unsigned* n_chg) {
   const int lane = threadIdx.x & 31;
+  const unsigned* s_base = R.s_base + soff;
+  const unsigned* s_pre = R.s_pre + 26 * soff;
+  const int* s_q = R.s_q + 25 * soff;
+  const int* s_lo = R.s_lo + 25 * soff;
+  const int* s_pos = R.s_pos + soff;
   // the slot holding u: the last one whose first unit is <= u
   // warp-parallel search (s_base is non-decreasing and s_base[0] = 0): each
   // step narrows the range to one of 32 equal parts with one load per lane
@@ -776,21 +786,21 @@ __device__ __forceinline__ void cover_units(const RoundArgs& R, unsigned u, unsi
   while (len > 32) {
     const int step = (len + 31) / 32;
     const int i = lo + lane * step;
-    const unsigned v = lane * step < len ? __ldcg(&R.s_base[i]) : 0xFFFFFFFFu;
+    const unsigned v = lane * step < len ? __ldcg(&s_base[i]) : 0xFFFFFFFFu;
     const int k = 31 - __clz(__ballot_sync(0xFFFFFFFFu, v <= u));
     lo += k * step;
     len = min(step, len - k * step);
   }
   {
-    const unsigned v = lane < len ? __ldcg(&R.s_base[lo + lane]) : 0xFFFFFFFFu;
+    const unsigned v = lane < len ? __ldcg(&s_base[lo + lane]) : 0xFFFFFFFFu;
     lo += 31 - __clz(__ballot_sync(0xFFFFFFFFu, v <= u));
   }
   int s = lo;
   for (;;) {
-    const unsigned pre = lane < 26 ? __ldcg(&R.s_pre[(long long)s * 26 + lane]) : 0xFFFFFFFFu;
-    const int q_l = lane < 25 ? __ldcg(&R.s_q[(long long)s * 25 + lane]) : -1;
-    const int lo_l = lane < 25 ? __ldcg(&R.s_lo[(long long)s * 25 + lane]) : 0;
-    const int sp = __ldcg(&R.s_pos[s]);
+    const unsigned pre = lane < 26 ? __ldcg(&s_pre[(long long)s * 26 + lane]) : 0xFFFFFFFFu;
+    const int q_l = lane < 25 ? __ldcg(&s_q[(long long)s * 25 + lane]) : -1;
+    const int lo_l = lane < 25 ? __ldcg(&s_lo[(long long)s * 25 + lane]) : 0;
+    const int sp = __ldcg(&s_pos[s]);
     const float spx = R.V.sX[sp], spy = R.V.sY[sp];
     for (;;) {
       const int k = 31 - __clz(__ballot_sync(0xFFFFFFFFu, pre <= u));
@@ -820,7 +830,9 @@ __device__ __forceinline__ void cover_units(const RoundArgs& R, unsigned u, unsi
           }
         }
       }
-      if (__any_sync(0xFFFFFFFFu, any) && lane == 0) mark_changed(R, q, round, chg, n_chg);
+      if constexpr (kMark) {
+        if (__any_sync(0xFFFFFFFFu, any) && lane == 0) mark_changed(R, q, round, chg, n_chg);
+      }
       if (++u >= u_end) return;
     }
     if (++s >= (int)n_new) return;
@@ -889,12 +901,305 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
       const unsigned total = (unsigned)(ctr & kUnitMask);
       const unsigned per = (unsigned)(((long long)total + n_warps - 1) / n_warps);
       const unsigned u0 = (unsigned)(warp_g * per);
-      if (per && u0 < total) cover_units(R, u0, min(total, u0 + per), n_new, round, chg, n_chg);
+      if (per && u0 < total) cover_units<true>(R, 0, u0, min(total, u0 + per), n_new, round, chg, n_chg);
     }
     if (!grid_barrier(R.bar, R.bar_sub, nblocks, R.status)) return;
     // nothing changed: a fixed point, where every cell is decided (the
     // earliest undecided candidate always progresses); k_mcheck verifies it
     if (*((volatile unsigned*)n_chg) == 0) {
+      if (warp_g == 0 && lane == 0) R.bar[2] = round + 1;  // diagnostics: rounds used
+      return;
+    }
+  }
+  if (warp_g == 0 && lane == 0) set_status(R.status, JABBA_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------------ 4b. rounds, one phase
+// The same cell greedy with one grid barrier per round.  Coverage by the
+// decided starts is tested on the fly: an evaluation gathers every decided
+// start of the 9 x 9 block of cells around its cell (a start within alpha of
+// an item of the 5 x 5 block lies there) and tests items against them (FP32
+// filter, exact test when it straddles), so it needs no coverage marks.  The
+// cov flags become hints, only ever set for items that a decided start
+// covers: the coverage units of the starts decided in round r are marked in
+// round r + 1 by warps without an evaluation, beside the evaluations, which
+// no longer wait for them.  An evaluation that changes its cell lists, for
+// the next round, the undecided cells whose verdict may change: the 9 x 9
+// block around a new start (its coverage reaches the 5 x 5 block, whose
+// items are scanned by the cells of the 9 x 9 block), the 5 x 5 block around
+// any other change (the cell itself when it stopped early).  A start is still
+// declared only when no undecided earlier item can cover it, so the starts
+// are those of the sequential greedy; the cell with the earliest uncovered
+// item is listed again after every event that can unblock it, so the rounds
+// end only when every cell is decided (k_mcheck verifies it).
+constexpr int kOwnChunks = 16;  // 32-item chunks an evaluation tests in its own cell before it yields
+
+struct NbScratch {               // one per warp, shared memory
+  int sp[81];                    // decided starts of the 9 x 9 block: sorted position
+  float sx[81], sy[81];          // and FP32 coordinates
+  int uq[24], ulo[24], uhi[24];  // undecided cells of the 5 x 5 block: cell, first item not known covered, end
+};
+
+// Item (sorted position r, FP32 x, y) covered by a gathered start that
+// precedes it.
+__device__ __forceinline__ bool covered_by_starts(const MergeView& V, const NbScratch& W, int ns, int r, float x,
+                                                  float y) {
+  for (int i = 0; i < ns; ++i) {
+    const int s = W.sp[i];
+    if (s >= r) continue;
+    const int f = filter_c(W.sx[i], W.sy[i], x, y, V.a2lo, V.a2hi);
+    if (f == 1) return true;
+    if (f == 2 && exact_within_sorted(V, s, r)) return true;
+  }
+  return false;
+}
+
+// List the undecided cells of the (2 rad + 1)^2 block around cell (cx, cy)
+// for the next round once each (eval_stamp = round + 2); the centre only
+// when `self`.
+__device__ __forceinline__ void push_block(const RoundArgs& R, const GridGeom& g, int cx, int cy, int rad, bool self,
+                                           unsigned round, int* lnxt, unsigned* lcnt_nxt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int side = 2 * rad + 1, nk = side * side;
+  int q[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = i * 32 + lane;
+    const int dx = k % side - rad, dy = k / side - rad;
+    q[i] = -1;
+    if (k < nk && (self || dx != 0 || dy != 0)) {
+      const int xx = cx + dx, yy = cy + dy;
+      if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) q[i] = R.cell_of_id[yy * g.ncx + xx];
+    }
+  }
+  bool c[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) c[i] = q[i] >= 0 && (unsigned)ld_state(&R.state[q[i]]) == kUndecided;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (c[i]) c[i] = atomicExch(&R.eval_stamp[q[i]], round + 2) != round + 2;
+  const unsigned m0 = __ballot_sync(0xFFFFFFFFu, c[0]), m1 = __ballot_sync(0xFFFFFFFFu, c[1]),
+                 m2 = __ballot_sync(0xFFFFFFFFu, c[2]);
+  const unsigned n0 = __popc(m0), n1 = __popc(m1), tot = n0 + n1 + __popc(m2);
+  if (tot == 0) return;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(lcnt_nxt, tot);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  if (c[0]) lnxt[base + __popc(m0 & lt)] = q[0];
+  if (c[1]) lnxt[base + n0 + __popc(m1 & lt)] = q[1];
+  if (c[2]) lnxt[base + n0 + n1 + __popc(m2 & lt)] = q[2];
+}
+
+// Evaluate undecided cell j (whole warp): its first item p not covered by a
+// decided start becomes its start unless an uncovered item of an undecided
+// neighbouring cell precedes p and may lie within alpha of it.
+__device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigned round, NbScratch& W, int* lnxt,
+                           unsigned* lcnt_nxt, unsigned long long* uctr_nxt, long long soff) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  __syncwarp();  // the previous evaluation of this warp is done with W
+  const unsigned long long st = __shfl_sync(0xFFFFFFFFu, ld_state(&R.state[j]), 0);
+  if ((unsigned)st != kUndecided) return;
+  const int id = R.cell_id[j];
+  const int end = R.cell_end[j];
+  const int cx = id % g.ncx, cy = id / g.ncx;
+  // ---- gather: decided starts of the 9 x 9 block, undecided cells of the 5 x 5 block
+  int q[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = i * 32 + lane;
+    const int dx = k % 9 - 4, dy = k / 9 - 4;
+    q[i] = -1;
+    if (k < 81 && (dx != 0 || dy != 0)) {
+      const int xx = cx + dx, yy = cy + dy;
+      if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) q[i] = R.cell_of_id[yy * g.ncx + xx];
+    }
+  }
+  unsigned long long sq[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) sq[i] = q[i] >= 0 ? ld_state(&R.state[q[i]]) : 0ull;
+  int ns = 0, nu = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = i * 32 + lane;
+    const int dx = k % 9 - 4, dy = k / 9 - 4;
+    const unsigned sv = (unsigned)sq[i];
+    const bool is_s = q[i] >= 0 && sv < kNoStart;
+    const bool is_u = q[i] >= 0 && sv == kUndecided && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2;
+    const unsigned ms = __ballot_sync(0xFFFFFFFFu, is_s), mu = __ballot_sync(0xFFFFFFFFu, is_u);
+    if (is_s) {
+      const int o = ns + __popc(ms & lt);
+      W.sp[o] = (int)sv;
+      W.sx[o] = R.V.sX[sv];
+      W.sy[o] = R.V.sY[sv];
+    }
+    if (is_u) {
+      const int o = nu + __popc(mu & lt);
+      W.uq[o] = q[i];
+      W.ulo[o] = (int)(sq[i] >> 32);
+      W.uhi[o] = R.cell_end[q[i]];
+    }
+    ns += __popc(ms);
+    nu += __popc(mu);
+  }
+  __syncwarp();
+  // ---- own items: the first one not covered (hints skipped, then tested)
+  int t = (int)(st >> 32);
+  int tp = end, p = 0;
+  float px = 0.f, py = 0.f;
+  bool yielded = false;
+  for (int chunks = 0;; ++chunks) {
+    t = first_uncovered(R.cov, t, end);
+    if (t >= end) break;
+    if (chunks == kOwnChunks) {
+      yielded = true;
+      break;
+    }
+    const int u = t + lane;
+    bool unc = false, cov_now = false;
+    int r = 0;
+    float ux = 0.f, uy = 0.f;
+    if (u < end && !__ldcg(&R.cov[u])) {
+      r = R.cord[u];
+      ux = R.cX[u];
+      uy = R.cY[u];
+      if (covered_by_starts(R.V, W, ns, r, ux, uy)) cov_now = true;
+      else unc = true;
+    }
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, unc);
+    const int first = b ? __ffs(b) - 1 : 32;
+    if (cov_now) R.cov[u] = 1;  // hint: covered by a decided start
+    if (b) {
+      tp = t + first;
+      p = __shfl_sync(0xFFFFFFFFu, r, first);
+      px = __shfl_sync(0xFFFFFFFFu, ux, first);
+      py = __shfl_sync(0xFFFFFFFFu, uy, first);
+      break;
+    }
+    t += 32;
+  }
+  // ---- verdict
+  unsigned result = kUndecided;
+  if (!yielded && tp >= end) {
+    result = kNoStart;
+  } else if (!yielded) {
+    bool need = false;
+    int lo = 0, hi = 0;
+    if (lane < nu) {
+      lo = W.ulo[lane];
+      hi = W.uhi[lane];
+      need = lo < hi && R.cord[lo] < p;
+    }
+    unsigned sm = __ballot_sync(0xFFFFFFFFu, need);
+    bool blocked = false;
+    while (!blocked && sm) {
+      const int l = __ffs(sm) - 1;
+      sm &= sm - 1;
+      const int qe = __shfl_sync(0xFFFFFFFFu, hi, l);
+      int u0 = __shfl_sync(0xFFFFFFFFu, lo, l);
+      for (int ch = 0;; ++ch, u0 += 32) {
+        u0 = first_uncovered(R.cov, u0, qe);
+        if (u0 >= qe) break;
+        if (ch == kScanChunks) {
+          blocked = true;
+          break;
+        }
+        const int u = u0 + lane;
+        bool past = true, hit = false;
+        if (u < qe) {
+          const int r = R.cord[u];
+          past = r >= p;
+          if (!past && !__ldcg(&R.cov[u])) {
+            const float ux = R.cX[u], uy = R.cY[u];
+            if (filter_c(ux, uy, px, py, R.V.a2lo, R.V.a2hi) != 0 && !covered_by_starts(R.V, W, ns, r, ux, uy))
+              hit = true;
+          }
+        }
+        if (__any_sync(0xFFFFFFFFu, hit)) {
+          blocked = true;
+          break;
+        }
+        if (__any_sync(0xFFFFFFFFu, past)) break;
+      }
+    }
+    if (!blocked) result = (unsigned)p;
+  }
+  const int tnew = yielded ? t : tp;
+  const unsigned long long nsv = ((unsigned long long)(unsigned)tnew << 32) | result;
+  if (nsv == st) return;
+  if (lane == 0) atomicExch(&R.state[j], nsv);
+  __syncwarp();
+  const bool start = result < kNoStart;
+  // ---- coverage units of a new start (marked next round)
+  if (start) {
+    const unsigned cu = lane < nu ? (unsigned)((W.uhi[lane] - W.ulo[lane] + kCoverUnit - 1) / kCoverUnit) : 0u;
+    unsigned incl = cu;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(uctr_nxt, (1ull << 40) | (unsigned long long)total);
+    old = __shfl_sync(0xFFFFFFFFu, old, 0);
+    const long long slot = soff + (long long)(old >> 40);
+    const unsigned base = (unsigned)(old & kUnitMask);
+    if (lane < 25) {
+      R.s_q[slot * 25 + lane] = lane < nu ? W.uq[lane] : -1;
+      R.s_lo[slot * 25 + lane] = lane < nu ? W.ulo[lane] : 0;
+    }
+    if (lane < 26) R.s_pre[slot * 26 + lane] = base + incl - cu;
+    if (lane == 0) {
+      R.s_pos[slot] = p;
+      R.s_base[slot] = base;
+    }
+  }
+  // ---- the cells whose verdict may change
+  push_block(R, g, cx, cy, start ? 4 : 2, yielded, round, lnxt, lcnt_nxt);
+}
+
+__global__ void __launch_bounds__(256) k_mrounds1(RoundArgs R) {
+  if (R.flags[0] || R.flags[1]) return;
+  __shared__ NbScratch W[8];
+  const long long n_cells = *R.n_cells_p;
+  const GridGeom g = *R.geom;
+  const unsigned nblocks = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  NbScratch& w = W[threadIdx.x >> 5];
+  const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const size_t stride = (size_t)(n_cells > 0 ? n_cells : 1);
+  for (unsigned round = 0; round < R.max_rounds; ++round) {
+    const int cur = round % 3, nxt = (round + 1) % 3, old = (round + 2) % 3;
+    const int* lcur = R.chg_list + (size_t)(round & 1) * stride;
+    int* lnxt = R.chg_list + (size_t)((round + 1) & 1) * stride;
+    // the counters of slot `old` were last read in the previous round
+    if (warp_g == 0 && lane == 0) {
+      R.lcnt[old] = 0;
+      R.uctr[old] = 0;
+    }
+    // evaluations (warps from the bottom)
+    const long long soff_new = (long long)(round & 1) * R.slot_stride;
+    if (round == 0) {
+      for (long long j = warp_g; j < n_cells; j += n_warps)
+        eval_cell1(R, g, (int)j, round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
+    } else {
+      const unsigned n_eval = *((volatile unsigned*)&R.lcnt[cur]);
+      for (long long i = warp_g; i < (long long)n_eval; i += n_warps)
+        eval_cell1(R, g, __ldcg(&lcur[i]), round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
+      // coverage hints of the previous round's starts (warps from the top)
+      const unsigned long long ctr = *((volatile unsigned long long*)&R.uctr[cur]);
+      const unsigned n_new = (unsigned)(ctr >> 40);
+      const unsigned total = (unsigned)(ctr & kUnitMask);
+      const unsigned per = (unsigned)(((long long)total + n_warps - 1) / n_warps);
+      const unsigned u0 = (unsigned)((n_warps - 1 - warp_g) * per);
+      if (per && u0 < total)
+        cover_units<false>(R, (long long)((round + 1) & 1) * R.slot_stride, u0, min(total, u0 + per), n_new, round,
+                           nullptr, nullptr);
+    }
+    if (!grid_barrier(R.bar, R.bar_sub, nblocks, R.status)) return;
+    if (*((volatile unsigned*)&R.lcnt[nxt]) == 0) {
       if (warp_g == 0 && lane == 0) R.bar[2] = round + 1;  // diagnostics: rounds used
       return;
     }
@@ -1227,7 +1532,10 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
     // cooperative launch: every block resident, so the bounded grid barrier can complete
     static int max_per_sm = -1;
     if (max_per_sm < 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm, k_mrounds, 256, 0);
+      int a = 0, b = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mrounds, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mrounds1, 256, 0);
+      max_per_sm = a < b ? a : b;
       if (max_per_sm < 1) max_per_sm = 1;
     }
     int blocks_per_sm = ws.tune.merge_ctas_per_sm;
@@ -1243,8 +1551,12 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    R.lcnt = B.bar + 4;
+    R.uctr = (unsigned long long*)(B.bar + 8);
+    R.slot_stride = B.slots;
     mark(mk.a0, st);
-    cudaLaunchKernelEx(&cfg, k_mrounds, R);
+    if (ws.tune.merge_form == 1) cudaLaunchKernelEx(&cfg, k_mrounds1, R);
+    else cudaLaunchKernelEx(&cfg, k_mrounds, R);
     mark(mk.a1, st);
   }
   k_mcheck<<<grid, 256, 0, st>>>(B.state, B.head_off + cap, B.flags, status);

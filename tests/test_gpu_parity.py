@@ -200,3 +200,18 @@ def test_merge_group_capacity_changes(C):
         sym = C.symbolize_step(c, l, m, N)
         C.sync_status(where="symbolize")
         assert np.array_equal(sym.cpu().numpy(), r["symbol"]), mult
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_merge_forms(form):
+    """Both forms of the Stage II rounds (two grid barriers per round with
+    coverage marks; one barrier with coverage tested on the fly) give the
+    oracle's result, on a dense workload and on one long chain."""
+    C2 = ctx()
+    C2.set_tuning(dict(merge_form=form))
+    for name, ms, extra in (("multivar", 2, {}), ("noise", None, dict(domain_value=8)), ("uneven", 25, {})):
+        x, off, cfg = synth.make(name, max_series=ms)
+        cfg = dict(cfg, **extra)
+        g, *_ = run_gpu(C2, x, off, cfg, recon=False)
+        r = run_oracle(x, off, cfg, recon=False)
+        assert_parity(g, r, recon=False)
