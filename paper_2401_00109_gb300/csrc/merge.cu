@@ -954,55 +954,21 @@ __device__ __forceinline__ bool covered_by_starts(const MergeView& V, const NbSc
   return false;
 }
 
-// List the undecided cells of the (2 rad + 1)^2 block around cell (cx, cy)
-// for the next round once each (eval_stamp = round + 2); the centre only
-// when `self`.
-__device__ __forceinline__ void push_block(const RoundArgs& R, const GridGeom& g, int cx, int cy, int rad, bool self,
-                                           unsigned round, int* lnxt, unsigned* lcnt_nxt) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const int side = 2 * rad + 1, nk = side * side;
-  int q[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int k = i * 32 + lane;
-    const int dx = k % side - rad, dy = k / side - rad;
-    q[i] = -1;
-    if (k < nk && (self || dx != 0 || dy != 0)) {
-      const int xx = cx + dx, yy = cy + dy;
-      if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) q[i] = R.cell_of_id[yy * g.ncx + xx];
-    }
-  }
-  bool c[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) c[i] = q[i] >= 0 && (unsigned)ld_state(&R.state[q[i]]) == kUndecided;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    if (c[i]) c[i] = atomicExch(&R.eval_stamp[q[i]], round + 2) != round + 2;
-  const unsigned m0 = __ballot_sync(0xFFFFFFFFu, c[0]), m1 = __ballot_sync(0xFFFFFFFFu, c[1]),
-                 m2 = __ballot_sync(0xFFFFFFFFu, c[2]);
-  const unsigned n0 = __popc(m0), n1 = __popc(m1), tot = n0 + n1 + __popc(m2);
-  if (tot == 0) return;
-  unsigned base = 0;
-  if (lane == 0) base = atomicAdd(lcnt_nxt, tot);
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  if (c[0]) lnxt[base + __popc(m0 & lt)] = q[0];
-  if (c[1]) lnxt[base + n0 + __popc(m1 & lt)] = q[1];
-  if (c[2]) lnxt[base + n0 + n1 + __popc(m2 & lt)] = q[2];
-}
-
 // Evaluate undecided cell j (whole warp): its first item p not covered by a
 // decided start becomes its start unless an uncovered item of an undecided
-// neighbouring cell precedes p and may lie within alpha of it.
+// neighbouring cell precedes p and may lie within alpha of it.  Loads that do
+// not depend on each other are issued together (the evaluations of a round
+// are latency bound).
 __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigned round, NbScratch& W, int* lnxt,
                            unsigned* lcnt_nxt, unsigned long long* uctr_nxt, long long soff) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   __syncwarp();  // the previous evaluation of this warp is done with W
-  const unsigned long long st = __shfl_sync(0xFFFFFFFFu, ld_state(&R.state[j]), 0);
-  if ((unsigned)st != kUndecided) return;
+  const unsigned long long st0 = ld_state(&R.state[j]);
   const int id = R.cell_id[j];
   const int end = R.cell_end[j];
+  const unsigned long long st = __shfl_sync(0xFFFFFFFFu, st0, 0);
+  if ((unsigned)st != kUndecided) return;
   const int cx = id % g.ncx, cy = id / g.ncx;
   // ---- gather: decided starts of the 9 x 9 block, undecided cells of the 5 x 5 block
   int q[3];
@@ -1020,13 +986,15 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
 #pragma unroll
   for (int i = 0; i < 3; ++i) sq[i] = q[i] >= 0 ? ld_state(&R.state[q[i]]) : 0ull;
   int ns = 0, nu = 0;
+  bool und[3];  // undecided when gathered (a cell decided since is skipped when evaluated)
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const int k = i * 32 + lane;
     const int dx = k % 9 - 4, dy = k / 9 - 4;
     const unsigned sv = (unsigned)sq[i];
     const bool is_s = q[i] >= 0 && sv < kNoStart;
-    const bool is_u = q[i] >= 0 && sv == kUndecided && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2;
+    und[i] = q[i] >= 0 && sv == kUndecided;
+    const bool is_u = und[i] && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2;
     const unsigned ms = __ballot_sync(0xFFFFFFFFu, is_s), mu = __ballot_sync(0xFFFFFFFFu, is_u);
     if (is_s) {
       const int o = ns + __popc(ms & lt);
@@ -1044,13 +1012,14 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
     nu += __popc(mu);
   }
   __syncwarp();
-  // ---- own items: the first one not covered (hints skipped, then tested)
+  // ---- own items: the first one not covered (the first chunk from the
+  // pointer, later ones after skipping hinted runs)
   int t = (int)(st >> 32);
   int tp = end, p = 0;
   float px = 0.f, py = 0.f;
   bool yielded = false;
   for (int chunks = 0;; ++chunks) {
-    t = first_uncovered(R.cov, t, end);
+    if (chunks > 0) t = first_uncovered(R.cov, t, end);
     if (t >= end) break;
     if (chunks == kOwnChunks) {
       yielded = true;
@@ -1060,17 +1029,20 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
     bool unc = false, cov_now = false;
     int r = 0;
     float ux = 0.f, uy = 0.f;
-    if (u < end && !__ldcg(&R.cov[u])) {
+    if (u < end) {
+      const unsigned char hint = __ldcg(&R.cov[u]);
       r = R.cord[u];
       ux = R.cX[u];
       uy = R.cY[u];
-      if (covered_by_starts(R.V, W, ns, r, ux, uy)) cov_now = true;
-      else unc = true;
+      if (!hint) {
+        if (covered_by_starts(R.V, W, ns, r, ux, uy)) cov_now = true;
+        else unc = true;
+      }
     }
     const unsigned b = __ballot_sync(0xFFFFFFFFu, unc);
-    const int first = b ? __ffs(b) - 1 : 32;
     if (cov_now) R.cov[u] = 1;  // hint: covered by a decided start
     if (b) {
+      const int first = __ffs(b) - 1;
       tp = t + first;
       p = __shfl_sync(0xFFFFFFFFu, r, first);
       px = __shfl_sync(0xFFFFFFFFu, ux, first);
@@ -1099,7 +1071,7 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       const int qe = __shfl_sync(0xFFFFFFFFu, hi, l);
       int u0 = __shfl_sync(0xFFFFFFFFu, lo, l);
       for (int ch = 0;; ++ch, u0 += 32) {
-        u0 = first_uncovered(R.cov, u0, qe);
+        if (ch > 0) u0 = first_uncovered(R.cov, u0, qe);
         if (u0 >= qe) break;
         if (ch == kScanChunks) {
           blocked = true;
@@ -1108,13 +1080,13 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
         const int u = u0 + lane;
         bool past = true, hit = false;
         if (u < qe) {
+          const unsigned char hint = __ldcg(&R.cov[u]);
           const int r = R.cord[u];
+          const float ux = R.cX[u], uy = R.cY[u];
           past = r >= p;
-          if (!past && !__ldcg(&R.cov[u])) {
-            const float ux = R.cX[u], uy = R.cY[u];
-            if (filter_c(ux, uy, px, py, R.V.a2lo, R.V.a2hi) != 0 && !covered_by_starts(R.V, W, ns, r, ux, uy))
-              hit = true;
-          }
+          if (!past && !hint && filter_c(ux, uy, px, py, R.V.a2lo, R.V.a2hi) != 0 &&
+              !covered_by_starts(R.V, W, ns, r, ux, uy))
+            hit = true;
         }
         if (__any_sync(0xFFFFFFFFu, hit)) {
           blocked = true;
@@ -1129,7 +1101,6 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
   const unsigned long long nsv = ((unsigned long long)(unsigned)tnew << 32) | result;
   if (nsv == st) return;
   if (lane == 0) atomicExch(&R.state[j], nsv);
-  __syncwarp();
   const bool start = result < kNoStart;
   // ---- coverage units of a new start (marked next round)
   if (start) {
@@ -1155,8 +1126,35 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       R.s_base[slot] = base;
     }
   }
-  // ---- the cells whose verdict may change
-  push_block(R, g, cx, cy, start ? 4 : 2, yielded, round, lnxt, lcnt_nxt);
+  // ---- list, once each (eval_stamp = round + 2), the cells whose verdict
+  // may change: the cells undecided when gathered in the 9 x 9 block of a new
+  // start or the 5 x 5 block of another change, and the cell itself when it
+  // stopped early.  The gathered cell ids and states serve: a cell decided
+  // since then is skipped when evaluated.
+  bool c[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = i * 32 + lane;
+    const int dx = k % 9 - 4, dy = k / 9 - 4;
+    c[i] = und[i] && (start || (dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2));
+    if (yielded && k == 40) {  // the centre
+      q[i] = j;
+      c[i] = true;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (c[i]) c[i] = atomicExch(&R.eval_stamp[q[i]], round + 2) != round + 2;
+  const unsigned m0 = __ballot_sync(0xFFFFFFFFu, c[0]), m1 = __ballot_sync(0xFFFFFFFFu, c[1]),
+                 m2 = __ballot_sync(0xFFFFFFFFu, c[2]);
+  const unsigned n0 = __popc(m0), n1 = __popc(m1), tot = n0 + n1 + __popc(m2);
+  if (tot == 0) return;
+  unsigned lbase = 0;
+  if (lane == 0) lbase = atomicAdd(lcnt_nxt, tot);
+  lbase = __shfl_sync(0xFFFFFFFFu, lbase, 0);
+  if (c[0]) lnxt[lbase + __popc(m0 & lt)] = q[0];
+  if (c[1]) lnxt[lbase + n0 + __popc(m1 & lt)] = q[1];
+  if (c[2]) lnxt[lbase + n0 + n1 + __popc(m2 & lt)] = q[2];
 }
 
 __global__ void __launch_bounds__(256) k_mrounds1(RoundArgs R) {
@@ -1185,9 +1183,12 @@ __global__ void __launch_bounds__(256) k_mrounds1(RoundArgs R) {
       for (long long j = warp_g; j < n_cells; j += n_warps)
         eval_cell1(R, g, (int)j, round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
     } else {
+      // the first entry of this warp is read beside the list size (past the
+      // size it is a stale entry of the buffer, not used)
+      const int j0 = warp_g < (long long)stride ? __ldcg(&lcur[warp_g]) : 0;
       const unsigned n_eval = *((volatile unsigned*)&R.lcnt[cur]);
       for (long long i = warp_g; i < (long long)n_eval; i += n_warps)
-        eval_cell1(R, g, __ldcg(&lcur[i]), round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
+        eval_cell1(R, g, i == warp_g ? j0 : __ldcg(&lcur[i]), round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
       // coverage hints of the previous round's starts (warps from the top)
       const unsigned long long ctr = *((volatile unsigned long long*)&R.uctr[cur]);
       const unsigned n_new = (unsigned)(ctr >> 40);
