@@ -117,7 +117,6 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.bounds = (int*)take(16);
     B.bar = (unsigned*)take(64);
     B.bar_sub = (unsigned*)take(4 * 32 * 17);
-    B.rinv = (float*)take(16);
     B.geom = (struct GridGeom*)take(64);
     B.flags = (int*)take(16);
     B.sX = (float*)take(4 * G);

@@ -11,7 +11,6 @@ struct MergeBufs {
   int* bounds = nullptr;             // [4] ordered-int min/max of the FP32 coordinates
   unsigned* bar = nullptr;           // [16] grid barrier generation and round counters
   unsigned* bar_sub = nullptr;       // [32 * 17] grid barrier arrival counters
-  float* rinv = nullptr;             // [2] 1/sigma in FP32
   struct GridGeom* geom = nullptr;   // grid geometry (device)
   int* flags = nullptr;              // [4] [0] = sequential fallback
   float* sX = nullptr;               // [cap] FP32 coordinates in key order

@@ -6,8 +6,8 @@
 // The greedy in key order is the lexicographically first maximal set of
 // "starts" pairwise farther than alpha apart; every other item joins the
 // earliest start within alpha.  It is computed in parallel:
-//  1. FP32 centre coordinates with rigorous relative error 2^-20 (binary64
-//     values are computed only for undecided comparisons);
+//  1. FP32 centre coordinates: the binary64 centres rounded to nearest
+//     (binary64 values are recomputed only for undecided comparisons);
 //  2. the exact order: a stable radix sort of the binary64 keys (computed
 //     once per item: at 10^7 centres the keys are denser than any FP32
 //     interval), ties in compact-index order;
@@ -78,15 +78,18 @@ __device__ __noinline__ bool exact_within_sorted(const MergeView& V, int a, int 
   return exact_within_c(ea, eb, V.a2);
 }
 
-// FP32 filter: |X32 - X| <= 2^-20 |X32|, same for Y.
+// FP32 filter on the coordinates rounded to nearest from binary64
+// (|X32 - X| <= 2^-24 |X|, same for Y): the additive margin is twice the
+// coordinate error, the factors cover the FP32 arithmetic here and the
+// binary64 rounding of the definition's d^2.
 __device__ __forceinline__ int filter_c(float xa, float ya, float xb, float yb, float a2lo, float a2hi) {
   const float dx = fabsf(xb - xa), dy = fabsf(yb - ya);
-  const float ex = 0x1p-19f * (fabsf(xa) + fabsf(xb)) + 0x1p-126f;
-  const float ey = 0x1p-19f * (fabsf(ya) + fabsf(yb)) + 0x1p-126f;
+  const float ex = 0x1p-22f * (fabsf(xa) + fabsf(xb)) + 0x1p-126f;
+  const float ey = 0x1p-22f * (fabsf(ya) + fabsf(yb)) + 0x1p-126f;
   const float hx = dx + ex, hy = dy + ey;
   const float lx = fmaxf(dx - ex, 0.f), ly = fmaxf(dy - ey, 0.f);
-  const float hi = fmaf(hx, hx, hy * hy) * (1.0f + 0x1p-21f);
-  const float lo = fmaf(lx, lx, ly * ly) * (1.0f - 0x1p-21f);
+  const float hi = fmaf(hx, hx, hy * hy) * (1.0f + 0x1p-20f);
+  const float lo = fmaf(lx, lx, ly * ly) * (1.0f - 0x1p-20f);
   if (hi < a2lo) return 1;
   if (lo > a2hi) return 0;
   return 2;
@@ -118,46 +121,23 @@ __device__ __forceinline__ float of_ord(int o) {
 }
 
 __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long long cap, const long long* dom_group_off,
-                        const float* rinv, const double* sigma, double scl, unsigned long long* keys, int* vals,
-                        int* rec_of, float* X32, float* Y32, int* bounds, const int* flags) {
+                        const double* sigma, double scl, unsigned long long* keys, int* vals, int* rec_of, float* X32,
+                        float* Y32, int* bounds, const int* flags) {
   if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
-  const float rl = rinv[0], ri = rinv[1], sc = (float)scl;
   int mnx = 0x7FFFFFFF, mxx = -0x7FFFFFFF, mny = 0x7FFFFFFF, mxy = -0x7FFFFFFF;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < G; r += (long long)gridDim.x * blockDim.x) {
     const jabba_group g = groups[r];
     const long long c = dom_group_off[g.domain] + g.local_id;
-    const float cnt = (float)g.count;
-    const float clen = __fdiv_rn(__ll2float_rn(g.lensum), cnt);
-    const float x = (sc * clen) * rl;
-    // FP32 image of the 192-bit increment sum (truncated to 24 bits), 2^-64 units
-    I192 v;
-    v.w0 = g.inc[0];
-    v.w1 = g.inc[1];
-    v.w2 = g.inc[2];
-    const bool neg = (long long)v.w2 < 0;
-    if (neg) {
-      v.w0 = ~v.w0; v.w1 = ~v.w1; v.w2 = ~v.w2;
-      add192(v, 1, 0, 0);
-    }
-    int top;
-    if (v.w2) top = 128 + 63 - __clzll((long long)v.w2);
-    else if (v.w1) top = 64 + 63 - __clzll((long long)v.w1);
-    else if (v.w0) top = 63 - __clzll((long long)v.w0);
-    else top = -1;
-    float incf = 0.f;
-    if (top >= 0) {
-      const int lo = top > 23 ? top - 23 : 0;
-      const u64 sig = shr192_lo(v.w0, v.w1, v.w2, lo);
-      incf = ldexpf((float)(unsigned)sig, lo - 64);
-    }
-    if (neg) incf = -incf;
-    const float y = __fdiv_rn(incf, cnt) * ri;
+    // the order needs the binary64 key itself (2e7 centres are denser than
+    // any FP32 key interval), so every item computes its binary64 centre
+    // (4 divisions, once); the FP32 coordinates are that centre rounded to
+    // nearest (relative error 2^-24)
+    const ExactCentre e = exact_centre(g, sigma[0], sigma[1], scl);
+    const float x = __double2float_rn(e.X), y = __double2float_rn(e.Y);
     X32[c] = x;
     Y32[c] = y;
-    // the order needs the binary64 key itself: 2e7 centres are denser than any
-    // FP32 key interval, so every item computes it (4 divisions, once)
-    keys[c] = (unsigned long long)__double_as_longlong(exact_key(exact_centre(g, sigma[0], sigma[1], scl)));
+    keys[c] = (unsigned long long)__double_as_longlong(exact_key(e));
     vals[c] = (int)c;
     rec_of[c] = (int)r;
     mnx = min(mnx, ord_of(x));
@@ -570,6 +550,7 @@ struct RoundArgs {
   unsigned* lcnt;            // [3] sizes of the evaluation lists (by round mod 3)
   unsigned long long* uctr;  // [3] packed new starts << 40 | coverage units (by round mod 3)
   long long slot_stride;     // slots per buffer of s_* (two buffers, by round parity)
+  long long item_cap;        // entries of the per-item arrays (cord, cX, cY, cov)
 };
 
 __device__ __forceinline__ unsigned long long ld_state(const unsigned long long* p) {
@@ -932,12 +913,13 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
 // are those of the sequential greedy; the cell with the earliest uncovered
 // item is listed again after every event that can unblock it, so the rounds
 // end only when every cell is decided (k_mcheck verifies it).
-constexpr int kOwnChunks = 16;  // 32-item chunks an evaluation tests in its own cell before it yields
+constexpr int kOwnSteps = 4;  // 128-item steps an evaluation tests in its own cell before it yields
 
 struct NbScratch {               // one per warp, shared memory
   int sp[81];                    // decided starts of the 9 x 9 block: sorted position
   float sx[81], sy[81];          // and FP32 coordinates
   int uq[24], ulo[24], uhi[24];  // undecided cells of the 5 x 5 block: cell, first item not known covered, end
+  int ucd[24];                   // and the sorted position of that first item
 };
 
 // Item (sorted position r, FP32 x, y) covered by a gathered start that
@@ -1004,52 +986,70 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
     }
     if (is_u) {
       const int o = nu + __popc(mu & lt);
+      const int lo = (int)(sq[i] >> 32);
       W.uq[o] = q[i];
-      W.ulo[o] = (int)(sq[i] >> 32);
+      W.ulo[o] = lo;
       W.uhi[o] = R.cell_end[q[i]];
+      W.ucd[o] = lo < R.item_cap ? R.cord[lo] : 0x7FFFFFFF;  // used only when lo < end
     }
     ns += __popc(ms);
     nu += __popc(mu);
   }
   __syncwarp();
-  // ---- own items: the first one not covered (the first chunk from the
-  // pointer, later ones after skipping hinted runs)
+  // ---- own items: the first one not covered, 128 items per step (four per
+  // lane, loads in flight together); the first step from the pointer, later
+  // ones after skipping hinted runs
   int t = (int)(st >> 32);
   int tp = end, p = 0;
   float px = 0.f, py = 0.f;
   bool yielded = false;
-  for (int chunks = 0;; ++chunks) {
-    if (chunks > 0) t = first_uncovered(R.cov, t, end);
+  for (int steps = 0;; ++steps) {
+    if (steps > 0) t = first_uncovered(R.cov, t, end);
     if (t >= end) break;
-    if (chunks == kOwnChunks) {
+    if (steps == kOwnSteps) {
       yielded = true;
       break;
     }
-    const int u = t + lane;
-    bool unc = false, cov_now = false;
-    int r = 0;
-    float ux = 0.f, uy = 0.f;
-    if (u < end) {
-      const unsigned char hint = __ldcg(&R.cov[u]);
-      r = R.cord[u];
-      ux = R.cX[u];
-      uy = R.cY[u];
-      if (!hint) {
-        if (covered_by_starts(R.V, W, ns, r, ux, uy)) cov_now = true;
-        else unc = true;
+    unsigned char h[4];
+    int r[4];
+    float ux[4], uy[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int u = t + i * 32 + lane;
+      h[i] = 1;
+      r[i] = 0;
+      ux[i] = uy[i] = 0.f;
+      if (u < end) {
+        h[i] = __ldcg(&R.cov[u]);
+        r[i] = R.cord[u];
+        ux[i] = R.cX[u];
+        uy[i] = R.cY[u];
       }
     }
-    const unsigned b = __ballot_sync(0xFFFFFFFFu, unc);
-    if (cov_now) R.cov[u] = 1;  // hint: covered by a decided start
-    if (b) {
-      const int first = __ffs(b) - 1;
-      tp = t + first;
-      p = __shfl_sync(0xFFFFFFFFu, r, first);
-      px = __shfl_sync(0xFFFFFFFFu, ux, first);
-      py = __shfl_sync(0xFFFFFFFFu, uy, first);
+    int found = -1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (found >= 0) continue;
+      const int u = t + i * 32 + lane;
+      bool unc = false;
+      if (!h[i]) {  // also false past the end
+        if (covered_by_starts(R.V, W, ns, r[i], ux[i], uy[i])) R.cov[u] = 1;  // hint: covered by a decided start
+        else unc = true;
+      }
+      const unsigned b = __ballot_sync(0xFFFFFFFFu, unc);
+      if (b) {
+        const int first = __ffs(b) - 1;
+        found = i * 32 + first;
+        p = __shfl_sync(0xFFFFFFFFu, r[i], first);
+        px = __shfl_sync(0xFFFFFFFFu, ux[i], first);
+        py = __shfl_sync(0xFFFFFFFFu, uy[i], first);
+      }
+    }
+    if (found >= 0) {
+      tp = t + found;
       break;
     }
-    t += 32;
+    t += 128;
   }
   // ---- verdict
   unsigned result = kUndecided;
@@ -1061,16 +1061,58 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
     if (lane < nu) {
       lo = W.ulo[lane];
       hi = W.uhi[lane];
-      need = lo < hi && R.cord[lo] < p;
+      need = lo < hi && W.ucd[lane] < p;
     }
     unsigned sm = __ballot_sync(0xFFFFFFFFu, need);
     bool blocked = false;
-    while (!blocked && sm) {
-      const int l = __ffs(sm) - 1;
-      sm &= sm - 1;
+    // the first chunks of up to four neighbours, their loads in flight together
+    unsigned pend = 0;  // neighbours (lane bits) still to scan from their second chunk
+    {
+      int nl[4], lo4[4], hi4[4], r4[4];
+      unsigned char h4[4];
+      float x4[4], y4[4];
+      bool v4[4];
+      unsigned m = sm;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        nl[i] = m ? __ffs(m) - 1 : -1;
+        if (m) m &= m - 1;
+      }
+      const unsigned rest = m;  // beyond four: scanned one by one below
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        lo4[i] = __shfl_sync(0xFFFFFFFFu, lo, nl[i] >= 0 ? nl[i] : 0);
+        hi4[i] = __shfl_sync(0xFFFFFFFFu, hi, nl[i] >= 0 ? nl[i] : 0);
+        const int u = lo4[i] + lane;
+        v4[i] = nl[i] >= 0 && u < hi4[i];
+        h4[i] = 1;
+        r4[i] = 0x7FFFFFFF;
+        x4[i] = y4[i] = 0.f;
+        if (v4[i]) {
+          h4[i] = __ldcg(&R.cov[u]);
+          r4[i] = R.cord[u];
+          x4[i] = R.cX[u];
+          y4[i] = R.cY[u];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (nl[i] < 0 || blocked) continue;
+        const bool past = !v4[i] || r4[i] >= p;  // past the end of the cell counts as past
+        const bool hit = !past && !h4[i] && filter_c(x4[i], y4[i], px, py, R.V.a2lo, R.V.a2hi) != 0 &&
+                         !covered_by_starts(R.V, W, ns, r4[i], x4[i], y4[i]);
+        if (__any_sync(0xFFFFFFFFu, hit)) blocked = true;
+        else if (!__any_sync(0xFFFFFFFFu, past)) pend |= 1u << nl[i];
+      }
+      if (!blocked) pend |= rest;
+    }
+    while (!blocked && pend) {
+      const int l = __ffs(pend) - 1;
+      const bool first_done = __popc(sm & ((1u << l) - 1u)) < 4;  // among the four scanned above
+      pend &= pend - 1;
       const int qe = __shfl_sync(0xFFFFFFFFu, hi, l);
-      int u0 = __shfl_sync(0xFFFFFFFFu, lo, l);
-      for (int ch = 0;; ++ch, u0 += 32) {
+      int u0 = __shfl_sync(0xFFFFFFFFu, lo, l) + (first_done ? 32 : 0);
+      for (int ch = first_done ? 1 : 0;; ++ch, u0 += 32) {
         if (ch > 0) u0 = first_uncovered(R.cov, u0, qe);
         if (u0 >= qe) break;
         if (ch == kScanChunks) {
@@ -1440,10 +1482,6 @@ __global__ void k_minit(int* bounds, unsigned* bar, unsigned* bar_sub, int* flag
   bar[2] = 0;
 }
 
-__global__ void k_mrinv(const double* sigma, float* rinv) {
-  rinv[0] = __double2float_rn(__ddiv_rn(1.0, sigma[0]));
-  rinv[1] = __double2float_rn(__ddiv_rn(1.0, sigma[1]));
-}
 
 static float rdown(double v) {
   float f = (float)v;
@@ -1465,8 +1503,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   const unsigned grid = (unsigned)(ws.num_sms * 8);
   MergeBufs& B = ws.mb;
   k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.bar_sub, B.flags, status, n_groups, cap);
-  k_mrinv<<<1, 1, 0, st>>>(sigma, B.rinv);
-  k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, B.rinv, sigma, scl, ws.m_k0, ws.m_v0, ws.m_rec,
+  k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, sigma, scl, ws.m_k0, ws.m_v0, ws.m_rec,
                                 ws.m_X32, ws.m_Y32, B.bounds, B.flags);
   unsigned long long* skey;
   int* sidx;
@@ -1555,6 +1592,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
     R.lcnt = B.bar + 4;
     R.uctr = (unsigned long long*)(B.bar + 8);
     R.slot_stride = B.slots;
+    R.item_cap = cap > 0 ? cap : 1;
     mark(mk.a0, st);
     if (ws.tune.merge_form == 1) cudaLaunchKernelEx(&cfg, k_mrounds1, R);
     else cudaLaunchKernelEx(&cfg, k_mrounds, R);
