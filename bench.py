@@ -387,15 +387,16 @@ def run_ours(args, ws, rank, local):
     #   local aggregation (tile kernels + routing + group offsets): 12 B per
     #     piece read (len, inc) + 4 B per piece written (label) + 48 B per group
     #     record + 12 B per domain (group count and offset);
-    #   k_mrounds: 13 B per local group (its FP32 centre, key-order position and
-    #     coverage flag, each read once).
+    #   merge rounds (k_mrounds1, or k_mrounds in the two-barrier form): 13 B
+    #     per local group (its FP32 centre, key-order position and coverage
+    #     flag, each read once).
     # The dominant one (largest time) is reported as `roofline`.
     peak, peak_kind = peaks()
     Dn = pl.D
     cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N),
             ("local aggregation (k_local_tile x5, k_local_classify, k_local_warp, scan)", loc_ms,
              16.0 * N + 48.0 * G + 12.0 * Dn),
-            ("k_mrounds", rnd_ms, 13.0 * G)]
+            ("k_mrounds1" if ctx.tuning()["merge_form"] == 1 else "k_mrounds", rnd_ms, 13.0 * G)]
     by_kernel = []
     for name, ms_list, alg in cand:
         t = float(np.mean(ms_list))

@@ -598,18 +598,77 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
       lab[a] = -1;
     }
     tile_sync<W>();
-    // 5. greedy in key order on the first warp: each start's window pass also
-    // finds the first piece left free behind the start (the next start)
-    if (t < 32) {
+    // 5. greedy in key order.  One warp (W = 1): each start's window pass
+    // also finds the first piece left free behind the start (the next
+    // start).  W warps: every window step covers 32 W pieces, the warps agree
+    // on the stop with one barrier per step and on the next start through a
+    // shared minimum (three slots, so that a slot is reset only after every
+    // thread has read it).
+    if constexpr (W == 1) {
+      if (t < 32) {
+        int G = 0, a = 0;
+        while (a < n) {
+          const float xs = sX[a], ys = sY[a];
+          const float Tk = key_stop(__uint_as_float(key32_of(xs, ys)), P.alpha_up);
+          if (lane == 0) lab[a] = (short)G;
+          int next = n;
+          int b0 = a + 1;
+          for (; b0 < n; b0 += 32) {
+            const int b = b0 + lane;
+            bool stop = true, fr = false;
+            if (b < n) {
+              const float xb = sX[b], yb = sY[b];
+              stop = __uint_as_float(key32_of(xb, yb)) * (1.0f - kKeyRel) > Tk;
+              if (lab[b] < 0) {
+                bool join = false;
+                if (!stop) {
+                  int w = filter_within(xs, ys, xb, yb, P.a2lo, P.a2hi);
+                  if (w == 2) {
+                    const int ps = idx[a], pb = idx[b];
+                    w = exact_within(P, plen[ps], pinc[ps], plen[pb], pinc[pb], a2) ? 1 : 0;
+                  }
+                  join = w != 0;
+                }
+                if (join) lab[b] = (short)G;
+                else fr = true;
+              }
+            }
+            const unsigned mf = __ballot_sync(0xFFFFFFFFu, fr);
+            if (mf && next == n) next = b0 + __ffs(mf) - 1;
+            if (__any_sync(0xFFFFFFFFu, stop)) break;
+          }
+          // nothing left free up to the window's last chunk: search on
+          if (next == n) {
+            for (b0 += 32; b0 < n; b0 += 32) {
+              const int b = b0 + lane;
+              const unsigned mf = __ballot_sync(0xFFFFFFFFu, b < n && lab[b] < 0);
+              if (mf) {
+                next = b0 + __ffs(mf) - 1;
+                break;
+              }
+            }
+          }
+          __syncwarp();
+          ++G;
+          a = next;
+        }
+        if (lane == 0) misc[13] = G;
+      }
+    } else {
+      int* s_next = misc + 20;  // [3] first free piece behind the start (by start index mod 3)
+      if (t < 3) s_next[t] = n;
+      __syncthreads();
+      const int warp = t >> 5;
       int G = 0, a = 0;
       while (a < n) {
+        const int sl = G % 3;
         const float xs = sX[a], ys = sY[a];
         const float Tk = key_stop(__uint_as_float(key32_of(xs, ys)), P.alpha_up);
-        if (lane == 0) lab[a] = (short)G;
-        int next = n;
+        if (t == 0) lab[a] = (short)G;
+        int next = n;  // this warp's first free piece
         int b0 = a + 1;
-        for (; b0 < n; b0 += 32) {
-          const int b = b0 + lane;
+        for (; b0 < n; b0 += T) {
+          const int b = b0 + t;
           bool stop = true, fr = false;
           if (b < n) {
             const float xb = sX[b], yb = sY[b];
@@ -629,25 +688,27 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
             }
           }
           const unsigned mf = __ballot_sync(0xFFFFFFFFu, fr);
-          if (mf && next == n) next = b0 + __ffs(mf) - 1;
-          if (__any_sync(0xFFFFFFFFu, stop)) break;
+          if (mf && next == n) next = b0 + warp * 32 + __ffs(mf) - 1;
+          if (__syncthreads_or(stop)) break;
         }
-        // nothing left free up to the window's last chunk: search on
-        if (next == n) {
-          for (b0 += 32; b0 < n; b0 += 32) {
-            const int b = b0 + lane;
+        if (lane == 0 && next < n) atomicMin(&s_next[sl], next);
+        if (t == 0) s_next[(G + 1) % 3] = n;
+        __syncthreads();
+        int nx = s_next[sl];
+        if (nx == n) {
+          // nothing left free up to the window's last step: search on
+          for (b0 += T; b0 < n; b0 += T) {
+            const int b = b0 + t;
             const unsigned mf = __ballot_sync(0xFFFFFFFFu, b < n && lab[b] < 0);
-            if (mf) {
-              next = b0 + __ffs(mf) - 1;
-              break;
-            }
+            if (mf && lane == 0) atomicMin(&s_next[sl], b0 + warp * 32 + __ffs(mf) - 1);
+            if (__syncthreads_or(mf != 0)) break;
           }
+          nx = s_next[sl];
         }
-        __syncwarp();
         ++G;
-        a = next;
+        a = nx;
       }
-      if (lane == 0) misc[13] = G;
+      if (t == 0) misc[13] = G;
     }
     tile_sync<W>();
     const int G = misc[13];
