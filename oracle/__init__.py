@@ -14,6 +14,8 @@ Functions follow the paper's steps (section in brackets):
   greedy             Sec. 3.2 greedy aggregation with the Sec. 5 pruning rule
   local_aggregate    Sec. 5 Stage I, one block per domain
   merge              Sec. 5 Stage II, merge of the local groups
+  block_digitize     Sec. 5 two-stage digitization in the block form (global
+                     sort, contiguous sorted blocks, merge of starting points)
   symbolize          Sec. 5 label propagation
   reconstruct        Sec. 3.3 inverse digitization, quantization, inverse compression
   mse                Sec. 3.3 reconstruction error
@@ -71,6 +73,8 @@ def lib():
                 "jo_centre": (None, [C.c_int64, C.c_int64, U64, F64, F64]),
                 "jo_merge": (C.c_int64, [I64, I64, U64, C.c_int64, C.c_double, C.c_double, C.c_double,
                                          C.c_double, I32, F64, F64, I64]),
+                "jo_merge_points": (C.c_int64, [F64, F64, I64, I64, U64, C.c_int64, C.c_double, I32, F64, F64,
+                                                I64]),
                 "jo_symbolize": (None, [I32, I64, I64, C.c_int64, I32, I32]),
                 "jo_reassign": (None, [I32, F64, C.c_int64, C.c_double, C.c_double, C.c_double, F64, F64,
                                        C.c_int64, I32]),
@@ -221,6 +225,61 @@ def merge(grp_count, grp_lensum, grp_incacc, sigma_len, sigma_inc, alpha, scl):
     k = lib().jo_merge(_p(cnt, I64), _p(ls, I64), _p(ia, U64), G, sigma_len, sigma_inc, alpha, scl,
                        _p(l2g, I32), _p(dl, F64), _p(di, F64), _p(dc, I64))
     return l2g[:G].copy(), dl[:k].copy(), di[:k].copy(), dc[:k].copy()
+
+
+def merge_points(X, Y, grp_count, grp_lensum, grp_incacc, alpha):
+    """Stage II over given points of the local groups (their starting points
+    in the block form).  Returns (l2g int32[G], dict_len, dict_inc, dict_count)."""
+    X = _c(X, np.float64)
+    Y = _c(Y, np.float64)
+    cnt = _c(grp_count, np.int64)
+    ls = _c(grp_lensum, np.int64)
+    ia = _c(grp_incacc, np.uint64).reshape(-1, 4)
+    G = len(cnt)
+    l2g = np.empty(max(G, 1), np.int32)
+    dl = np.empty(max(G, 1), np.float64)
+    di = np.empty(max(G, 1), np.float64)
+    dc = np.empty(max(G, 1), np.int64)
+    k = lib().jo_merge_points(_p(X, F64), _p(Y, F64), _p(cnt, I64), _p(ls, I64), _p(ia, U64), G, alpha,
+                              _p(l2g, I32), _p(dl, F64), _p(di, F64), _p(dc, I64))
+    return l2g[:G].copy(), dl[:k].copy(), di[:k].copy(), dc[:k].copy()
+
+
+def block_digitize(piece_len, piece_inc, sigma_len, sigma_inc, alpha, scl, n_blocks):
+    """Two-stage digitization as Sec. 5 states it (the block form): one
+    global sort of the normalised pieces by the key rho = X*X + Y*Y (binary64,
+    equal keys in compact-piece order); the sorted order cut into n_blocks
+    contiguous blocks of ceil(N / n_blocks) pieces (the last ones shorter or
+    empty); Stage I aggregates each block by the greedy in its sorted order;
+    Stage II merges the local groups' starting points (the first piece of
+    each group in key order) by the same greedy; symbols by label
+    propagation, returned in compact-piece order.  Returns a dict."""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    N = len(ln)
+    X, Y = normalised(ln, inc, sigma_len, sigma_inc, scl)
+    key = X * X + Y * Y
+    order = np.lexsort((np.arange(N), key)).astype(np.int64)   # compact index at sorted position
+    B = -(-N // n_blocks) if N else 0
+    blk_off = np.minimum(np.arange(n_blocks + 1, dtype=np.int64) * B, N)
+    lab, goff, cnt, ls, ia = local_aggregate(ln[order], inc[order], blk_off, sigma_len, sigma_inc, alpha, scl)
+    G = len(cnt)
+    start = np.empty(G, np.int64)       # sorted position of each local group's start
+    for b in range(n_blocks):
+        a0, a1 = int(blk_off[b]), int(blk_off[b + 1])
+        seen = set()
+        for i in range(a0, a1):
+            g = int(goff[b]) + int(lab[i])
+            if g not in seen:
+                seen.add(g)
+                start[g] = i
+    l2g, dl, di, dc = merge_points(X[order[start]], Y[order[start]], cnt, ls, ia, alpha)
+    sym_sorted = l2g[goff[np.searchsorted(blk_off, np.arange(N), side="right") - 1] + lab]
+    symbol = np.empty(N, np.int32)
+    symbol[order] = sym_sorted
+    return dict(order=order, blk_piece_off=blk_off, block_label=lab, blk_group_off=goff, grp_count=cnt,
+                grp_lensum=ls, grp_incacc=ia, start=start, l2g=l2g, dict_len=dl, dict_inc=di, dict_count=dc,
+                symbol=symbol)
 
 
 def symbolize(local_label, dom_piece_off, dom_group_off, l2g):

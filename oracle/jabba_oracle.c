@@ -489,6 +489,38 @@ int64_t jo_merge(const int64_t* grp_count, const int64_t* grp_lensum, const uint
   return k;
 }
 
+/* Stage II over given points (Sec. 5 as the paper states it: the local
+ * starting points are merged): the same pruned greedy over the points
+ * (X[g], Y[g]) of the G local groups, in index order for equal keys;
+ * l2g[g] = global group (creation order); the dictionary entry of a global
+ * group is the exact mean of the pieces of its local groups (their exact
+ * sums), as in jo_merge.  Returns k. */
+int64_t jo_merge_points(const double* X, const double* Y, const int64_t* grp_count, const int64_t* grp_lensum,
+                        const uint64_t* grp_incacc, int64_t G, double alpha, int32_t* l2g, double* dict_len,
+                        double* dict_inc, int64_t* dict_count) {
+  int64_t* lab = (int64_t*)malloc(sizeof(int64_t) * (size_t)(G ? G : 1));
+  int64_t k = jo_greedy(X, Y, G, alpha, 1, lab, NULL);
+  int64_t* cnt = (int64_t*)calloc((size_t)(k ? k : 1), sizeof(int64_t));
+  int64_t* ls = (int64_t*)calloc((size_t)(k ? k : 1), sizeof(int64_t));
+  jo_fx* ia = (jo_fx*)calloc((size_t)(k ? k : 1), sizeof(jo_fx));
+  for (int64_t g = 0; g < G; ++g) {
+    int64_t c = lab[g];
+    l2g[g] = (int32_t)c;
+    cnt[c] += grp_count[g];
+    ls[c] += grp_lensum[g];
+    fx_add_fx(&ia[c], (const jo_fx*)(grp_incacc + 4 * g));
+  }
+  for (int64_t c = 0; c < k; ++c) {
+    jo_centre(cnt[c], ls[c], ia[c].w, &dict_len[c], &dict_inc[c]);
+    dict_count[c] = cnt[c];
+  }
+  free(lab);
+  free(cnt);
+  free(ls);
+  free(ia);
+  return k;
+}
+
 /* Label propagation (Sec. 5): l_i = l~_g for a piece in local group g. */
 void jo_symbolize(const int32_t* local_label, const int64_t* dom_piece_off, const int64_t* dom_group_off,
                   int64_t n_domains, const int32_t* l2g, int32_t* symbol) {

@@ -291,3 +291,95 @@ def test_reassign_matches_vectorized_argmin_and_beats_two_stage(seed):
     assert s_re <= s_two
     ref = math.fsum(d2[rows, lab])
     assert abs(s_re - ref) <= len(ln) * 2.0**-64 + 2 * math.ulp(ref)
+
+
+# ---------------------------------------------------------------- block form (Sec. 5 as stated)
+def _block_inputs(name="small", max_series=6):
+    x, off, cfg = synth.make(name, max_series=max_series)
+    b, e, _ = oracle.domains(off, cfg["domain_mode"], cfg["domain_value"])
+    ln, inc, po = oracle.compress(x, b, e, cfg["tol"], 4)
+    sl, si = oracle.sigma(ln, inc)
+    return ln, inc, po, sl, si, cfg
+
+
+def _exact_means(ln, inc, symbol, k):
+    """Dictionary by the definition: per symbol the binary64 mean length and
+    the exactly summed, once-rounded increment divided by the count."""
+    dl = np.empty(k)
+    di = np.empty(k)
+    dc = np.zeros(k, np.int64)
+    for c in range(k):
+        m = symbol == c
+        n = int(m.sum())
+        dc[c] = n
+        dl[c] = float(int(ln[m].astype(np.int64).sum())) / n
+        di[c] = float(sum(Fraction(v) for v in inc[m])) / n
+    return dl, di, dc
+
+
+@pytest.mark.parametrize("which", ["one block", "one piece per block"])
+def test_block_form_reduces_to_the_plain_greedy(which):
+    """With one block, Stage I is the greedy over all pieces and its starts
+    are pairwise farther than alpha, so Stage II keeps every one; with one
+    piece per block, Stage II is the greedy over all pieces.  Either way the
+    block form is the plain greedy of Sec. 3.2 (unpruned here), with the
+    exact means as the dictionary."""
+    ln, inc, po, sl, si, cfg = _block_inputs()
+    N = len(ln)
+    M = 1 if which == "one block" else N
+    r = oracle.block_digitize(ln, inc, sl, si, cfg["alpha"], cfg["scl"], M)
+    X, Y = oracle.normalised(ln, inc, sl, si, cfg["scl"])
+    lab, _ = oracle.greedy(X, Y, cfg["alpha"], prune=False)
+    assert np.array_equal(r["symbol"], lab.astype(np.int32))
+    k = int(lab.max()) + 1
+    dl, di, dc = _exact_means(ln, inc, lab, k)
+    assert np.array_equal(r["dict_count"], dc)
+    assert np.array_equal(r["dict_len"], dl) and np.array_equal(r["dict_inc"], di)
+
+
+@pytest.mark.parametrize("M", [3, 17, 200])
+def test_block_form_invariants(M):
+    """Blocks are contiguous ranges of the global key order; in each block
+    the members lie within alpha of their local start and the local starts
+    are pairwise farther apart; the global starts are pairwise farther than
+    alpha and every local start lies within alpha of its global start; the
+    dictionary holds the exact means of the pieces of each symbol."""
+    ln, inc, po, sl, si, cfg = _block_inputs("uneven", 3)
+    a = cfg["alpha"]
+    a2 = a * a
+    r = oracle.block_digitize(ln, inc, sl, si, a, cfg["scl"], M)
+    X, Y = oracle.normalised(ln, inc, sl, si, cfg["scl"])
+    key = X * X + Y * Y
+    o = r["order"]
+    N = len(ln)
+    assert np.array_equal(np.sort(o), np.arange(N))
+    ks = key[o]
+    assert np.all(ks[1:] >= ks[:-1])
+    tie = ks[1:] == ks[:-1]
+    assert np.all(o[1:][tie] > o[:-1][tie])
+    bo, go, lab, st = r["blk_piece_off"], r["blk_group_off"], r["block_label"], r["start"]
+    Xs, Ys = X[o], Y[o]
+    d2 = lambda i, j: (Xs[j] - Xs[i]) * (Xs[j] - Xs[i]) + (Ys[j] - Ys[i]) * (Ys[j] - Ys[i])
+    for b in range(M):
+        for i in range(bo[b], bo[b + 1]):
+            g = go[b] + lab[i]
+            assert bo[b] <= st[g] <= i and d2(st[g], i) <= a2
+        starts = [st[g] for g in range(go[b], go[b + 1])]
+        for u in range(len(starts)):
+            for v in range(u + 1, len(starts)):
+                assert d2(starts[u], starts[v]) > a2
+    l2g = r["l2g"]
+    k = len(r["dict_len"])
+    gstart = {}
+    for g in np.argsort(ks[st], kind="stable"):
+        gstart.setdefault(int(l2g[g]), st[g])
+    assert sorted(gstart) == list(range(k))
+    gs = [gstart[c] for c in range(k)]
+    for g in range(len(st)):
+        assert d2(gstart[int(l2g[g])], st[g]) <= a2
+    for u in range(k):
+        for v in range(u + 1, k):
+            assert d2(gs[u], gs[v]) > a2
+    dl, di, dc = _exact_means(ln, inc, r["symbol"], k)
+    assert np.array_equal(r["dict_count"], dc)
+    assert np.array_equal(r["dict_len"], dl) and np.array_equal(r["dict_inc"], di)
