@@ -445,6 +445,29 @@ def run_ours(args, ws, rank, local):
         reassign = dict(ms=ra_ms, sse_label_propagation=s_two, sse_reassigned=s_re,
                         sse_ratio=s_two / s_re if s_re > 0 else None, pieces_changed=changed)
 
+    # ---- the block form of Sec. 5 (one global sort of the pieces, contiguous
+    # sorted blocks, Stage II over the starting points) on the same batch, as
+    # many blocks as domains: its dictionary and SSE beside the per-domain
+    # form's (one eager pass, own context; timed end to end with its syncs)
+    block = None
+    if not args.no_block_form and rank == 0:
+        res = pl.as_result()
+        cbx = jb.Context(local)
+        cbx.set_tuning(dict(ctx.tuning(), per_domain_launch=0))
+        torch.cuda.synchronize()
+        t0b = time.perf_counter()
+        bo = cbx.symbolize_blocks(pl.x, pl.series_off, p, series_off_host=off_np)
+        torch.cuda.synchronize()
+        t_blk = time.perf_counter() - t0b
+        s_blk = float(cbx.sse(bo, p, bo["symbol"]).item())
+        s_dom = float(ctx.sse(res, p, res["symbol"]).item())
+        cbx.sync_status(where="block form")
+        block = dict(seconds_eager=t_blk, n_blocks=bo["n_blocks"], local_groups=bo["n_groups_host"],
+                     dictionary=bo["k_host"], sse=s_blk, per_domain=dict(local_groups=G, dictionary=k, sse=s_dom),
+                     sse_ratio_block_to_domain=s_blk / s_dom if s_dom > 0 else None)
+        del bo, cbx
+        torch.cuda.empty_cache()
+
     if rank == 0:
         single = dict(value=value, unit="Gpts/s", ms_per_step=ms_all, tuning=tuning,
                       form="one batch at a time: CUDA-graph replay of the whole step")
@@ -468,6 +491,8 @@ def run_ours(args, ws, rank, local):
                     diagnostics=diag, input_gen_s=t_gen)
         if sweep is not None:
             line["partition_sweep"] = sweep
+        if block is not None:
+            line["block_form"] = block
         if reassign is not None:
             line["reassignment"] = reassign
         print(json.dumps(line), flush=True)
@@ -602,6 +627,7 @@ def main():
     ap.add_argument("--plain-series", type=int, default=300, help="series in the plain-form sample")
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-reassign", action="store_true", help="skip the full-reassignment comparison")
+    ap.add_argument("--no-block-form", action="store_true", help="skip the block-form (Sec. 5 as stated) comparison")
     ap.add_argument("--partition-sweep", action="store_true",
                     help="add the Gaussian-noise partition sweep (Sec. 7.3) to the JSON line")
     ap.add_argument("--no-e2e", action="store_true")

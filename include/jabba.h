@@ -173,6 +173,51 @@ jabba_status jabba_merge_global(jabba_ctx* ctx, const jabba_group* groups, const
                                 const jabba_params* p, int32_t* l2g, double* dict_len, double* dict_inc,
                                 int64_t* dict_count, int64_t dict_capacity, int64_t* k, jabba_stream stream);
 
+/* Stage II over given points (the block form below merges the local groups'
+ * starting points, as Sec. 5 states Stage II): as jabba_merge_global, but
+ * group record r is taken as the binary64 point (item_X[r], item_Y[r])
+ * (indexed like `groups`) instead of its centre; the dictionary entries are
+ * still the exact means of the member pieces. */
+jabba_status jabba_merge_global_points(jabba_ctx* ctx, const jabba_group* groups, const double* item_X,
+                                       const double* item_Y, const int64_t* n_groups, int64_t group_capacity,
+                                       const int64_t* dom_group_off, const double* sigma, const jabba_params* p,
+                                       int32_t* l2g, double* dict_len, double* dict_inc, int64_t* dict_count,
+                                       int64_t dict_capacity, int64_t* k, jabba_stream stream);
+
+/* ---------------------------------------------------------------- 4b. block form of Sec. 5
+ * The two-stage digitization as Sec. 5 states it, for comparison with the
+ * per-domain form above: (1) jabba_block_order sorts ALL pieces once by
+ * rho = X*X + Y*Y (binary64, Eq. 4 coordinates; equal keys in compact-piece
+ * order) and cuts the sorted order into n_blocks contiguous blocks of
+ * ceil(N / n_blocks) pieces (the last ones shorter or empty); it writes sigma
+ * (as jabba_digitize_local), order[i] = compact index of the piece at sorted
+ * position i, the pieces in sorted order (blk_len, blk_inc [N]) and the
+ * blocks as domains: blk_slot_off [n_blocks+1], blk_piece_cnt [n_blocks].
+ * (2) jabba_digitize_local on those arrays is Stage I (each block aggregated
+ * in its sorted order).  (3) jabba_block_items writes, for every group record
+ * r, the normalised point of the group's starting piece (its first piece in
+ * key order) into item_X/item_Y [group_capacity].  (4)
+ * jabba_merge_global_points merges those points (Stage II).  (5)
+ * jabba_symbolize with the block arrays (dom_piece_off = blk_slot_off) gives
+ * the symbols in sorted order; jabba_block_scatter(order, ...) puts them in
+ * compact-piece order.  Scratch for n_pieces items (about 36 B each) is
+ * allocated on the first call that needs more (not during graph capture:
+ * JABBA_ERR_STATE); jabba_block_items before any jabba_block_order ->
+ * JABBA_ERR_STATE.  n_pieces (host) = the compact piece count. */
+jabba_status jabba_block_order(jabba_ctx* ctx, const int32_t* piece_len, const double* piece_inc,
+                               const int64_t* dom_slot_off, const int32_t* dom_piece_cnt, const int64_t* dom_piece_off,
+                               int64_t n_domains, int64_t n_pieces, const void* piece_stats, const jabba_params* p,
+                               int64_t n_blocks, double* sigma, int32_t* order, int32_t* blk_len, double* blk_inc,
+                               int64_t* blk_slot_off, int32_t* blk_piece_cnt, jabba_stream stream);
+jabba_status jabba_block_items(jabba_ctx* ctx, const int32_t* local_label, const int64_t* blk_slot_off,
+                               const int32_t* blk_piece_cnt, const int64_t* blk_group_off, int64_t n_blocks,
+                               const int32_t* blk_len, const double* blk_inc, const jabba_group* groups,
+                               const int64_t* n_groups, int64_t group_capacity, const double* sigma,
+                               const jabba_params* p, double* item_X, double* item_Y, jabba_stream stream);
+/* dst[order[i]] = src[i] for i < n. */
+jabba_status jabba_block_scatter(jabba_ctx* ctx, const int32_t* order, const int32_t* src, int64_t n, int32_t* dst,
+                                 jabba_stream stream);
+
 /* ---------------------------------------------------------------- 5. symbolize
  * Sec. 5 label propagation: symbol[dom_piece_off[d] + j] =
  * l2g[dom_group_off[d] + local_label[dom_slot_off[d] + j]], j < dom_piece_cnt[d].
@@ -263,7 +308,7 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
  * kernels.  Every configuration computes the same results (bit for bit); only
  * the speed differs.  Domains of up to 512 pieces are aggregated by one warp
  * each; larger domains by the number of warps chosen here.
- * Defaults: {2, 1, 4, 4, 4, 0, 1, 0, 1}. */
+ * Defaults: {2, 1, 4, 4, 4, 0, 1, 0, 1, 8}. */
 typedef struct {
   int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
@@ -281,6 +326,7 @@ typedef struct {
   int32_t merge_form;           /* merge rounds: 1 = one grid barrier per round, coverage by the decided
                                    starts tested on the fly (default); 0 = two barriers per round, coverage
                                    marked between them                                                       */
+  int32_t merge_warps;          /* warps per CTA of the one-barrier rounds kernel: 8 (default) or 4           */
 } jabba_tuning;
 
 /* Autotuning mode.  While enabled (enable = 1), each call of jabba_compress,
@@ -290,7 +336,8 @@ typedef struct {
  * `stream` (the outputs are those of the call, as without tuning).  Candidates:
  * compression {1, 2, 3} CTAs per SM x {packed, in order}; local aggregation
  * {1, 4} warps per domain of 513..1024 pieces, {1, 2, 4, 8} of 1025..2048 and
- * {4, 8} of 2049..4096; merge {1, 2, 4} CTAs per SM.  Tuning calls must not be captured in a CUDA graph
+ * {4, 8} of 2049..4096; merge {1, 2, 4} CTAs per SM (x {8, 4} warps per CTA in the
+ * one-barrier form).  Tuning calls must not be captured in a CUDA graph
  * (JABBA_ERR_STATE).  enable = 0 ends the mode; the choice stays in effect. */
 jabba_status jabba_autotune(jabba_ctx* ctx, int enable);
 /* Current configuration of the context. */

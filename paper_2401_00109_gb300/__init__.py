@@ -64,11 +64,12 @@ class Params:
 class _Tuning(C.Structure):
     _fields_ = [("compress_ctas_per_sm", C.c_int32), ("compress_pack", C.c_int32), ("local_mid_warps", C.c_int32),
                 ("local_big_warps", C.c_int32), ("merge_ctas_per_sm", C.c_int32), ("per_domain_launch", C.c_int32),
-                ("local_k_warps", C.c_int32), ("local_ctas_cap", C.c_int32), ("merge_form", C.c_int32)]
+                ("local_k_warps", C.c_int32), ("local_ctas_cap", C.c_int32), ("merge_form", C.c_int32),
+                ("merge_warps", C.c_int32)]
 
 
 TUNING_FIELDS = ("compress_ctas_per_sm", "compress_pack", "local_mid_warps", "local_big_warps", "merge_ctas_per_sm",
-                 "per_domain_launch", "local_k_warps", "local_ctas_cap", "merge_form")
+                 "per_domain_launch", "local_k_warps", "local_ctas_cap", "merge_form", "merge_warps")
 
 JABBA_GROUP_BYTES = 48
 PIECE_STATS_BYTES = 256
@@ -105,6 +106,13 @@ def load():
                                                    V, V]),
                 "jabba_merge_global": (C.c_int, [V, V, V, I64, V, V, C.POINTER(_Params), V, V, V, V, I64, V, V]),
                 "jabba_symbolize": (C.c_int, [V, V, V, V, V, V, I64, V, V, V]),
+                "jabba_merge_global_points": (C.c_int, [V, V, V, V, V, I64, V, V, C.POINTER(_Params), V, V, V, V,
+                                                        I64, V, V]),
+                "jabba_block_order": (C.c_int, [V, V, V, V, V, V, I64, I64, V, C.POINTER(_Params), I64, V, V, V, V,
+                                                V, V, V]),
+                "jabba_block_items": (C.c_int, [V, V, V, V, V, I64, V, V, V, V, I64, V, C.POINTER(_Params), V, V,
+                                                V]),
+                "jabba_block_scatter": (C.c_int, [V, V, V, I64, V, V]),
                 "jabba_reconstruct": (C.c_int, [V, V, I64, V, I64, V, V, V, V, V, C.POINTER(_Params), V, V, V]),
                 "jabba_reconstruct_backward": (C.c_int, [V, V, I64, V, I64, V, V, V, V, V, I64, V, V]),
                 "jabba_mse": (C.c_int, [V, V, V, I64, V, V]),
@@ -246,7 +254,10 @@ class Context:
         o["group_capacity"] = group_capacity
         return o
 
-    def merge_global(self, l: dict, p: Params, dict_capacity: int | None = None, stream=None):
+    def merge_global(self, l: dict, p: Params, dict_capacity: int | None = None, stream=None, items=None):
+        """Stage II.  items = (item_X, item_Y): binary64 points of the group
+        records to merge (the block form's starting points); None merges the
+        records' centres."""
         torch = _torch()
         dev = l["groups"].device
         cap = l["group_capacity"]
@@ -259,10 +270,17 @@ class Context:
             dict_count=torch.empty(max(dict_capacity, 1), dtype=torch.int64, device=dev),
             k=torch.zeros(1, dtype=torch.int64, device=dev),
         )
-        _check(self.lib.jabba_merge_global(
-            self.h, _ptr(l["groups"]), _ptr(l["n_groups"]), cap, _ptr(l["dom_group_off"]), _ptr(l["sigma"]),
-            C.byref(p.c()), _ptr(o["l2g"]), _ptr(o["dict_len"]), _ptr(o["dict_inc"]), _ptr(o["dict_count"]),
-            dict_capacity, _ptr(o["k"]), self._stream(stream)), "jabba_merge_global")
+        if items is None:
+            _check(self.lib.jabba_merge_global(
+                self.h, _ptr(l["groups"]), _ptr(l["n_groups"]), cap, _ptr(l["dom_group_off"]), _ptr(l["sigma"]),
+                C.byref(p.c()), _ptr(o["l2g"]), _ptr(o["dict_len"]), _ptr(o["dict_inc"]), _ptr(o["dict_count"]),
+                dict_capacity, _ptr(o["k"]), self._stream(stream)), "jabba_merge_global")
+        else:
+            _check(self.lib.jabba_merge_global_points(
+                self.h, _ptr(l["groups"]), _ptr(items[0]), _ptr(items[1]), _ptr(l["n_groups"]), cap,
+                _ptr(l["dom_group_off"]), _ptr(l["sigma"]), C.byref(p.c()), _ptr(o["l2g"]), _ptr(o["dict_len"]),
+                _ptr(o["dict_inc"]), _ptr(o["dict_count"]), dict_capacity, _ptr(o["k"]), self._stream(stream)),
+                "jabba_merge_global_points")
         return o
 
     def symbolize_step(self, c: dict, l: dict, m: dict, n_pieces: int, stream=None):
@@ -291,6 +309,56 @@ class Context:
         out.update(m)
         out.update(symbol=sym, n_pieces=N, n_groups_host=G, k_host=k, dict_len=m["dict_len"][:k],
                    dict_inc=m["dict_inc"][:k], dict_count=m["dict_count"][:k])
+        return out
+
+    def symbolize_blocks(self, x, series_off, p: Params, n_blocks: int | None = None, series_off_host=None,
+                         stream=None):
+        """The two-stage digitization in the block form of Sec. 5: one global
+        sort of the pieces by rho, n_blocks contiguous sorted blocks (default:
+        as many as the collection has domains) aggregated by Stage I, and
+        Stage II over the local groups' starting points.  Returns the
+        compression outputs, the dictionary and the symbols in compact-piece
+        order (plus the block arrays)."""
+        torch = _torch()
+        c = self.compress(x, series_off, p, series_off_host, stream)
+        self.sync_status(stream, "jabba_compress")
+        N = int(c["dom_piece_off"][-1].item())
+        M = int(n_blocks) if n_blocks else max(1, c["n_domains"])
+        dev = x.device
+        b = dict(
+            sigma=torch.empty(2, dtype=torch.float64, device=dev),
+            order=torch.empty(max(N, 1), dtype=torch.int32, device=dev),
+            piece_len=torch.empty(max(N, 1), dtype=torch.int32, device=dev),
+            piece_inc=torch.empty(max(N, 1), dtype=torch.float64, device=dev),
+            dom_slot_off=torch.empty(M + 1, dtype=torch.int64, device=dev),
+            dom_piece_cnt=torch.empty(M, dtype=torch.int32, device=dev),
+        )
+        _check(self.lib.jabba_block_order(
+            self.h, _ptr(c["piece_len"]), _ptr(c["piece_inc"]), _ptr(c["dom_slot_off"]), _ptr(c["dom_piece_cnt"]),
+            _ptr(c["dom_piece_off"]), c["n_domains"], N, _ptr(c["piece_stats"]), C.byref(p.c()), M,
+            _ptr(b["sigma"]), _ptr(b["order"]), _ptr(b["piece_len"]), _ptr(b["piece_inc"]), _ptr(b["dom_slot_off"]),
+            _ptr(b["dom_piece_cnt"]), self._stream(stream)), "jabba_block_order")
+        b.update(dom_piece_off=b["dom_slot_off"], n_domains=M, n_slots=max(N, 1), piece_stats=c["piece_stats"])
+        l = self.digitize_local(b, p, stream=stream)
+        cap = l["group_capacity"]
+        iX = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+        iY = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+        _check(self.lib.jabba_block_items(
+            self.h, _ptr(l["local_label"]), _ptr(b["dom_slot_off"]), _ptr(b["dom_piece_cnt"]), _ptr(l["dom_group_off"]),
+            M, _ptr(b["piece_len"]), _ptr(b["piece_inc"]), _ptr(l["groups"]), _ptr(l["n_groups"]), cap,
+            _ptr(l["sigma"]), C.byref(p.c()), _ptr(iX), _ptr(iY), self._stream(stream)), "jabba_block_items")
+        m = self.merge_global(l, p, stream=stream, items=(iX, iY))
+        self.sync_status(stream, "jabba_merge_global_points")
+        k = int(m["k"].item())
+        sym_b = self.symbolize_step(b, l, m, N, stream)
+        sym = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+        _check(self.lib.jabba_block_scatter(self.h, _ptr(b["order"]), _ptr(sym_b), N, _ptr(sym),
+                                            self._stream(stream)), "jabba_block_scatter")
+        self.sync_status(stream, "jabba_block_scatter")
+        out = dict(c)
+        out.update(blocks=b, local=l, n_blocks=M, l2g=m["l2g"], symbol=sym[:N], n_pieces=N, k_host=k,
+                   n_groups_host=int(l["n_groups"].item()), sigma=l["sigma"], dict_len=m["dict_len"][:k],
+                   dict_inc=m["dict_inc"][:k], dict_count=m["dict_count"][:k], k=m["k"])
         return out
 
     def reconstruct(self, x, series_off, out: dict, p: Params, dict_inc=None, stream=None):
@@ -646,10 +714,12 @@ def tune_inflight(pipelines, base: dict, steps: int = 4):
     step, an InFlight runner captured with it)."""
     torch = _torch()
     best = None
+    m_opts = [(1, 8), (2, 8), (1, 4), (2, 4)] if base.get("merge_form", 1) == 1 else [(1, 8), (2, 8)]
     for c_sm in (1, 2):
         for cap in (2, 3, 4):
-            for m_sm in (1, 2):
-                cfg = dict(base, compress_ctas_per_sm=c_sm, local_ctas_cap=cap, merge_ctas_per_sm=m_sm)
+            for m_sm, m_w in m_opts:
+                cfg = dict(base, compress_ctas_per_sm=c_sm, local_ctas_cap=cap, merge_ctas_per_sm=m_sm,
+                           merge_warps=m_w)
                 for pl in pipelines:
                     pl.ctx.set_tuning(cfg)
                 fl = InFlight(pipelines)

@@ -26,6 +26,9 @@ struct jabba_ctx {
   void* rapool = nullptr;      // scratch of the full reassignment and the SSE (allocated on first use)
   long long cap_ra = -1;
   RaScratch ra;
+  void* bfpool = nullptr;      // scratch of the block form (allocated on first use)
+  long long cap_bf = -1;
+  BlockScratch bf;
   bool tuning = false;         // autotuning mode (jabba_autotune)
 };
 
@@ -226,6 +229,7 @@ bool tuning_ok(const jabba_tuning* t) {
   if (t->per_domain_launch != 0 && t->per_domain_launch != 1) return false;
   if (t->local_ctas_cap < 0 || t->local_ctas_cap > 16) return false;
   if (t->merge_form != 0 && t->merge_form != 1) return false;
+  if (t->merge_warps != 4 && t->merge_warps != 8) return false;
   return true;
 }
 
@@ -291,6 +295,40 @@ jabba_status ensure_ra(jabba_ctx* c, long long entries, cudaStream_t st) {
   return JABBA_OK;
 }
 
+jabba_status ensure_bf(jabba_ctx* c, long long n, cudaStream_t st) {
+  if (n <= c->cap_bf) return JABBA_OK;
+  if (st && capturing(st)) return JABBA_ERR_STATE;
+  if (cudaDeviceSynchronize() != cudaSuccess) return JABBA_ERR_CUDA;
+  if (c->bfpool) cudaFree(c->bfpool);
+  c->bfpool = nullptr;
+  c->cap_bf = -1;
+  const long long e = n > 0 ? n : 1;
+  size_t sz[10] = {8 * (size_t)e, 8 * (size_t)e, 4 * (size_t)e, 4 * (size_t)e, 4 * (size_t)e, 8 * (size_t)e,
+                   4 * (size_t)bf_hist_words(e), 64, 64, 4 * (size_t)e};
+  size_t at[10], off = 0;
+  for (int i = 0; i < 10; ++i) {
+    at[i] = off;
+    off += align_up(sz[i]);
+  }
+  if (cudaMalloc(&c->bfpool, off) != cudaSuccess) return JABBA_ERR_CUDA;
+  unsigned char* b = (unsigned char*)c->bfpool;
+  // the sort's look-back status words must start without a valid tag
+  if (cudaMemset(b + at[6], 0, sz[6]) != cudaSuccess) return JABBA_ERR_CUDA;
+  BlockScratch& S = c->bf;
+  S.k0 = (unsigned long long*)(b + at[0]);
+  S.k1 = (unsigned long long*)(b + at[1]);
+  S.v0 = (int*)(b + at[2]);
+  S.v1 = (int*)(b + at[3]);
+  S.clen = (int*)(b + at[4]);
+  S.cinc = (double*)(b + at[5]);
+  S.hist = (unsigned*)(b + at[6]);
+  S.n_dev = (long long*)(b + at[7]);
+  S.flags = (int*)(b + at[8]);
+  S.start = (int*)(b + at[9]);
+  c->cap_bf = n;
+  return JABBA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -342,6 +380,7 @@ void jabba_destroy(jabba_ctx* c) {
   if (c->pool) cudaFree(c->pool);
   if (c->rpool) cudaFree(c->rpool);
   if (c->rapool) cudaFree(c->rapool);
+  if (c->bfpool) cudaFree(c->bfpool);
   if (c->status) cudaFree(c->status);
   delete c;
 }
@@ -512,10 +551,13 @@ jabba_status jabba_digitize_local(jabba_ctx* c, const int32_t* piece_len, const 
   return cuda_ok(cudaGetLastError());
 }
 
-jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const int64_t* n_groups,
-                                int64_t group_capacity, const int64_t* dom_group_off, const double* sigma,
-                                const jabba_params* p, int32_t* l2g, double* dict_len, double* dict_inc,
-                                int64_t* dict_count, int64_t dict_capacity, int64_t* k, jabba_stream stream) {
+}  // extern "C"
+
+namespace {
+jabba_status merge_impl(jabba_ctx* c, const jabba_group* groups, const double* item_X, const double* item_Y,
+                        const int64_t* n_groups, int64_t group_capacity, const int64_t* dom_group_off,
+                        const double* sigma, const jabba_params* p, int32_t* l2g, double* dict_len, double* dict_inc,
+                        int64_t* dict_count, int64_t dict_capacity, int64_t* k, jabba_stream stream) {
   if (!c || !params_ok(p) || group_capacity < 0 || dict_capacity < 0) return JABBA_ERR_INVALID_ARG;
   if (!n_groups || !dom_group_off || !sigma || !k) return JABBA_ERR_INVALID_ARG;
   if (group_capacity > 0 && (!groups || !l2g)) return JABBA_ERR_INVALID_ARG;
@@ -531,29 +573,36 @@ jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const i
       mk.a0 = prof_event(c, 5, 0);
       mk.a1 = prof_event(c, 5, 1);
     }
-    launch_merge(groups, (const long long*)n_groups, group_capacity, (const long long*)dom_group_off, sigma,
-                 p->alpha, p->scl, l2g, dict_len, dict_inc, (long long*)dict_count, dict_capacity, (long long*)k,
-                 c->ws, c->status, st, mk);
+    launch_merge(groups, item_X, item_Y, (const long long*)n_groups, group_capacity,
+                 (const long long*)dom_group_off, sigma, p->alpha, p->scl, l2g, dict_len, dict_inc,
+                 (long long*)dict_count, dict_capacity, (long long*)k, c->ws, c->status, st, mk);
   };
   if (c->tuning) {
     if (capturing(st)) return JABBA_ERR_STATE;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return JABBA_ERR_CUDA;
+    // CTAs per SM {1, 2, 4} x (one-barrier form) warps per CTA {8, 4}
     const int cand[3] = {1, 2, 4};
-    int best = c->ws.tune.merge_ctas_per_sm;
+    const int nw = c->ws.tune.merge_form == 1 ? 2 : 1;
+    int best = c->ws.tune.merge_ctas_per_sm, best_w = c->ws.tune.merge_warps;
     float best_ms = 3.0e38f;
     for (int r = 0; r < 3; ++r) {
-      c->ws.tune.merge_ctas_per_sm = cand[r];
-      cudaEventRecord(e0, st);
-      run();
-      cudaEventRecord(e1, st);
-      const float ms = elapsed_ms(e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = cand[r];
+      for (int w = 0; w < nw; ++w) {
+        c->ws.tune.merge_ctas_per_sm = cand[r];
+        c->ws.tune.merge_warps = w ? 4 : 8;
+        cudaEventRecord(e0, st);
+        run();
+        cudaEventRecord(e1, st);
+        const float ms = elapsed_ms(e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = cand[r];
+          best_w = c->ws.tune.merge_warps;
+        }
       }
     }
     c->ws.tune.merge_ctas_per_sm = best;
+    c->ws.tune.merge_warps = best_w;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return cuda_ok(cudaGetLastError());
@@ -561,6 +610,84 @@ jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const i
   mark(prof_event(c, 3, 0), st);
   run();
   mark(prof_event(c, 3, 1), st);
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+jabba_status jabba_merge_global(jabba_ctx* c, const jabba_group* groups, const int64_t* n_groups,
+                                int64_t group_capacity, const int64_t* dom_group_off, const double* sigma,
+                                const jabba_params* p, int32_t* l2g, double* dict_len, double* dict_inc,
+                                int64_t* dict_count, int64_t dict_capacity, int64_t* k, jabba_stream stream) {
+  return merge_impl(c, groups, nullptr, nullptr, n_groups, group_capacity, dom_group_off, sigma, p, l2g, dict_len,
+                    dict_inc, dict_count, dict_capacity, k, stream);
+}
+
+jabba_status jabba_merge_global_points(jabba_ctx* c, const jabba_group* groups, const double* item_X,
+                                       const double* item_Y, const int64_t* n_groups, int64_t group_capacity,
+                                       const int64_t* dom_group_off, const double* sigma, const jabba_params* p,
+                                       int32_t* l2g, double* dict_len, double* dict_inc, int64_t* dict_count,
+                                       int64_t dict_capacity, int64_t* k, jabba_stream stream) {
+  if (group_capacity > 0 && (!item_X || !item_Y)) return JABBA_ERR_INVALID_ARG;
+  return merge_impl(c, groups, item_X, item_Y, n_groups, group_capacity, dom_group_off, sigma, p, l2g, dict_len,
+                    dict_inc, dict_count, dict_capacity, k, stream);
+}
+
+jabba_status jabba_block_order(jabba_ctx* c, const int32_t* piece_len, const double* piece_inc,
+                               const int64_t* dom_slot_off, const int32_t* dom_piece_cnt, const int64_t* dom_piece_off,
+                               int64_t n_domains, int64_t n_pieces, const void* piece_stats, const jabba_params* p,
+                               int64_t n_blocks, double* sigma, int32_t* order, int32_t* blk_len, double* blk_inc,
+                               int64_t* blk_slot_off, int32_t* blk_piece_cnt, jabba_stream stream) {
+  if (!c || !params_ok(p) || n_domains < 0 || n_pieces < 0 || n_blocks < 1) return JABBA_ERR_INVALID_ARG;
+  if (n_pieces >= 0x7FFFFFFFll) return JABBA_ERR_RANGE;
+  if (!piece_stats || !sigma || !dom_piece_off || !blk_slot_off || !blk_piece_cnt) return JABBA_ERR_INVALID_ARG;
+  if (n_domains > 0 && (!piece_len || !piece_inc || !dom_slot_off || !dom_piece_cnt)) return JABBA_ERR_INVALID_ARG;
+  if (n_pieces > 0 && (!order || !blk_len || !blk_inc)) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the blocks are the domains of the next jabba_digitize_local: size its
+  // per-domain scratch and the arena for blocks above the tile size
+  const long long B = n_pieces > 0 ? (n_pieces + n_blocks - 1) / n_blocks : 1;
+  jabba_status r = ensure(c, c->ws.cap_series, n_blocks, c->ws.cap_slots > n_pieces ? c->ws.cap_slots : n_pieces,
+                          c->ws.cap_groups, c->ws.cap_big > B ? c->ws.cap_big : B, st);
+  if (r != JABBA_OK) return r;
+  r = ensure_bf(c, n_pieces, st);
+  if (r != JABBA_OK) return r;
+  launch_sigma((const long long*)piece_stats, sigma, st);
+  launch_block_order(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt,
+                     (const long long*)dom_piece_off, n_domains, n_pieces, n_blocks, sigma, p->scl, c->bf, order,
+                     blk_len, blk_inc, (long long*)blk_slot_off, blk_piece_cnt, c->ws.num_sms, c->status, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_block_items(jabba_ctx* c, const int32_t* local_label, const int64_t* blk_slot_off,
+                               const int32_t* blk_piece_cnt, const int64_t* blk_group_off, int64_t n_blocks,
+                               const int32_t* blk_len, const double* blk_inc, const jabba_group* groups,
+                               const int64_t* n_groups, int64_t group_capacity, const double* sigma,
+                               const jabba_params* p, double* item_X, double* item_Y, jabba_stream stream) {
+  if (!c || !params_ok(p) || n_blocks < 0 || group_capacity < 0) return JABBA_ERR_INVALID_ARG;
+  if (!n_groups || !sigma || !blk_group_off) return JABBA_ERR_INVALID_ARG;
+  if (n_blocks > 0 && (!local_label || !blk_slot_off || !blk_piece_cnt || !blk_len || !blk_inc))
+    return JABBA_ERR_INVALID_ARG;
+  if (group_capacity > 0 && (!groups || !item_X || !item_Y)) return JABBA_ERR_INVALID_ARG;
+  if (c->cap_bf < 0) return JABBA_ERR_STATE;  // jabba_block_order first
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // every local group holds a piece, so at most cap_bf groups have a start
+  const long long gcap = group_capacity < c->cap_bf ? group_capacity : (c->cap_bf > 0 ? c->cap_bf : 1);
+  launch_block_items(local_label, (const long long*)blk_slot_off, blk_piece_cnt, (const long long*)blk_group_off,
+                     n_blocks, blk_len, blk_inc, groups, (const long long*)n_groups, gcap, sigma, p->scl, c->bf.start,
+                     c->cap_bf, item_X, item_Y, c->ws.num_sms, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+jabba_status jabba_block_scatter(jabba_ctx* c, const int32_t* order, const int32_t* src, int64_t n, int32_t* dst,
+                                 jabba_stream stream) {
+  if (!c || n < 0 || (n > 0 && (!order || !src || !dst))) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  launch_block_scatter(order, src, n, dst, c->ws.num_sms, (cudaStream_t)stream);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -709,6 +836,7 @@ jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
   out->local_k_warps = t.local_k_warps;
   out->local_ctas_cap = t.local_ctas_cap;
   out->merge_form = t.merge_form;
+  out->merge_warps = t.merge_warps;
   return JABBA_OK;
 }
 
@@ -724,6 +852,7 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.local_k_warps = in->local_k_warps;
   t.local_ctas_cap = in->local_ctas_cap;
   t.merge_form = in->merge_form;
+  t.merge_warps = in->merge_warps;
   return JABBA_OK;
 }
 

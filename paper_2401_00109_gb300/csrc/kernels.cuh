@@ -56,6 +56,7 @@ struct Tuning {
   int per_domain_launch = 0;     // 1: the plain form, one launch per domain for compression and Stage I
   int local_ctas_cap = 0;        // at most this many resident CTAs per SM per local kernel (0: all that fit)
   int merge_form = 1;            // merge rounds: 1 = one barrier per round (coverage tested on the fly), 0 = two
+  int merge_warps = 8;           // warps per CTA of the one-barrier rounds kernel (4 or 8)
 };
 
 // Events around the local-aggregation kernels of the tiles (tuning only).
@@ -183,11 +184,40 @@ void launch_sse(const int* piece_len, const double* piece_inc, const long long* 
                 const double* dict_len, const double* dict_inc, const int* symbol, double scl, double* out,
                 RaScratch& R, Scratch& ws, cudaStream_t st);
 
-void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
-                  const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
-                  double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,
-                  Scratch& ws, unsigned* status, cudaStream_t st,
+// item_X / item_Y (nullable): binary64 points of the group records to merge
+// (the block form's starting points); null merges the records' centres.
+void launch_merge(const jabba_group* groups, const double* item_X, const double* item_Y, const long long* n_groups,
+                  long long group_capacity, const long long* dom_group_off, const double* sigma, double alpha,
+                  double scl, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,
+                  long long dict_capacity, long long* k, Scratch& ws, unsigned* status, cudaStream_t st,
                   const Marks& mk);
+
+// Block form of Sec. 5 (global key sort, contiguous sorted blocks, merge of
+// starting points): scratch for N pieces.
+struct BlockScratch {
+  unsigned long long* k0 = nullptr;  // [N] keys, sort ping-pong
+  unsigned long long* k1 = nullptr;
+  int* v0 = nullptr;                 // [N] compact indices, sort ping-pong
+  int* v1 = nullptr;
+  int* clen = nullptr;               // [N] compact copies of the pieces
+  double* cinc = nullptr;
+  unsigned* hist = nullptr;          // radix sort scratch for N items
+  long long* n_dev = nullptr;        // [1] N on the device
+  int* flags = nullptr;              // [4] zero (the sort's skip flags)
+  int* start = nullptr;              // [N] first piece of every local group
+};
+long long bf_hist_words(long long n);
+void launch_block_order(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
+                        const int* dom_piece_cnt, const long long* dom_piece_off, long long n_domains, long long n,
+                        long long n_blocks, const double* sigma, double scl, BlockScratch& S, int* order, int* blen,
+                        double* binc, long long* blk_off, int* blk_cnt, int num_sms, unsigned* status,
+                        cudaStream_t st);
+void launch_block_items(const int* local_label, const long long* blk_off, const int* blk_cnt,
+                        const long long* blk_group_off, long long n_blocks, const int* blen, const double* binc,
+                        const jabba_group* groups, const long long* n_groups, long long group_capacity,
+                        const double* sigma, double scl, int* start, long long n_items, double* item_X,
+                        double* item_Y, int num_sms, cudaStream_t st);
+void launch_block_scatter(const int* order, const int* src, long long n, int* dst, int num_sms, cudaStream_t st);
 
 void launch_symbolize(const int* local_label, const long long* dom_slot_off, const int* dom_piece_cnt,
                       const long long* dom_piece_off, const long long* dom_group_off, long long n_domains,

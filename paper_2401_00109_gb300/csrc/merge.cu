@@ -66,15 +66,28 @@ struct MergeView {
   const float* sX;      // FP32 coordinates at sorted position a
   const float* sY;
   const double* sigma;  // binary64 sigma_len, sigma_inc
+  const double* iX;     // item points by record (null: the records' centres)
+  const double* iY;
   double scl, a2;
   float a2lo, a2hi;
 };
 
+// Binary64 point of record r: its centre, or the point given for it.
+__device__ __forceinline__ ExactCentre item_point(const jabba_group* groups, const double* iX, const double* iY,
+                                                  long long r, const double* sigma, double scl) {
+  if (iX) {
+    ExactCentre e;
+    e.X = iX[r];
+    e.Y = iY[r];
+    return e;
+  }
+  return exact_centre(groups[r], sigma[0], sigma[1], scl);
+}
+
 // 1 = within alpha, 0 = not, decided exactly when the FP32 interval straddles.
 __device__ __noinline__ bool exact_within_sorted(const MergeView& V, int a, int b) {
-  const double sl = V.sigma[0], si = V.sigma[1];
-  const ExactCentre ea = exact_centre(V.groups[V.rec[V.sidx[a]]], sl, si, V.scl);
-  const ExactCentre eb = exact_centre(V.groups[V.rec[V.sidx[b]]], sl, si, V.scl);
+  const ExactCentre ea = item_point(V.groups, V.iX, V.iY, V.rec[V.sidx[a]], V.sigma, V.scl);
+  const ExactCentre eb = item_point(V.groups, V.iX, V.iY, V.rec[V.sidx[b]], V.sigma, V.scl);
   return exact_within_c(ea, eb, V.a2);
 }
 
@@ -120,9 +133,10 @@ __device__ __forceinline__ float of_ord(int o) {
   return o >= 0 ? __int_as_float(o) : __int_as_float((int)(0x80000000u - (unsigned)o));
 }
 
-__global__ void k_mprep(const jabba_group* groups, const long long* n_p, long long cap, const long long* dom_group_off,
-                        const double* sigma, double scl, unsigned long long* keys, int* vals, int* rec_of, float* X32,
-                        float* Y32, int* bounds, const int* flags) {
+__global__ void k_mprep(const jabba_group* groups, const double* iX, const double* iY, const long long* n_p,
+                        long long cap, const long long* dom_group_off, const double* sigma, double scl,
+                        unsigned long long* keys, int* vals, int* rec_of, float* X32, float* Y32, int* bounds,
+                        const int* flags) {
   if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
   int mnx = 0x7FFFFFFF, mxx = -0x7FFFFFFF, mny = 0x7FFFFFFF, mxy = -0x7FFFFFFF;
@@ -133,7 +147,7 @@ __global__ void k_mprep(const jabba_group* groups, const long long* n_p, long lo
     // any FP32 key interval), so every item computes its binary64 centre
     // (4 divisions, once); the FP32 coordinates are that centre rounded to
     // nearest (relative error 2^-24)
-    const ExactCentre e = exact_centre(g, sigma[0], sigma[1], scl);
+    const ExactCentre e = item_point(groups, iX, iY, r, sigma, scl);
     const float x = __double2float_rn(e.X), y = __double2float_rn(e.Y);
     X32[c] = x;
     Y32[c] = y;
@@ -373,8 +387,8 @@ long long rs_hist_words(long long cap) {
 // Stable sort of (keys, vals) by the low `bits` bits of the keys; the result
 // ends in the buffers returned through kres/vres.
 static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, const long long* n_p,
-                       long long cap, int bits, Scratch& ws, unsigned* status_word, unsigned long long** kres,
-                       int** vres, const int* flags, cudaStream_t st) {
+                       long long cap, int bits, unsigned* hist_words, int num_sms, unsigned* status_word,
+                       unsigned long long** kres, int** vres, const int* flags, cudaStream_t st) {
   const long long n_tiles = (cap + kRsTile - 1) / kRsTile;
   static bool attr = false;
   if (!attr) {
@@ -385,11 +399,11 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
   // it: the layout does not depend on cap, so the epoch persists across sorts
   // of any size and no status word left by an earlier sort carries a live tag.
   RsScratch R;
-  R.ghist = ws.m_hist;
+  R.ghist = hist_words;
   R.gbase = R.ghist + kRsPasses * 256;
   R.tile_ctr = R.gbase + kRsPasses * 256;
   R.epoch = R.tile_ctr + 16;
-  R.status = (unsigned long long*)(ws.m_hist + 2 * kRsPasses * 256 + 64);
+  R.status = (unsigned long long*)(hist_words + 2 * kRsPasses * 256 + 64);
   const int passes = (bits + 7) / 8;
   unsigned long long* kin = k0;
   unsigned long long* kout = k1;
@@ -397,7 +411,7 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
   int* vout = v1;
   if (n_tiles > 0) {
     cudaMemsetAsync(R.ghist, 0, sizeof(unsigned) * kRsPasses * 256, st);
-    k_rs_global_hist<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(k0, n_p, cap, passes, R.ghist, flags);
+    k_rs_global_hist<<<(unsigned)(num_sms * 4), 256, 0, st>>>(k0, n_p, cap, passes, R.ghist, flags);
     k_rs_bases<<<1, 32 * kRsPasses, 0, st>>>(R.ghist, passes, R.gbase, R.tile_ctr, R.epoch);
   }
   for (int pass = 0; pass < passes && n_tiles > 0; ++pass) {
@@ -1199,9 +1213,10 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
   if (c[2]) lnxt[lbase + n0 + n1 + __popc(m2 & lt)] = q[2];
 }
 
-__global__ void __launch_bounds__(256) k_mrounds1(RoundArgs R) {
+template <int kWarps>
+__global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
   if (R.flags[0] || R.flags[1]) return;
-  __shared__ NbScratch W[8];
+  __shared__ NbScratch W[kWarps];
   const long long n_cells = *R.n_cells_p;
   const GridGeom g = *R.geom;
   const unsigned nblocks = gridDim.x;
@@ -1294,13 +1309,13 @@ __global__ void __launch_bounds__(256) k_mlabel(MergeView V, const int* cord, co
 }
 
 // ------------------------------------------------------------------ fallback: sequential greedy (binary64)
-__global__ void k_mexact_prep(const jabba_group* groups, const int* rec_of, const int* sidx, const long long* n_p,
-                              long long cap, const double* sigma, double scl, const int* flags, double* eX,
-                              double* eY, double* ekey) {
+__global__ void k_mexact_prep(const jabba_group* groups, const double* iX, const double* iY, const int* rec_of,
+                              const int* sidx, const long long* n_p, long long cap, const double* sigma, double scl,
+                              const int* flags, double* eX, double* eY, double* ekey) {
   if (!flags[0] || flags[1]) return;
   const long long n = clamp_groups(n_p, cap);
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
-    const ExactCentre e = exact_centre(groups[rec_of[sidx[a]]], sigma[0], sigma[1], scl);
+    const ExactCentre e = item_point(groups, iX, iY, rec_of[sidx[a]], sigma, scl);
     eX[a] = e.X;
     eY[a] = e.Y;
     ekey[a] = exact_key(e);
@@ -1494,22 +1509,23 @@ static float rup(double v) {
   return f;
 }
 
-void launch_merge(const jabba_group* groups, const long long* n_groups, long long group_capacity,
-                  const long long* dom_group_off, const double* sigma, double alpha, double scl, int* l2g,
-                  double* dict_len, double* dict_inc, long long* dict_count, long long dict_capacity, long long* k,
-                  Scratch& ws, unsigned* status, cudaStream_t st,
+void launch_merge(const jabba_group* groups, const double* item_X, const double* item_Y, const long long* n_groups,
+                  long long group_capacity, const long long* dom_group_off, const double* sigma, double alpha,
+                  double scl, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,
+                  long long dict_capacity, long long* k, Scratch& ws, unsigned* status, cudaStream_t st,
                   const Marks& mk) {
   const long long cap = group_capacity;
   const unsigned grid = (unsigned)(ws.num_sms * 8);
   MergeBufs& B = ws.mb;
   k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.bar_sub, B.flags, status, n_groups, cap);
-  k_mprep<<<grid, 256, 0, st>>>(groups, n_groups, cap, dom_group_off, sigma, scl, ws.m_k0, ws.m_v0, ws.m_rec,
-                                ws.m_X32, ws.m_Y32, B.bounds, B.flags);
+  k_mprep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, n_groups, cap, dom_group_off, sigma, scl, ws.m_k0, ws.m_v0,
+                                ws.m_rec, ws.m_X32, ws.m_Y32, B.bounds, B.flags);
   unsigned long long* skey;
   int* sidx;
   // keys are non-negative binary64: their bit patterns order as the values;
   // the sort is stable and starts in compact-index order, so ties keep it
-  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws, status, &skey, &sidx, B.flags, st);
+  radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws.m_hist, ws.num_sms, status, &skey, &sidx,
+             B.flags, st);
   k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
   // the cell sort ping-pongs in the buffers the key sort left free
   unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
@@ -1518,7 +1534,7 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   unsigned long long* ckey;
   int* cord;
   // cell ids are below cap_cells = 2^23: three 8-bit passes order them
-  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws, status, &ckey, &cord, B.flags, st);
+  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws.m_hist, ws.num_sms, status, &ckey, &cord, B.flags, st);
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
@@ -1535,6 +1551,8 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   V.sX = B.sX;
   V.sY = B.sY;
   V.sigma = sigma;
+  V.iX = item_X;
+  V.iY = item_Y;
   V.scl = scl;
   V.a2 = alpha * alpha;
   V.a2lo = rdown(V.a2 * (1.0 - 0x1p-20));
@@ -1568,20 +1586,22 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   R.max_rounds = 1u << 22;
   {
     // cooperative launch: every block resident, so the bounded grid barrier can complete
-    static int max_per_sm = -1;
-    if (max_per_sm < 0) {
-      int a = 0, b = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mrounds, 256, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mrounds1, 256, 0);
-      max_per_sm = a < b ? a : b;
-      if (max_per_sm < 1) max_per_sm = 1;
+    // (the one-phase kernel in CTAs of 4 or 8 warps, jabba_tuning.merge_warps)
+    static int max_per_sm[3] = {-1, -1, -1};  // k_mrounds, k_mrounds1<8>, k_mrounds1<4>
+    if (max_per_sm[0] < 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm[0], k_mrounds, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm[1], k_mrounds1<8>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm[2], k_mrounds1<4>, 128, 0);
+      for (int i = 0; i < 3; ++i)
+        if (max_per_sm[i] < 1) max_per_sm[i] = 1;
     }
+    const int form = ws.tune.merge_form == 1 ? (ws.tune.merge_warps == 4 ? 2 : 1) : 0;
     int blocks_per_sm = ws.tune.merge_ctas_per_sm;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
-    if (blocks_per_sm > max_per_sm) blocks_per_sm = max_per_sm;  // co-residency of the cooperative grid
+    if (blocks_per_sm > max_per_sm[form]) blocks_per_sm = max_per_sm[form];  // co-residency of the cooperative grid
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ws.num_sms * blocks_per_sm));
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(form == 2 ? 128 : 256);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1594,7 +1614,8 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
     R.slot_stride = B.slots;
     R.item_cap = cap > 0 ? cap : 1;
     mark(mk.a0, st);
-    if (ws.tune.merge_form == 1) cudaLaunchKernelEx(&cfg, k_mrounds1, R);
+    if (form == 2) cudaLaunchKernelEx(&cfg, k_mrounds1<4>, R);
+    else if (form == 1) cudaLaunchKernelEx(&cfg, k_mrounds1<8>, R);
     else cudaLaunchKernelEx(&cfg, k_mrounds, R);
     mark(mk.a1, st);
   }
@@ -1603,7 +1624,8 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   k_mlabel<<<grid, 256, 0, st>>>(V, cord, B.cX, B.cY, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab,
                                  B.is_start);
   // sequential fallback (only acts when flags[0] is set)
-  k_mexact_prep<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, n_groups, cap, sigma, scl, B.flags, B.eX, B.eY, B.ekey);
+  k_mexact_prep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, ws.m_rec, sidx, n_groups, cap, sigma, scl, B.flags,
+                                      B.eX, B.eY, B.ekey);
   k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, B.flags, B.lab, B.is_start);
   exclusive_scan<int>(B.is_start, cap, B.start_off, ws.scan_tiles, st);
   k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, n_groups, cap, dict_capacity, l2g, k, status, B.flags);
@@ -1611,6 +1633,140 @@ void launch_merge(const jabba_group* groups, const long long* n_groups, long lon
   k_dict_accumulate<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, cord, B.lab, B.start_off, n_groups, cap, k,
                                           dict_capacity, ws.d_acc, B.flags);
   k_dict_finalize<<<grid, 256, 0, st>>>(ws.d_acc, k, dict_capacity, dict_len, dict_inc, dict_count);
+}
+
+// ------------------------------------------------------------------ block form of Sec. 5
+// The two-stage digitization as the paper states it: one global sort of the
+// normalised pieces by rho = X*X + Y*Y (binary64; equal keys in compact-piece
+// order), the sorted order cut into contiguous blocks of ceil(N / M) pieces,
+// each block aggregated by Stage I (the tile kernels, whose own sort keeps the
+// block's order), and Stage II over the local groups' starting points.
+
+// Binary64 key, compact index and compact copies of every piece (warp per domain).
+__global__ void k_bf_keys(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
+                          const int* dom_piece_cnt, const long long* dom_piece_off, long long n_domains,
+                          const double* sigma, double scl, unsigned long long* keys, int* vals, int* clen,
+                          double* cinc) {
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const double sl = sigma[0], si = sigma[1];
+  for (long long d = w; d < n_domains; d += nw) {
+    const int n = dom_piece_cnt[d];
+    const long long s0 = dom_slot_off[d], c0 = dom_piece_off[d];
+    for (int j = lane; j < n; j += 32) {
+      const int len = piece_len[s0 + j];
+      const double inc = piece_inc[s0 + j];
+      const double X = __ddiv_rn(__dmul_rn(scl, (double)len), sl);
+      const double Y = __ddiv_rn(inc, si);
+      const double key = __dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y));
+      const long long c = c0 + j;
+      keys[c] = (unsigned long long)__double_as_longlong(key);
+      vals[c] = (int)c;
+      clen[c] = len;
+      cinc[c] = inc;
+    }
+  }
+}
+
+__global__ void k_bf_count(const long long* dom_piece_off, long long n_domains, long long* n_dev, int* flags) {
+  *n_dev = dom_piece_off[n_domains];
+  flags[0] = flags[1] = flags[2] = flags[3] = 0;
+}
+
+// Pieces in key order (block order) and the blocks' ranges.
+__global__ void k_bf_gather(const int* sidx, const int* clen, const double* cinc, long long n, long long B, long long M,
+                            int* order, int* blen, double* binc, long long* blk_off, int* blk_cnt) {
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+  for (long long i = i0; i < n; i += step) {
+    const int c = sidx[i];
+    order[i] = c;
+    blen[i] = clen[c];
+    binc[i] = cinc[c];
+  }
+  for (long long b = i0; b <= M; b += step) {
+    const long long lo = b * B < n ? b * B : n;
+    blk_off[b] = lo;
+    if (b < M) blk_cnt[b] = (int)((lo + B < n ? lo + B : n) - lo);
+  }
+}
+
+// First piece (block order) of every local group: labels are assigned in
+// key order, so the start is the group's smallest position.
+__global__ void k_bf_start_init(int* start, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    start[i] = 0x7FFFFFFF;
+}
+__global__ void k_bf_starts(const int* local_label, const long long* blk_off, const int* blk_cnt,
+                            const long long* blk_group_off, long long M, int* start) {
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long b = w; b < M; b += nw) {
+    const long long o = blk_off[b], g0 = blk_group_off[b];
+    const int n = blk_cnt[b];
+    for (int j = lane; j < n; j += 32) atomicMin(&start[g0 + local_label[o + j]], (int)(o + j));
+  }
+}
+
+// Binary64 point of every group record: its start piece, normalised (Eq. 4).
+__global__ void k_bf_items(const jabba_group* groups, const long long* n_groups, long long cap,
+                           const long long* blk_group_off, const int* start, const int* blen, const double* binc,
+                           long long n_items, const double* sigma, double scl, double* iX, double* iY) {
+  const long long G = clamp_groups(n_groups, cap);
+  const double sl = sigma[0], si = sigma[1];
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < G; r += (long long)gridDim.x * blockDim.x) {
+    const jabba_group g = groups[r];
+    const int i = start[blk_group_off[g.domain] + g.local_id];
+    if (i < 0 || i >= n_items) {  // a group without a piece: not produced by Stage I
+      iX[r] = iY[r] = 0.0;
+      continue;
+    }
+    iX[r] = __ddiv_rn(__dmul_rn(scl, (double)blen[i]), sl);
+    iY[r] = __ddiv_rn(binc[i], si);
+  }
+}
+
+__global__ void k_bf_scatter(const int* order, const int* src, long long n, int* dst) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[order[i]] = src[i];
+}
+
+long long bf_hist_words(long long n) { return rs_hist_words(n); }
+
+void launch_block_order(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
+                        const int* dom_piece_cnt, const long long* dom_piece_off, long long n_domains, long long n,
+                        long long n_blocks, const double* sigma, double scl, BlockScratch& S, int* order, int* blen,
+                        double* binc, long long* blk_off, int* blk_cnt, int num_sms, unsigned* status,
+                        cudaStream_t st) {
+  const unsigned grid = (unsigned)(num_sms * 8);
+  k_bf_count<<<1, 1, 0, st>>>(dom_piece_off, n_domains, S.n_dev, S.flags);
+  if (n_domains > 0)
+    k_bf_keys<<<grid, 256, 0, st>>>(piece_len, piece_inc, dom_slot_off, dom_piece_cnt, dom_piece_off, n_domains, sigma,
+                                    scl, S.k0, S.v0, S.clen, S.cinc);
+  unsigned long long* skey = S.k0;
+  int* sidx = S.v0;
+  if (n > 0)
+    radix_sort(S.k0, S.v0, S.k1, S.v1, S.n_dev, n, 64, S.hist, num_sms, status, &skey, &sidx, S.flags, st);
+  const long long B = n > 0 ? (n + n_blocks - 1) / n_blocks : 1;
+  k_bf_gather<<<grid, 256, 0, st>>>(sidx, S.clen, S.cinc, n, B, n_blocks, order, blen, binc, blk_off, blk_cnt);
+}
+
+void launch_block_items(const int* local_label, const long long* blk_off, const int* blk_cnt,
+                        const long long* blk_group_off, long long n_blocks, const int* blen, const double* binc,
+                        const jabba_group* groups, const long long* n_groups, long long group_capacity,
+                        const double* sigma, double scl, int* start, long long n_items, double* item_X,
+                        double* item_Y, int num_sms, cudaStream_t st) {
+  const unsigned grid = (unsigned)(num_sms * 8);
+  k_bf_start_init<<<grid, 256, 0, st>>>(start, group_capacity);
+  if (n_blocks > 0)
+    k_bf_starts<<<grid, 256, 0, st>>>(local_label, blk_off, blk_cnt, blk_group_off, n_blocks, start);
+  k_bf_items<<<grid, 256, 0, st>>>(groups, n_groups, group_capacity, blk_group_off, start, blen, binc, n_items,
+                                   sigma, scl, item_X, item_Y);
+}
+
+void launch_block_scatter(const int* order, const int* src, long long n, int* dst, int num_sms, cudaStream_t st) {
+  if (n > 0) k_bf_scatter<<<(unsigned)(num_sms * 8), 256, 0, st>>>(order, src, n, dst);
 }
 
 }  // namespace jabba

@@ -215,3 +215,35 @@ def test_merge_forms(form):
         g, *_ = run_gpu(C2, x, off, cfg, recon=False)
         r = run_oracle(x, off, cfg, recon=False)
         assert_parity(g, r, recon=False)
+
+
+@pytest.mark.parametrize("name,max_series,M", [("small", None, None), ("small", None, 1), ("uneven", 20, None),
+                                               ("uneven", 20, 7), ("multivar", 1, None), ("noise", None, 3)])
+def test_block_form_parity(C, name, max_series, M):
+    """The block form of Sec. 5 (global key sort, contiguous sorted blocks,
+    Stage I per block, Stage II over the starting points) equals the oracle's
+    block_digitize bit for bit: the key order, the local labels, the map, the
+    dictionary and the symbols (M = None: as many blocks as domains)."""
+    import oracle
+    import torch
+    from _gpu import params
+    x, off, cfg = synth.make(name, max_series=max_series)
+    p = params(cfg)
+    out = C.symbolize_blocks(torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda(), p, n_blocks=M,
+                             series_off_host=off)
+    r0 = run_oracle(x, off, cfg, recon=False)
+    Mb = out["n_blocks"]
+    r = oracle.block_digitize(r0["piece_len"], r0["piece_inc"], r0["sigma_len"], r0["sigma_inc"], cfg["alpha"],
+                              cfg["scl"], Mb)
+    N = out["n_pieces"]
+    assert np.array_equal(out["blocks"]["order"][:N].cpu().numpy(), r["order"])
+    assert np.array_equal(out["blocks"]["dom_slot_off"].cpu().numpy(), r["blk_piece_off"])
+    assert np.array_equal(out["local"]["local_label"][:N].cpu().numpy(), r["block_label"])
+    assert np.array_equal(out["local"]["dom_group_off"].cpu().numpy(), r["blk_group_off"])
+    G = out["n_groups_host"]
+    assert np.array_equal(out["l2g"][:G].cpu().numpy(), r["l2g"])
+    assert np.array_equal(out["dict_count"].cpu().numpy(), r["dict_count"])
+    assert np.array_equal(out["dict_len"].cpu().numpy(), r["dict_len"])
+    assert np.array_equal(out["dict_inc"].cpu().numpy(), r["dict_inc"])
+    assert np.array_equal(out["symbol"].cpu().numpy(), r["symbol"])
+    C.sync_status(where="block form")
