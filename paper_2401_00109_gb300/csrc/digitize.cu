@@ -566,13 +566,27 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
     const long long slot = P.dom_slot_off[d];
     const int* plen = P.piece_len + slot;
     const double* pinc = P.piece_inc + slot;
-    // 1. FP32 keys by position
-    for (int i = t; i < n; i += T) {
-      unsigned mh;
-      const float x = x32_of(P, plen[i]);
-      const float y = f64_to_f32_trunc(pinc[i], mh) * rinv;
-      key[i] = key32_of(x, y);
-      idx[i] = (unsigned short)i;
+    // 1. FP32 keys by position (the loads of four pieces in flight together)
+    for (int i0 = t; i0 < n; i0 += 4 * T) {
+      int L4[4];
+      double I4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * T;
+        L4[u] = i < n ? plen[i] : 0;
+        I4[u] = i < n ? pinc[i] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * T;
+        if (i < n) {
+          unsigned mh;
+          const float x = x32_of(P, L4[u]);
+          const float y = f64_to_f32_trunc(I4[u], mh) * rinv;
+          key[i] = key32_of(x, y);
+          idx[i] = (unsigned short)i;
+        }
+      }
     }
     tile_sync<W>();
     // 2. sort by (key32, position)
@@ -590,20 +604,32 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
     }
     // 4. coordinates in key order (gathered again from the pieces, which are
     // in L1/L2), over the keys and the sort temp
-    for (int a = t; a < n; a += T) {
-      const int p = idx[a];
-      unsigned mh;
-      sX[a] = x32_of(P, plen[p]);
-      sY[a] = f64_to_f32_trunc(pinc[p], mh) * rinv;
-      lab[a] = -1;
+    for (int a0 = t; a0 < n; a0 += 4 * T) {
+      int L4[4];
+      double I4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int a = a0 + u * T;
+        const int p = a < n ? idx[a] : 0;
+        L4[u] = a < n ? plen[p] : 0;
+        I4[u] = a < n ? pinc[p] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int a = a0 + u * T;
+        if (a < n) {
+          unsigned mh;
+          sX[a] = x32_of(P, L4[u]);
+          sY[a] = f64_to_f32_trunc(I4[u], mh) * rinv;
+          lab[a] = -1;
+        }
+      }
     }
     tile_sync<W>();
     // 5. greedy in key order.  One warp (W = 1): each start's window pass
     // also finds the first piece left free behind the start (the next
-    // start).  W warps: every window step covers 32 W pieces, the warps agree
-    // on the stop with one barrier per step and on the next start through a
-    // shared minimum (three slots, so that a slot is reset only after every
-    // thread has read it).
+    // start).  W warps: every window step covers 32 W pieces and the warps
+    // agree on the stop and on the next start with one barrier per step.
     if constexpr (W == 1) {
       if (t < 32) {
         int G = 0, a = 0;
@@ -655,18 +681,25 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
         if (lane == 0) misc[13] = G;
       }
     } else {
-      int* s_next = misc + 20;  // [3] first free piece behind the start (by start index mod 3)
-      if (t < 3) s_next[t] = n;
-      __syncthreads();
+      // each warp publishes its first free piece behind the start before every
+      // step's barrier; after the last one every thread takes the minimum.
+      // Two slots by start parity: a slot is written again only after the
+      // next start's barrier, which every reader of it has passed.
+      int* cand = (int*)hist;  // [2][W] (the sort's histograms are free now)
+      int* srch = misc + 20;   // [2] first free piece found beyond the window
       const int warp = t >> 5;
       int G = 0, a = 0;
       while (a < n) {
-        const int sl = G % 3;
+        const int sl = G & 1;
         const float xs = sX[a], ys = sY[a];
         const float Tk = key_stop(__uint_as_float(key32_of(xs, ys)), P.alpha_up);
-        if (t == 0) lab[a] = (short)G;
+        if (t == 0) {
+          lab[a] = (short)G;
+          srch[sl] = n;
+        }
         int next = n;  // this warp's first free piece
         int b0 = a + 1;
+        const bool stepped = b0 < n;
         for (; b0 < n; b0 += T) {
           const int b = b0 + t;
           bool stop = true, fr = false;
@@ -689,21 +722,23 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
           }
           const unsigned mf = __ballot_sync(0xFFFFFFFFu, fr);
           if (mf && next == n) next = b0 + warp * 32 + __ffs(mf) - 1;
+          if (lane == 0) cand[sl * W + warp] = next;
           if (__syncthreads_or(stop)) break;
         }
-        if (lane == 0 && next < n) atomicMin(&s_next[sl], next);
-        if (t == 0) s_next[(G + 1) % 3] = n;
-        __syncthreads();
-        int nx = s_next[sl];
-        if (nx == n) {
-          // nothing left free up to the window's last step: search on
-          for (b0 += T; b0 < n; b0 += T) {
-            const int b = b0 + t;
-            const unsigned mf = __ballot_sync(0xFFFFFFFFu, b < n && lab[b] < 0);
-            if (mf && lane == 0) atomicMin(&s_next[sl], b0 + warp * 32 + __ffs(mf) - 1);
-            if (__syncthreads_or(mf != 0)) break;
+        int nx = n;
+        if (stepped) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) nx = min(nx, cand[sl * W + w]);
+          if (nx == n) {
+            // nothing left free up to the window's last step: search on
+            for (b0 += T; b0 < n; b0 += T) {
+              const int b = b0 + t;
+              const unsigned mf = __ballot_sync(0xFFFFFFFFu, b < n && lab[b] < 0);
+              if (mf && lane == 0) atomicMin(&srch[sl], b0 + warp * 32 + __ffs(mf) - 1);
+              if (__syncthreads_or(mf != 0)) break;
+            }
+            nx = srch[sl];
           }
-          nx = s_next[sl];
         }
         ++G;
         a = nx;
