@@ -704,41 +704,51 @@ class InFlight:
             s.wait_stream(cur)
 
 
-def tune_inflight(pipelines, base: dict, steps: int = 4):
+def tune_inflight(pipelines, base: dict, steps: int = 4, finalists: int = 4, final_steps: int = 10):
     """Pick the launch configuration of two batches in flight: the front
     half's kernels must leave room on every SM for the other batch's
     cooperative merge, so the resident CTAs per SM of compression, of the
-    local-aggregation kernels and of the merge rounds are searched around
-    `base` (the single-batch autotuned configuration), timing a few steps of
-    each candidate with CUDA events.  Returns (best configuration, its ms per
+    local-aggregation kernels and of the merge rounds (and its warps per CTA)
+    are searched around `base` (the single-batch autotuned configuration),
+    timing a few steps of each candidate with CUDA events; the `finalists`
+    fastest are timed again over `final_steps` steps (step times vary from
+    run to run by a few percent).  Returns (best configuration, its ms per
     step, an InFlight runner captured with it)."""
     torch = _torch()
-    best = None
+
+    def timed(cfg, n):
+        for pl in pipelines:
+            pl.ctx.set_tuning(cfg)
+        fl = InFlight(pipelines)
+        for _ in range(2):
+            fl.step()
+        fl.join()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fl.fork(st)
+        for _ in range(n):
+            fl.step()
+        fl.join(st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n, fl
+
     m_opts = [(1, 8), (2, 8), (1, 4), (2, 4)] if base.get("merge_form", 1) == 1 else [(1, 8), (2, 8)]
+    first = []
     for c_sm in (1, 2):
         for cap in (2, 3, 4):
             for m_sm, m_w in m_opts:
                 cfg = dict(base, compress_ctas_per_sm=c_sm, local_ctas_cap=cap, merge_ctas_per_sm=m_sm,
                            merge_warps=m_w)
-                for pl in pipelines:
-                    pl.ctx.set_tuning(cfg)
-                fl = InFlight(pipelines)
-                for _ in range(2):
-                    fl.step()
-                fl.join()
-                torch.cuda.synchronize()
-                st = torch.cuda.current_stream()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                fl.fork(st)
-                for _ in range(steps):
-                    fl.step()
-                fl.join(st)
-                e1.record(st)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / steps
-                if best is None or ms < best[1]:
-                    best = (cfg, ms, fl)
+                first.append((timed(cfg, steps)[0], cfg))
+    first.sort(key=lambda r: r[0])
+    best = None
+    for _, cfg in first[:max(1, finalists)]:
+        ms, fl = timed(cfg, final_steps)
+        if best is None or ms < best[1]:
+            best = (cfg, ms, fl)
     for pl in pipelines:
         pl.ctx.set_tuning(best[0])
         pl.ctx.sync_status(where="in-flight tuning")
