@@ -131,32 +131,81 @@ __device__ void sort_run(const LocalParams& P, const int* plen, const double* pi
   }
 }
 
+// The same re-sort for a run of at most 32 members: the warp computes each
+// member's binary64 key once (lane i, member a + i) into kbuf, then lane 0
+// insertion-sorts on those keys.
+template <typename IdxT>
+__device__ void sort_run32(const LocalParams& P, const int* plen, const double* pinc, unsigned* key, IdxT* idx, int a,
+                           int b, double* kbuf) {
+  const int lane = threadIdx.x & 31;
+  const int r = b - a + 1;
+  if (lane < r) {
+    const int p = idx[a + lane];
+    kbuf[lane] = key64_of(P, plen[p], pinc[p]);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int u = 1; u < r; ++u) {
+      const double ku = kbuf[u];
+      const int pu = idx[a + u];
+      const unsigned ku32 = key[a + u];
+      int v = u - 1;
+      while (v >= 0 && (kbuf[v] > ku || (kbuf[v] == ku && (int)idx[a + v] > pu))) {
+        kbuf[v + 1] = kbuf[v];
+        idx[a + v + 1] = idx[a + v];
+        key[a + v + 1] = key[a + v];
+        --v;
+      }
+      kbuf[v + 1] = ku;
+      idx[a + v + 1] = (IdxT)pu;
+      key[a + v + 1] = ku32;
+    }
+  }
+  __syncwarp();
+}
+
 // Runs of neighbours whose key intervals overlap, found 32 pairs at a time
 // (links from the keys as sorted: a run's last key bounds all its members, so
-// the order across runs is settled by the FP32 keys); lane 0 re-sorts each
-// run by the binary64 keys, ties by position.
+// the order across runs is settled by the FP32 keys); each run is re-sorted by
+// the binary64 keys, ties by position.  Whole warp; the run boundaries are
+// found by bit scans of the link masks; kbuf: 32 doubles of scratch.
 template <typename IdxT>
-__device__ void fix_runs(const LocalParams& P, const int* plen, const double* pinc, unsigned* key, IdxT* idx, int n) {
+__device__ void fix_runs(const LocalParams& P, const int* plen, const double* pinc, unsigned* key, IdxT* idx, int n,
+                         double* kbuf) {
   const int lane = threadIdx.x & 31;
   int run_start = -1;                          // run open across chunks (uniform)
+  auto sort_members = [&](int a, int b) {
+    if (b - a + 1 <= 32) {
+      sort_run32<IdxT>(P, plen, pinc, key, idx, a, b, kbuf);
+    } else {
+      if (lane == 0) sort_run<IdxT>(P, plen, pinc, key, idx, a, b);
+      __syncwarp();
+    }
+  };
   for (int a0 = 0; a0 + 1 < n; a0 += 32) {
     const int a = a0 + lane;
     const bool link = a + 1 < n && keys_overlap32(key[a], key[a + 1]);
-    const unsigned m = __ballot_sync(0xFFFFFFFFu, link);
+    const int lim = min(32, n - 1 - a0);       // pairs a0 .. a0 + lim - 1 exist
+    const unsigned valid = lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, link) & valid;
     if (m == 0 && run_start < 0) continue;
-    for (int l = 0; l < 32 && a0 + l + 1 < n; ++l) {
-      const bool lk = (m >> l) & 1u;
-      if (lk && run_start < 0) {
+    int l = 0;
+    while (l < lim) {
+      if (run_start < 0) {
+        const unsigned mm = m & (0xFFFFFFFFu << l);
+        if (!mm) break;
+        l = __ffs(mm) - 1;
         run_start = a0 + l;
-      } else if (!lk && run_start >= 0) {
-        if (lane == 0) sort_run<IdxT>(P, plen, pinc, key, idx, run_start, a0 + l);
-        __syncwarp();
-        run_start = -1;
       }
+      const unsigned nm = ~m & valid & (0xFFFFFFFFu << l);
+      if (!nm) break;                          // the run goes on into the next chunk
+      l = __ffs(nm) - 1;                       // first pair past the run: its last member is a0 + l
+      sort_members(run_start, a0 + l);
+      run_start = -1;
+      ++l;
     }
   }
-  if (run_start >= 0 && lane == 0) sort_run<IdxT>(P, plen, pinc, key, idx, run_start, n - 1);
-  __syncwarp();
+  if (run_start >= 0) sort_members(run_start, n - 1);
 }
 
 // Counting-sort scratch view of one warp's arena.
@@ -235,7 +284,7 @@ __device__ void warp_radix_sort(unsigned* key, int* val, unsigned* tk, int* tv, 
 }
 
 __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
-  __shared__ unsigned hist_all[kLocWarps][256];
+  __shared__ __align__(16) unsigned hist_all[kLocWarps][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long warp_global = (long long)blockIdx.x * kLocWarps + warp;
   unsigned* hist = hist_all[warp];
@@ -276,7 +325,7 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
     if (n > 1) warp_radix_sort(A.key, A.sidx, A.tk, A.tv, n, hist);
     __syncwarp();
     // 3. runs of overlapping key intervals: re-sort by the binary64 keys
-    fix_runs<int>(P, plen, pinc, A.key, A.sidx, n);
+    fix_runs<int>(P, plen, pinc, A.key, A.sidx, n, (double*)hist);
     // 4. greedy in key order
     int G = 0;
     {
@@ -598,7 +647,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
       bool ov = false;
       for (int a = t; a + 1 < n; a += T) ov = ov || keys_overlap32(key[a], key[a + 1]);
       if (tile_sync_or<W>(ov)) {
-        if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n);
+        if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n, (double*)hist);
         tile_sync<W>();
       }
     }
