@@ -391,21 +391,27 @@ def run_ours(args, ws, rank, local):
     #     per local group (its FP32 centre, key-order position and coverage
     #     flag, each read once).
     # The dominant one (largest time) is reported as `roofline`.
+    # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is known for
+    # the Stage I tiles of the scale workload from one ncu capture of its
+    # first 10,000 series (the five tile launches of a step: 223.2 MB read,
+    # 62.6 MB written for 17,479,524 pieces), scaled to a launch by its pieces
+    # (the traffic grows with them); null elsewhere.
+    local_traffic = 285.827328e6 / 17479524 * N if args.workload == "scale" else None
     peak, peak_kind = peaks()
     Dn = pl.D
-    cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N),
+    cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N, None),
             ("local aggregation (k_local_tile x5, k_local_classify, k_local_warp, scan)", loc_ms,
-             16.0 * N + 48.0 * G + 12.0 * Dn),
-            ("k_mrounds1" if ctx.tuning()["merge_form"] == 1 else "k_mrounds", rnd_ms, 13.0 * G)]
+             16.0 * N + 48.0 * G + 12.0 * Dn, local_traffic),
+            ("k_mrounds1" if ctx.tuning()["merge_form"] == 1 else "k_mrounds", rnd_ms, 13.0 * G, None)]
     by_kernel = []
-    for name, ms_list, alg in cand:
+    for name, ms_list, alg, traffic in cand:
         t = float(np.mean(ms_list))
         ach = alg / (t * 1e-3) / 1e9
         by_kernel.append(dict(kernel=name, ms_per_launch=t, algorithmic_bytes_per_launch=alg, achieved=ach,
-                              frac=ach / peak))
+                              frac=ach / peak, traffic=traffic))
     dom = max(by_kernel, key=lambda r: r["ms_per_launch"])
     roofline = dict(bound="hbm", achieved=dom["achieved"], peak=peak, unit="GB/s", frac=dom["frac"],
-                    traffic=None, kernel=dom["kernel"], peak_source=peak_kind,
+                    traffic=dom["traffic"], kernel=dom["kernel"], peak_source=peak_kind,
                     algorithmic_bytes_per_launch=dom["algorithmic_bytes_per_launch"],
                     ms_per_launch=dom["ms_per_launch"], by_kernel=by_kernel,
                     path_frac_of_point_roofline=value / ws / (peak / 8.0))
