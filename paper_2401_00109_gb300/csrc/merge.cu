@@ -1,7 +1,9 @@
 // merge.cu -- Stage II of the two-stage digitization (Sec. 5): the local
-// groups, taken at their centres, are aggregated once more by the same greedy
-// (Sec. 3.2); the result maps every local group to a global group, and the
-// dictionary entries are the exact means of their member pieces.
+// groups, taken at their centres (or at given points: the starting points of
+// the block form at the end of this file), are aggregated once more by the
+// same greedy (Sec. 3.2); the result maps every local group to a global
+// group, and the dictionary entries are the exact means of their member
+// pieces.
 //
 // The greedy in key order is the lexicographically first maximal set of
 // "starts" pairwise farther than alpha apart; every other item joins the
@@ -18,7 +20,9 @@
 //  4. rounds (one cooperative kernel, bounded grid barriers): each undecided
 //     cell skips its items covered by known neighbouring starts; its next item
 //     becomes a start once no undecided neighbouring item that precedes it in
-//     key order lies within alpha (such an item could still become a start);
+//     key order lies within alpha (such an item could still become a start).
+//     k_mrounds1 tests coverage on the fly (one barrier per round), k_mrounds
+//     marks it between two barriers;
 //  5. every item's label is the earliest start within alpha among the starts
 //     of its 5 x 5 cell neighbourhood; global ids follow key order.
 // If the coordinates span too many cells for the grid, or their error
