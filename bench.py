@@ -188,6 +188,40 @@ def run_reference(args, ws, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+def roofline_table(workload, n, N, G, D, comp_ms, loc_ms, rnd_ms, rounds_name, peak, peak_kind):
+    """Roofline entries of the three largest stages (lists of per-step
+    milliseconds in) and the dominant one (largest time) as the `roofline`
+    object.  Algorithmic bytes per launch, per unit processed:
+      k_compress: 8 B per point read + 12 B per piece written (len, end value);
+      local aggregation (tile kernels + routing + group offsets): 12 B per
+        piece read (len, inc) + 4 B per piece written (label) + 48 B per group
+        record + 12 B per domain (group count and offset);
+      merge rounds (k_mrounds1, or k_mrounds in the two-barrier form): 13 B per
+        local group (its FP32 centre, key-order position and coverage flag,
+        each read once).
+    DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is known for
+    the Stage I tiles of the scale workload from one ncu capture of its first
+    10,000 series (the five tile launches of a step: 223.2 MB read, 62.6 MB
+    written for 17,479,524 pieces), scaled to a launch by its pieces (the
+    traffic grows with them); null elsewhere."""
+    local_traffic = 285.827328e6 / 17479524 * N if workload == "scale" else None
+    cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N, None),
+            ("local aggregation (k_local_tile x5, k_local_classify, k_local_warp, scan)", loc_ms,
+             16.0 * N + 48.0 * G + 12.0 * D, local_traffic),
+            (rounds_name, rnd_ms, 13.0 * G, None)]
+    by_kernel = []
+    for name, ms_list, alg, traffic in cand:
+        t = float(np.mean(ms_list))
+        ach = alg / (t * 1e-3) / 1e9
+        by_kernel.append(dict(kernel=name, ms_per_launch=t, algorithmic_bytes_per_launch=alg, achieved=ach,
+                              frac=ach / peak, traffic=traffic))
+    dom = max(by_kernel, key=lambda r: r["ms_per_launch"])
+    return dict(bound="hbm", achieved=dom["achieved"], peak=peak, unit="GB/s", frac=dom["frac"],
+                traffic=dom["traffic"], kernel=dom["kernel"], peak_source=peak_kind,
+                algorithmic_bytes_per_launch=dom["algorithmic_bytes_per_launch"],
+                ms_per_launch=dom["ms_per_launch"], by_kernel=by_kernel)
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -381,40 +415,12 @@ def run_ours(args, ws, rank, local):
                    ms_per_step=ems, batches_in_flight=2 if inflight is not None else 1)
         ctx.sync_status(where="e2e steps")
 
-    # ---- rooflines (HBM; nothing here is a dense contraction).  Algorithmic
-    # bytes per launch, per unit processed:
-    #   k_compress: 8 B per point read + 12 B per piece written (len, end value);
-    #   local aggregation (tile kernels + routing + group offsets): 12 B per
-    #     piece read (len, inc) + 4 B per piece written (label) + 48 B per group
-    #     record + 12 B per domain (group count and offset);
-    #   merge rounds (k_mrounds1, or k_mrounds in the two-barrier form): 13 B
-    #     per local group (its FP32 centre, key-order position and coverage
-    #     flag, each read once).
-    # The dominant one (largest time) is reported as `roofline`.
-    # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is known for
-    # the Stage I tiles of the scale workload from one ncu capture of its
-    # first 10,000 series (the five tile launches of a step: 223.2 MB read,
-    # 62.6 MB written for 17,479,524 pieces), scaled to a launch by its pieces
-    # (the traffic grows with them); null elsewhere.
-    local_traffic = 285.827328e6 / 17479524 * N if args.workload == "scale" else None
+    # ---- rooflines (HBM; nothing here is a dense contraction): the three
+    # largest stages and the dominant one (roofline_table)
     peak, peak_kind = peaks()
-    Dn = pl.D
-    cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N, None),
-            ("local aggregation (k_local_tile x5, k_local_classify, k_local_warp, scan)", loc_ms,
-             16.0 * N + 48.0 * G + 12.0 * Dn, local_traffic),
-            ("k_mrounds1" if ctx.tuning()["merge_form"] == 1 else "k_mrounds", rnd_ms, 13.0 * G, None)]
-    by_kernel = []
-    for name, ms_list, alg, traffic in cand:
-        t = float(np.mean(ms_list))
-        ach = alg / (t * 1e-3) / 1e9
-        by_kernel.append(dict(kernel=name, ms_per_launch=t, algorithmic_bytes_per_launch=alg, achieved=ach,
-                              frac=ach / peak, traffic=traffic))
-    dom = max(by_kernel, key=lambda r: r["ms_per_launch"])
-    roofline = dict(bound="hbm", achieved=dom["achieved"], peak=peak, unit="GB/s", frac=dom["frac"],
-                    traffic=dom["traffic"], kernel=dom["kernel"], peak_source=peak_kind,
-                    algorithmic_bytes_per_launch=dom["algorithmic_bytes_per_launch"],
-                    ms_per_launch=dom["ms_per_launch"], by_kernel=by_kernel,
-                    path_frac_of_point_roofline=value / ws / (peak / 8.0))
+    roofline = roofline_table(args.workload, n, N, G, pl.D, comp_ms, loc_ms, rnd_ms,
+                              "k_mrounds1" if ctx.tuning()["merge_form"] == 1 else "k_mrounds", peak, peak_kind)
+    roofline["path_frac_of_point_roofline"] = value / ws / (peak / 8.0)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
