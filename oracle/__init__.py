@@ -16,6 +16,8 @@ Functions follow the paper's steps (section in brackets):
   merge              Sec. 5 Stage II, merge of the local groups
   block_digitize     Sec. 5 two-stage digitization in the block form (global
                      sort, contiguous sorted blocks, merge of starting points)
+  pca_axis           Sec. 5 "PCA projection" key: first principal axis
+  pipeline(key="pca")  the path with the PCA key in Stage I and II
   symbolize          Sec. 5 label propagation
   reconstruct        Sec. 3.3 inverse digitization, quantization, inverse compression
   mse                Sec. 3.3 reconstruction error
@@ -68,13 +70,16 @@ def lib():
                 "jo_compress_all": (None, [F64, I64, I64, C.c_int64, I64, C.c_double, I32, F64, I64, C.c_int]),
                 "jo_sigma": (None, [I32, F64, C.c_int64, F64, F64]),
                 "jo_greedy": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_int, I64, I64]),
+                "jo_greedy_proj": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
+                                               I64, I64]),
+                "jo_group_sums": (None, [I32, F64, C.c_int64, I64, C.c_int64, I64, I64, U64]),
                 "jo_local_aggregate": (C.c_int64, [I32, F64, C.c_int64, C.c_double, C.c_double, C.c_double,
                                                    C.c_double, I32, I64, I64, U64]),
                 "jo_centre": (None, [C.c_int64, C.c_int64, U64, F64, F64]),
                 "jo_merge": (C.c_int64, [I64, I64, U64, C.c_int64, C.c_double, C.c_double, C.c_double,
                                          C.c_double, I32, F64, F64, I64]),
-                "jo_merge_points": (C.c_int64, [F64, F64, I64, I64, U64, C.c_int64, C.c_double, I32, F64, F64,
-                                                I64]),
+                "jo_merge_points": (C.c_int64, [F64, F64, I64, I64, U64, C.c_int64, C.c_double, C.c_int,
+                                                C.c_double, C.c_double, I32, F64, F64, I64]),
                 "jo_symbolize": (None, [I32, I64, I64, C.c_int64, I32, I32]),
                 "jo_reassign": (None, [I32, F64, C.c_int64, C.c_double, C.c_double, C.c_double, F64, F64,
                                        C.c_int64, I32]),
@@ -159,14 +164,68 @@ def sigma(piece_len, piece_inc):
     return sl.value, si.value
 
 
-def greedy(X, Y, alpha: float, prune: bool = True):
+def greedy(X, Y, alpha: float, prune: bool = True, axis=None):
+    """Greedy aggregation (Sec. 3.2) in key order: the squared norm, or with
+    axis = (vx, vy) the projection on that unit axis (the PCA key)."""
     X = _c(X, np.float64)
     Y = _c(Y, np.float64)
     n = len(X)
     lab = np.empty(max(n, 1), np.int64)
     st = np.empty(max(n, 1), np.int64)
-    g = lib().jo_greedy(_p(X, F64), _p(Y, F64), n, alpha, int(prune), _p(lab, I64), _p(st, I64))
+    if axis is None:
+        g = lib().jo_greedy(_p(X, F64), _p(Y, F64), n, alpha, int(prune), _p(lab, I64), _p(st, I64))
+    else:
+        g = lib().jo_greedy_proj(_p(X, F64), _p(Y, F64), n, alpha, float(axis[0]), float(axis[1]), int(prune),
+                                 _p(lab, I64), _p(st, I64))
     return lab[:n], st[:g]
+
+
+def pca_axis(piece_len, piece_inc, sigma_len, sigma_inc, scl):
+    """First principal axis of the normalised pieces (the PCA key of Sec. 5).
+    The population covariance of the binary64 points (X, Y) is evaluated
+    exactly (rational arithmetic) and rounded once to binary64 entries a =
+    var X, b = cov(X, Y), c = var Y; the leading eigenvector of [[a, b],
+    [b, c]] then follows in binary64 by the closed form lam = (a + c) / 2 +
+    sqrt(((a - c) / 2)^2 + b^2), v ~ (lam - c, b) when a >= c, else
+    (b, lam - a), normalised, with vx > 0 (or vx = 0 and vy > 0); b = 0
+    gives the axis of the larger variance ((1, 0) when a >= c)."""
+    from fractions import Fraction
+    X, Y = normalised(piece_len, piece_inc, sigma_len, sigma_inc, scl)
+    n = len(X)
+    if n == 0:
+        return 1.0, 0.0
+    fx = [Fraction(float(v)) for v in X]
+    fy = [Fraction(float(v)) for v in Y]
+    mx = sum(fx) / n
+    my = sum(fy) / n
+    a = float(sum((u - mx) * (u - mx) for u in fx) / n)
+    c = float(sum((w - my) * (w - my) for w in fy) / n)
+    b = float(sum((u - mx) * (w - my) for u, w in zip(fx, fy)) / n)
+    f = np.float64
+    a, b, c = f(a), f(b), f(c)
+    if b == 0.0:
+        return (1.0, 0.0) if a >= c else (0.0, 1.0)
+    h = (a - c) / f(2.0)
+    lam = (a + c) / f(2.0) + np.sqrt(h * h + b * b)
+    vx, vy = (lam - c, b) if a >= c else (b, lam - a)
+    s_ = np.sqrt(vx * vx + vy * vy)
+    vx, vy = vx / s_, vy / s_
+    if vx < 0.0 or (vx == 0.0 and vy < 0.0):
+        vx, vy = -vx, -vy
+    return float(vx), float(vy)
+
+
+def group_sums(piece_len, piece_inc, labels, G):
+    """Exact sums (count, lensum, incacc) of the groups labels[i] in [0, G)."""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    lab = _c(labels, np.int64)
+    cnt = np.empty(max(G, 1), np.int64)
+    ls = np.empty(max(G, 1), np.int64)
+    ia = np.zeros((max(G, 1), 4), np.uint64)
+    lib().jo_group_sums(_p(ln, I32), _p(inc, F64), len(ln), _p(lab, I64), G, _p(cnt, I64), _p(ls, I64),
+                        _p(ia, U64))
+    return cnt[:G].copy(), ls[:G].copy(), ia[:G].copy()
 
 
 def normalised(piece_len, piece_inc, sigma_len, sigma_inc, scl):
@@ -227,9 +286,10 @@ def merge(grp_count, grp_lensum, grp_incacc, sigma_len, sigma_inc, alpha, scl):
     return l2g[:G].copy(), dl[:k].copy(), di[:k].copy(), dc[:k].copy()
 
 
-def merge_points(X, Y, grp_count, grp_lensum, grp_incacc, alpha):
+def merge_points(X, Y, grp_count, grp_lensum, grp_incacc, alpha, axis=None):
     """Stage II over given points of the local groups (their starting points
-    in the block form).  Returns (l2g int32[G], dict_len, dict_inc, dict_count)."""
+    in the block form, their centres with the PCA key); axis as in greedy.
+    Returns (l2g int32[G], dict_len, dict_inc, dict_count)."""
     X = _c(X, np.float64)
     Y = _c(Y, np.float64)
     cnt = _c(grp_count, np.int64)
@@ -240,8 +300,9 @@ def merge_points(X, Y, grp_count, grp_lensum, grp_incacc, alpha):
     dl = np.empty(max(G, 1), np.float64)
     di = np.empty(max(G, 1), np.float64)
     dc = np.empty(max(G, 1), np.int64)
-    k = lib().jo_merge_points(_p(X, F64), _p(Y, F64), _p(cnt, I64), _p(ls, I64), _p(ia, U64), G, alpha,
-                              _p(l2g, I32), _p(dl, F64), _p(di, F64), _p(dc, I64))
+    mode, vx, vy = (0, 0.0, 0.0) if axis is None else (1, float(axis[0]), float(axis[1]))
+    k = lib().jo_merge_points(_p(X, F64), _p(Y, F64), _p(cnt, I64), _p(ls, I64), _p(ia, U64), G, alpha, mode, vx,
+                              vy, _p(l2g, I32), _p(dl, F64), _p(di, F64), _p(dc, I64))
     return l2g[:G].copy(), dl[:k].copy(), di[:k].copy(), dc[:k].copy()
 
 
@@ -403,14 +464,49 @@ def fx_value(limbs) -> int:
 
 
 # ---------------------------------------------------------------- whole path
+def local_aggregate_pca(piece_len, piece_inc, dom_piece_off, sigma_len, sigma_inc, alpha, scl, axis):
+    """Stage I per domain with the PCA key (projection on `axis`); outputs as
+    local_aggregate."""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    off = _c(dom_piece_off, np.int64)
+    X, Y = normalised(ln, inc, sigma_len, sigma_inc, scl)
+    label = np.empty(len(ln), np.int32)
+    goff = np.zeros(len(off), np.int64)
+    sums = []
+    for d in range(len(off) - 1):
+        a, b = int(off[d]), int(off[d + 1])
+        lab, st = greedy(X[a:b], Y[a:b], alpha, True, axis)
+        label[a:b] = lab
+        sums.append(group_sums(ln[a:b], inc[a:b], lab, len(st)))
+        goff[d + 1] = goff[d] + len(st)
+    cnt = np.concatenate([s_[0] for s_ in sums]) if sums else np.zeros(0, np.int64)
+    ls = np.concatenate([s_[1] for s_ in sums]) if sums else np.zeros(0, np.int64)
+    ia = np.concatenate([s_[2] for s_ in sums]) if sums else np.zeros((0, 4), np.uint64)
+    return label, goff, cnt, ls, ia
+
+
 def pipeline(x, series_off, tol, alpha, scl=1.0, domain_mode=0, domain_value=4, threads=1,
-             with_reconstruct=True, round_mode=0):
-    """The whole forward path on one collection; returns a dict of every stage."""
+             with_reconstruct=True, round_mode=0, key="norm"):
+    """The whole forward path on one collection; returns a dict of every
+    stage.  key = "pca": Stage I and II sort by the projection on the first
+    principal axis of the normalised pieces (pca_axis) instead of the norm."""
     b, e, ds = domains(series_off, domain_mode, domain_value)
     ln, inc, po = compress(x, b, e, tol, threads)
     sl, si = sigma(ln, inc)
-    lab, go, gc, gl, gi = local_aggregate(ln, inc, po, sl, si, alpha, scl)
-    l2g, dl, di, dc = merge(gc, gl, gi, sl, si, alpha, scl)
+    if key == "pca":
+        axis = pca_axis(ln, inc, sl, si, scl)
+        lab, go, gc, gl, gi = local_aggregate_pca(ln, inc, po, sl, si, alpha, scl, axis)
+        # local centres, normalised (Eq. 4) as in jo_merge
+        cX, cY = np.empty(len(gc)), np.empty(len(gc))
+        for g in range(len(gc)):
+            cl, ci = centre(int(gc[g]), int(gl[g]), gi[g])
+            cX[g] = (scl * cl) / sl
+            cY[g] = ci / si
+        l2g, dl, di, dc = merge_points(cX, cY, gc, gl, gi, alpha, axis)
+    else:
+        lab, go, gc, gl, gi = local_aggregate(ln, inc, po, sl, si, alpha, scl)
+        l2g, dl, di, dc = merge(gc, gl, gi, sl, si, alpha, scl)
     sym = symbolize(lab, po, go, l2g)
     out = dict(dom_begin=b, dom_end=e, dom_series=ds, piece_len=ln, piece_inc=inc, dom_piece_off=po,
                sigma_len=sl, sigma_inc=si, local_label=lab, dom_group_off=go, grp_count=gc,

@@ -374,12 +374,16 @@ static double dist2(double xa, double ya, double xb, double yb) {
 
 /* Generic greedy over n points (X[], Y[]); labels[i] receives the group id in
  * creation order; returns the number of groups; starts[g] = first point.
- * prune = 0 gives the unpruned greedy (used only by the tests). */
-int64_t jo_greedy(const double* X, const double* Y, int64_t n, double alpha, int prune,
-                  int64_t* labels, int64_t* starts) {
+ * prune = 0 gives the unpruned greedy (used only by the tests).
+ * mode 0: the squared-norm key above.  mode 1 (the PCA key of Sec. 5): the
+ * projection key vx * X + vy * Y on a unit axis (vx, vy); a projection on a
+ * unit vector changes by at most the distance, so the scan stops once the key
+ * gap exceeds alpha (margin 2^-40 of the coordinates' size for rounding). */
+static int64_t greedy_core(const double* X, const double* Y, int64_t n, double alpha, int prune, int mode,
+                           double vx, double vy, int64_t* labels, int64_t* starts) {
   jo_kp* o = (jo_kp*)malloc(sizeof(jo_kp) * (size_t)(n ? n : 1));
   for (int64_t i = 0; i < n; ++i) {
-    o[i].key = X[i] * X[i] + Y[i] * Y[i];
+    o[i].key = mode ? vx * X[i] + vy * Y[i] : X[i] * X[i] + Y[i] * Y[i];
     o[i].pos = i;
     labels[i] = -1;
   }
@@ -391,12 +395,17 @@ int64_t jo_greedy(const double* X, const double* Y, int64_t n, double alpha, int
     if (labels[i] >= 0) continue;
     labels[i] = g;
     if (starts) starts[g] = i;
-    double ri = sqrt(o[a].key);
+    double ri = mode ? o[a].key : sqrt(o[a].key);
     for (int64_t b = a + 1; b < n; ++b) {
       int64_t j = o[b].pos;
       if (prune) {
-        double rj = sqrt(o[b].key);
-        if (rj - ri > alpha + 0x1p-40 * (alpha + rj)) break;
+        if (mode) {
+          double m = 0x1p-40 * (alpha + fabs(X[i]) + fabs(Y[i]) + fabs(X[j]) + fabs(Y[j]));
+          if (o[b].key - ri > alpha + m) break;
+        } else {
+          double rj = sqrt(o[b].key);
+          if (rj - ri > alpha + 0x1p-40 * (alpha + rj)) break;
+        }
       }
       if (labels[j] < 0 && dist2(X[i], Y[i], X[j], Y[j]) <= a2) labels[j] = g;
     }
@@ -404,6 +413,33 @@ int64_t jo_greedy(const double* X, const double* Y, int64_t n, double alpha, int
   }
   free(o);
   return g;
+}
+
+int64_t jo_greedy(const double* X, const double* Y, int64_t n, double alpha, int prune,
+                  int64_t* labels, int64_t* starts) {
+  return greedy_core(X, Y, n, alpha, prune, 0, 0.0, 0.0, labels, starts);
+}
+
+int64_t jo_greedy_proj(const double* X, const double* Y, int64_t n, double alpha, double vx, double vy, int prune,
+                       int64_t* labels, int64_t* starts) {
+  return greedy_core(X, Y, n, alpha, prune, 1, vx, vy, labels, starts);
+}
+
+/* Exact sums of the groups given by labels[i] in [0, G): count, lensum,
+ * incacc (fixed point, 4 limbs per group). */
+void jo_group_sums(const int32_t* len, const double* inc, int64_t n, const int64_t* labels, int64_t G,
+                   int64_t* grp_count, int64_t* grp_lensum, uint64_t* grp_incacc) {
+  for (int64_t g = 0; g < G; ++g) {
+    grp_count[g] = 0;
+    grp_lensum[g] = 0;
+    memset(grp_incacc + 4 * g, 0, 32);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t g = labels[i];
+    grp_count[g] += 1;
+    grp_lensum[g] += len[i];
+    fx_add_double((jo_fx*)(grp_incacc + 4 * g), inc[i]);
+  }
 }
 
 /* Normalised coordinates of a piece (Eq. 4). */
@@ -491,15 +527,16 @@ int64_t jo_merge(const int64_t* grp_count, const int64_t* grp_lensum, const uint
 
 /* Stage II over given points (Sec. 5 as the paper states it: the local
  * starting points are merged): the same pruned greedy over the points
- * (X[g], Y[g]) of the G local groups, in index order for equal keys;
+ * (X[g], Y[g]) of the G local groups (key by mode as in greedy_core), in
+ * index order for equal keys;
  * l2g[g] = global group (creation order); the dictionary entry of a global
  * group is the exact mean of the pieces of its local groups (their exact
  * sums), as in jo_merge.  Returns k. */
 int64_t jo_merge_points(const double* X, const double* Y, const int64_t* grp_count, const int64_t* grp_lensum,
-                        const uint64_t* grp_incacc, int64_t G, double alpha, int32_t* l2g, double* dict_len,
-                        double* dict_inc, int64_t* dict_count) {
+                        const uint64_t* grp_incacc, int64_t G, double alpha, int mode, double vx, double vy,
+                        int32_t* l2g, double* dict_len, double* dict_inc, int64_t* dict_count) {
   int64_t* lab = (int64_t*)malloc(sizeof(int64_t) * (size_t)(G ? G : 1));
-  int64_t k = jo_greedy(X, Y, G, alpha, 1, lab, NULL);
+  int64_t k = greedy_core(X, Y, G, alpha, 1, mode, vx, vy, lab, NULL);
   int64_t* cnt = (int64_t*)calloc((size_t)(k ? k : 1), sizeof(int64_t));
   int64_t* ls = (int64_t*)calloc((size_t)(k ? k : 1), sizeof(int64_t));
   jo_fx* ia = (jo_fx*)calloc((size_t)(k ? k : 1), sizeof(jo_fx));

@@ -383,3 +383,74 @@ def test_block_form_invariants(M):
     dl, di, dc = _exact_means(ln, inc, r["symbol"], k)
     assert np.array_equal(r["dict_count"], dc)
     assert np.array_equal(r["dict_len"], dl) and np.array_equal(r["dict_inc"], di)
+
+
+# ---------------------------------------------------------------- PCA key (Sec. 5 "norm or PCA projection")
+@pytest.mark.parametrize("name,scl", [("small", 1.0), ("uneven", 1.0), ("small", 3.0), ("multivar", 0.25)])
+def test_pca_axis_is_the_leading_eigenvector(name, scl):
+    """pca_axis against numpy's symmetric eigensolver on the covariance of
+    the normalised points; with scl = 1 both variances are 1 and the axis is
+    the diagonal (1, sign(r)) / sqrt(2) whatever the correlation r."""
+    ln, inc, po, sl, si, cfg = _block_inputs(name, 4)
+    ax = np.array(oracle.pca_axis(ln, inc, sl, si, scl))
+    X, Y = oracle.normalised(ln, inc, sl, si, scl)
+    w, V = np.linalg.eigh(np.cov(np.vstack([X, Y]), bias=True))
+    v = V[:, -1] * (1 if V[0, -1] > 0 else -1)
+    assert abs(np.hypot(*ax) - 1.0) < 1e-15
+    assert np.max(np.abs(ax - v)) < 1e-9
+    if scl == 1.0:
+        r = np.corrcoef(X, Y)[0, 1]
+        assert np.max(np.abs(ax - np.array([1.0, np.sign(r)]) / np.sqrt(2.0))) < 1e-9
+
+
+def test_pca_axis_degenerate():
+    ln = np.full(10, 3, np.int32)
+    inc = np.full(10, 0.5)
+    assert oracle.pca_axis(ln, inc, 1.0, 1.0, 1.0) == (1.0, 0.0)
+    assert oracle.pca_axis(ln[:0], inc[:0], 1.0, 1.0, 1.0) == (1.0, 0.0)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_pca_greedy_order_pruning_and_invariants(seed):
+    """The greedy with the projection key: pruning loses nothing (the key
+    gap bounds the distance), every start is the first item in key order
+    (ties by position) among those no earlier group covers, members lie
+    within alpha of their start and the starts are pairwise farther apart."""
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, 600)
+    Y = 0.5 * X + rng.normal(0, 0.3, 600)
+    alpha = 0.3
+    th = rng.uniform(0, np.pi)
+    ax = (float(np.cos(th)), float(np.sin(th)))
+    lab, st = oracle.greedy(X, Y, alpha, True, ax)
+    lab0, st0 = oracle.greedy(X, Y, alpha, False, ax)
+    assert np.array_equal(lab, lab0) and np.array_equal(st, st0)
+    key = ax[0] * X + ax[1] * Y
+    order = np.lexsort((np.arange(len(X)), key))
+    rank = np.empty(len(X), np.int64)
+    rank[order] = np.arange(len(X))
+    for g, s in enumerate(st):
+        free = np.nonzero(lab >= g)[0]
+        assert s == free[np.argmin(rank[free])]
+        m = np.nonzero(lab == g)[0]
+        assert np.all((X[m] - X[s]) ** 2 + (Y[m] - Y[s]) ** 2 <= alpha * alpha)
+    for u in range(len(st)):
+        d = (X[st[u + 1:]] - X[st[u]]) ** 2 + (Y[st[u + 1:]] - Y[st[u]]) ** 2
+        assert np.all(d > alpha * alpha)
+
+
+def test_pca_pipeline_exact_means_and_composition():
+    """The two-stage path with the PCA key: the symbols are the composition
+    of the local labels and the map, and every dictionary entry is the exact
+    mean of the pieces of its symbol."""
+    x, off, cfg = synth.make("small", max_series=6)
+    r = oracle.pipeline(x, off, cfg["tol"], cfg["alpha"], cfg["scl"], cfg["domain_mode"], cfg["domain_value"],
+                        key="pca", with_reconstruct=False)
+    po, go = r["dom_piece_off"], r["dom_group_off"]
+    for d in range(len(po) - 1):
+        for p in range(po[d], po[d + 1]):
+            assert r["symbol"][p] == r["l2g"][go[d] + r["local_label"][p]]
+    k = len(r["dict_len"])
+    dl, di, dc = _exact_means(r["piece_len"], r["piece_inc"], r["symbol"], k)
+    assert np.array_equal(r["dict_count"], dc)
+    assert np.array_equal(r["dict_len"], dl) and np.array_equal(r["dict_inc"], di)
