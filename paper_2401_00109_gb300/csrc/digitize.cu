@@ -439,11 +439,13 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
 // ------------------------------------------------------------------ shared-memory tiles
 // Domains of at most CAP pieces: W warps own one domain at a time with every
 // per-piece array in shared memory (W = 1: several independent warps per CTA).
-// The W warps share the sort and the sums; the greedy, which walks the starts
-// one after another, runs on the tile's first warp (one ballot pass per start
-// in the common case of a window shorter than 32 pieces).  Domains are routed
-// to the smallest tile that holds them (k_local_classify), so small domains
-// run many warps per SM.
+// The W warps share the sort, the sums and the greedy's window passes (the
+// starts follow one another; each start's window is scanned 32 W pieces per
+// step, one ballot per warp and one barrier per step).  Domains are routed to
+// the smallest tile that holds them (k_local_classify), so small domains run
+// many warps per SM.  After the sort, the W * 1024 histogram bytes serve as
+// scratch: the binary64 keys of an overlapping-key run, then the greedy's
+// per-warp next-start candidates.
 //
 // Per-tile shared memory: W * 1024 histogram bytes, then per piece 4 B key
 // (later sY), 4 B sort temp (later sX), 2 B position, 2 B sort temp (later
