@@ -72,3 +72,32 @@ def test_create_without_gpu_fails_loudly():
         jb.Context()
     h = C.c_void_p()
     assert jb.load().jabba_create(C.byref(h), 0) != 0
+
+
+def header_params():
+    """Parameter counts of the functions that include/jabba.h declares."""
+    src = open(os.path.join(ROOT, "include", "jabba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(jabba_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else len([a for a in args.split(",") if a.strip()])
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point the Python binding declares with ctypes takes as
+    many arguments as include/jabba.h says (a binding that drifts from the
+    header would pass wrong pointers)."""
+    import paper_2401_00109_gb300 as jb
+    L = jb.load()
+    counts = header_params()
+    assert len(counts) >= 20
+    checked = 0
+    for name, n in counts.items():
+        f = getattr(L, name)
+        if f.argtypes is None:
+            continue
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+        checked += 1
+    assert checked >= 20
