@@ -454,3 +454,29 @@ def test_pca_pipeline_exact_means_and_composition():
     dl, di, dc = _exact_means(r["piece_len"], r["piece_inc"], r["symbol"], k)
     assert np.array_equal(r["dict_count"], dc)
     assert np.array_equal(r["dict_len"], dl) and np.array_equal(r["dict_inc"], di)
+
+
+def test_block_form_hand_starts_not_centres():
+    """Hand-derived block form (Sec. 5 as stated: the STARTING points are
+    merged).  scl = 0 puts every piece at X = 0, sigma_inc = 1 makes Y = inc;
+    alpha = 0.1, six pieces in two blocks of three.
+      block 0 (keys ascend: 0, .30, .39): start 0 alone; start .30 takes .39
+        (gap .09)                               -> groups {0}, {.30, .39}
+      block 1 (.42, .60, .65): start .42 alone (.18 to .60); start .60 takes
+        .65                                     -> groups {.42}, {.60, .65}
+      Stage II over the starts 0, .30, .42, .60: consecutive gaps .30, .12,
+        .18 all exceed alpha                    -> four symbols.
+    Merging the centres instead would join {.30, .39} (centre .345) with
+    {.42} (gap .075 <= alpha): three symbols."""
+    inc = np.array([0.0, 0.30, 0.39, 0.42, 0.60, 0.65])
+    ln = np.ones(6, np.int32)
+    r = oracle.block_digitize(ln, inc, 1.0, 1.0, 0.1, 0.0, 2)
+    assert list(r["order"]) == [0, 1, 2, 3, 4, 5]
+    assert list(r["symbol"]) == [0, 1, 1, 2, 3, 3]
+    assert list(r["dict_count"]) == [1, 2, 1, 2]
+    exp = [float(sum(Fraction(v) for v in inc[r["symbol"] == c])) / float((r["symbol"] == c).sum()) for c in range(4)]
+    assert list(r["dict_inc"]) == exp and list(r["dict_len"]) == [1.0] * 4
+    # the per-domain reading (one domain = one block of all six, centres merged) differs
+    lab, goff, cnt, ls, ia = oracle.local_aggregate(ln, inc, np.array([0, 3, 6]), 1.0, 1.0, 0.1, 0.0)
+    l2g, dl, di, dc = oracle.merge(cnt, ls, ia, 1.0, 1.0, 0.1, 0.0)
+    assert len(dl) == 3 and list(dc) == [1, 3, 2]
