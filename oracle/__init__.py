@@ -66,8 +66,13 @@ def lib():
                 "jo_piece_error": (C.c_double, [F64, C.c_int64, C.c_int64]),
                 "jo_piece_error_l2": (C.c_double, [F64, C.c_int64, C.c_int64]),
                 "jo_piece_admissible": (C.c_int, [F64, C.c_int64, C.c_int64, C.c_double]),
-                "jo_compress_domain": (C.c_int64, [F64, C.c_int64, C.c_int64, C.c_double, I32, F64]),
-                "jo_compress_all": (None, [F64, I64, I64, C.c_int64, I64, C.c_double, I32, F64, I64, C.c_int]),
+                "jo_piece_error_plain": (C.c_double, [F64, C.c_int64, C.c_int64]),
+                "jo_piece_admissible_plain": (C.c_int, [F64, C.c_int64, C.c_int64, C.c_double]),
+                "jo_piece_end": (C.c_int64, [F64, C.c_int64, C.c_int64, C.c_double, C.c_int]),
+                "jo_piece_ends": (None, [F64, I64, I64, C.c_int64, C.c_double, C.c_int, I64, C.c_int]),
+                "jo_compress_domain": (C.c_int64, [F64, C.c_int64, C.c_int64, C.c_double, C.c_int, I32, F64]),
+                "jo_compress_all": (None, [F64, I64, I64, C.c_int64, I64, C.c_double, C.c_int, I32, F64, I64,
+                                           C.c_int]),
                 "jo_sigma": (None, [I32, F64, C.c_int64, F64, F64]),
                 "jo_greedy": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_int, I64, I64]),
                 "jo_greedy_proj": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
@@ -126,13 +131,66 @@ def piece_error(x, s: int, e: int) -> float:
     return lib().jo_piece_error(_p(x, F64), s, e)
 
 
-def admissible(x, s: int, e: int, tol: float) -> bool:
+_FORMS = {"l2": 0, "plain": 1}
+
+
+def admissible(x, s: int, e: int, tol: float, form: str = "l2") -> bool:
     x = _c(x, np.float64)
-    return bool(lib().jo_piece_admissible(_p(x, F64), s, e, tol))
+    f = lib().jo_piece_admissible_plain if _FORMS[form] else lib().jo_piece_admissible
+    return bool(f(_p(x, F64), s, e, tol))
 
 
-def compress(x, dom_begin, dom_end, tol: float, threads: int = 1):
+def piece_error_plain(x, s: int, e: int) -> float:
+    """Eq. 1 error of piece (s, e) in the plain reading: residuals from the
+    chord summed sequentially in ascending order (binary64)."""
+    x = _c(x, np.float64)
+    return lib().jo_piece_error_plain(_p(x, F64), s, e)
+
+
+def piece_ends(x, starts, dom_ends, tol: float, form: str = "plain", threads: int = 1):
+    """End that the greedy of Eq. 1 (in the given reading) reaches from each
+    start, inside a domain ending at dom_ends[i]."""
+    x = _c(x, np.float64)
+    s = _c(starts, np.int64)
+    e = _c(dom_ends, np.int64)
+    out = np.empty(max(len(s), 1), np.int64)
+    lib().jo_piece_ends(_p(x, F64), _p(s, I64), _p(e, I64), len(s), tol, _FORMS[form], _p(out, I64), threads)
+    return out[:len(s)].copy()
+
+
+def breakpoint_flips(x, dom_begin, dom_end, piece_len, dom_piece_off, tol: float, threads: int = 1,
+                     form: str = "plain"):
+    """Compare a chain of pieces (any implementation's, compact layout) with
+    the greedy of Eq. 1 in the given reading, decision by decision: from every
+    piece start s, the reading's greedy reaches some end e'; where e' differs
+    from the chain's end e, the two disagree on the admissibility of (s, t),
+    t = min(e, e') + 1 (a breakpoint flip).  Returns a dict with the number of
+    pieces checked, the flips, and for each flip (s, t, err, bound) with err
+    the reading's Eq. 1 error of (s, t) and bound = (t - s - 1) tol^2."""
+    ln = np.asarray(piece_len, np.int64)
+    po = np.asarray(dom_piece_off, np.int64)
+    cnt = np.diff(po)
+    dom_of = np.repeat(np.arange(len(cnt)), cnt)
+    csum = np.concatenate([[0], np.cumsum(ln)])               # csum[i] = total length before piece i
+    ends = np.asarray(dom_begin, np.int64)[dom_of] + csum[1:] - csum[po[dom_of]]
+    starts = ends - ln
+    dend = np.asarray(dom_end, np.int64)[dom_of]
+    got = piece_ends(x, starts, dend, tol, form, threads)
+    bad = np.nonzero(got != ends)[0]
+    t2 = tol * tol
+    err_f = piece_error_plain if form == "plain" else piece_error
+    flips = []
+    for i in bad:
+        s0 = int(starts[i])
+        t = int(min(got[i], ends[i])) + 1
+        flips.append((s0, t, err_f(x, s0, t), float((t - s0 - 1) * t2)))
+    return {"pieces": int(len(ln)), "flips": flips}
+
+
+def compress(x, dom_begin, dom_end, tol: float, threads: int = 1, form: str = "l2"):
     """Pieces of every domain, concatenated in domain order (Sec. 4.1.3).
+    form = "l2": Eq. 1 multiplied through by L^2 with an exact sum (default);
+    form = "plain": the sequential sum of squared residuals as printed.
     Returns (piece_len int32[N], piece_inc float64[N], dom_piece_off int64[D+1])."""
     x = _c(x, np.float64)
     b = _c(dom_begin, np.int64)
@@ -145,7 +203,7 @@ def compress(x, dom_begin, dom_end, tol: float, threads: int = 1):
     ln = np.empty(max(total, 1), np.int32)
     inc = np.empty(max(total, 1), np.float64)
     cnt = np.zeros(max(D, 1), np.int64)
-    lib().jo_compress_all(_p(x, F64), _p(b, I64), _p(e, I64), D, _p(cap_off, I64), tol,
+    lib().jo_compress_all(_p(x, F64), _p(b, I64), _p(e, I64), D, _p(cap_off, I64), tol, _FORMS[form],
                           _p(ln, I32), _p(inc, F64), _p(cnt, I64), threads)
     cnt = cnt[:D]
     off = np.zeros(D + 1, np.int64)
@@ -458,7 +516,7 @@ def fx_round(limbs) -> float:
 
 
 def fx_value(limbs) -> int:
-    """Signed integer value (in units of 2^-96) of 4 little-endian limbs."""
+    """Signed integer value (in units of 2^-64) of 4 little-endian limbs."""
     u = sum(int(limbs[i]) << (64 * i) for i in range(4))
     return u - (1 << 256) if u >> 255 else u
 

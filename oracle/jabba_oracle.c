@@ -210,7 +210,8 @@ int64_t jo_build_domains(const int64_t* series_off, int64_t n_series, int mode, 
 /*    end reached by extension, which keeps the method linear);              */
 /*  - the sum runs over interior points only (the endpoint residuals are     */
 /*    zero in exact arithmetic);                                             */
-/*  - Eq. 1 is used multiplied through by L^2 (L = e - s > 0), which leaves   */
+/*  - Eq. 1 is used multiplied through by L^2 (L = e - s > 0; form 0, the    */
+/*    default; the plain form 1 follows below), which leaves                 */
 /*    the criterion unchanged in exact arithmetic and needs no division:     */
 /*      sum_{k=1}^{L-1} n_k^2 <= ((L - 1) tol^2) L^2,                         */
 /*      n_k = (x_s L + inc k) - x_{s+k} L,  inc = x_e - x_s,                  */
@@ -264,12 +265,51 @@ int jo_piece_admissible(const double* x, int64_t s, int64_t e, double tol) {
   return jo_piece_error_l2(x, s, e) <= ((double)(e - s - 1) * (tol * tol)) * (dL * dL);
 }
 
-int64_t jo_compress_domain(const double* x, int64_t b, int64_t e_dom, double tol,
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 in its plain form, the formula read as printed: the residual of     */
+/* interior point s+k from the chord is r_k = (x_s + (inc * k) / L) - x_{s+k} */
+/* (binary64, in that order, no fused operations), the squares are summed    */
+/* sequentially in ascending k, and the piece is admissible when the sum is  */
+/* at most (L - 1) * (tol * tol).  This is the second reading of Eq. 1 kept  */
+/* beside the L^2-scaled exact form above: the two agree in exact arithmetic */
+/* and may differ only where the error lies within rounding of the bound (a  */
+/* "breakpoint flip"; the tests count them and check how close they are).   */
+/* ------------------------------------------------------------------------ */
+double jo_piece_error_plain(const double* x, int64_t s, int64_t e) {
+  int64_t L = e - s;
+  if (L < 2) return 0.0;
+  double dL = (double)L;
+  double inc = x[e] - x[s];
+  double err = 0.0;
+  for (int64_t k = 1; k < L; ++k) {
+    double r = (x[s] + (inc * (double)k) / dL) - x[s + k];
+    err = err + r * r;
+  }
+  return err;
+}
+
+int jo_piece_admissible_plain(const double* x, int64_t s, int64_t e, double tol) {
+  return jo_piece_error_plain(x, s, e) <= (double)(e - s - 1) * (tol * tol);
+}
+
+/* Admissibility in the chosen reading: form 0 = L^2-scaled exact sum,
+ * form 1 = plain sequential sum. */
+static int admissible_form(const double* x, int64_t s, int64_t e, double tol, int form) {
+  return form ? jo_piece_admissible_plain(x, s, e, tol) : jo_piece_admissible(x, s, e, tol);
+}
+
+/* End of the greedy piece that starts at s in a domain ending at e_dom. */
+int64_t jo_piece_end(const double* x, int64_t s, int64_t e_dom, double tol, int form) {
+  int64_t e = s + 1;                           /* a one-interval piece is always admissible */
+  while (e + 1 <= e_dom && admissible_form(x, s, e + 1, tol, form)) ++e;
+  return e;
+}
+
+int64_t jo_compress_domain(const double* x, int64_t b, int64_t e_dom, double tol, int form,
                            int32_t* len_out, double* inc_out) {
   int64_t n = 0, s = b;
   while (s < e_dom) {
-    int64_t e = s + 1;                         /* a one-interval piece is always admissible */
-    while (e + 1 <= e_dom && jo_piece_admissible(x, s, e + 1, tol)) ++e;
+    int64_t e = jo_piece_end(x, s, e_dom, tol, form);
     len_out[n] = (int32_t)(e - s);
     inc_out[n] = x[e] - x[s];
     ++n;
@@ -284,28 +324,59 @@ int64_t jo_compress_domain(const double* x, int64_t b, int64_t e_dom, double tol
  * over POSIX threads exactly as the paper's multicore compression does. */
 typedef struct {
   const double* x; const int64_t* b; const int64_t* e; const int64_t* cap_off;
-  double tol; int32_t* len; double* inc; int64_t* count; int64_t d0, d1;
+  double tol; int form; int32_t* len; double* inc; int64_t* count; int64_t d0, d1;
 } jo_cjob;
 
 static void* compress_worker(void* p) {
   jo_cjob* j = (jo_cjob*)p;
   for (int64_t d = j->d0; d < j->d1; ++d)
-    j->count[d] = jo_compress_domain(j->x, j->b[d], j->e[d], j->tol, j->len + j->cap_off[d], j->inc + j->cap_off[d]);
+    j->count[d] = jo_compress_domain(j->x, j->b[d], j->e[d], j->tol, j->form, j->len + j->cap_off[d],
+                                     j->inc + j->cap_off[d]);
   return NULL;
 }
 
 void jo_compress_all(const double* x, const int64_t* dom_begin, const int64_t* dom_end, int64_t n_domains,
-                     const int64_t* dom_cap_off, double tol, int32_t* len, double* inc, int64_t* dom_count,
-                     int n_threads) {
+                     const int64_t* dom_cap_off, double tol, int form, int32_t* len, double* inc,
+                     int64_t* dom_count, int n_threads) {
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 256) n_threads = 256;
   pthread_t th[256];
   jo_cjob jobs[256];
   for (int t = 0; t < n_threads; ++t) {
-    jobs[t] = (jo_cjob){x, dom_begin, dom_end, dom_cap_off, tol, len, inc, dom_count,
+    jobs[t] = (jo_cjob){x, dom_begin, dom_end, dom_cap_off, tol, form, len, inc, dom_count,
                         n_domains * t / n_threads, n_domains * (t + 1) / n_threads};
     if (n_threads == 1) compress_worker(&jobs[t]);
     else pthread_create(&th[t], NULL, compress_worker, &jobs[t]);
+  }
+  if (n_threads > 1)
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+}
+
+/* End reached from each of n given piece starts (starts[i] in a domain that
+ * ends at dom_ends[i]) by the greedy of the given form; the check of another
+ * implementation's breakpoints against either reading of Eq. 1.  Pieces are
+ * dealt to the threads round robin (their costs differ widely). */
+typedef struct {
+  const double* x; const int64_t* s; const int64_t* e; int64_t n; double tol; int form; int64_t* out;
+  int t, nt;
+} jo_ejob;
+
+static void* ends_worker(void* p) {
+  jo_ejob* j = (jo_ejob*)p;
+  for (int64_t i = j->t; i < j->n; i += j->nt) j->out[i] = jo_piece_end(j->x, j->s[i], j->e[i], j->tol, j->form);
+  return NULL;
+}
+
+void jo_piece_ends(const double* x, const int64_t* starts, const int64_t* dom_ends, int64_t n, double tol,
+                   int form, int64_t* out, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  jo_ejob jobs[256];
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t] = (jo_ejob){x, starts, dom_ends, n, tol, form, out, t, n_threads};
+    if (n_threads == 1) ends_worker(&jobs[t]);
+    else pthread_create(&th[t], NULL, ends_worker, &jobs[t]);
   }
   if (n_threads > 1)
     for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
@@ -629,7 +700,9 @@ double jo_sse(const int32_t* len, const double* inc, int64_t n, double sigma_len
 /*   dropped; a short chain leaves the tail at the final level.               */
 /* qlen receives l^_j.                                                        */
 /* ------------------------------------------------------------------------ */
-static double round_half_even(double v) { return rint(v); } /* default mode: nearest, ties to even */
+/* round_mode 1: nearest, ties to even (rint in the default rounding mode).
+ * round_mode 0 (the default) is C's round(): nearest, ties away from zero. */
+static double round_half_even(double v) { return rint(v); }
 
 void jo_reconstruct_series(const int32_t* symbol, int64_t n_pieces, const double* dict_len, const double* dict_inc,
                            double x0, int64_t n_s, int round_mode, int32_t* qlen, double* xhat) {

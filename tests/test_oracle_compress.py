@@ -58,15 +58,17 @@ def test_domains_cover_and_share_endpoints(mode, value):
             assert np.all(e[idx] - b[idx] <= value)
 
 
-def test_compress_hand():
+@pytest.mark.parametrize("form", ["l2", "plain"])
+def test_compress_hand(form):
     g = load("compress_hand.txt")
     x = g["x"]
-    ln, inc, off = oracle.compress(x, np.array([0]), np.array([len(x) - 1]), float(g["tol"][0]))
+    ln, inc, off = oracle.compress(x, np.array([0]), np.array([len(x) - 1]), float(g["tol"][0]), form=form)
     assert ln.tolist() == g["len"].astype(int).tolist()
     assert inc.tolist() == g["inc"].tolist()
 
 
-def test_tol0_kinks_are_breakpoints():
+@pytest.mark.parametrize("form", ["l2", "plain"])
+def test_tol0_kinks_are_breakpoints(form):
     """Integer-valued piecewise-linear series with integer slopes: residuals
     are exactly zero on each segment, so with tol = 0 the breakpoints are the
     kinks plus the domain boundaries, nothing else."""
@@ -88,7 +90,7 @@ def test_tol0_kinks_are_breakpoints():
     off = np.array([0, len(x)], np.int64)
     for M in (1, 3, 7):
         b, e, _ = oracle.domains(off, 0, M)
-        ln, inc, po = oracle.compress(x, b, e, 0.0)
+        ln, inc, po = oracle.compress(x, b, e, 0.0, form=form)
         bp = set()
         for dd in range(len(b)):
             lens = ln[po[dd]:po[dd + 1]]
@@ -97,18 +99,20 @@ def test_tol0_kinks_are_breakpoints():
         assert bp == expect
 
 
+@pytest.mark.parametrize("form", ["l2", "plain"])
 @pytest.mark.parametrize("M", [1, 4])
-def test_straight_line_one_piece_per_domain(M):
+def test_straight_line_one_piece_per_domain(M, form):
     x = 0.25 * np.arange(1000) - 3.0
     off = np.array([0, 1000], np.int64)
     b, e, _ = oracle.domains(off, 0, M)
-    ln, inc, po = oracle.compress(x, b, e, 0.01)
+    ln, inc, po = oracle.compress(x, b, e, 0.01, form=form)
     assert np.all(np.diff(po) == 1)
     assert ln.tolist() == (e - b).tolist()
 
 
+@pytest.mark.parametrize("form", ["l2", "plain"])
 @pytest.mark.parametrize("tol", [0.05, 0.3, 1.0])
-def test_pieces_admissible_maximal_exact(tol):
+def test_pieces_admissible_maximal_exact(tol, form):
     """Every piece satisfies Eq. 1 and (unless it ends at the domain end) the
     next end violates it; both checked in exact rational arithmetic.  Together
     with tiling this characterizes the greedy output."""
@@ -116,7 +120,7 @@ def test_pieces_admissible_maximal_exact(tol):
     x = np.cumsum(rng.standard_normal(300)) * 0.3 + np.sin(np.arange(300) / 7.0)
     off = np.array([0, 300], np.int64)
     b, e, _ = oracle.domains(off, 0, 3)
-    ln, inc, po = oracle.compress(x, b, e, tol)
+    ln, inc, po = oracle.compress(x, b, e, tol, form=form)
     t2 = Fraction(tol) * Fraction(tol)
     slack = Fraction(1, 10**9)
     for d in range(len(b)):
@@ -152,9 +156,42 @@ def test_piece_error_matches_exact():
     rng = np.random.default_rng(3)
     x = rng.standard_normal(50)
     for s, t in [(0, 5), (3, 40), (10, 11), (0, 49)]:
-        a = oracle.piece_error(x, s, t)
         ex = float(exact_err(x, s, t))
-        assert abs(a - ex) <= 1e-13 * max(1.0, ex)
+        for a in (oracle.piece_error(x, s, t), oracle.piece_error_plain(x, s, t)):
+            assert abs(a - ex) <= 1e-13 * max(1.0, ex)
+
+
+def test_forms_agree_away_from_the_bound():
+    """The two readings of Eq. 1 (L^2-scaled exact sum, plain sequential sum)
+    give the same chain on seeded walks; any breakpoint where they could
+    differ must have its error within rounding of the bound."""
+    x, off, p = synth.make("small")
+    b, e, _ = oracle.domains(off, 0, 4)
+    a = oracle.compress(x, b, e, p["tol"], form="l2")
+    c = oracle.compress(x, b, e, p["tol"], form="plain")
+    for u, v in zip(a, c):
+        assert np.array_equal(u, v)
+    r = oracle.breakpoint_flips(x, b, e, a[0], a[2], p["tol"], threads=2)
+    assert r["pieces"] == len(a[0]) and r["flips"] == []
+
+
+def test_breakpoint_flips_reports_a_wrong_breakpoint():
+    """The flip checker against a planted mistake: a chain whose first piece
+    is cut one interval early (every later piece kept, so the chain still
+    tiles the domain) is reported at that piece, with an error far from the
+    bound."""
+    rng = np.random.default_rng(11)
+    x = np.cumsum(rng.standard_normal(400)) * 0.3
+    off = np.array([0, 400], np.int64)
+    b, e, _ = oracle.domains(off, 0, 1)
+    ln, inc, po = oracle.compress(x, b, e, 0.5, form="plain")
+    assert ln[0] >= 3
+    bad = np.concatenate([[ln[0] - 1, 1], ln[1:]]).astype(np.int32)
+    r = oracle.breakpoint_flips(x, b, e, bad, np.array([0, len(bad)]), 0.5)
+    assert r["pieces"] == len(bad)
+    s0, t, err, bound = r["flips"][0]
+    assert (s0, t) == (0, int(ln[0]))                   # the cut end: admissible, yet the chain stopped
+    assert err <= bound and abs(err - bound) > 1e-12 * bound
 
 
 def test_compress_threads_identical():

@@ -22,6 +22,48 @@ def test_quantize_hand():
     assert xh.tolist() == g["xhat"].tolist()
 
 
+def test_quantize_half_even_hand():
+    """round_mode 1 (ties to even) on exact ties, with a zero-length piece."""
+    g = load("quantize_even_hand.txt")
+    k = len(g["lt"])
+    sym = np.arange(k, dtype=np.int32)
+    n = len(g["xhat"])
+    x = np.zeros(n)
+    off = np.array([0, n], np.int64)
+    spo = np.array([0, k], np.int64)
+    ql, xh = oracle.reconstruct(sym, spo, g["lt"], g["it"], x, off, round_mode=1)
+    assert ql.tolist() == g["qlen"].astype(int).tolist()
+    assert xh.tolist() == g["xhat"].tolist()
+    ql0, _ = oracle.reconstruct(sym, spo, g["lt"], g["it"], x, off, round_mode=0)
+    assert ql0.tolist() == [2, 1, 1, 3, 3, 2, 1]                      # the two modes differ here
+
+
+def test_quantize_half_even_dyadic_cumulative_rounding():
+    """round_mode 1 with dyadic lengths (exact in binary64): the carry makes
+    the value rounded at piece j equal to v_j = (exact cumulative length
+    through j) - (quantized lengths before j), so each quantized length is
+    v_j rounded to nearest with ties to even, and the cumulative quantized
+    length never drifts more than 1/2 from the exact cumulative length.
+    (Ties to even do not commute with adding an odd integer, so unlike
+    round_mode 0 the cumulative lengths are not simply the rounded exact
+    cumulative sums.)"""
+    rng = np.random.default_rng(8)
+    lt = rng.integers(2, 40, 500) / 2.0                   # multiples of 1/2: many exact ties
+    sym = np.arange(500, dtype=np.int32)
+    n = int(lt.sum()) + 10
+    x = np.zeros(n)
+    ql, _ = oracle.reconstruct(sym, np.array([0, 500]), lt, np.zeros(500), x, np.array([0, n]), round_mode=1)
+    cum = np.cumsum(lt)
+    before = np.concatenate([[0], np.cumsum(ql)[:-1]])
+    v = cum - before
+    fl = np.floor(v)
+    frac = v - fl
+    want = np.where(frac > 0.5, fl + 1, np.where(frac < 0.5, fl, fl + (fl % 2)))
+    assert np.array_equal(ql, want)
+    assert np.any(frac == 0.5) and np.any((frac == 0.5) & (fl % 2 == 1))   # both kinds of tie occur
+    assert np.all(np.abs(cum - np.cumsum(ql)) <= 0.5)
+
+
 def test_quantize_dyadic_cumulative_rounding():
     """With dyadic lengths (exact in FP) the carry makes every cumulative
     length equal to round-half-away of the exact cumulative sum; |e| <= 1/2."""
