@@ -433,6 +433,10 @@ def run_ours(args, ws, rank, local):
                    sample=f"first {args.cpu_series} series of the workload ({len(xs)} points), one pass; "
                           f"compression on {threads} threads, digitization serial")
 
+    flips = None
+    if rank == 0 and not args.no_cpu_baseline:
+        flips = flip_count(pl, x_host.numpy(), cfg, args.cpu_series)
+
     if args.verify and rank == 0:
         verify_sample(pl, x_host.numpy(), off_np, cfg, args.verify)
     sweep = partition_sweep(jb, synth, local) if args.partition_sweep and rank == 0 else None
@@ -496,6 +500,7 @@ def run_ours(args, ws, rank, local):
                                 l2="input 8 B/point >> L2 (no flush needed)" if 8 * n > 2e9 else "input fits L2",
                                 form=form, tuning=inflight["tuning"] if inflight else tuning),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, plain=plain, single_batch=single, clocks=clocks,
+                    breakpoint_flips=flips,
                     gpu_launches=kernels_per_step * args.steps,
                     stage_ms=dict(compress=float(np.mean(comp_ms)), finish=float(np.mean(fin_ms)),
                                   local=float(np.mean(loc_ms)), merge=float(np.mean(mrg_ms)),
@@ -598,6 +603,32 @@ def partition_sweep(jb, synth, local, steps=20):
                          mse=mse, gpu_ms=float(np.median(ts)), oracle_1thread_ms=1e3 * t_cpu))
         del pl, g, c
     return rows
+
+
+def flip_count(pl, x, cfg, n_series):
+    """Breakpoint flips of the GPU's pieces against Eq. 1 read literally (the
+    plain sequential sum of squared residuals, oracle) on the domains of the
+    first n_series series: the library decides Eq. 1 in its L^2-scaled exact
+    form, and the two may differ only where the error lies within rounding of
+    the bound.  Counts the flips and the largest |err - bound| / bound."""
+    import oracle
+    b = pl.b
+    S = min(n_series, pl.S)
+    Ds = int(b["series_dom_off"][S].item())
+    db = b["dom_begin"][:Ds].cpu().numpy()
+    de = b["dom_end"][:Ds].cpu().numpy()
+    so = b["dom_slot_off"][:Ds].cpu().numpy()
+    cnt = b["dom_piece_cnt"][:Ds].cpu().numpy().astype(np.int64)
+    end = int(so[-1] + cnt[-1]) if Ds else 0
+    plen = b["piece_len"][:end].cpu().numpy()
+    ln = np.concatenate([plen[so[d]:so[d] + cnt[d]] for d in range(Ds)]) if Ds else np.zeros(0, np.int32)
+    po = np.concatenate([[0], np.cumsum(cnt)])
+    r = oracle.breakpoint_flips(x, db, de, ln, po, cfg["tol"], threads=os.cpu_count() or 1)
+    gaps = [abs(err - bound) / bound for _, _, err, bound in r["flips"] if bound > 0]
+    return dict(flips=len(r["flips"]), pieces_checked=r["pieces"], max_rel_gap=max(gaps) if gaps else None,
+                rule="|err - bound| < 1e-12 bound at every flip",
+                rule_holds=all(g < 1e-12 for g in gaps) and all(bd > 0 for _, _, _, bd in r["flips"]),
+                sample=f"domains of the first {S} series ({Ds} domains)")
 
 
 def verify_sample(pl, x, off, cfg, n_dom):

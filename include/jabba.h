@@ -100,6 +100,17 @@ const char* jabba_version(void);
  * clear it. */
 jabba_status jabba_sync_status(jabba_ctx* ctx, jabba_stream stream);
 
+/* Poll limit of the context's bounded device-side waits (no counterpart in
+ * the paper): the compression's waits for its staged series chunks, the
+ * merge sort's look-back and the merge rounds' grid barrier each give up
+ * after `polls` unsuccessful polls, set JABBA_ERR_TIMEOUT and leave their
+ * kernel (the compression still lets its copies in flight land first).
+ * 0 restores the default (2^26 polls, far beyond any wait that can end).
+ * Synchronizes the device; kernels read the limit when they start.  Meant
+ * for tests of the timeout path: a small limit makes waits that would have
+ * ended give up. */
+jabba_status jabba_set_spin_limit(jabba_ctx* ctx, uint32_t polls);
+
 /* Host-side planning (Alg. 1 Phase I): number of domains, of slots (total
  * intervals) and the largest domain (in intervals) for
  * series_off_host[n_series+1].  max_dom_intervals may be NULL. */
@@ -118,10 +129,19 @@ jabba_status jabba_reserve(jabba_ctx* ctx, int64_t n_points, int64_t n_series, i
  * Builds the domain table (Alg. 1 Phase I, Sec. 4.1.1: consecutive domains of
  * one series share an endpoint, s_{k+1} = e_k) and compresses every domain
  * independently (Sec. 3.1 Eq. 1, greedy extension): from start s the end e
- * grows while the next end is admissible,
- *     sum_{k=1}^{L-1} ((x_s + (inc * k) / L) - x_{s+k})^2 <= (L - 1) * (tol * tol),
- * L = e - s, inc = x_e - x_s (FP64, evaluated in that order), and stops at the
- * first inadmissible end.  A piece is (len = L, inc).
+ * grows while the next end is admissible and stops at the first inadmissible
+ * end.  Admissibility is Eq. 1 multiplied through by L^2 (the same criterion
+ * in exact arithmetic, with no division):
+ *     sum_{k=1}^{L-1} n_k^2 <= ((L - 1) * (tol * tol)) * (L * L),
+ *     n_k = ((x_s * L) + (inc * k)) - (x_{s+k} * L),
+ * L = e - s, inc = x_e - x_s; every n_k and n_k * n_k is a binary64 operation
+ * in that order (no fused multiply-add), the squares are summed EXACTLY
+ * (each truncated to a multiple of 2^-96, summed as an integer, the total
+ * rounded once to nearest-even), so the sum has no summation order.  Eq. 1
+ * read literally (residuals (x_s + (inc * k) / L) - x_{s+k} summed in
+ * ascending k, compared with (L - 1) * (tol * tol)) agrees with this except
+ * where the error lies within rounding of the bound.  A piece is
+ * (len = L, inc).
  * Outputs (device):
  *   dom_begin, dom_end [n_domains]  inclusive global indices into x
  *   dom_series [n_domains]          series of each domain
@@ -362,7 +382,12 @@ jabba_status jabba_set_tuning(jabba_ctx* ctx, const jabba_tuning* in);
  * calls that overlap on the GPU (different streams, concurrent host threads)
  * race and must be serialized by the caller.  Arguments as for
  * jabba_reconstruct, plus n_pieces (host value, the number of compact
- * symbols) and round_mode. */
+ * symbols) and round_mode.  The kernels also check on the device that every
+ * series' first piece dom_piece_off[series_dom_off[s]] lies in [0, n_pieces]
+ * (so an understated n_pieces cannot make them write past the scratch or
+ * qlen); when it does not, the call writes nothing and records
+ * JABBA_ERR_CAPACITY in a status word that jabba_reconstruct_noalloc_status
+ * returns. */
 #define JABBA_NOALLOC_MAX_PIECES (1 << 18)
 #define JABBA_NOALLOC_MAX_SERIES (1 << 14)
 jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_points, const int64_t* series_off,
@@ -370,6 +395,11 @@ jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_points, const 
                                        const int64_t* dom_piece_off, int64_t n_pieces, const int32_t* symbol,
                                        const double* dict_len, const double* dict_inc, int32_t round_mode,
                                        int32_t* qlen, double* xhat, jabba_stream stream);
+/* Synchronize `stream` and return (and clear) the status word of the
+ * allocation-free reconstruction on the current device: JABBA_OK, or
+ * JABBA_ERR_CAPACITY when a call since the last query failed its device-side
+ * bounds check (that call wrote no output). */
+jabba_status jabba_reconstruct_noalloc_status(jabba_stream stream);
 
 #ifdef __cplusplus
 }

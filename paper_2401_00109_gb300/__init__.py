@@ -119,12 +119,14 @@ def load():
                 "jabba_profile_slot": (C.c_int, [V, C.c_int]),
                 "jabba_diagnostics": (C.c_int, [V, C.POINTER(C.c_int64), C.c_int]),
                 "jabba_reconstruct_noalloc": (C.c_int, [V, I64, V, I64, V, V, I64, V, V, V, C.c_int32, V, V, V]),
+                "jabba_reconstruct_noalloc_status": (C.c_int, [V]),
                 "jabba_profile_elapsed": (C.c_int, [V, C.c_int, C.c_int, C.POINTER(C.c_float)]),
                 "jabba_autotune": (C.c_int, [V, C.c_int]),
                 "jabba_reassign": (C.c_int, [V, V, V, V, V, V, I64, V, V, V, V, I64, C.POINTER(_Params), V, V]),
                 "jabba_sse": (C.c_int, [V, V, V, V, V, V, I64, V, V, V, V, C.POINTER(_Params), V, V]),
                 "jabba_get_tuning": (C.c_int, [V, C.POINTER(_Tuning)]),
                 "jabba_set_tuning": (C.c_int, [V, C.POINTER(_Tuning)]),
+                "jabba_set_spin_limit": (C.c_int, [V, C.c_uint32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -180,6 +182,14 @@ class Context:
 
     def sync_status(self, stream=None, where: str = "device"):
         _check(self.lib.jabba_sync_status(self.h, self._stream(stream)), where)
+
+    def status(self, stream=None) -> int:
+        """Synchronize and return (and clear) the device status code."""
+        return int(self.lib.jabba_sync_status(self.h, self._stream(stream)))
+
+    def set_spin_limit(self, polls: int):
+        """Poll limit of the bounded device waits (0 = the default)."""
+        _check(self.lib.jabba_set_spin_limit(self.h, int(polls)), "jabba_set_spin_limit")
 
     @staticmethod
     def plan(series_off_host: np.ndarray, p: Params, with_max: bool = False):
@@ -454,26 +464,40 @@ NOALLOC_MAX_PIECES = 1 << 18
 NOALLOC_MAX_SERIES = 1 << 14
 
 
-def reconstruct_noalloc(x, series_off, out: dict, p: Params, qlen=None, xhat=None, dict_inc=None, stream=None):
+def reconstruct_noalloc(x, series_off, out: dict, p: Params, qlen=None, xhat=None, dict_inc=None, stream=None,
+                        n_pieces=None):
     """jabba_reconstruct_noalloc: the reconstruction without a context and
     without any device allocation by the library (fixed internal scratch;
     at most NOALLOC_MAX_PIECES pieces and NOALLOC_MAX_SERIES series).  The
     output buffers may be passed in (qlen, xhat) so that nothing is
-    allocated on this path at all."""
+    allocated on this path at all.  n_pieces overrides the piece count passed
+    to the library (the device-side bounds check is tested with it)."""
     torch = _torch()
     L = load()
-    s = torch.cuda.current_stream(x.device) if stream is None else stream
-    N = int(out["n_pieces"])
-    if qlen is None:
-        qlen = torch.empty(max(N, 1), dtype=torch.int32, device=x.device)
-    if xhat is None:
-        xhat = torch.empty_like(x)
-    di = out["dict_inc"] if dict_inc is None else dict_inc
-    _check(L.jabba_reconstruct_noalloc(
-        _ptr(x), x.numel(), _ptr(series_off), out["n_series"], _ptr(out["series_dom_off"]), _ptr(out["dom_piece_off"]),
-        N, _ptr(out["symbol"]), _ptr(out["dict_len"]), _ptr(di), int(p.round_mode), _ptr(qlen), _ptr(xhat),
-        V(s.cuda_stream)), "jabba_reconstruct_noalloc")
+    N = int(out["n_pieces"]) if n_pieces is None else int(n_pieces)
+    # the C call works on the current device: make it the inputs' device
+    with torch.cuda.device(x.device):
+        s = torch.cuda.current_stream(x.device) if stream is None else stream
+        if qlen is None:
+            qlen = torch.empty(max(N, 1), dtype=torch.int32, device=x.device)
+        if xhat is None:
+            xhat = torch.empty_like(x)
+        di = out["dict_inc"] if dict_inc is None else dict_inc
+        _check(L.jabba_reconstruct_noalloc(
+            _ptr(x), x.numel(), _ptr(series_off), out["n_series"], _ptr(out["series_dom_off"]),
+            _ptr(out["dom_piece_off"]), N, _ptr(out["symbol"]), _ptr(out["dict_len"]), _ptr(di), int(p.round_mode),
+            _ptr(qlen), _ptr(xhat), V(s.cuda_stream)), "jabba_reconstruct_noalloc")
     return qlen[:N], xhat
+
+
+def reconstruct_noalloc_status(device=None, stream=None) -> int:
+    """Synchronize and return (and clear) the status word of the
+    allocation-free reconstruction on `device` (0 or ERR_CAPACITY)."""
+    torch = _torch()
+    dev = torch.cuda.current_device() if device is None else device
+    with torch.cuda.device(dev):
+        s = torch.cuda.current_stream(dev) if stream is None else stream
+        return int(load().jabba_reconstruct_noalloc_status(V(s.cuda_stream)))
 
 
 def _autograd_function():

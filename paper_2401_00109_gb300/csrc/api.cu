@@ -358,7 +358,9 @@ jabba_status jabba_create(jabba_ctx** out, int device) {
   jabba_ctx* c = new (std::nothrow) jabba_ctx();
   if (!c) return JABBA_ERR_CUDA;
   c->device = device;
-  if (cudaMalloc(&c->status, sizeof(unsigned)) != cudaSuccess || cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) {
+  // status word and the poll limit of the bounded waits (0 = the default)
+  if (cudaMalloc(&c->status, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->status, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
     delete c;
     return JABBA_ERR_CUDA;
   }
@@ -395,6 +397,14 @@ jabba_status jabba_sync_status(jabba_ctx* c, jabba_stream stream) {
   if (cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) return JABBA_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return JABBA_ERR_CUDA;
   return (jabba_status)h;
+}
+
+jabba_status jabba_set_spin_limit(jabba_ctx* c, uint32_t polls) {
+  if (!c) return JABBA_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return JABBA_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return JABBA_ERR_CUDA;
+  if (cudaMemcpy(c->status + 1, &polls, sizeof(unsigned), cudaMemcpyHostToDevice) != cudaSuccess) return JABBA_ERR_CUDA;
+  return JABBA_OK;
 }
 
 jabba_status jabba_plan(const int64_t* series_off_host, int64_t n_series, const jabba_params* p,

@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_compress(CompressParam
   const long long n_tasks = (P.n_order + 31) / 32;
   LaneState L;
   L.amax = 0;
+  const unsigned lim = spin_limit(P.status);
 
   for (;;) {
     long long task = 0;
@@ -381,12 +382,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_compress(CompressParam
         unsigned spins = 0;
         bool ok = true;
         while (!mbar_try_wait(bar, ph)) {
-          if (++spins > kSpinLimit) { ok = false; break; }
+          if (++spins > lim) { ok = false; break; }
         }
         if (!__all_sync(0xFFFFFFFFu, ok)) {
           set_status(P.status, JABBA_ERR_TIMEOUT);
-          // give the copies still in flight a bounded time to land before the
-          // CTA's shared memory is released
+          // the pieces found so far stay valid (within the domain's slots), so
+          // the kernels after this one read in bounds
+          if (d < P.n_domains) P.dom_piece_cnt[d] = L.cnt;
+          // give the copies still in flight a bounded time (the full limit,
+          // whatever the run-time one) to land before the CTA's shared
+          // memory is released
           unsigned sp = 0;
           while (!mbar_try_wait(bar0, phase0) && ++sp < kSpinLimit) {}
           sp = 0;

@@ -932,12 +932,12 @@ template <int W, int CAP>
 static void launch_tile_one(const LocalParams& P, const int* list, const unsigned* one, unsigned* ctr,
                             cudaStream_t st) {
   using Cfg = TileCfg<W, CAP>;
-  static bool attr = false;
-  if (!attr) {
+  static PerDevice attr;
+  attr.get([] {
     cudaFuncSetAttribute(k_local_tile<W, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((Cfg::kBlock / Cfg::kThreads) * Cfg::kBytes));
-    attr = true;
-  }
+    return 1;
+  });
   k_local_tile<W, CAP><<<1, Cfg::kThreads, Cfg::kBytes, st>>>(P, list, one, ctr);
 }
 
@@ -947,12 +947,13 @@ static void launch_tile(const LocalParams& P, const int* list, const unsigned* c
   using Cfg = TileCfg<W, CAP>;
   constexpr int kBlock = Cfg::kBlock;
   constexpr size_t kSmem = (size_t)(kBlock / Cfg::kThreads) * Cfg::kBytes;
-  static int blocks_per_sm = 0;
-  if (!blocks_per_sm) {
+  static PerDevice occ;
+  const int blocks_per_sm = occ.get([] {
     cudaFuncSetAttribute(k_local_tile<W, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_local_tile<W, CAP>, kBlock, kSmem);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_local_tile<W, CAP>, kBlock, kSmem);
+    return b < 1 ? 1 : b;
+  });
   const int per_sm = cap_per_sm > 0 && cap_per_sm < blocks_per_sm ? cap_per_sm : blocks_per_sm;
   k_local_tile<W, CAP><<<(unsigned)(num_sms * per_sm), kBlock, kSmem, st>>>(P, list, cnt, ctr);
 }

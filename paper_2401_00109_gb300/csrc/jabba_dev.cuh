@@ -18,6 +18,14 @@ __device__ __forceinline__ void set_status(unsigned* st, unsigned code) { atomic
 // Bounded spin limit for every device-side wait (mbarrier phases, flags).
 constexpr unsigned kSpinLimit = 1u << 26;
 
+// The context's status word is followed by the poll limit of its bounded
+// waits (jabba_set_spin_limit; 0 = kSpinLimit).  Kernels that wait read it
+// once at their start.
+__device__ __forceinline__ unsigned spin_limit(const unsigned* status) {
+  const unsigned v = ((volatile const unsigned*)status)[1];
+  return v ? v : kSpinLimit;
+}
+
 // ---------------------------------------------------------------- f64 -> f32 by integer ops
 // Truncating conversion of a binary64 value to binary32 using integer
 // instructions only (this GPU's FP64 and F2F pipes run at ~1/64 of FP32).

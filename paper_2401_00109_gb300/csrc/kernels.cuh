@@ -1,10 +1,34 @@
 // kernels.cuh -- launch interfaces between the C ABI (api.cu) and the CUDA
 // kernels of the JABBA path.
 #pragma once
+#include <mutex>
+
 #include "jabba_dev.cuh"
 #include "scan.cuh"
 
 namespace jabba {
+
+// Per-device, thread-safe one-time set-up of a kernel's launch attributes
+// (dynamic shared-memory limit, occupancy): get(f) runs f() the first time it
+// is reached with a device current and returns f()'s value for that device
+// on every later call.
+struct PerDevice {
+  std::mutex m;
+  unsigned long long done = 0;  // bit d: device d is set up
+  int value[64] = {};
+  template <class F>
+  int get(F f) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    std::lock_guard<std::mutex> lock(m);
+    if (!(done >> dev & 1ull)) {
+      value[dev] = f();
+      done |= 1ull << dev;
+    }
+    return value[dev];
+  }
+};
 
 // Buffers of the global merge (sizes: cap = group capacity, cells = grid cells).
 struct MergeBufs {

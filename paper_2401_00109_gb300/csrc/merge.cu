@@ -271,7 +271,9 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
                                                           const int* flags, unsigned* status_word) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RsSmem& S = *(RsSmem*)smem_raw;
-  const long long n = flags[1] ? 0 : clamp_groups(n_p, cap);
+  // after an error (a look-back of an earlier pass gave up, so the keys no
+  // longer match the digit histograms) the remaining passes do nothing
+  const long long n = (flags[1] || *(volatile unsigned*)status_word) ? 0 : clamp_groups(n_p, cap);
   const int shift = 8 * pass;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) S.tile = atomicAdd(&R.tile_ctr[pass], 1u);
@@ -314,11 +316,12 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
       *(volatile unsigned long long*)mine = rs_word(tag, 1, run);
       long long t = (long long)tile - 1;
       unsigned spins = 0;
+      const unsigned lim = spin_limit(status_word);
       while (t >= 0) {
         const unsigned long long w = vs[t * 256 + d];
         const unsigned wt = (unsigned)(w >> 33), st = (unsigned)(w >> 31) & 3u;
         if (wt != tag || st == 0) {
-          if (++spins > kSpinLimit) { ok = 0; break; }
+          if (++spins > lim) { ok = 0; break; }
           if (spins > 64) __nanosleep(64);
           continue;
         }
@@ -394,11 +397,11 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
                        long long cap, int bits, unsigned* hist_words, int num_sms, unsigned* status_word,
                        unsigned long long** kres, int** vres, const int* flags, cudaStream_t st) {
   const long long n_tiles = (cap + kRsTile - 1) / kRsTile;
-  static bool attr = false;
-  if (!attr) {
+  static PerDevice attr;
+  attr.get([] {
     cudaFuncSetAttribute(k_rs_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem));
-    attr = true;
-  }
+    return 1;
+  });
   // Fixed header (histograms, tile counters, epoch) first, status words after
   // it: the layout does not depend on cap, so the epoch persists across sorts
   // of any size and no status word left by an earlier sort carries a live tag.
@@ -521,6 +524,12 @@ __global__ void k_mcell_end(const int* cell_beg, const long long* n_cells_p, con
     cell_end[j] = j + 1 < nc ? cell_beg[j + 1] : (int)n;
 }
 
+// A bounded wait of the sort or of the rounds gave up: the kernels after it
+// leave the merge outputs alone (flags[1]), as after an earlier error.
+__global__ void k_mflag_status(int* flags, const unsigned* status) {
+  if (*status != 0u) flags[1] = 1;
+}
+
 __global__ void k_clear_i32(int* p, long long n, int v) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -606,8 +615,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned* sub, unsigned nblocks, uns
     }
     if (!released) {
       unsigned spins = 0;
+      const unsigned lim = spin_limit(status);
       while (*gen == g) {
-        if (++spins > kSpinLimit) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
+        if (++spins > lim) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
         __nanosleep(32);
       }
     }
@@ -1530,6 +1540,7 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   // the sort is stable and starts in compact-index order, so ties keep it
   radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws.m_hist, ws.num_sms, status, &skey, &sidx,
              B.flags, st);
+  k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
   k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
   // the cell sort ping-pongs in the buffers the key sort left free
   unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
@@ -1539,6 +1550,7 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   int* cord;
   // cell ids are below cap_cells = 2^23: three 8-bit passes order them
   radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws.m_hist, ws.num_sms, status, &ckey, &cord, B.flags, st);
+  k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
@@ -1591,14 +1603,11 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   {
     // cooperative launch: every block resident, so the bounded grid barrier can complete
     // (the one-phase kernel in CTAs of 4 or 8 warps, jabba_tuning.merge_warps)
-    static int max_per_sm[3] = {-1, -1, -1};  // k_mrounds, k_mrounds1<8>, k_mrounds1<4>
-    if (max_per_sm[0] < 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm[0], k_mrounds, 256, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm[1], k_mrounds1<8>, 256, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm[2], k_mrounds1<4>, 128, 0);
-      for (int i = 0; i < 3; ++i)
-        if (max_per_sm[i] < 1) max_per_sm[i] = 1;
-    }
+    static PerDevice occ[3];  // k_mrounds, k_mrounds1<8>, k_mrounds1<4>
+    const int max_per_sm[3] = {
+        occ[0].get([] { int b = 0; cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mrounds, 256, 0); return b < 1 ? 1 : b; }),
+        occ[1].get([] { int b = 0; cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mrounds1<8>, 256, 0); return b < 1 ? 1 : b; }),
+        occ[2].get([] { int b = 0; cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mrounds1<4>, 128, 0); return b < 1 ? 1 : b; })};
     const int form = ws.tune.merge_form == 1 ? (ws.tune.merge_warps == 4 ? 2 : 1) : 0;
     int blocks_per_sm = ws.tune.merge_ctas_per_sm;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
@@ -1623,6 +1632,7 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
     else cudaLaunchKernelEx(&cfg, k_mrounds, R);
     mark(mk.a1, st);
   }
+  k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
   k_mcheck<<<grid, 256, 0, st>>>(B.state, B.head_off + cap, B.flags, status);
   k_clear_i32<<<grid, 256, 0, st>>>(B.is_start, cap, 0);
   k_mlabel<<<grid, 256, 0, st>>>(V, cord, B.cX, B.cY, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab,
@@ -1680,10 +1690,14 @@ __global__ void k_bf_count(const long long* dom_piece_off, long long n_domains, 
 
 // Pieces in key order (block order) and the blocks' ranges.
 __global__ void k_bf_gather(const int* sidx, const int* clen, const double* cinc, long long n, long long B, long long M,
-                            int* order, int* blen, double* binc, long long* blk_off, int* blk_cnt) {
+                            int* order, int* blen, double* binc, long long* blk_off, int* blk_cnt,
+                            const unsigned* status) {
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+  // after an error the sort's output may be incomplete: the identity order
+  // keeps every later index in bounds
+  const bool err = *status != 0u;
   for (long long i = i0; i < n; i += step) {
-    const int c = sidx[i];
+    const int c = err ? (int)i : sidx[i];
     order[i] = c;
     blen[i] = clen[c];
     binc[i] = cinc[c];
@@ -1753,7 +1767,8 @@ void launch_block_order(const int* piece_len, const double* piece_inc, const lon
   if (n > 0)
     radix_sort(S.k0, S.v0, S.k1, S.v1, S.n_dev, n, 64, S.hist, num_sms, status, &skey, &sidx, S.flags, st);
   const long long B = n > 0 ? (n + n_blocks - 1) / n_blocks : 1;
-  k_bf_gather<<<grid, 256, 0, st>>>(sidx, S.clen, S.cinc, n, B, n_blocks, order, blen, binc, blk_off, blk_cnt);
+  k_bf_gather<<<grid, 256, 0, st>>>(sidx, S.clen, S.cinc, n, B, n_blocks, order, blen, binc, blk_off, blk_cnt,
+                                    status);
 }
 
 void launch_block_items(const int* local_label, const long long* blk_off, const int* blk_cnt,

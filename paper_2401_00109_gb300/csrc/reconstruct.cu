@@ -15,11 +15,14 @@ __global__ void k_series_piece_off(const long long* series_dom_off, const long l
 // Sequential pass per series (one thread): quantization with the carry
 // v = l~ + e, l^ = round(v), e = v - l^ (Sec. 3.3), and the chain's level and
 // position before each piece.  With qlen_in given, the lengths are taken as
-// they are (the adjoint holds them fixed).
+// they are (the adjoint holds them fixed).  A non-null `skip` pointing to a
+// nonzero word makes the kernel do nothing (the allocation-free entry point's
+// device-side bounds check failed).
 __global__ void k_recon_seq(const double* x, const long long* series_off, long long n_series, const long long* spo,
                             const int* symbol, const double* dict_len, const double* dict_inc, int round_mode,
                             const int* qlen_in, int* qlen_out, double* level_out, long long* pos_out,
-                            long long* tail_pos, double* tail_level) {
+                            long long* tail_pos, double* tail_level, const unsigned* skip) {
+  if (skip && *skip) return;
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n_series;
        s += (long long)gridDim.x * blockDim.x) {
     const long long o = series_off[s];
@@ -63,8 +66,9 @@ __device__ __forceinline__ long long find_series(const long long* spo, long long
 
 // Inverse compression, one thread per piece: xhat[pos + q] = level + (i~ q) / l^.
 __global__ void k_recon_fill(const long long* series_off, long long n_series, const long long* spo,
-                             long long n_pieces_hint, const int* symbol, const double* dict_inc, const int* qlen,
+                             const unsigned* skip, const int* symbol, const double* dict_inc, const int* qlen,
                              const double* level, const long long* pos, double* xhat) {
+  if (skip && *skip) return;
   const long long N = spo[n_series];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
     const long long s = find_series(spo, n_series, j);
@@ -74,12 +78,12 @@ __global__ void k_recon_fill(const long long* series_off, long long n_series, co
     const long long p = pos[j];
     for (int q = 1; q <= L && p + q <= n_s - 1; ++q) xhat[o + p + q] = __dadd_rn(lv, __ddiv_rn(__dmul_rn(inc, (double)q), lh));
   }
-  (void)n_pieces_hint;
 }
 
 // t_0 and the tail after the last piece (final level), one warp per series.
 __global__ void k_recon_ends(const double* x, const long long* series_off, long long n_series,
-                             const long long* tail_pos, const double* tail_level, double* xhat) {
+                             const long long* tail_pos, const double* tail_level, double* xhat, const unsigned* skip) {
+  if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -101,9 +105,10 @@ void launch_reconstruct(const double* x, long long n_points, const long long* se
   k_series_piece_off<<<g, 256, 0, st>>>(series_dom_off, dom_piece_off, n_series, spo);
   k_recon_seq<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(x, series_off, n_series, spo, symbol, dict_len,
                                                                    dict_inc, round_mode, nullptr, qlen, ws.r_level,
-                                                                   ws.r_pos, ws.r_tailpos, ws.r_tail_level);
-  k_recon_fill<<<g, 256, 0, st>>>(series_off, n_series, spo, 0, symbol, dict_inc, qlen, ws.r_level, ws.r_pos, xhat);
-  k_recon_ends<<<g, 256, 0, st>>>(x, series_off, n_series, ws.r_tailpos, ws.r_tail_level, xhat);
+                                                                   ws.r_pos, ws.r_tailpos, ws.r_tail_level, nullptr);
+  k_recon_fill<<<g, 256, 0, st>>>(series_off, n_series, spo, nullptr, symbol, dict_inc, qlen, ws.r_level, ws.r_pos,
+                                  xhat);
+  k_recon_ends<<<g, 256, 0, st>>>(x, series_off, n_series, ws.r_tailpos, ws.r_tail_level, xhat, nullptr);
   (void)n_points;
 }
 
@@ -172,7 +177,7 @@ void launch_reconstruct_backward(const double* x, long long n_points, const long
   k_series_piece_off<<<g, 256, 0, st>>>(series_dom_off, dom_piece_off, n_series, spo);
   k_recon_seq<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(x, series_off, n_series, spo, symbol, nullptr,
                                                                    dict_inc, 0, qlen, nullptr, ws.r_level, ws.r_pos,
-                                                                   ws.r_tailpos, ws.r_tail_level);
+                                                                   ws.r_tailpos, ws.r_tail_level, nullptr);
   k_grad_piece<<<g, 256, 0, st>>>(x, series_off, n_series, spo, symbol, dict_inc, qlen, ws.r_level, ws.r_pos,
                                    ws.r_tsum, ws.r_wsum);
   k_grad_tail<<<g, 256, 0, st>>>(x, series_off, n_series, ws.r_tailpos, ws.r_tail_level, ws.r_tail);
@@ -242,8 +247,10 @@ namespace {
 constexpr long long kNaPieces = JABBA_NOALLOC_MAX_PIECES;
 constexpr long long kNaSeries = JABBA_NOALLOC_MAX_SERIES;
 // layout (8-byte words): level[kNaPieces] | pos[kNaPieces] | spo[kNaSeries + 1] |
-// tail_pos[kNaSeries] | tail_level[kNaSeries]
-constexpr long long kNaWords = 2 * kNaPieces + 3 * (kNaSeries + 1);
+// tail_pos[kNaSeries] | tail_level[kNaSeries] | flags (status word of the
+// bounds check, sticky until read by jabba_reconstruct_noalloc_status; the
+// skip word of the current call)
+constexpr long long kNaWords = 2 * kNaPieces + 3 * (kNaSeries + 1) + 1;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNaWords];
 
@@ -268,7 +275,39 @@ cudaError_t noalloc_scratch(unsigned long long** out) {
   return cudaSuccess;
 }
 
+// Device-side bounds check of one call: every piece offset spo[s] of the
+// n_series + 1 series boundaries must lie in [0, n_pieces] (n_pieces <=
+// kNaPieces was checked on the host), so that the pieces the kernels visit,
+// j in [spo[s], spo[s+1]), index the scratch and qlen in bounds.  Otherwise
+// the call's kernels skip all their work and the sticky status word records
+// JABBA_ERR_CAPACITY.  One CTA.
+__global__ void k_na_guard(const long long* spo, long long n_series, long long n_pieces, unsigned* flags) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (long long s = threadIdx.x; s <= n_series; s += blockDim.x) {
+    const long long v = spo[s];
+    if (v < 0 || v > n_pieces) bad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    flags[1] = bad ? 1u : 0u;
+    if (bad) atomicCAS(&flags[0], 0u, (unsigned)JABBA_ERR_CAPACITY);
+  }
+}
+
 }  // namespace
+
+extern "C" jabba_status jabba_reconstruct_noalloc_status(jabba_stream stream) {
+  unsigned long long* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return JABBA_ERR_CUDA;
+  unsigned* flags = (unsigned*)(base + kNaWords - 1);
+  unsigned h = 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return JABBA_ERR_CUDA;
+  if (cudaMemcpy(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return JABBA_ERR_CUDA;
+  if (h && cudaMemset(flags, 0, sizeof(unsigned)) != cudaSuccess) return JABBA_ERR_CUDA;
+  return (jabba_status)h;
+}
 
 extern "C" jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_points, const int64_t* series_off,
                                                   int64_t n_series, const int64_t* series_dom_off,
@@ -290,6 +329,7 @@ extern "C" jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_poi
   long long* spo = (long long*)(base + 2 * kNaPieces);
   long long* tail_pos = spo + (kNaSeries + 1);
   double* tail_level = (double*)(tail_pos + kNaSeries);
+  unsigned* flags = (unsigned*)(base + kNaWords - 1);
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -298,11 +338,14 @@ extern "C" jabba_status jabba_reconstruct_noalloc(const double* x, int64_t n_poi
   // every scratch entry these kernels read is written earlier in the same call
   k_series_piece_off<<<g, 256, 0, st>>>((const long long*)series_dom_off, (const long long*)dom_piece_off, n_series,
                                         spo);
+  k_na_guard<<<1, 256, 0, st>>>(spo, n_series, n_pieces, flags);
   k_recon_seq<<<(unsigned)((n_series + 127) / 128), 128, 0, st>>>(x, (const long long*)series_off, n_series, spo,
                                                                    symbol, dict_len, dict_inc, round_mode, nullptr,
-                                                                   qlen, level, pos, tail_pos, tail_level);
-  k_recon_fill<<<g, 256, 0, st>>>((const long long*)series_off, n_series, spo, 0, symbol, dict_inc, qlen, level, pos,
-                                  xhat);
-  k_recon_ends<<<g, 256, 0, st>>>(x, (const long long*)series_off, n_series, tail_pos, tail_level, xhat);
-  return cudaGetLastError() == cudaSuccess ? JABBA_OK : JABBA_ERR_CUDA;
+                                                                   qlen, level, pos, tail_pos, tail_level, flags + 1);
+  k_recon_fill<<<g, 256, 0, st>>>((const long long*)series_off, n_series, spo, flags + 1, symbol, dict_inc, qlen,
+                                  level, pos, xhat);
+  k_recon_ends<<<g, 256, 0, st>>>(x, (const long long*)series_off, n_series, tail_pos, tail_level, xhat, flags + 1);
+  // a launch error is reported without being cleared (cudaGetLastError would
+  // also consume an error left pending by someone else's earlier work)
+  return cudaPeekAtLastError() == cudaSuccess ? JABBA_OK : JABBA_ERR_CUDA;
 }

@@ -1,8 +1,14 @@
 """Helpers shared by the GPU tests: run the CUDA path through the C ABI and
-bring its outputs back to the host in the oracle's (compact) layout."""
+bring its outputs back to the host in the oracle's (compact) layout; count
+breakpoint flips against Eq. 1 read literally; check a dictionary against
+exact means of its pieces on the device."""
 import numpy as np
 
 import oracle
+
+# (label, pieces checked, flips) of every flip check of the session; the
+# terminal summary (conftest.py) prints them.
+FLIP_LOG = []
 
 
 def ctx():
@@ -89,3 +95,64 @@ def assert_parity(g, r, recon=True):
         scale = max(1.0, float(np.abs(r["xhat"]).max()))
         assert np.abs(g["xhat"] - r["xhat"]).max() <= 1e-9 * scale
         assert abs(g["mse"] - r["mse"]) <= 1e-9 * max(r["mse"], 1e-300)
+
+
+def check_flips(label, x, dom_begin, dom_end, piece_len, dom_piece_off, tol, threads=16):
+    """Breakpoint flips of a GPU chain against Eq. 1 read literally (the
+    plain sequential sum of squared residuals): the library decides Eq. 1 in
+    its L^2-scaled exact form, which agrees except where the error lies within
+    rounding of the bound.  Every flip must have |err - bound| < 1e-12 bound;
+    the count is logged."""
+    r = oracle.breakpoint_flips(x, dom_begin, dom_end, piece_len, dom_piece_off, tol, threads=threads)
+    for s0, t, err, bound in r["flips"]:
+        assert abs(err - bound) < 1e-12 * bound, (label, s0, t, err, bound)
+    FLIP_LOG.append((label, r["pieces"], len(r["flips"])))
+    return r
+
+
+def _fx_chunks(torch, v):
+    """trunc(|v| * 2^64) of float64 values |v| < 2^32 as three 32-bit chunks
+    (int64 tensors, low first) and the sign, by integer operations only."""
+    f, e = torch.frexp(v.abs())                         # |v| = f 2^e, f in [0.5, 1)
+    m = torch.ldexp(f, torch.full_like(e, 53)).to(torch.int64)   # 53-bit integer mantissa
+    s = e.to(torch.int64) + 11                           # |v| 2^64 = m 2^s
+    zero = m == 0
+    mask = (1 << 32) - 1
+    out = []
+    for i in range(3):
+        sh = s - 32 * i
+        left = torch.clamp(sh, 0, 31)
+        keep = torch.bitwise_left_shift(torch.ones_like(m), 32 - left) - 1
+        c_left = torch.bitwise_left_shift(torch.bitwise_and(m, keep), left)
+        c_right = torch.bitwise_and(torch.bitwise_right_shift(m, torch.clamp(-sh, 0, 63)), mask)
+        c = torch.where(sh >= 32, torch.zeros_like(m), torch.where(sh >= 0, c_left, c_right))
+        out.append(torch.where(zero, torch.zeros_like(m), c))
+    return out, v < 0
+
+
+def check_dictionary_exact(piece_len, piece_inc, symbol, dict_len, dict_inc, dict_count):
+    """Every dictionary entry is the exact mean of the pieces that carry its
+    symbol (device tensors, compact layout): count, length sum (integers) and
+    the increment sum at 2^-64 (each term truncated toward zero, summed as an
+    integer, rounded once to binary64), then lensum / count and
+    round(sum inc) / count in binary64.  Sums over all pieces on the device."""
+    import torch
+    k = dict_count.numel()
+    sym = symbol.long()
+    cnt = torch.bincount(sym, minlength=k)
+    assert torch.equal(cnt, dict_count), "dictionary counts"
+    lensum = torch.zeros(k, dtype=torch.int64, device=sym.device).index_add_(0, sym, piece_len.long())
+    assert torch.equal(lensum.double() / cnt.double(), dict_len), "dictionary lengths"
+    chunks, neg = _fx_chunks(torch, piece_inc)
+    sums = []
+    for c in chunks:
+        signed = torch.where(neg, -c, c)
+        sums.append(torch.zeros(k, dtype=torch.int64, device=sym.device).index_add_(0, sym, signed).cpu().numpy())
+    cnt_h = cnt.cpu().numpy()
+    want = np.empty(k)
+    for j in range(k):
+        tot = int(sums[0][j]) + (int(sums[1][j]) << 32) + (int(sums[2][j]) << 64)
+        want[j] = (float(tot) * 2.0**-64) / float(cnt_h[j])     # int -> float rounds to nearest even
+    got = dict_inc.cpu().numpy()
+    bad = np.nonzero(want != got)[0]
+    assert len(bad) == 0, ("dictionary increments", len(bad), bad[:5])

@@ -101,3 +101,18 @@ def test_binding_signatures_match_the_header():
         assert len(f.argtypes) == n, (name, len(f.argtypes), n)
         checked += 1
     assert checked >= 20
+
+
+def test_noalloc_limits_match_the_header():
+    """The Python-side limits of the allocation-free reconstruction are the
+    header's #defines (the binding rejects nothing the library would accept
+    and the other way round)."""
+    import paper_2401_00109_gb300 as jb
+    src = open(os.path.join(ROOT, "include", "jabba.h")).read()
+    vals = {}
+    for name in ("JABBA_NOALLOC_MAX_PIECES", "JABBA_NOALLOC_MAX_SERIES"):
+        m = re.search(r"#define\s+" + name + r"\s+\(?\s*1\s*<<\s*(\d+)\s*\)?", src)
+        assert m, name
+        vals[name] = 1 << int(m.group(1))
+    assert jb.NOALLOC_MAX_PIECES == vals["JABBA_NOALLOC_MAX_PIECES"]
+    assert jb.NOALLOC_MAX_SERIES == vals["JABBA_NOALLOC_MAX_SERIES"]

@@ -151,6 +151,8 @@ def test_uneven_full():
     gl, gi, _ = _compact_pieces(h)
     assert np.array_equal(po, h["dom_piece_off"])
     assert np.array_equal(ln, gl) and np.array_equal(inc, gi)
+    from _gpu import check_flips
+    check_flips("uneven full size", x, b, e, gl, h["dom_piece_off"], cfg["tol"])
     sl, si = oracle.sigma(ln, inc)
     assert (sl, si) == (float(h["sigma"][0]), float(h["sigma"][1]))
     # Stage I on sampled domains
@@ -165,17 +167,78 @@ def test_uneven_full():
     _check_merge(h, cfg)
 
 
-def test_scale_full_sampled():
+def _records_by_compact(h):
+    """Row of each group record, indexed by compact group index."""
+    comp = h["dom_group_off"][h["g_domain"]] + h["g_local"]
+    rec = np.empty(h["G"], np.int64)
+    rec[comp] = np.arange(h["G"])
+    return rec
+
+
+def _device_compact(pl):
+    """Compact (domain-order) device views of the slotted per-piece arrays."""
+    import torch
+    b = pl.b
+    D = pl.D
+    cnt = b["dom_piece_cnt"][:D].long()
+    first = torch.repeat_interleave(b["dom_slot_off"][:D], cnt)
+    within = torch.arange(first.numel(), device=first.device) - torch.repeat_interleave(b["dom_piece_off"][:D], cnt)
+    idx = first + within
+    dom = torch.repeat_interleave(torch.arange(D, device=first.device), cnt)
+    return idx, dom
+
+
+def test_scale_full_labels():
+    """The scale-stress workload at full size (100,000 series, 1.44e9 points,
+    182 M pieces): compression of sampled domains equals the oracle's; sigma
+    equals the oracle's over all pieces; Stage I of sampled domains (the
+    GPU's pieces and sigma through the oracle's greedy) gives the same labels
+    and group sums; Stage II satisfies its defining properties; every symbol
+    is the composition l2g[dom_group_off[d] + local_label] (all pieces); every
+    dictionary entry is the exact mean of the pieces carrying its symbol (all
+    pieces); breakpoint flips of the sampled domains against the plain-form
+    Eq. 1 are logged."""
+    import torch
+    from _gpu import check_dictionary_exact, check_flips
     x, off, cfg, pl = _pipeline("scale")
     h = _host(pl)
     rng = np.random.default_rng(1)
     D = len(h["cnt"])
-    for d in rng.choice(D, 400, replace=False):
+    sl, si = float(h["sigma"][0]), float(h["sigma"][1])
+    gl, gi, _ = _compact_pieces(h)
+    assert oracle.sigma(gl, gi) == (sl, si)
+    rec = _records_by_compact(h)
+    sample = np.sort(rng.choice(D, 400, replace=False))
+    for d in sample:
         ln, inc, _ = oracle.compress(x, h["dom_begin"][d:d + 1], h["dom_end"][d:d + 1], cfg["tol"])
         s0 = h["dom_slot_off"][d]
         n = h["cnt"][d]
-        assert np.array_equal(ln, h["piece_len"][s0:s0 + n]) and np.array_equal(inc, h["piece_inc"][s0:s0 + n]), d
-    assert h["dict_count"].sum() == h["dom_piece_off"][-1]
+        pln, pinc = h["piece_len"][s0:s0 + n], h["piece_inc"][s0:s0 + n]
+        assert np.array_equal(ln, pln) and np.array_equal(inc, pinc), d
+        lab, go, gc, gls, gii = oracle.local_aggregate(pln, pinc, np.array([0, n]), sl, si, cfg["alpha"], cfg["scl"])
+        assert np.array_equal(lab, h["local_label"][s0:s0 + n]), d
+        g0, g1 = h["dom_group_off"][d], h["dom_group_off"][d + 1]
+        assert g1 - g0 == len(gc), d
+        rows = rec[g0:g1]
+        assert np.array_equal(h["g_count"][rows], gc) and np.array_equal(h["g_lensum"][rows], gls), d
+        for j, r_ in enumerate(rows):
+            assert _i192(h["g_inc"][r_]) == oracle.fx_value(gii[j]), (d, j)
+    po_s = np.concatenate([[0], np.cumsum(h["cnt"][sample])])
+    ln_s = np.concatenate([h["piece_len"][h["dom_slot_off"][d]:h["dom_slot_off"][d] + h["cnt"][d]] for d in sample])
+    check_flips("scale full size (400 sampled domains)", x, h["dom_begin"][sample], h["dom_end"][sample], ln_s, po_s,
+                cfg["tol"])
+    _check_merge(h, cfg)
+    del h, gl, gi
+    b = pl.b
+    N = int(b["dom_piece_off"][-1].item())
+    k = int(b["k"][0].item())
+    idx, dom = _device_compact(pl)
+    lab = b["local_label"][idx].long()
+    want = b["l2g"][b["dom_group_off"][dom] + lab]
+    assert torch.equal(b["symbol"][:N], want)
+    del lab, want, dom
+    check_dictionary_exact(b["piece_len"][idx], b["piece_inc"][idx], b["symbol"][:N], b["dict_len"][:k],
+                           b["dict_inc"][:k], b["dict_count"][:k])
 
 
 def test_diff_full_adjoint_and_refinement():
@@ -192,6 +255,8 @@ def test_diff_full_adjoint_and_refinement():
     g, out, x, off = run_gpu(C, x_np, off_np, cfg)
     r = run_oracle(x_np, off_np, cfg, threads=16)
     assert_parity(g, r)
+    from _gpu import check_flips
+    check_flips("diff full size", x_np, g["dom_begin"], g["dom_end"], g["piece_len"], g["dom_piece_off"], cfg["tol"])
     p = params(cfg)
     qlen = torch.from_numpy(g["qlen"]).cuda()
     di = out["dict_inc"].clone()
@@ -286,8 +351,9 @@ def test_full_size_bit_exact(name):
     full size: every output of the path and the reconstruction equal the
     oracle's (pieces, sigma, local labels, map, dictionary, symbols, quantized
     lengths bit for bit; reconstruction within 1e-9)."""
-    from _gpu import assert_parity, ctx, run_gpu, run_oracle
+    from _gpu import assert_parity, check_flips, ctx, run_gpu, run_oracle
     x, off, cfg = synth.make(name)
     g, *_ = run_gpu(ctx(), x, off, cfg)
     r = run_oracle(x, off, cfg, threads=16)
     assert_parity(g, r)
+    check_flips(f"{name} full size", x, g["dom_begin"], g["dom_end"], g["piece_len"], g["dom_piece_off"], cfg["tol"])

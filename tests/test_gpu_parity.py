@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from _gpu import assert_parity, ctx, run_gpu, run_oracle
+from _gpu import assert_parity, check_flips, ctx, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +24,8 @@ def test_workload_parity(C, name, max_series):
     r = run_oracle(x, off, cfg)
     assert len(r["piece_len"]) > 0
     assert_parity(g, r)
+    check_flips(f"{name} sample ({max_series or 'all'} series)", x, g["dom_begin"], g["dom_end"], g["piece_len"],
+                g["dom_piece_off"], cfg["tol"])
 
 
 @pytest.mark.parametrize("round_mode", [0, 1])

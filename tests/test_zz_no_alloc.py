@@ -36,8 +36,13 @@ def test_reconstruct_noalloc_matches_reconstruct_twice():
     q_buf = torch.empty(max(out["n_pieces"], 1), dtype=torch.int32, device=x.device)
     x_buf = torch.empty_like(x)
     for call in range(2):
+        torch.cuda.synchronize()
+        before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
         q, xh = jb.reconstruct_noalloc(x, off, out, p, qlen=q_buf, xhat=x_buf)
         torch.cuda.synchronize()
+        if call == 1:  # the first call on a device may load the module (its own one-time set-up)
+            assert (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]) == before
+        assert jb.reconstruct_noalloc_status() == 0
         assert np.array_equal(q.cpu().numpy(), q_ref), call
         assert np.abs(xh.cpu().numpy() - x_ref).max() <= 1e-9 * scale, call
     # a second, different collection through the same shared scratch
@@ -64,3 +69,31 @@ def test_reconstruct_noalloc_rejects_oversize():
                                     jb.NOALLOC_MAX_PIECES + 1, C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), 0,
                                     C.c_void_p(8), C.c_void_p(8), None)
     assert r == jb.ERR_CAPACITY
+
+
+def test_reconstruct_noalloc_checks_piece_offsets_on_the_device():
+    """An understated piece count (the host check passes, the device offsets
+    run past it) is caught on the device: the call writes nothing, the status
+    query returns JABBA_ERR_CAPACITY once, and the next correct call works."""
+    import torch
+    import paper_2401_00109_gb300 as jb
+    x_np, off_np, cfg = synth.make("small", max_series=6)
+    p = jb.Params(tol=cfg["tol"], alpha=cfg["alpha"], scl=cfg["scl"], domain_mode=cfg["domain_mode"],
+                  domain_value=cfg["domain_value"])
+    ctx = jb.Context()
+    x = torch.from_numpy(x_np).cuda()
+    off = torch.from_numpy(off_np).cuda()
+    out = ctx.symbolize(x, off, p, series_off_host=off_np)
+    N = out["n_pieces"]
+    q_ref, x_ref = ctx.reconstruct(x, off, out, p)
+    ctx.sync_status(where="reference reconstruction")
+    assert jb.reconstruct_noalloc_status() == 0
+    q_buf = torch.full((N,), -7, dtype=torch.int32, device=x.device)
+    x_buf = torch.full_like(x, 123.0)
+    jb.reconstruct_noalloc(x, off, out, p, qlen=q_buf, xhat=x_buf, n_pieces=N // 2)
+    assert jb.reconstruct_noalloc_status() == jb.ERR_CAPACITY
+    assert jb.reconstruct_noalloc_status() == 0
+    assert bool((q_buf == -7).all()) and bool((x_buf == 123.0).all())
+    q, xh = jb.reconstruct_noalloc(x, off, out, p, qlen=q_buf, xhat=x_buf)
+    assert jb.reconstruct_noalloc_status() == 0
+    assert torch.equal(q, q_ref) and float((xh - x_ref).abs().max()) <= 1e-9 * max(1.0, float(x_ref.abs().max()))
