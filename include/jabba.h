@@ -108,7 +108,8 @@ jabba_status jabba_sync_status(jabba_ctx* ctx, jabba_stream stream);
  * 0 restores the default (2^26 polls, far beyond any wait that can end).
  * Synchronizes the device; kernels read the limit when they start.  Meant
  * for tests of the timeout path: a small limit makes waits that would have
- * ended give up. */
+ * ended give up (below 1024 the compression polls without suspending, so
+ * each poll returns at once). */
 jabba_status jabba_set_spin_limit(jabba_ctx* ctx, uint32_t polls);
 
 /* Host-side planning (Alg. 1 Phase I): number of domains, of slots (total

@@ -96,6 +96,7 @@ void launch_build_domains(const long long* series_off, long long n_series, int m
 // lengths no longer exact) take the exact path at every point.
 // Otherwise the whole warp evaluates the binary64 definition for that lane
 // (32 terms at a time, exact fixed-point sum): see warp_exact_admissible.
+constexpr unsigned kQuickPollLimit = 1024;  // run-time poll limits below this poll without suspending
 constexpr int kChunk = 16;                 // points per lane per stage
 constexpr int kRow = kChunk + 2;           // doubles per staged row (16-byte multiple, alignment slack)
 constexpr int kWarpsPerCta = 8;
@@ -180,6 +181,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
   unsigned done;
   asm volatile(
       "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+// Non-blocking poll of the phase (returns at once).
+__device__ __forceinline__ bool mbar_test_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(done) : "r"(bar), "r"(parity) : "memory");
   return done != 0;
 }
@@ -379,9 +388,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_compress(CompressParam
       {
         const unsigned bar = buf ? bar1 : bar0;
         const unsigned ph = buf ? phase1 : phase0;
+        // try_wait may suspend the thread for a while on each poll; under a
+        // small run-time limit (a test of the timeout path) the polls use
+        // test_wait, which returns at once, so the limit bounds the wait
         unsigned spins = 0;
         bool ok = true;
-        while (!mbar_try_wait(bar, ph)) {
+        while (!(lim < kQuickPollLimit ? mbar_test_wait(bar, ph) : mbar_try_wait(bar, ph))) {
           if (++spins > lim) { ok = false; break; }
         }
         if (!__all_sync(0xFFFFFFFFu, ok)) {
