@@ -5,7 +5,7 @@ context usable.
 The context's poll limit (jabba_set_spin_limit) is lowered to one poll, so
 waits that would have ended give up instead:
   - the compression kernel's waits for its staged series chunks (mbarrier
-    phases of the bulk copies);
+    phases of the bulk copies), in the plain one-lane-per-launch form;
   - the merge rounds' grid barrier, on a merge of fewer local groups than one
     sort tile (the sort then has no look-back wait, so the barrier is the only
     wait that runs);
@@ -38,18 +38,22 @@ def _device(x_np, off_np):
 
 
 def test_compression_wait_times_out():
+    """In the plain form (one launch, one CTA and one active lane per domain)
+    each wait follows right after its copy was issued, so with a limit of
+    one poll the first wait of a launch gives up before the chunk lands.  (In
+    the batched form the issue of a warp's 32 copies takes longer than they
+    do to land, so its waits rarely fail; three tries make a miss here very
+    unlikely.)"""
     C = ctx()
-    x_np, off_np, cfg = synth.make("multivar", max_series=16)
+    x_np, off_np, cfg = synth.make("small")
     p = params(cfg)
     x, off = _device(x_np, off_np)
+    C.set_tuning(dict(C.tuning(), per_domain_launch=1))
     C.compress(x, off, p, series_off_host=off_np)
     assert C.status() == 0
     codes = []
     C.set_spin_limit(1)
     try:
-        # a wait gives up when its chunk has not landed after two polls; the
-        # first chunks of ~1,000 warps are requested at once, so some wait
-        # gives up in practice (three tries make a miss very unlikely)
         for _ in range(3):
             C.compress(x, off, p, series_off_host=off_np)
             codes.append(C.status())
@@ -57,6 +61,7 @@ def test_compression_wait_times_out():
                 break
     finally:
         C.set_spin_limit(0)
+        C.set_tuning(dict(C.tuning(), per_domain_launch=0))
     assert ERR_TIMEOUT in codes and set(codes) <= {0, ERR_TIMEOUT}, codes
     _clean_run(C)
 
