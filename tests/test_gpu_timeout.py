@@ -39,11 +39,12 @@ def _device(x_np, off_np):
 
 def test_compression_wait_times_out():
     """In the plain form (one launch, one CTA and one active lane per domain)
-    each wait follows right after its copy was issued, so with a limit of
-    one poll the first wait of a launch gives up before the chunk lands.  (In
-    the batched form the issue of a warp's 32 copies takes longer than they
-    do to land, so its waits rarely fail; three tries make a miss here very
-    unlikely.)"""
+    the first wait of a launch follows right after its copy was issued; with
+    the series out of L2 (a larger buffer written just before) and a limit of
+    one poll it gives up before the chunk lands from HBM.  (Later waits find
+    their chunk already there: it was issued a chunk of work earlier.  In the
+    batched form the issue of a warp's 32 copies takes about as long as they
+    take to land.)  Three tries make a miss very unlikely."""
     C = ctx()
     x_np, off_np, cfg = synth.make("small")
     p = params(cfg)
@@ -52,9 +53,12 @@ def test_compression_wait_times_out():
     C.compress(x, off, p, series_off_host=off_np)
     assert C.status() == 0
     codes = []
+    import torch
+    flush = torch.empty(64 << 20, dtype=torch.float64, device=x.device)   # 512 MB: more than L2
     C.set_spin_limit(1)
     try:
         for _ in range(3):
+            flush.fill_(1.0)  # the series leave L2, so the first chunk of a launch comes from HBM
             C.compress(x, off, p, series_off_host=off_np)
             codes.append(C.status())
             if codes[-1] == ERR_TIMEOUT:
