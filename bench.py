@@ -196,10 +196,9 @@ def roofline_table(workload, n, N, G, D, comp_ms, loc_ms, rnd_ms, rounds_name, p
       local aggregation (tile kernels + routing + group offsets): 12 B per
         piece read (len, inc) + 4 B per piece written (label) + 48 B per group
         record + 12 B per domain (group count and offset);
-      merge rounds + sweep (k_mrounds1 and, after the hand-over round, the
-        pending-item collection, its sort and the one-CTA sweep; or k_mrounds in
-        the two-barrier form): 13 B per local group (its FP32 centre, key-order
-        position and coverage flag, each read once).
+      merge rounds (k_mrounds1, or k_mrounds in the two-barrier form): 13 B per
+        local group (its FP32 centre, key-order position and coverage flag,
+        each read once).
     DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is known for
     the Stage I tiles of the scale workload from one ncu capture of its first
     10,000 series (the five tile launches of a step: 223.2 MB read, 62.6 MB
@@ -420,8 +419,7 @@ def run_ours(args, ws, rank, local):
     # largest stages and the dominant one (roofline_table)
     peak, peak_kind = peaks()
     roofline = roofline_table(args.workload, n, N, G, pl.D, comp_ms, loc_ms, rnd_ms,
-                              ("k_mrounds1 + k_msweep" if ctx.tuning()["merge_sweep_round"] else "k_mrounds1")
-                              if ctx.tuning()["merge_form"] == 1 else "k_mrounds", peak, peak_kind)
+                              "k_mrounds1" if ctx.tuning()["merge_form"] == 1 else "k_mrounds", peak, peak_kind)
     roofline["path_frac_of_point_roofline"] = value / ws / (peak / 8.0)
 
     cpu = None

@@ -329,7 +329,7 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
  * kernels.  Every configuration computes the same results (bit for bit); only
  * the speed differs.  Domains of up to 512 pieces are aggregated by one warp
  * each; larger domains by the number of warps chosen here.
- * Defaults: {2, 1, 4, 4, 4, 0, 1, 0, 1, 8, 128}. */
+ * Defaults: {2, 1, 4, 4, 4, 0, 1, 0, 1, 8}. */
 typedef struct {
   int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
@@ -348,9 +348,6 @@ typedef struct {
                                    starts tested on the fly (default); 0 = two barriers per round, coverage
                                    marked between them                                                       */
   int32_t merge_warps;          /* warps per CTA of the one-barrier rounds kernel: 8 (default) or 4           */
-  int32_t merge_sweep_round;    /* the one-barrier rounds stop after this many rounds and one CTA decides the
-                                   remaining cells by a sweep in key order (the same result); 0 = rounds only;
-                                   0..2^20, default 128                                                      */
 } jabba_tuning;
 
 /* Autotuning mode.  While enabled (enable = 1), each call of jabba_compress,
@@ -361,7 +358,7 @@ typedef struct {
  * compression {1, 2, 3} CTAs per SM x {packed, in order}; local aggregation
  * {1, 4} warps per domain of 513..1024 pieces, {1, 2, 4, 8} of 1025..2048 and
  * {4, 8} of 2049..4096; merge {1, 2, 4} CTAs per SM (x {8, 4} warps per CTA in the
- * one-barrier form), then the sweep round {0, 64, 128, 192, 320}.  Tuning calls must not be captured in a CUDA graph
+ * one-barrier form).  Tuning calls must not be captured in a CUDA graph
  * (JABBA_ERR_STATE).  enable = 0 ends the mode; the choice stays in effect. */
 jabba_status jabba_autotune(jabba_ctx* ctx, int enable);
 /* Current configuration of the context. */

@@ -65,12 +65,11 @@ class _Tuning(C.Structure):
     _fields_ = [("compress_ctas_per_sm", C.c_int32), ("compress_pack", C.c_int32), ("local_mid_warps", C.c_int32),
                 ("local_big_warps", C.c_int32), ("merge_ctas_per_sm", C.c_int32), ("per_domain_launch", C.c_int32),
                 ("local_k_warps", C.c_int32), ("local_ctas_cap", C.c_int32), ("merge_form", C.c_int32),
-                ("merge_warps", C.c_int32), ("merge_sweep_round", C.c_int32)]
+                ("merge_warps", C.c_int32)]
 
 
 TUNING_FIELDS = ("compress_ctas_per_sm", "compress_pack", "local_mid_warps", "local_big_warps", "merge_ctas_per_sm",
-                 "per_domain_launch", "local_k_warps", "local_ctas_cap", "merge_form", "merge_warps",
-                 "merge_sweep_round")
+                 "per_domain_launch", "local_k_warps", "local_ctas_cap", "merge_form", "merge_warps")
 
 JABBA_GROUP_BYTES = 48
 PIECE_STATS_BYTES = 256

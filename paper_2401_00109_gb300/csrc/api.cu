@@ -230,7 +230,6 @@ bool tuning_ok(const jabba_tuning* t) {
   if (t->local_ctas_cap < 0 || t->local_ctas_cap > 16) return false;
   if (t->merge_form != 0 && t->merge_form != 1) return false;
   if (t->merge_warps != 4 && t->merge_warps != 8) return false;
-  if (t->merge_sweep_round < 0 || t->merge_sweep_round > (1 << 20)) return false;
   return true;
 }
 
@@ -614,24 +613,6 @@ jabba_status merge_impl(jabba_ctx* c, const jabba_group* groups, const double* i
     }
     c->ws.tune.merge_ctas_per_sm = best;
     c->ws.tune.merge_warps = best_w;
-    if (c->ws.tune.merge_form == 1) {
-      // then the round after which the sweep takes over (0: rounds only)
-      const int sw[5] = {0, 64, 128, 192, 320};
-      int best_s = c->ws.tune.merge_sweep_round;
-      best_ms = 3.0e38f;
-      for (int i = 0; i < 5; ++i) {
-        c->ws.tune.merge_sweep_round = sw[i];
-        cudaEventRecord(e0, st);
-        run();
-        cudaEventRecord(e1, st);
-        const float ms = elapsed_ms(e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_s = sw[i];
-        }
-      }
-      c->ws.tune.merge_sweep_round = best_s;
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return cuda_ok(cudaGetLastError());
@@ -866,7 +847,6 @@ jabba_status jabba_get_tuning(jabba_ctx* c, jabba_tuning* out) {
   out->local_ctas_cap = t.local_ctas_cap;
   out->merge_form = t.merge_form;
   out->merge_warps = t.merge_warps;
-  out->merge_sweep_round = t.merge_sweep_round;
   return JABBA_OK;
 }
 
@@ -883,7 +863,6 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.local_ctas_cap = in->local_ctas_cap;
   t.merge_form = in->merge_form;
   t.merge_warps = in->merge_warps;
-  t.merge_sweep_round = in->merge_sweep_round;
   return JABBA_OK;
 }
 

@@ -81,8 +81,6 @@ struct Tuning {
   int local_ctas_cap = 0;        // at most this many resident CTAs per SM per local kernel (0: all that fit)
   int merge_form = 1;            // merge rounds: 1 = one barrier per round (coverage tested on the fly), 0 = two
   int merge_warps = 8;           // warps per CTA of the one-barrier rounds kernel (4 or 8)
-  int merge_sweep_round = 128;   // one-barrier rounds hand the undecided cells to the sweep after this many
-                                 // rounds (0: never)
 };
 
 // Events around the local-aggregation kernels of the tiles (tuning only).

@@ -578,13 +578,6 @@ struct RoundArgs {
   unsigned long long* uctr;  // [3] packed new starts << 40 | coverage units (by round mod 3)
   long long slot_stride;     // slots per buffer of s_* (two buffers, by round parity)
   long long item_cap;        // entries of the per-item arrays (cord, cX, cY, cov)
-  // hand-over to the sweep (k_msweep): the rounds stop after round
-  // sweep_round - 1 (0: never) with cells still undecided and set
-  // sweep_flags[0]; a resumed launch (resume = 1) continues the rounds from
-  // round bar[2] when the sweep could not finish (sweep_flags[1])
-  unsigned sweep_round;
-  int resume;
-  int* sweep_flags;
 };
 
 __device__ __forceinline__ unsigned long long ld_state(const unsigned long long* p) {
@@ -1237,7 +1230,6 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
 template <int kWarps>
 __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
   if (R.flags[0] || R.flags[1]) return;
-  if (R.resume && !R.sweep_flags[1]) return;  // the sweep finished: nothing to resume
   __shared__ NbScratch W[kWarps];
   const long long n_cells = *R.n_cells_p;
   const GridGeom g = *R.geom;
@@ -1247,10 +1239,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
   const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
   const size_t stride = (size_t)(n_cells > 0 ? n_cells : 1);
-  // a resumed launch starts where the first one stopped: the round number
-  // keeps growing, so the evaluation stamps of the first launch never match
-  const unsigned round0 = R.resume ? *((volatile unsigned*)&R.bar[2]) : 0u;
-  for (unsigned round = round0; round < R.max_rounds; ++round) {
+  for (unsigned round = 0; round < R.max_rounds; ++round) {
     const int cur = round % 3, nxt = (round + 1) % 3, old = (round + 2) % 3;
     const int* lcur = R.chg_list + (size_t)(round & 1) * stride;
     int* lnxt = R.chg_list + (size_t)((round + 1) & 1) * stride;
@@ -1261,7 +1250,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
     }
     // evaluations (warps from the bottom)
     const long long soff_new = (long long)(round & 1) * R.slot_stride;
-    if (round == round0) {
+    if (round == 0) {
       for (long long j = warp_g; j < n_cells; j += n_warps)
         eval_cell1(R, g, (int)j, round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
     } else {
@@ -1286,319 +1275,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
       if (warp_g == 0 && lane == 0) R.bar[2] = round + 1;  // diagnostics: rounds used
       return;
     }
-    if (R.sweep_round && round + 1 >= R.sweep_round) {  // hand the undecided cells to the sweep
-      if (warp_g == 0 && lane == 0) {
-        R.bar[2] = round + 1;
-        R.sweep_flags[0] = 1;
-      }
-      return;
-    }
   }
   if (warp_g == 0 && lane == 0) set_status(R.status, JABBA_ERR_TIMEOUT);
-}
-
-// ------------------------------------------------------------------ 4c. the sweep
-// Once the rounds have decided the dense interior, the cells still undecided
-// hold few items, and what is left to decide is a thin front of increasing
-// key (norm) that advances by about alpha / 2 per round: hundreds of rounds
-// that each decide a few dozen cells, bound by the latency of a grid-wide
-// round.  The sweep decides them in ONE CTA with its working set in shared
-// memory, in key order:
-//  1. pending items (k_mpend_collect, radix sort, k_mpend_gather): the items
-//     of undecided cells not covered by a decided start that precedes them,
-//     in key order.  Decided starts are final, and no undecided item can
-//     change a decided cell, so the remaining greedy is the sequential greedy
-//     restricted to the pending items;
-//  2. batches of kSwBatch consecutive pending items (k_msweep): an item is
-//     covered when an earlier start of the sweep lies within alpha (the
-//     sweep's starts are kept in a ring in key order, hashed by grid cell;
-//     starts more than alpha below the batch in norm can cover nothing left
-//     and leave the ring); the rest are resolved among themselves by
-//     CTA-local rounds: an item becomes a start once no earlier undecided
-//     item of the batch may lie within alpha, and is covered once an earlier
-//     start of the batch lies within alpha (FP32 filter, binary64 test when
-//     it straddles);
-//  3. a new start sets its cell's state; cells still undecided after the
-//     sweep have no start (k_mfinish_cells).  If the ring overflows, the
-//     sweep stops and the rounds resume from the cells' states.
-constexpr int kSwBatch = 1024;          // pending items per batch (one per thread)
-constexpr int kSwRing = 4096;           // sweep starts kept (ring, key order)
-constexpr int kSwSHash = 8192;          // start hash slots (open addressing on the grid cell)
-constexpr int kSwBHash = 2048;          // batch hash slots (chains)
-constexpr unsigned short kSwEmpty = 0xFFFFu;
-constexpr int kSwUnd = 0, kSwCov = 1, kSwStart = 2;
-
-struct SweepArgs {
-  MergeView V;
-  const int* cord;           // item (sorted position) at cell-order index t
-  const float* cX;           // FP32 coordinates at cell-order index t
-  const float* cY;
-  const int* cell_end;
-  const int* cell_id;
-  const int* cell_of_id;
-  unsigned long long* state;
-  const unsigned char* cov;
-  const long long* n_cells_p;
-  const GridGeom* geom;
-  const int* flags;
-  int* sweep_flags;          // [0] sweep needed (set by the rounds), [1] sweep incomplete (ring overflow)
-  unsigned long long* pk;    // pending: sorted position (sort key)
-  int* pv;                   // pending: cell-order index
-  long long* pn;             // pending count
-  int* qa;                   // pending items in key order: sorted position, cell, FP32 coordinates
-  int* qj;
-  float* qx;
-  float* qy;
-  float alpha_hi;            // alpha rounded up
-};
-
-// Pending items of the undecided cells (one warp per cell), appended in any
-// order: sorted position and cell-order index.
-__global__ void __launch_bounds__(256) k_mpend_collect(SweepArgs A) {
-  if (A.flags[0] || A.flags[1] || !A.sweep_flags[0]) return;
-  __shared__ NbScratch W[8];
-  NbScratch& w = W[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const long long n_cells = *A.n_cells_p;
-  const GridGeom g = *A.geom;
-  const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long j = warp_g; j < n_cells; j += n_warps) {
-    const unsigned long long st = A.state[j];
-    if ((unsigned)st != kUndecided) continue;
-    const int id = A.cell_id[j];
-    const int cx = id % g.ncx, cy = id / g.ncx;
-    // decided starts of the 5 x 5 block
-    int q = -1;
-    if (lane < 25 && lane != 12) {
-      const int xx = cx + lane % 5 - 2, yy = cy + lane / 5 - 2;
-      if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) q = A.cell_of_id[yy * g.ncx + xx];
-    }
-    const unsigned sv = q >= 0 ? (unsigned)A.state[q] : kNoStart;
-    const bool is_s = sv < kNoStart;
-    const unsigned ms = __ballot_sync(0xFFFFFFFFu, is_s);
-    __syncwarp();
-    if (is_s) {
-      const int o = __popc(ms & lt);
-      w.sp[o] = (int)sv;
-      w.sx[o] = A.V.sX[sv];
-      w.sy[o] = A.V.sY[sv];
-    }
-    __syncwarp();
-    const int ns = __popc(ms);
-    const int end = A.cell_end[j];
-    for (int t0 = (int)(st >> 32); t0 < end; t0 += 32) {
-      const int u = t0 + lane;
-      bool pend = false;
-      int r = 0;
-      if (u < end && !__ldcg(&A.cov[u])) {
-        r = A.cord[u];
-        pend = !covered_by_starts(A.V, w, ns, r, A.cX[u], A.cY[u]);
-      }
-      const unsigned mp = __ballot_sync(0xFFFFFFFFu, pend);
-      if (!mp) continue;
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd((unsigned long long*)A.pn, (unsigned long long)__popc(mp));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (pend) {
-        const long long o = (long long)base + __popc(mp & lt);
-        A.pk[o] = (unsigned long long)(unsigned)r;
-        A.pv[o] = u;
-      }
-    }
-  }
-}
-
-// Pending items in key order (after the sort): position, cell, coordinates.
-__global__ void k_mpend_gather(SweepArgs A, const unsigned long long* pk_sorted, const int* pv_sorted) {
-  if (A.flags[0] || A.flags[1] || !A.sweep_flags[0]) return;
-  const long long m = *A.pn;
-  const GridGeom g = *A.geom;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
-    const int t = pv_sorted[i];
-    const float x = A.cX[t], y = A.cY[t];
-    A.qa[i] = (int)pk_sorted[i];
-    A.qx[i] = x;
-    A.qy[i] = y;
-    A.qj[i] = A.cell_of_id[cell_of(g, x, y)];
-  }
-}
-
-__device__ __forceinline__ unsigned sw_hash(int gid) { return (unsigned)gid * 2654435761u; }
-
-struct SweepSmem {
-  float rx[kSwRing], ry[kSwRing], rn[kSwRing];  // ring of the sweep's starts: coordinates, norm
-  int ra[kSwRing], rg[kSwRing];                 // sorted position, grid cell
-  unsigned short sh[kSwSHash];                   // start hash: ring slot or kSwEmpty
-  float bx[kSwBatch], by[kSwBatch];              // batch items
-  int ba[kSwBatch], bg[kSwBatch], bst[kSwBatch], bnext[kSwBatch];
-  int bh[kSwBHash];                              // batch hash: first item of the chain or -1
-  int wsum[32];
-  int r_tail, r_head;
-  float first_nrm;
-};
-
-__global__ void __launch_bounds__(kSwBatch, 1) k_msweep(SweepArgs A) {
-  if (A.flags[0] || A.flags[1] || !A.sweep_flags[0]) return;
-  extern __shared__ __align__(16) unsigned char sw_raw[];
-  SweepSmem& S = *(SweepSmem*)sw_raw;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const long long m = *A.pn;
-  const GridGeom g = *A.geom;
-  const MergeView& V = A.V;
-  if (t == 0) {
-    S.r_tail = 0;
-    S.r_head = 0;
-  }
-  // the first batch's item of this thread; later ones are loaded a batch ahead
-  int na = 0, nj = 0;
-  float nx = 0.f, ny = 0.f;
-  if (t < m) {
-    na = A.qa[t];
-    nj = A.qj[t];
-    nx = A.qx[t];
-    ny = A.qy[t];
-  }
-  for (long long i0 = 0; i0 < m; i0 += kSwBatch) {
-    const long long nb = m - i0 < kSwBatch ? m - i0 : kSwBatch;
-    const bool valid = t < nb;
-    const int a = na, j = nj;
-    const float x = nx, y = ny;
-    if (i0 + kSwBatch + t < m) {
-      const long long k = i0 + kSwBatch + t;
-      na = A.qa[k];
-      nj = A.qj[k];
-      nx = A.qx[k];
-      ny = A.qy[k];
-    }
-    int cx = (int)floorf((x - g.x0) * g.inv_h), cy = (int)floorf((y - g.y0) * g.inv_h);
-    cx = min(max(cx, 0), g.ncx - 1);
-    cy = min(max(cy, 0), g.ncy - 1);
-    const int gid = cy * g.ncx + cx;
-    const float nrm = sqrtf(x * x + y * y);
-    if (t == 0) S.first_nrm = nrm;  // the batch's smallest key
-    __syncthreads();
-    if (t == 0) {
-      // starts more than alpha (with the FP32 rounding margin) below the
-      // batch's first item in norm lie farther than alpha from every item left
-      const float thr = S.first_nrm - A.alpha_hi * (1.0f + 0x1p-10f) - 0x1p-18f * (S.first_nrm + 1.0f);
-      int tl = S.r_tail;
-      while (tl < S.r_head && S.rn[tl & (kSwRing - 1)] < thr) ++tl;
-      S.r_tail = tl;
-    }
-    for (int k = t; k < kSwSHash; k += kSwBatch) S.sh[k] = kSwEmpty;
-    for (int k = t; k < kSwBHash; k += kSwBatch) S.bh[k] = -1;
-    __syncthreads();
-    // live starts into the start hash (one start per grid cell at most)
-    for (int e = S.r_tail + t; e < S.r_head; e += kSwBatch) {
-      const int slot = e & (kSwRing - 1);
-      unsigned h = sw_hash(S.rg[slot]) >> 19;  // 13 bits
-      while (atomicCAS(&S.sh[h], kSwEmpty, (unsigned short)slot) != kSwEmpty) h = (h + 1) & (kSwSHash - 1);
-    }
-    S.bx[t] = x;
-    S.by[t] = y;
-    S.ba[t] = a;
-    S.bg[t] = gid;
-    __syncthreads();
-    // covered by a start of an earlier batch (every such start precedes the item)
-    int status = valid ? kSwUnd : kSwCov;
-    if (valid) {
-      bool cov = false;
-      for (int dy = -2; dy <= 2 && !cov; ++dy) {
-        const int yy = cy + dy;
-        if (yy < 0 || yy >= g.ncy) continue;
-        for (int dx = -2; dx <= 2 && !cov; ++dx) {
-          const int xx = cx + dx;
-          if (xx < 0 || xx >= g.ncx) continue;
-          const int g2 = yy * g.ncx + xx;
-          unsigned h = sw_hash(g2) >> 19;
-          for (;;) {
-            const unsigned short e = S.sh[h];
-            if (e == kSwEmpty) break;
-            if (S.rg[e] == g2) {
-              const int f = filter_c(S.rx[e], S.ry[e], x, y, V.a2lo, V.a2hi);
-              cov = f == 1 || (f == 2 && exact_within_sorted(V, S.ra[e], a));
-              break;
-            }
-            h = (h + 1) & (kSwSHash - 1);
-          }
-        }
-      }
-      if (cov) status = kSwCov;
-    }
-    S.bst[t] = status;
-    if (status == kSwUnd) S.bnext[t] = atomicExch(&S.bh[sw_hash(gid) >> 21], t);  // 11 bits
-    __syncthreads();
-    // CTA-local rounds among the batch's undecided items (the earliest one is
-    // never blocked, so every round decides at least one)
-    volatile int* bst = S.bst;
-    for (;;) {
-      if (valid && bst[t] == kSwUnd) {
-        bool cov = false, blk = false;
-        for (int dy = -2; dy <= 2 && !cov; ++dy) {
-          const int yy = cy + dy;
-          if (yy < 0 || yy >= g.ncy) continue;
-          for (int dx = -2; dx <= 2 && !cov; ++dx) {
-            const int xx = cx + dx;
-            if (xx < 0 || xx >= g.ncx) continue;
-            const int g2 = yy * g.ncx + xx;
-            for (int u = S.bh[sw_hash(g2) >> 21]; u >= 0 && !cov; u = S.bnext[u]) {
-              if (u >= t || S.bg[u] != g2) continue;  // earlier items of that cell only
-              const int su = bst[u];
-              if (su == kSwStart) {
-                const int f = filter_c(S.bx[u], S.by[u], x, y, V.a2lo, V.a2hi);
-                cov = f == 1 || (f == 2 && exact_within_sorted(V, S.ba[u], a));
-              } else if (su == kSwUnd && !blk) {
-                blk = filter_c(S.bx[u], S.by[u], x, y, V.a2lo, V.a2hi) != 0;
-              }
-            }
-          }
-        }
-        // a start read early or late only decides sooner or later: a start is
-        // final once set, and an item that may still become one blocks
-        if (cov) bst[t] = kSwCov;
-        else if (!blk) bst[t] = kSwStart;
-      }
-      if (!__syncthreads_or(valid && bst[t] == kSwUnd)) break;
-    }
-    // the batch's starts join the ring in key order and set their cells
-    const bool is_new = valid && bst[t] == kSwStart;
-    const unsigned mw = __ballot_sync(0xFFFFFFFFu, is_new);
-    if (lane == 0) S.wsum[warp] = __popc(mw);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < kSwBatch / 32; ++w) {
-      const int c = S.wsum[w];
-      if (w < warp) before += c;
-      total += c;
-    }
-    if (S.r_head - S.r_tail + total > kSwRing) {  // more live starts than the ring holds
-      if (t == 0) A.sweep_flags[1] = 1;           // the rounds resume from the cells' states
-      return;
-    }
-    if (is_new) {
-      const int slot = (S.r_head + before + __popc(mw & ((1u << lane) - 1u))) & (kSwRing - 1);
-      S.rx[slot] = x;
-      S.ry[slot] = y;
-      S.rn[slot] = nrm;
-      S.ra[slot] = a;
-      S.rg[slot] = gid;
-      A.state[j] = (A.state[j] & 0xFFFFFFFF00000000ull) | (unsigned)a;
-    }
-    __syncthreads();
-    if (t == 0) S.r_head += total;
-    __syncthreads();
-  }
-}
-
-// After a complete sweep: every cell still undecided has no start.
-__global__ void k_mfinish_cells(unsigned long long* state, const long long* n_cells_p, const int* flags,
-                                const int* sweep_flags) {
-  if (flags[0] || flags[1] || !sweep_flags[0] || sweep_flags[1]) return;
-  const long long n = *n_cells_p;
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
-    if ((unsigned)state[j] == kUndecided) state[j] = (state[j] & 0xFFFFFFFF00000000ull) | kNoStart;
 }
 
 // Count of cells left undecided (0 after a complete run).
@@ -1824,8 +1502,6 @@ __global__ void k_minit(int* bounds, unsigned* bar, unsigned* bar_sub, int* flag
   for (int i = 3; i < 16; ++i) bar[i] = 0;  // [2] rounds used, [4..5] changed cells, [8..11] new starts
   flags[0] = 0;
   flags[1] = (*status != 0u || *n_p > cap) ? 1 : 0;  // earlier error: leave the merge outputs alone
-  flags[2] = 0;  // sweep needed
-  flags[3] = 0;  // sweep incomplete
   bounds[0] = 0x7FFFFFFF;
   bounds[1] = -0x7FFFFFFF;
   bounds[2] = 0x7FFFFFFF;
@@ -1950,64 +1626,10 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
     R.uctr = (unsigned long long*)(B.bar + 8);
     R.slot_stride = B.slots;
     R.item_cap = cap > 0 ? cap : 1;
-    R.sweep_flags = B.flags + 2;
-    R.resume = 0;
-    // the one-barrier rounds hand the last cells to the sweep after
-    // merge_sweep_round rounds (0: never)
-    R.sweep_round = form != 0 ? (unsigned)ws.tune.merge_sweep_round : 0u;
     mark(mk.a0, st);
     if (form == 2) cudaLaunchKernelEx(&cfg, k_mrounds1<4>, R);
     else if (form == 1) cudaLaunchKernelEx(&cfg, k_mrounds1<8>, R);
     else cudaLaunchKernelEx(&cfg, k_mrounds, R);
-    if (R.sweep_round) {
-      SweepArgs A;
-      A.V = V;
-      A.cord = cord;
-      A.cX = B.cX;
-      A.cY = B.cY;
-      A.cell_end = B.cell_end;
-      A.cell_id = B.cell_id;
-      A.cell_of_id = B.cell_of_id;
-      A.state = B.state;
-      A.cov = B.cov;
-      A.n_cells_p = B.head_off + cap;
-      A.geom = B.geom;
-      A.flags = B.flags;
-      A.sweep_flags = B.flags + 2;
-      // scratch the merge no longer needs at this point: the cell sort's
-      // input pair and key buffer, the cell heads, and the buffers of the
-      // sequential fallback (which never runs with the grid)
-      A.pk = ck0;
-      A.pv = cv0;
-      A.pn = (long long*)(B.bar + 14);
-      A.qa = (int*)B.eX;
-      A.qj = (int*)B.eX + (cap > 0 ? cap : 1);
-      A.qx = (float*)B.eY;
-      A.qy = (float*)B.eY + (cap > 0 ? cap : 1);
-      {
-        float ah = (float)alpha;
-        if ((double)ah < alpha) ah = nextafterf(ah, INFINITY);
-        A.alpha_hi = ah;
-      }
-      k_mpend_collect<<<grid, 256, 0, st>>>(A);
-      unsigned long long* pks;
-      int* pvs;
-      const int bits = cap > 1 ? 64 - __builtin_clzll((unsigned long long)(cap - 1)) : 1;
-      radix_sort(ck0, cv0, ckey, B.head, A.pn, cap, bits, ws.m_hist, ws.num_sms, status, &pks, &pvs, B.flags, st);
-      k_mpend_gather<<<grid, 256, 0, st>>>(A, pks, pvs);
-      static PerDevice sw_attr;
-      sw_attr.get([] {
-        cudaFuncSetAttribute(k_msweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SweepSmem));
-        return 1;
-      });
-      k_msweep<<<1, kSwBatch, sizeof(SweepSmem), st>>>(A);
-      k_mfinish_cells<<<grid, 256, 0, st>>>(B.state, A.n_cells_p, B.flags, B.flags + 2);
-      // the sweep's ring overflowed: the rounds resume from the cells' states
-      R.resume = 1;
-      R.sweep_round = 0;
-      if (form == 2) cudaLaunchKernelEx(&cfg, k_mrounds1<4>, R);
-      else cudaLaunchKernelEx(&cfg, k_mrounds1<8>, R);
-    }
     mark(mk.a1, st);
   }
   k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);

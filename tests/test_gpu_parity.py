@@ -204,15 +204,13 @@ def test_merge_group_capacity_changes(C):
         assert np.array_equal(sym.cpu().numpy(), r["symbol"]), mult
 
 
-@pytest.mark.parametrize("form,sweep", [(0, 0), (1, 0), (1, 1), (1, 3), (1, 40), (1, 128)])
-def test_merge_forms(form, sweep):
+@pytest.mark.parametrize("form", [0, 1])
+def test_merge_forms(form):
     """Both forms of the Stage II rounds (two grid barriers per round with
-    coverage marks; one barrier with coverage tested on the fly), the latter
-    with the sweep taking over after `sweep` rounds (0: never; 1: after the
-    first round, so the sweep decides almost everything), give the oracle's
-    result, on a dense workload and on one long chain."""
+    coverage marks; one barrier with coverage tested on the fly) give the
+    oracle's result, on a dense workload and on one long chain."""
     C2 = ctx()
-    C2.set_tuning(dict(merge_form=form, merge_sweep_round=sweep))
+    C2.set_tuning(dict(merge_form=form))
     for name, ms, extra in (("multivar", 2, {}), ("noise", None, dict(domain_value=8)), ("uneven", 25, {})):
         x, off, cfg = synth.make(name, max_series=ms)
         cfg = dict(cfg, **extra)
@@ -251,42 +249,3 @@ def test_block_form_parity(C, name, max_series, M):
     assert np.array_equal(out["dict_inc"].cpu().numpy(), r["dict_inc"])
     assert np.array_equal(out["symbol"].cpu().numpy(), r["symbol"])
     C.sync_status(where="block form")
-
-
-def test_merge_sweep_ring_overflow_resumes_rounds():
-    """A chain of starts all at nearly the same norm: points on a circle of
-    radius 70 centred at the origin, 0.51 alpha apart along the arc, their
-    radius growing by 1e-9 per point (so key order is angle order).  Every
-    other point becomes a start (about 4,300 of them), and all of them stay
-    within alpha in norm of the points still to come, so the sweep's ring of
-    live starts (4,096) overflows and the rounds resume from the cells'
-    states.  The map and the dictionary equal the oracle's greedy over the
-    same points."""
-    import torch
-    import oracle
-    import paper_2401_00109_gb300 as jb
-    alpha, R = 0.1, 70.0
-    G = int(2 * np.pi * R / (0.51 * alpha))
-    ang = np.arange(G) * (2 * np.pi / G)
-    rad = R + np.arange(G) * 1e-9
-    X = np.ascontiguousarray(rad * np.cos(ang))
-    Y = np.ascontiguousarray(rad * np.sin(ang))
-    rec = np.zeros((G, 6), np.uint64)
-    rec[:, 3] = 1                                                                  # lensum
-    rec[:, 4] = np.uint64(1) | (np.arange(G, dtype=np.uint64) << np.uint64(32))   # count 1, local id g
-    dev = "cuda"
-    l = dict(groups=torch.from_numpy(rec.view(np.int64).reshape(-1)).to(dev),
-             n_groups=torch.tensor([G], dtype=torch.int64, device=dev), group_capacity=G,
-             dom_group_off=torch.tensor([0, G], dtype=torch.int64, device=dev),
-             sigma=torch.tensor([1.0, 1.0], dtype=torch.float64, device=dev))
-    p = jb.Params(alpha=alpha)
-    C2 = ctx()
-    C2.set_tuning(dict(merge_form=1, merge_sweep_round=2))
-    m = C2.merge_global(l, p, items=(torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)))
-    C2.sync_status(where="merge")
-    k = int(m["k"].item())
-    cnt = np.ones(G, np.int64)
-    l2g, dl, di, dc = oracle.merge_points(X, Y, cnt, cnt, np.zeros((G, 4), np.uint64), alpha)
-    assert k == len(dc) > 4096
-    assert np.array_equal(m["l2g"][:G].cpu().numpy(), l2g)
-    assert np.array_equal(m["dict_count"][:k].cpu().numpy(), dc)

@@ -25,16 +25,16 @@ def sample():
 
 CONFIGS = [
     dict(compress_ctas_per_sm=1, compress_pack=0, local_mid_warps=2, local_big_warps=4, merge_ctas_per_sm=1,
-         per_domain_launch=0, local_k_warps=4, local_ctas_cap=1, merge_form=0, merge_warps=8, merge_sweep_round=0),
+         per_domain_launch=0, local_k_warps=4, local_ctas_cap=1, merge_form=0, merge_warps=8),
     dict(compress_ctas_per_sm=2, compress_pack=1, local_mid_warps=8, local_big_warps=8, merge_ctas_per_sm=2,
-         per_domain_launch=0, local_k_warps=1, local_ctas_cap=3, merge_form=1, merge_warps=4, merge_sweep_round=1),
+         per_domain_launch=0, local_k_warps=1, local_ctas_cap=3, merge_form=1, merge_warps=4),
     dict(compress_ctas_per_sm=3, compress_pack=1, local_mid_warps=1, local_big_warps=4, merge_ctas_per_sm=4,
-         per_domain_launch=0, local_k_warps=1, local_ctas_cap=0, merge_form=0, merge_warps=4, merge_sweep_round=128),
+         per_domain_launch=0, local_k_warps=1, local_ctas_cap=0, merge_form=0, merge_warps=4),
     dict(compress_ctas_per_sm=3, compress_pack=1, local_mid_warps=4, local_big_warps=4, merge_ctas_per_sm=4,
-         per_domain_launch=0, local_k_warps=4, local_ctas_cap=0, merge_form=1, merge_warps=8, merge_sweep_round=6),
+         per_domain_launch=0, local_k_warps=4, local_ctas_cap=0, merge_form=1, merge_warps=8),
     # the plain form: one launch per domain for compression and Stage I
     dict(compress_ctas_per_sm=3, compress_pack=1, local_mid_warps=4, local_big_warps=4, merge_ctas_per_sm=4,
-         per_domain_launch=1, local_k_warps=1, local_ctas_cap=0, merge_form=1, merge_warps=4, merge_sweep_round=128),
+         per_domain_launch=1, local_k_warps=1, local_ctas_cap=0, merge_form=1, merge_warps=4),
 ]
 
 
@@ -62,13 +62,12 @@ def test_autotune_picks_valid_configuration(C, sample):
     assert t["local_mid_warps"] in (1, 2, 4, 8) and t["local_big_warps"] in (4, 8)
     assert t["local_k_warps"] in (1, 4)
     assert t["merge_ctas_per_sm"] in (1, 2, 4) and t["per_domain_launch"] == 0 and t["merge_warps"] in (4, 8)
-    assert t["merge_sweep_round"] in (0, 64, 128, 192, 320)
     # the configuration chosen keeps producing the oracle's result
     g, *_ = run_gpu(C, x, off, cfg, recon=False)
     assert_parity(g, r, recon=False)
     for bad in (dict(compress_ctas_per_sm=4), dict(local_mid_warps=3), dict(merge_ctas_per_sm=0),
                 dict(per_domain_launch=2), dict(local_k_warps=2), dict(local_ctas_cap=17), dict(merge_form=2),
-                dict(merge_warps=6), dict(merge_sweep_round=-1)):
+                dict(merge_warps=6)):
         with pytest.raises(jb.JabbaError):
             C.set_tuning(bad)
     assert C.tuning() == t
