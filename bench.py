@@ -369,17 +369,32 @@ def run_ours(args, ws, rank, local):
             dc_host[:k].copy_(pl.b["dict_count"][:k], non_blocking=True)
 
         if inflight is not None:
-            # the same two pipelines: each step copies its input in, runs,
-            # and copies its symbols and dictionary out on its own stream,
-            # so one step's transfers overlap the other's kernels
+            # the same two pipelines: the host->device copies run back to back
+            # on a copy stream of their own (the copy of a step waits only
+            # until the front half of the step two before it, on the same
+            # pipeline, has read its input), each step waits for its copy,
+            # runs, and copies its symbols and dictionary out on its stream,
+            # so the link stays busy while the kernels of the steps overlap
             syms = [sym_host, torch.empty_like(sym_host).pin_memory()]
             dicts = [(dl_host, di_host, dc_host),
                      tuple(torch.empty_like(t).pin_memory() for t in (dl_host, di_host, dc_host))]
             pls = [pl, pl2]
+            cs = torch.cuda.Stream()
+            copied = [torch.cuda.Event() for _ in pls]
+            issued = [0, 0]
 
-            def h2d(i, s):
-                pls[i].x.copy_(x_host, non_blocking=True)
-                pls[i].series_off.copy_(off_host, non_blocking=True)
+            def h2d_issue():
+                i = fl.next_index()
+                with torch.cuda.stream(cs):
+                    if issued[i]:
+                        cs.wait_event(fl.front_done[i])
+                    pls[i].x.copy_(x_host, non_blocking=True)
+                    pls[i].series_off.copy_(off_host, non_blocking=True)
+                    copied[i].record(cs)
+                issued[i] += 1
+
+            def wait_copy(i, s):
+                s.wait_event(copied[i])
 
             def d2h(i, s):
                 b = pls[i].b
@@ -387,16 +402,22 @@ def run_ours(args, ws, rank, local):
                 for dst, key in zip(dicts[i], ("dict_len", "dict_inc", "dict_count")):
                     dst[:k].copy_(b[key][:k], non_blocking=True)
 
-            for _ in range(2):
-                fl.step(h2d, d2h)
+            def e2e_steps(n_steps):
+                for _ in range(n_steps):
+                    h2d_issue()
+                    fl.step(wait_copy, d2h)
+
+            cs.wait_stream(st)
+            e2e_steps(2)
             fl.join()
             torch.cuda.synchronize()
             barrier(ws)
             e0.record(st)
             fl.fork(st)
-            for _ in range(args.steps):
-                fl.step(h2d, d2h)
+            cs.wait_stream(st)
+            e2e_steps(args.steps)
             fl.join(st)
+            st.wait_stream(cs)
             e1.record(st)
         else:
             e2e_step()

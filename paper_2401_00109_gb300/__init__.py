@@ -690,13 +690,20 @@ class InFlight:
             s.wait_stream(torch.cuda.current_stream())
         self.halves = [p.capture_halves(s) for p, s in zip(self.pl, self.streams)]
         self.back_done = [torch.cuda.Event() for _ in self.pl]
+        # recorded after each front half: the pipeline's input series are no
+        # longer read, so the next batch may be copied into them
+        self.front_done = [torch.cuda.Event() for _ in self.pl]
         self.count = 0
+
+    def next_index(self) -> int:
+        """Pipeline that the next step() runs on."""
+        return self.count % len(self.pl)
 
     def step(self, before=None, after=None):
         """Issue one step on the next pipeline.  before(i, stream) and
         after(i, stream), if given, enqueue work on that pipeline's stream
-        around the step (e.g. the host->device copy of its input and the
-        device->host copy of its symbols)."""
+        around the step (e.g. a wait for the host->device copy of its input
+        and the device->host copy of its symbols)."""
         torch = _torch()
         i = self.count % len(self.pl)
         j = (i + len(self.pl) - 1) % len(self.pl)
@@ -706,6 +713,7 @@ class InFlight:
             if before is not None:
                 before(i, s)
             front.replay()
+            self.front_done[i].record(s)
             s.wait_event(self.back_done[j])
             back.replay()
             self.back_done[i].record(s)
