@@ -74,6 +74,7 @@ def lib():
                 "jo_compress_all": (None, [F64, I64, I64, C.c_int64, I64, C.c_double, C.c_int, I32, F64, I64,
                                            C.c_int]),
                 "jo_sigma": (None, [I32, F64, C.c_int64, F64, F64]),
+                "jo_pca_axis": (None, [I32, F64, C.c_int64, C.c_double, F64]),
                 "jo_greedy": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_int, I64, I64]),
                 "jo_greedy_proj": (C.c_int64, [F64, F64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
                                                I64, I64]),
@@ -238,39 +239,19 @@ def greedy(X, Y, alpha: float, prune: bool = True, axis=None):
     return lab[:n], st[:g]
 
 
-def pca_axis(piece_len, piece_inc, sigma_len, sigma_inc, scl):
-    """First principal axis of the normalised pieces (the PCA key of Sec. 5).
-    The population covariance of the binary64 points (X, Y) is evaluated
-    exactly (rational arithmetic) and rounded once to binary64 entries a =
-    var X, b = cov(X, Y), c = var Y; the leading eigenvector of [[a, b],
-    [b, c]] then follows in binary64 by the closed form lam = (a + c) / 2 +
-    sqrt(((a - c) / 2)^2 + b^2), v ~ (lam - c, b) when a >= c, else
-    (b, lam - a), normalised, with vx > 0 (or vx = 0 and vy > 0); b = 0
-    gives the axis of the larger variance ((1, 0) when a >= c)."""
-    from fractions import Fraction
-    X, Y = normalised(piece_len, piece_inc, sigma_len, sigma_inc, scl)
-    n = len(X)
-    if n == 0:
-        return 1.0, 0.0
-    fx = [Fraction(float(v)) for v in X]
-    fy = [Fraction(float(v)) for v in Y]
-    mx = sum(fx) / n
-    my = sum(fy) / n
-    a = float(sum((u - mx) * (u - mx) for u in fx) / n)
-    c = float(sum((w - my) * (w - my) for w in fy) / n)
-    b = float(sum((u - mx) * (w - my) for u, w in zip(fx, fy)) / n)
-    f = np.float64
-    a, b, c = f(a), f(b), f(c)
-    if b == 0.0:
-        return (1.0, 0.0) if a >= c else (0.0, 1.0)
-    h = (a - c) / f(2.0)
-    lam = (a + c) / f(2.0) + np.sqrt(h * h + b * b)
-    vx, vy = (lam - c, b) if a >= c else (b, lam - a)
-    s_ = np.sqrt(vx * vx + vy * vy)
-    vx, vy = vx / s_, vy / s_
-    if vx < 0.0 or (vx == 0.0 and vy < 0.0):
-        vx, vy = -vx, -vy
-    return float(vx), float(vy)
+def pca_axis(piece_len, piece_inc, sigma_len=None, sigma_inc=None, scl=1.0, with_r=False):
+    """First principal axis of the normalised pieces (the PCA key of Sec. 5),
+    from exact order-independent sums (jo_pca_axis): normalisation by the
+    standard deviations makes the covariance [[scl^2, scl r], [scl r, 1]]
+    with r the correlation of length and increment; its leading eigenvector
+    by a closed form in binary64, vx > 0.  (sigma_len, sigma_inc are implied
+    by the same sums and accepted for the caller's convenience.)"""
+    ln = _c(piece_len, np.int32)
+    inc = _c(piece_inc, np.float64)
+    out = np.zeros(3, np.float64)
+    lib().jo_pca_axis(_p(ln, I32), _p(inc, F64), len(ln), float(scl), _p(out, F64))
+    ax = (float(out[0]), float(out[1]))
+    return (ax, float(out[2])) if with_r else ax
 
 
 def group_sums(piece_len, piece_inc, labels, G):

@@ -417,6 +417,91 @@ void jo_sigma(const int32_t* len, const double* inc, int64_t n, double* sigma_le
 }
 
 /* ------------------------------------------------------------------------ */
+/* PCA key (Sec. 5: the sort key is "norm or PCA projection").  The first    */
+/* principal axis of the normalised pieces X = (scl len) / sigma_len,        */
+/* Y = inc / sigma_inc.  Normalising by the population standard deviations   */
+/* makes their covariance, in exact arithmetic,                             */
+/*     [[scl^2, scl r], [scl r, 1]],  r = cov(len, inc) / (sigma_len sigma_inc) */
+/* (a variance that is 0 stays 0).  Reading: r comes from the same exact     */
+/* order-independent sums as the standard deviations plus the exact sum of   */
+/* the products len * inc (each truncated toward zero at 2^-64), all rounded */
+/* once; in binary64, in this order:                                        */
+/*     m_l = S_l / N, m_i = S_i / N, c = S_li / N - m_l * m_i,                */
+/*     r = c / (sigma_len * sigma_inc),                                      */
+/*     a = scl * scl (0 when var len = 0), d = 1 (0 when var inc = 0),        */
+/*     b = scl * r (0 when either variance is 0);                            */
+/* the leading eigenvector of [[a, b], [b, d]] by the closed form            */
+/*     b = 0: (1, 0) if a >= d else (0, 1);                                   */
+/*     h = (a - d) / 2, lam = (a + d) / 2 + sqrt(h * h + b * b),              */
+/*     v = (lam - d, b) if a >= d else (b, lam - a), v /= sqrt(vx^2 + vy^2),  */
+/* with the sign that makes vx > 0 (or vx = 0 and vy > 0).                   */
+/* ------------------------------------------------------------------------ */
+void jo_pca_axis(const int32_t* len, const double* inc, int64_t n, double scl, double* out /* vx, vy, r */) {
+  out[0] = 1.0;
+  out[1] = 0.0;
+  out[2] = 0.0;
+  if (n <= 0) return;
+  int64_t s1 = 0;
+  unsigned __int128 s2 = 0;
+  jo_fx i1, i2, li;
+  fx_zero(&i1);
+  fx_zero(&i2);
+  fx_zero(&li);
+  for (int64_t j = 0; j < n; ++j) {
+    s1 += len[j];
+    s2 += (unsigned __int128)((int64_t)len[j] * (int64_t)len[j]);
+    fx_add_double(&i1, inc[j]);
+    jo_fx t;
+    fx_from_square(&t, inc[j]);
+    fx_add_fx(&i2, &t);
+    if (inc[j] != 0.0) {                       /* exact product len * inc, truncated at 2^-64 */
+      uint64_t m;
+      int E;
+      split_double(inc[j], &m, &E);
+      fx_from_scaled(&t, (unsigned __int128)m * (uint64_t)len[j], E + 64, inc[j] < 0);
+      fx_add_fx(&li, &t);
+    }
+  }
+  const double dn = (double)n;
+  const double ml = (double)s1 / dn, mi = fx_to_double(&i1) / dn;
+  const double vl = u128_to_double(s2) / dn - ml * ml;
+  const double vi = fx_to_double(&i2) / dn - mi * mi;
+  const double sl = sigma_from((double)s1, u128_to_double(s2), dn);
+  const double si = sigma_from(fx_to_double(&i1), fx_to_double(&i2), dn);
+  const double c = fx_to_double(&li) / dn - ml * mi;
+  const double r = c / (sl * si);
+  const int var_l = vl > 0.0, var_i = vi > 0.0;
+  const double a = var_l ? scl * scl : 0.0;
+  const double d = var_i ? 1.0 : 0.0;
+  const double b = (var_l && var_i) ? scl * r : 0.0;
+  out[2] = (var_l && var_i) ? r : 0.0;
+  if (b == 0.0) {
+    out[0] = a >= d ? 1.0 : 0.0;
+    out[1] = a >= d ? 0.0 : 1.0;
+    return;
+  }
+  const double h = (a - d) / 2.0;
+  const double lam = (a + d) / 2.0 + sqrt(h * h + b * b);
+  double vx, vy;
+  if (a >= d) {
+    vx = lam - d;
+    vy = b;
+  } else {
+    vx = b;
+    vy = lam - a;
+  }
+  const double sn = sqrt(vx * vx + vy * vy);
+  vx = vx / sn;
+  vy = vy / sn;
+  if (vx < 0.0 || (vx == 0.0 && vy < 0.0)) {
+    vx = -vx;
+    vy = -vy;
+  }
+  out[0] = vx;
+  out[1] = vy;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Greedy aggregation (Sec. 3.2, fABBA; pruning rule of Sec. 5).             */
 /* Points p = (X, Y): X = (scl * len) / sigma_len, Y = inc / sigma_inc        */
 /* (Eq. 4).  Sort key: the squared norm X*X + Y*Y (orders exactly as the     */

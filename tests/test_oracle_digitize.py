@@ -403,6 +403,34 @@ def test_pca_axis_is_the_leading_eigenvector(name, scl):
         assert np.max(np.abs(ax - np.array([1.0, np.sign(r)]) / np.sqrt(2.0))) < 1e-9
 
 
+@pytest.mark.parametrize("scl", [1.0, 0.5])
+def test_pca_correlation_from_exact_sums(scl):
+    """The correlation r behind the PCA axis equals the population
+    correlation of (len, inc) in exact rational arithmetic (up to the 2^-64
+    truncation of the sums and binary64 rounding), and the axis is the
+    leading eigenvector of [[scl^2, scl r], [scl r, 1]] (checked against the
+    closed form evaluated in exact-enough floating point)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    ln = rng.integers(1, 60, 500).astype(np.int32)
+    inc = 0.3 * ln * rng.normal(0, 1, 500) + rng.normal(0, 2, 500)
+    (vx, vy), r = oracle.pca_axis(ln, inc, scl=scl, with_r=True)
+    n = len(ln)
+    fl = [Fraction(int(v)) for v in ln]
+    fi = [Fraction(float(v)) for v in inc]
+    ml, mi = sum(fl) / n, sum(fi) / n
+    cov = sum((a - ml) * (b - mi) for a, b in zip(fl, fi)) / n
+    vl = sum((a - ml) ** 2 for a in fl) / n
+    vi = sum((b - mi) ** 2 for b in fi) / n
+    r_exact = float(cov) / (math.sqrt(float(vl)) * math.sqrt(float(vi)))
+    assert abs(r - r_exact) <= 1e-12 * abs(r_exact)
+    M = np.array([[scl * scl, scl * r], [scl * r, 1.0]])
+    w, V = np.linalg.eigh(M)
+    v = V[:, -1] * (1 if V[0, -1] > 0 else -1)
+    assert np.max(np.abs(np.array([vx, vy]) - v)) < 1e-12
+    assert abs(math.hypot(vx, vy) - 1.0) < 1e-15
+
+
 def test_pca_axis_degenerate():
     ln = np.full(10, 3, np.int32)
     inc = np.full(10, 0.5)
