@@ -74,6 +74,11 @@ typedef struct {
                            1 = FIXED_LEN: domains of `value` intervals (last one shorter)      */
   int32_t round_mode;   /* quantization rounding (Sec. 3.3): 0 = half away from zero, 1 = half to even */
   int64_t domain_value; /* M (EQUAL_COUNT) or interval count (FIXED_LEN), >= 1                  */
+  int32_t key_mode;     /* sort key of the greedy aggregation (Sec. 5 "norm or PCA projection"):
+                           0 = X*X + Y*Y (orders as the norm); 1 = vx X + vy Y, the projection on
+                           the first principal axis of the normalised pieces (see
+                           jabba_digitize_local); the block form accepts 0 only                 */
+  int32_t reserved;     /* 0                                                                     */
 } jabba_params;
 
 /* Local group record (Sec. 5 Stage I output), 48 bytes.  Exact sums make every
@@ -167,7 +172,22 @@ jabba_status jabba_compress(jabba_ctx* ctx, const double* x, int64_t n_points, c
  * Stage I with one block per domain): pieces in order of X*X + Y*Y (ties by
  * position); each unassigned piece starts a group and every later unassigned
  * piece q with (X_q - X_p)^2 + (Y_q - Y_p)^2 <= alpha^2 joins it.
- * Outputs: sigma[2] = {sigma_len, sigma_inc}; local_label [n_slots] (slotted,
+ * Sort key (key_mode): X*X + Y*Y, or with key_mode = 1 the projection
+ * vx * X + vy * Y on the first principal axis (vx, vy) of the normalised
+ * pieces.  The axis: normalising by the standard deviations makes the
+ * covariance of (X, Y) [[scl^2, scl r], [scl r, 1]] in exact arithmetic (a
+ * zero variance stays zero), r = (S_li / N - m_l * m_i) / (sigma_len *
+ * sigma_inc) with S_li the exact sum of the products len * inc (each
+ * truncated toward zero at 2^-64) and m_l, m_i the means; with a = scl * scl,
+ * d = 1, b = scl * r (0 for a zero variance), the leading eigenvector is
+ * (1, 0) or (0, 1) when b = 0 (a >= d picks the first), else, with
+ * h = (a - d) / 2 and lam = (a + d) / 2 + sqrt(h * h + b * b), the vector
+ * (lam - d, b) if a >= d, else (b, lam - a), divided by its norm and signed
+ * so that vx > 0 (or vx = 0 and vy > 0); binary64 in this order.  The
+ * greedy's key gap bound becomes |key_q - key_p| > alpha (a projection on a
+ * unit axis changes by at most the distance).
+ * Outputs: sigma[2] = {sigma_len, sigma_inc} (sigma[4] with key_mode = 1:
+ * then sigma[2], sigma[3] = vx, vy); local_label [n_slots] (slotted,
  * group id within the domain); dom_group_cnt [n_domains]; dom_group_off
  * [n_domains+1] (exclusive scan); groups[group_capacity] (one record per
  * local group, in no particular order; record identity = (domain, local_id));
@@ -183,7 +203,9 @@ jabba_status jabba_digitize_local(jabba_ctx* ctx, const int32_t* piece_len, cons
  * Sec. 5 Stage II: the same greedy over all local groups, each taken as the
  * point (X, Y) of its centre (c_len = lensum / count, c_inc = round(inc) / count,
  * X = (scl * c_len) / sigma_len, Y = c_inc / sigma_inc), ordered by X*X + Y*Y
- * with ties broken by compact group index dom_group_off[domain] + local_id.
+ * (key_mode = 1: by vx * X + vy * Y with the axis sigma[2..3] that
+ * jabba_digitize_local wrote) with ties broken by compact group index
+ * dom_group_off[domain] + local_id.
  * Global ids follow creation order.  Outputs: l2g [G] indexed by compact
  * group index; dictionary entry c = exact mean of its member pieces:
  * dict_len[c] = lensum / count, dict_inc[c] = round(sum inc) / count,

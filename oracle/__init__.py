@@ -533,6 +533,7 @@ def pipeline(x, series_off, tol, alpha, scl=1.0, domain_mode=0, domain_value=4, 
     b, e, ds = domains(series_off, domain_mode, domain_value)
     ln, inc, po = compress(x, b, e, tol, threads)
     sl, si = sigma(ln, inc)
+    axis = None
     if key == "pca":
         axis = pca_axis(ln, inc, sl, si, scl)
         lab, go, gc, gl, gi = local_aggregate_pca(ln, inc, po, sl, si, alpha, scl, axis)
@@ -548,7 +549,7 @@ def pipeline(x, series_off, tol, alpha, scl=1.0, domain_mode=0, domain_value=4, 
         l2g, dl, di, dc = merge(gc, gl, gi, sl, si, alpha, scl)
     sym = symbolize(lab, po, go, l2g)
     out = dict(dom_begin=b, dom_end=e, dom_series=ds, piece_len=ln, piece_inc=inc, dom_piece_off=po,
-               sigma_len=sl, sigma_inc=si, local_label=lab, dom_group_off=go, grp_count=gc,
+               sigma_len=sl, sigma_inc=si, axis=axis, local_label=lab, dom_group_off=go, grp_count=gc,
                grp_lensum=gl, grp_incacc=gi, l2g=l2g, dict_len=dl, dict_inc=di, dict_count=dc, symbol=sym)
     if with_reconstruct:
         spo = series_piece_offsets(series_off, ds, po)

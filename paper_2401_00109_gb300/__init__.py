@@ -42,23 +42,26 @@ class JabbaError(RuntimeError):
 
 class _Params(C.Structure):
     _fields_ = [("tol", C.c_double), ("alpha", C.c_double), ("scl", C.c_double), ("domain_mode", C.c_int32),
-                ("round_mode", C.c_int32), ("domain_value", C.c_int64)]
+                ("round_mode", C.c_int32), ("domain_value", C.c_int64), ("key_mode", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 @dataclass
 class Params:
     """Method parameters (Eq. 1 tol; Sec. 3.2 alpha, scl; Sec. 4.1.1 domains;
-    Sec. 3.3 rounding of the quantization)."""
+    Sec. 3.3 rounding of the quantization; Sec. 5 sort key: 0 = norm,
+    1 = PCA projection)."""
     tol: float = 0.1
     alpha: float = 0.1
     scl: float = 1.0
     domain_mode: int = EQUAL_COUNT
     domain_value: int = 4
     round_mode: int = 0
+    key_mode: int = 0
 
     def c(self) -> _Params:
         return _Params(float(self.tol), float(self.alpha), float(self.scl), int(self.domain_mode),
-                       int(self.round_mode), int(self.domain_value))
+                       int(self.round_mode), int(self.domain_value), int(self.key_mode), 0)
 
 
 class _Tuning(C.Structure):
@@ -241,7 +244,7 @@ class Context:
             group_capacity = max(1, min(c["n_slots"], max(1 << 16, c["n_slots"] // 4)))
         while True:
             o = dict(
-                sigma=torch.empty(2, dtype=torch.float64, device=dev),
+                sigma=torch.empty(4, dtype=torch.float64, device=dev),   # sigma_len, sigma_inc (+ PCA axis)
                 local_label=torch.empty(max(c["n_slots"], 1), dtype=torch.int32, device=dev),
                 dom_group_cnt=torch.empty(max(D, 1), dtype=torch.int32, device=dev),
                 dom_group_off=torch.empty(D + 1, dtype=torch.int64, device=dev),
@@ -573,7 +576,7 @@ class Pipeline:
         self.b = dict(dom_begin=e(D, i64), dom_end=e(D, i64), dom_series=e(D, i32), series_dom_off=e(self.S + 1, i64),
                       dom_slot_off=e(D + 1, i64), piece_len=e(slots, i32), piece_inc=e(slots, f64),
                       dom_piece_cnt=e(D, i32), dom_piece_off=e(D + 1, i64), piece_stats=e(PIECE_STATS_BYTES // 8, i64),
-                      sigma=e(2, f64), local_label=e(slots, i32), dom_group_cnt=e(D, i32), dom_group_off=e(D + 1, i64),
+                      sigma=e(4, f64), local_label=e(slots, i32), dom_group_cnt=e(D, i32), dom_group_off=e(D + 1, i64),
                       groups=e(self.gcap * JABBA_GROUP_BYTES // 8, i64), n_groups=e(1, i64), l2g=e(self.gcap, i32),
                       dict_len=e(self.kcap, f64), dict_inc=e(self.kcap, f64), dict_count=e(self.kcap, i64),
                       k=e(1, i64), symbol=e(slots, i32))

@@ -51,6 +51,7 @@ bool params_ok(const jabba_params* p) {
   if (p->domain_mode != 0 && p->domain_mode != 1) return false;
   if (p->round_mode != 0 && p->round_mode != 1) return false;
   if (p->domain_value < 1) return false;
+  if (p->key_mode != 0 && p->key_mode != 1) return false;
   return true;
 }
 
@@ -467,7 +468,7 @@ jabba_status jabba_compress(jabba_ctx* c, const double* x, int64_t n_points, con
   auto run = [&](const Marks& m) {
     launch_compress(x, n_points, (const long long*)dom_begin, (const long long*)dom_end,
                     (const long long*)dom_slot_off, n_domains, p->tol, piece_len, piece_inc, dom_piece_cnt,
-                    (long long*)dom_piece_off, (long long*)piece_stats, c->ws, c->status, st, m);
+                    (long long*)dom_piece_off, (long long*)piece_stats, p->key_mode == 1, c->ws, c->status, st, m);
   };
   if (c->ws.tune.per_domain_launch && (capturing(st) || c->tuning)) return JABBA_ERR_STATE;
   if (c->tuning) {
@@ -518,9 +519,9 @@ jabba_status jabba_digitize_local(jabba_ctx* c, const int32_t* piece_len, const 
   jabba_status r = ensure(c, c->ws.cap_series, n_domains, c->ws.cap_slots, c->ws.cap_groups, c->ws.cap_big, st);
   if (r != JABBA_OK) return r;
   auto run = [&]() {
-    launch_sigma((const long long*)piece_stats, sigma, st);
+    launch_sigma((const long long*)piece_stats, sigma, p->key_mode, p->scl, st);
     launch_local(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt, n_domains, sigma, p->alpha,
-                 p->scl, local_label, dom_group_cnt, (long long*)dom_group_off, groups, group_capacity,
+                 p->scl, p->key_mode, local_label, dom_group_cnt, (long long*)dom_group_off, groups, group_capacity,
                  (long long*)n_groups, c->ws, c->status, st);
   };
   if (c->ws.tune.per_domain_launch && (capturing(st) || c->tuning)) return JABBA_ERR_STATE;
@@ -584,7 +585,7 @@ jabba_status merge_impl(jabba_ctx* c, const jabba_group* groups, const double* i
       mk.a1 = prof_event(c, 5, 1);
     }
     launch_merge(groups, item_X, item_Y, (const long long*)n_groups, group_capacity,
-                 (const long long*)dom_group_off, sigma, p->alpha, p->scl, l2g, dict_len, dict_inc,
+                 (const long long*)dom_group_off, sigma, p->alpha, p->scl, p->key_mode, l2g, dict_len, dict_inc,
                  (long long*)dict_count, dict_capacity, (long long*)k, c->ws, c->status, st, mk);
   };
   if (c->tuning) {
@@ -651,6 +652,7 @@ jabba_status jabba_block_order(jabba_ctx* c, const int32_t* piece_len, const dou
                                int64_t n_blocks, double* sigma, int32_t* order, int32_t* blk_len, double* blk_inc,
                                int64_t* blk_slot_off, int32_t* blk_piece_cnt, jabba_stream stream) {
   if (!c || !params_ok(p) || n_domains < 0 || n_pieces < 0 || n_blocks < 1) return JABBA_ERR_INVALID_ARG;
+  if (p->key_mode != 0) return JABBA_ERR_INVALID_ARG;  // the block form sorts by the norm key
   if (n_pieces >= 0x7FFFFFFFll) return JABBA_ERR_RANGE;
   if (!piece_stats || !sigma || !dom_piece_off || !blk_slot_off || !blk_piece_cnt) return JABBA_ERR_INVALID_ARG;
   if (n_domains > 0 && (!piece_len || !piece_inc || !dom_slot_off || !dom_piece_cnt)) return JABBA_ERR_INVALID_ARG;
@@ -665,7 +667,7 @@ jabba_status jabba_block_order(jabba_ctx* c, const int32_t* piece_len, const dou
   if (r != JABBA_OK) return r;
   r = ensure_bf(c, n_pieces, st);
   if (r != JABBA_OK) return r;
-  launch_sigma((const long long*)piece_stats, sigma, st);
+  launch_sigma((const long long*)piece_stats, sigma, 0, p->scl, st);
   launch_block_order(piece_len, piece_inc, (const long long*)dom_slot_off, dom_piece_cnt,
                      (const long long*)dom_piece_off, n_domains, n_pieces, n_blocks, sigma, p->scl, c->bf, order,
                      blk_len, blk_inc, (long long*)blk_slot_off, blk_piece_cnt, c->ws.num_sms, c->status, st);

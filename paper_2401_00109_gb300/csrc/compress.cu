@@ -512,7 +512,10 @@ __global__ void k_dom_iota(long long n_domains, int* order) {
 // sum len^2 (integers) and sum inc, sum inc^2 (exact squares), the latter two
 // as 2^-64 fixed point.  stats layout (int64): [0] N, [1] sum len,
 // [2..5] sum len^2 in four 32-bit deferred-carry limbs, [6..11] sum inc and
-// [12..17] sum inc^2 in six 32-bit deferred-carry limbs each.
+// [12..17] sum inc^2 in six 32-bit deferred-carry limbs each; with kProd
+// (the PCA key) also [18..23] sum len * inc (exact products, each truncated
+// toward zero at 2^-64), six limbs.
+template <bool kProd>
 __global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const long long* dom_begin,
                                                        const long long* dom_slot_off, const int* dom_piece_cnt,
                                                        long long n_domains, const int* piece_len, double* piece_inc,
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const lo
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
   unsigned long long n = 0, s1 = 0;
   U128 s2 = {0, 0};
-  I192 a1 = {0, 0, 0}, a2 = {0, 0, 0};
+  I192 a1 = {0, 0, 0}, a2 = {0, 0, 0}, a3 = {0, 0, 0};
   for (long long d = warp_g; d < n_domains; d += n_warps) {
     const int cnt = dom_piece_cnt[d];
     const long long slot = dom_slot_off[d];
@@ -549,11 +552,13 @@ __global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const lo
         acc_signed(a1, m, neg);
         const U128 q = fx_square(inc);
         add192(a2, q.lo, q.hi, 0);
+        if (kProd) acc_signed(a3, fx_prod(inc, (unsigned)len), neg);
       }
     }
   }
   // warp reduction of limbs, then one set of atomics per warp
-  i64 L[18];
+  constexpr int kL = kProd ? 24 : 18;
+  i64 L[24];
   L[0] = (i64)n;
   L[1] = (i64)s1;
   L[2] = (i64)(s2.lo & 0xFFFFFFFFull);
@@ -562,15 +567,16 @@ __global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const lo
   L[5] = (i64)(s2.hi >> 32);
   limbs6(a1, L + 6);
   limbs6(a2, L + 12);
+  if (kProd) limbs6(a3, L + 18);
 #pragma unroll
-  for (int i = 0; i < 18; ++i) {
+  for (int i = 0; i < kL; ++i) {
     i64 v = L[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     L[i] = v;
   }
   if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < 18; ++i)
+    for (int i = 0; i < kL; ++i)
       if (L[i]) atomicAdd((unsigned long long*)&stats[i], (unsigned long long)L[i]);
   }
 }
@@ -584,7 +590,54 @@ __device__ double sigma_from(double s1, double s2, double n) {
   return __dsqrt_rn(v);
 }
 
-__global__ void k_sigma(const long long* stats, double* sigma) {
+// PCA key (Sec. 5 "PCA projection"): the first principal axis of the
+// normalised pieces.  Normalising by the population standard deviations makes
+// their covariance [[scl^2, scl r], [scl r, 1]] in exact arithmetic (a zero
+// variance stays zero), r = cov(len, inc) / (sigma_len sigma_inc) from the
+// exact sums; the leading eigenvector by the closed form
+//   b = 0: (1, 0) if a >= d else (0, 1); h = (a - d) / 2,
+//   lam = (a + d) / 2 + sqrt(h h + b b), v = (lam - d, b) if a >= d else
+//   (b, lam - a), normalised, vx > 0 (or vx = 0 and vy > 0);
+// binary64 operations in this order.
+__device__ void pca_axis(double n, double s1, double s2, double i1, double i2, double li, double scl, double* vx_out,
+                         double* vy_out) {
+  const double ml = __ddiv_rn(s1, n), mi = __ddiv_rn(i1, n);
+  const double vl = __dsub_rn(__ddiv_rn(s2, n), __dmul_rn(ml, ml));
+  const double vi = __dsub_rn(__ddiv_rn(i2, n), __dmul_rn(mi, mi));
+  const double sl = sigma_from(s1, s2, n), si = sigma_from(i1, i2, n);
+  const double c = __dsub_rn(__ddiv_rn(li, n), __dmul_rn(ml, mi));
+  const double r = __ddiv_rn(c, __dmul_rn(sl, si));
+  const bool var_l = vl > 0.0, var_i = vi > 0.0;
+  const double a = var_l ? __dmul_rn(scl, scl) : 0.0;
+  const double d = var_i ? 1.0 : 0.0;
+  const double b = (var_l && var_i) ? __dmul_rn(scl, r) : 0.0;
+  double vx, vy;
+  if (b == 0.0) {
+    vx = a >= d ? 1.0 : 0.0;
+    vy = a >= d ? 0.0 : 1.0;
+  } else {
+    const double h = __ddiv_rn(__dsub_rn(a, d), 2.0);
+    const double lam = __dadd_rn(__ddiv_rn(__dadd_rn(a, d), 2.0), __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), __dmul_rn(b, b))));
+    if (a >= d) {
+      vx = __dsub_rn(lam, d);
+      vy = b;
+    } else {
+      vx = b;
+      vy = __dsub_rn(lam, a);
+    }
+    const double sn = __dsqrt_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
+    vx = __ddiv_rn(vx, sn);
+    vy = __ddiv_rn(vy, sn);
+    if (vx < 0.0 || (vx == 0.0 && vy < 0.0)) {
+      vx = -vx;
+      vy = -vy;
+    }
+  }
+  *vx_out = vx;
+  *vy_out = vy;
+}
+
+__global__ void k_sigma(const long long* stats, double* sigma, int key_mode, double scl) {
   const double n = __ll2double_rn(stats[0]);
   const double s1 = __ll2double_rn(stats[1]);
   // sum len^2 from four unsigned 32-bit deferred-carry limbs
@@ -606,12 +659,23 @@ __global__ void k_sigma(const long long* stats, double* sigma) {
   const double i2 = i192_to_double(from_limbs6(L2));
   sigma[0] = sigma_from(s1, s2, n);
   sigma[1] = sigma_from(i1, i2, n);
+  if (key_mode == 1) {  // sigma[2], sigma[3]: the PCA axis
+    i64 L3[6];
+    for (int i = 0; i < 6; ++i) L3[i] = stats[18 + i];
+    const double li = i192_to_double(from_limbs6(L3));
+    if (!(n > 0.0)) {
+      sigma[2] = 1.0;
+      sigma[3] = 0.0;
+    } else {
+      pca_axis(n, s1, s2, i1, i2, li, scl, &sigma[2], &sigma[3]);
+    }
+  }
 }
 
 void launch_compress(const double* x, long long n_points, const long long* dom_begin, const long long* dom_end,
                      const long long* dom_slot_off, long long n_domains, double tol, int* piece_len,
                      double* piece_inc, int* dom_piece_cnt, long long* dom_piece_off, long long* stats,
-                     Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk) {
+                     bool with_products, Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk) {
   CompressParams P;
   P.x = x;
   P.n_points = n_points;
@@ -674,13 +738,16 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   if (n_domains > 0) {
     long long blocks = (n_domains + 7) / 8;
     if (blocks > (long long)ws.num_sms * 16) blocks = (long long)ws.num_sms * 16;
-    k_finish_pieces<<<(unsigned)blocks, 256, 0, st>>>(x, dom_begin, dom_slot_off, dom_piece_cnt, n_domains,
+    auto fin = with_products ? k_finish_pieces<true> : k_finish_pieces<false>;
+    fin<<<(unsigned)blocks, 256, 0, st>>>(x, dom_begin, dom_slot_off, dom_piece_cnt, n_domains,
                                                       piece_len, piece_inc, stats);
   }
   exclusive_scan<int>(dom_piece_cnt, n_domains, dom_piece_off, ws.scan_tiles, st);
   mark(mk.b1, st);
 }
 
-void launch_sigma(const long long* stats, double* sigma, cudaStream_t st) { k_sigma<<<1, 1, 0, st>>>(stats, sigma); }
+void launch_sigma(const long long* stats, double* sigma, int key_mode, double scl, cudaStream_t st) {
+  k_sigma<<<1, 1, 0, st>>>(stats, sigma, key_mode, scl);
+}
 
 }  // namespace jabba

@@ -42,6 +42,7 @@ struct LocalParams {
   double alpha, scl;
   float a2lo, a2hi;       // alpha^2 (1 -+ 2^-20) in FP32 (rounded outward)
   float alpha_up;         // alpha (1 + 2^-20) rounded up
+  int pca;                // sort key: 0 = X*X + Y*Y, 1 = the projection vx X + vy Y on the PCA axis
   int* local_label;
   int* dom_group_cnt;
   jabba_group* groups;
@@ -67,9 +68,34 @@ __device__ __forceinline__ float x32_of(const LocalParams& P, int len) {
 }
 __device__ __forceinline__ double y64_of(const LocalParams& P, double inc) { return __ddiv_rn(inc, P.sigma[1]); }
 
+// The sort key in binary64 (the definition): X*X + Y*Y, or with the PCA key
+// vx * X + vy * Y (the axis in sigma[2..3]); ties by position.
 __device__ __forceinline__ double key64_of(const LocalParams& P, int len, double inc) {
   const double X = x64_of(P, len), Y = y64_of(P, inc);
+  if (P.pca) return __dadd_rn(__dmul_rn(P.sigma[2], X), __dmul_rn(P.sigma[3], Y));
   return __dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y));
+}
+
+// FP32 key of a piece from its FP32 coordinates.  Norm key: x*x + y*y lies
+// within key (1 +- 2^-19).  PCA key: vx32 x + vy32 y (vx32, vy32 the axis
+// rounded to FP32) lies within pca_err of the binary64 projection (|x32 - X|
+// <= 2^-24 |X|, |y32 - Y| <= 2^-22 |Y|, |v32 - v| <= 2^-24 |v|, two FP32
+// roundings: the error is below 2^-21 (|x| + |y|) + 2^-24 |k|).
+__device__ __forceinline__ float key32f(const LocalParams& P, float x, float y, float vx32, float vy32) {
+  return P.pca ? fmaf(vx32, x, vy32 * y) : fmaf(x, x, y * y);
+}
+__device__ __forceinline__ float pca_err(float x, float y, float k) {
+  return 0x1p-20f * (fabsf(x) + fabsf(y) + fabsf(k)) + 0x1p-120f;
+}
+// Order-preserving unsigned image of an FP32 key (signed keys of the PCA
+// axis included): the sign bit set for non-negative values, every bit
+// flipped for negative ones.
+__device__ __forceinline__ unsigned key_bits(float k) {
+  const unsigned u = __float_as_uint(k);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_val(unsigned b) {
+  return __uint_as_float((b & 0x80000000u) ? (b & 0x7FFFFFFFu) : ~b);
 }
 
 // binary64 membership test of the definition
@@ -99,12 +125,33 @@ __device__ __forceinline__ float key_stop(float key_start, float alpha_up) {
   return r * r * (1.0f + 0x1p-18f);
 }
 
+// Scan bound of the start at (xs, ys): a later piece past it lies farther
+// than alpha from the start in binary64 (Sec. 5 pruning).  Norm key: key32
+// (1 - 2^-19) > (sqrt(key32_s (1 + 2^-19)) + alpha)^2; PCA key: the key gap
+// exceeds alpha with both error bounds (a projection on a unit axis changes
+// by at most the distance).
+__device__ __forceinline__ float scan_bound(const LocalParams& P, float xs, float ys, float vx32, float vy32) {
+  const float k = key32f(P, xs, ys, vx32, vy32);
+  if (P.pca) return (k + pca_err(xs, ys, k)) + P.alpha_up * (1.0f + 0x1p-20f);
+  return key_stop(k, P.alpha_up);
+}
+__device__ __forceinline__ bool past_bound(const LocalParams& P, float xb, float yb, float T, float vx32, float vy32) {
+  const float k = key32f(P, xb, yb, vx32, vy32);
+  if (P.pca) return k - pca_err(xb, yb, k) > T;
+  return k * (1.0f - kKeyRel) > T;
+}
+
 
 // Runs of neighbours whose key intervals overlap, found 32 pairs at a time;
 // lane 0 re-sorts each run (insertion sort) by the binary64 keys, ties by
 // position.  KeyT/IdxT: the key (FP32 bits) and position arrays of the view.
-__device__ __forceinline__ bool keys_overlap32(unsigned k0, unsigned k1) {
-  return __uint_as_float(k1) * (1.0f - kKeyRel) <= __uint_as_float(k0) * (1.0f + kKeyRel) * (1.0f + 0x1p-22f);
+// Whether the error intervals of two neighbouring sorted keys overlap (then
+// their order is settled by the binary64 keys): relative bounds for the norm
+// key, the domain's largest absolute bound `edom` for the PCA key.
+__device__ __forceinline__ bool keys_overlap32(const LocalParams& P, unsigned k0, unsigned k1, float edom) {
+  const float v0 = key_val(k0), v1 = key_val(k1);
+  if (P.pca) return v1 - edom <= v0 + edom;
+  return v1 * (1.0f - kKeyRel) <= v0 * (1.0f + kKeyRel) * (1.0f + 0x1p-22f);
 }
 
 template <typename IdxT>
@@ -171,7 +218,7 @@ __device__ void sort_run32(const LocalParams& P, const int* plen, const double* 
 // found by bit scans of the link masks; kbuf: 32 doubles of scratch.
 template <typename IdxT>
 __device__ void fix_runs(const LocalParams& P, const int* plen, const double* pinc, unsigned* key, IdxT* idx, int n,
-                         double* kbuf) {
+                         double* kbuf, float edom) {
   const int lane = threadIdx.x & 31;
   int run_start = -1;                          // run open across chunks (uniform)
   auto sort_members = [&](int a, int b) {
@@ -184,7 +231,7 @@ __device__ void fix_runs(const LocalParams& P, const int* plen, const double* pi
   };
   for (int a0 = 0; a0 + 1 < n; a0 += 32) {
     const int a = a0 + lane;
-    const bool link = a + 1 < n && keys_overlap32(key[a], key[a + 1]);
+    const bool link = a + 1 < n && keys_overlap32(P, key[a], key[a + 1], edom);
     const int lim = min(32, n - 1 - a0);       // pairs a0 .. a0 + lim - 1 exist
     const unsigned valid = lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
     const unsigned m = __ballot_sync(0xFFFFFFFFu, link) & valid;
@@ -291,6 +338,7 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
   const Arena A = arena_of(P, warp_global);
   const double a2 = __dmul_rn(P.alpha, P.alpha);
   const float rinv = *P.rinv32;
+  const float vx32 = P.pca ? __double2float_rn(P.sigma[2]) : 0.f, vy32 = P.pca ? __double2float_rn(P.sigma[3]) : 0.f;
   const unsigned n_list = *P.list_count;
   for (;;) {
     unsigned task = 0;
@@ -310,22 +358,26 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
       continue;
     }
     // 1. FP32 coordinates and keys
+    float edom = 0.f;  // largest error bound of a PCA key of the domain
     for (int i = lane; i < n; i += 32) {
       unsigned mh;
       const float x = x32_of(P, plen[i]);
       const float y = f64_to_f32_trunc(pinc[i], mh) * rinv;
+      const float k = key32f(P, x, y, vx32, vy32);
       A.X[i] = x;
       A.Y[i] = y;
-      A.key[i] = __float_as_uint(fmaf(x, x, y * y));
+      A.key[i] = key_bits(k);
       A.sidx[i] = i;
       A.label[i] = -1;
+      if (P.pca) edom = fmaxf(edom, pca_err(x, y, k));
     }
+    for (int o = 16; o > 0; o >>= 1) edom = fmaxf(edom, __shfl_xor_sync(0xFFFFFFFFu, edom, o));
     __syncwarp();
     // 2. sort by (key32, position)
     if (n > 1) warp_radix_sort(A.key, A.sidx, A.tk, A.tv, n, hist);
     __syncwarp();
     // 3. runs of overlapping key intervals: re-sort by the binary64 keys
-    fix_runs<int>(P, plen, pinc, A.key, A.sidx, n, (double*)hist);
+    fix_runs<int>(P, plen, pinc, A.key, A.sidx, n, (double*)hist, edom);
     // 4. greedy in key order
     int G = 0;
     {
@@ -342,17 +394,18 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
         if (a >= n) break;
         const int ps = A.sidx[a];
         const float xs = A.X[ps], ys = A.Y[ps];
-        const float T = key_stop(__uint_as_float(A.key[a]), P.alpha_up);
+        const float T = scan_bound(P, xs, ys, vx32, vy32);
         if (lane == 0) A.label[ps] = G;
         for (int b0 = a + 1; b0 < n; b0 += 32) {
           const int b = b0 + lane;
           bool stop = true;
           if (b < n) {
-            stop = __uint_as_float(A.key[b]) * (1.0f - kKeyRel) > T;
+            const int pb = A.sidx[b];
+            const float xb = A.X[pb], yb = A.Y[pb];
+            stop = past_bound(P, xb, yb, T, vx32, vy32);
             if (!stop) {
-              const int pb = A.sidx[b];
               if (A.label[pb] < 0) {
-                int w = filter_within(xs, ys, A.X[pb], A.Y[pb], P.a2lo, P.a2hi);
+                int w = filter_within(xs, ys, xb, yb, P.a2lo, P.a2hi);
                 if (w == 2) w = exact_within(P, plen[ps], pinc[ps], plen[pb], pinc[pb], a2) ? 1 : 0;
                 if (w) A.label[pb] = G;
               }
@@ -486,7 +539,6 @@ __device__ __forceinline__ bool tile_sync_or(bool p) {
   return __syncthreads_or(p) != 0;
 }
 
-__device__ __forceinline__ unsigned key32_of(float x, float y) { return __float_as_uint(fmaf(x, x, y * y)); }
 
 // Stable LSD radix sort of (key, val) by key with 8-bit digits over the W
 // warps of a tile: warp w ranks the contiguous segment [w seg, (w+1) seg) of
@@ -599,6 +651,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
   long long* gbase_s = (long long*)(misc + 16);                      // group record base
   const double a2 = __dmul_rn(P.alpha, P.alpha);
   const float rinv = *P.rinv32;
+  const float vx32 = P.pca ? __double2float_rn(P.sigma[2]) : 0.f, vy32 = P.pca ? __double2float_rn(P.sigma[3]) : 0.f;
   const unsigned n_list = *list_count;
   for (;;) {
     unsigned task = 0;
@@ -606,7 +659,10 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
     if (W == 1) {
       task = __shfl_sync(0xFFFFFFFFu, task, 0);
     } else {
-      if (t == 0) misc[12] = (int)task;
+      if (t == 0) {
+        misc[12] = (int)task;
+        misc[14] = 0;  // the domain's largest PCA key error bound (FP32 bits)
+      }
       __syncthreads();
       task = (unsigned)misc[12];
       __syncthreads();
@@ -618,6 +674,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
     const int* plen = P.piece_len + slot;
     const double* pinc = P.piece_inc + slot;
     // 1. FP32 keys by position (the loads of four pieces in flight together)
+    float edom = 0.f;
     for (int i0 = t; i0 < n; i0 += 4 * T) {
       int L4[4];
       double I4[4];
@@ -634,12 +691,19 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
           unsigned mh;
           const float x = x32_of(P, L4[u]);
           const float y = f64_to_f32_trunc(I4[u], mh) * rinv;
-          key[i] = key32_of(x, y);
+          const float k = key32f(P, x, y, vx32, vy32);
+          key[i] = key_bits(k);
           idx[i] = (unsigned short)i;
+          if (P.pca) edom = fmaxf(edom, pca_err(x, y, k));
         }
       }
     }
+    if (P.pca) {
+      for (int o = 16; o > 0; o >>= 1) edom = fmaxf(edom, __shfl_xor_sync(0xFFFFFFFFu, edom, o));
+      if (W > 1 && lane == 0) atomicMax(&misc[14], __float_as_int(edom));
+    }
     tile_sync<W>();
+    if (W > 1 && P.pca) edom = __int_as_float(misc[14]);
     // 2. sort by (key32, position)
     if (n > 1) tile_radix_sort16<W>(key, idx, tk, tv, n, hist, wsum);
     tile_sync<W>();
@@ -647,9 +711,9 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
     // the whole tile first checks whether any neighbouring pair overlaps)
     {
       bool ov = false;
-      for (int a = t; a + 1 < n; a += T) ov = ov || keys_overlap32(key[a], key[a + 1]);
+      for (int a = t; a + 1 < n; a += T) ov = ov || keys_overlap32(P, key[a], key[a + 1], edom);
       if (tile_sync_or<W>(ov)) {
-        if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n, (double*)hist);
+        if (t < 32) fix_runs<unsigned short>(P, plen, pinc, key, idx, n, (double*)hist, edom);
         tile_sync<W>();
       }
     }
@@ -686,7 +750,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
         int G = 0, a = 0;
         while (a < n) {
           const float xs = sX[a], ys = sY[a];
-          const float Tk = key_stop(__uint_as_float(key32_of(xs, ys)), P.alpha_up);
+          const float Tk = scan_bound(P, xs, ys, vx32, vy32);
           if (lane == 0) lab[a] = (short)G;
           int next = n;
           int b0 = a + 1;
@@ -695,7 +759,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
             bool stop = true, fr = false;
             if (b < n) {
               const float xb = sX[b], yb = sY[b];
-              stop = __uint_as_float(key32_of(xb, yb)) * (1.0f - kKeyRel) > Tk;
+              stop = past_bound(P, xb, yb, Tk, vx32, vy32);
               if (lab[b] < 0) {
                 bool join = false;
                 if (!stop) {
@@ -743,7 +807,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
       while (a < n) {
         const int sl = G & 1;
         const float xs = sX[a], ys = sY[a];
-        const float Tk = key_stop(__uint_as_float(key32_of(xs, ys)), P.alpha_up);
+        const float Tk = scan_bound(P, xs, ys, vx32, vy32);
         if (t == 0) {
           lab[a] = (short)G;
           srch[sl] = n;
@@ -756,7 +820,7 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
           bool stop = true, fr = false;
           if (b < n) {
             const float xb = sX[b], yb = sY[b];
-            stop = __uint_as_float(key32_of(xb, yb)) * (1.0f - kKeyRel) > Tk;
+            stop = past_bound(P, xb, yb, Tk, vx32, vy32);
             if (lab[b] < 0) {
               bool join = false;
               if (!stop) {
@@ -960,7 +1024,7 @@ static void launch_tile(const LocalParams& P, const int* list, const unsigned* c
 
 void launch_local(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
                   const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
-                  int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
+                  int key_mode, int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
                   long long group_capacity, long long* n_groups, Scratch& ws, unsigned* status, cudaStream_t st) {
   // loc_ctr[0..5]: list sizes of the tiers and the arena; [8..13]: their task counters
   unsigned* list_cnt = ws.loc_ctr;
@@ -982,6 +1046,7 @@ void launch_local(const int* piece_len, const double* piece_inc, const long long
   P.cap_len = ws.cap_len;
   P.alpha = alpha;
   P.scl = scl;
+  P.pca = key_mode == 1 ? 1 : 0;
   const double a2 = alpha * alpha;
   P.a2lo = round_down_f(a2 * (1.0 - 0x1p-20));
   P.a2hi = round_up_f(a2 * (1.0 + 0x1p-20));

@@ -112,6 +112,28 @@ __device__ __forceinline__ U128 fx_square(double v) {
   return shr128(sq, -s);
 }
 
+// trunc(|v| * L * 2^64) for the EXACT product of a finite double v,
+// |v| < 2^32, and an integer 0 <= L < 2^32 (the product is below 2^128).
+__device__ __forceinline__ U128 fx_prod(double v, unsigned L) {
+  const u64 bits = (u64)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  U128 z = {0, 0};
+  if (e == 0 || L == 0) return z;
+  const u64 m = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  U128 p;
+  p.lo = m * (u64)L;
+  p.hi = __umul64hi(m, (u64)L);                          // m L < 2^85
+  const int s = e - 1011;                                // |v| L 2^64 = m L 2^s
+  if (s >= 0) {
+    if (s == 0) return p;
+    U128 r;                                              // s <= 42 under the range contract
+    r.lo = p.lo << s;
+    r.hi = (p.hi << s) | (p.lo >> (64 - s));
+    return r;
+  }
+  return shr128(p, -s);
+}
+
 // Signed add of a magnitude into a 192-bit accumulator.
 __device__ __forceinline__ void acc_signed(I192& a, U128 m, bool neg) {
   if (neg) sub192(a, m.lo, m.hi, 0); else add192(a, m.lo, m.hi, 0);

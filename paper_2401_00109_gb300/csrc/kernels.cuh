@@ -155,7 +155,7 @@ void launch_pack_domains(const long long* dom_begin, const long long* dom_end, l
 void launch_compress(const double* x, long long n_points, const long long* dom_begin, const long long* dom_end,
                      const long long* dom_slot_off, long long n_domains, double tol, int* piece_len,
                      double* piece_inc, int* dom_piece_cnt, long long* dom_piece_off, long long* stats,
-                     Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk);
+                     bool with_products, Scratch& ws, unsigned* status, cudaStream_t st, const Marks& mk);
 
 // Records an event on `st`; inside stream capture the record becomes a graph
 // node (external record) so that replays time the same kernels.
@@ -167,14 +167,15 @@ inline void mark(cudaEvent_t e, cudaStream_t st) {
   else cudaEventRecord(e, st);
 }
 
-void launch_sigma(const long long* stats, double* sigma, cudaStream_t st);
+// sigma[0..1]; with key_mode 1 (PCA key) also the axis sigma[2..3].
+void launch_sigma(const long long* stats, double* sigma, int key_mode, double scl, cudaStream_t st);
 
 long long local_arena_words(long long cap_items, long long n_warps);
 int local_warps_per_cta();
 
 void launch_local(const int* piece_len, const double* piece_inc, const long long* dom_slot_off,
                   const int* dom_piece_cnt, long long n_domains, const double* sigma, double alpha, double scl,
-                  int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
+                  int key_mode, int* local_label, int* dom_group_cnt, long long* dom_group_off, jabba_group* groups,
                   long long group_capacity, long long* n_groups, Scratch& ws, unsigned* status, cudaStream_t st);
 
 long long rs_hist_words(long long cap);  // radix-sort histogram words for cap items
@@ -212,7 +213,7 @@ void launch_sse(const int* piece_len, const double* piece_inc, const long long* 
 // (the block form's starting points); null merges the records' centres.
 void launch_merge(const jabba_group* groups, const double* item_X, const double* item_Y, const long long* n_groups,
                   long long group_capacity, const long long* dom_group_off, const double* sigma, double alpha,
-                  double scl, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,
+                  double scl, int key_mode, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,
                   long long dict_capacity, long long* k, Scratch& ws, unsigned* status, cudaStream_t st,
                   const Marks& mk);
 

@@ -54,8 +54,21 @@ __device__ __forceinline__ ExactCentre exact_centre(const jabba_group& g, double
   return e;
 }
 
-__device__ __forceinline__ double exact_key(const ExactCentre& e) {
+// The sort key in binary64: X*X + Y*Y, or with the PCA key (pca = 1) the
+// projection vx X + vy Y on the axis sigma[2..3].
+__device__ __forceinline__ double exact_key(const ExactCentre& e, int pca, const double* sigma) {
+  if (pca) return __dadd_rn(__dmul_rn(sigma[2], e.X), __dmul_rn(sigma[3], e.Y));
   return __dadd_rn(__dmul_rn(e.X, e.X), __dmul_rn(e.Y, e.Y));
+}
+
+// Order-preserving unsigned image of a binary64 key (negative PCA keys
+// included): the sign bit set for non-negative values, every bit flipped for
+// negative ones.  -0 is mapped as +0 (the two compare equal, so their order
+// is that of equal keys: the compact index).
+__device__ __forceinline__ unsigned long long key_image(double k) {
+  if (k == 0.0) k = 0.0;
+  const unsigned long long u = (unsigned long long)__double_as_longlong(k);
+  return (u >> 63) ? ~u : (u | (1ull << 63));
 }
 
 __device__ __forceinline__ bool exact_within_c(const ExactCentre& a, const ExactCentre& b, double a2) {
@@ -138,7 +151,7 @@ __device__ __forceinline__ float of_ord(int o) {
 }
 
 __global__ void k_mprep(const jabba_group* groups, const double* iX, const double* iY, const long long* n_p,
-                        long long cap, const long long* dom_group_off, const double* sigma, double scl,
+                        long long cap, const long long* dom_group_off, const double* sigma, double scl, int pca,
                         unsigned long long* keys, int* vals, int* rec_of, float* X32, float* Y32, int* bounds,
                         const int* flags) {
   if (flags[1]) return;
@@ -155,7 +168,7 @@ __global__ void k_mprep(const jabba_group* groups, const double* iX, const doubl
     const float x = __double2float_rn(e.X), y = __double2float_rn(e.Y);
     X32[c] = x;
     Y32[c] = y;
-    keys[c] = (unsigned long long)__double_as_longlong(exact_key(e));
+    keys[c] = key_image(exact_key(e, pca, sigma));
     vals[c] = (int)c;
     rec_of[c] = (int)r;
     mnx = min(mnx, ord_of(x));
@@ -1325,19 +1338,19 @@ __global__ void __launch_bounds__(256) k_mlabel(MergeView V, const int* cord, co
 // ------------------------------------------------------------------ fallback: sequential greedy (binary64)
 __global__ void k_mexact_prep(const jabba_group* groups, const double* iX, const double* iY, const int* rec_of,
                               const int* sidx, const long long* n_p, long long cap, const double* sigma, double scl,
-                              const int* flags, double* eX, double* eY, double* ekey) {
+                              int pca, const int* flags, double* eX, double* eY, double* ekey) {
   if (!flags[0] || flags[1]) return;
   const long long n = clamp_groups(n_p, cap);
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (long long)gridDim.x * blockDim.x) {
     const ExactCentre e = item_point(groups, iX, iY, rec_of[sidx[a]], sigma, scl);
     eX[a] = e.X;
     eY[a] = e.Y;
-    ekey[a] = exact_key(e);
+    ekey[a] = exact_key(e, pca, sigma);
   }
 }
 
 __global__ void __launch_bounds__(1024) k_mexact_greedy(const double* eX, const double* eY, const double* ekey,
-                                                       const long long* n_p, long long cap, double alpha,
+                                                       const long long* n_p, long long cap, double alpha, int pca,
                                                        const int* flags, int* lab, int* is_start) {
   if (!flags[0] || flags[1]) return;
   __shared__ int s_next;
@@ -1363,8 +1376,16 @@ __global__ void __launch_bounds__(1024) k_mexact_greedy(const double* eX, const 
     }
     if (a >= n) break;
     const double xi = eX[a], yi = eY[a];
-    const double r = __dadd_rn(__dsqrt_rn(ekey[a]), alpha);
-    const double T = __dmul_rn(__dmul_rn(r, r), 1.0 + 0x1p-30);
+    // scan bound (Sec. 5 pruning, lossless): the norm changes by at most the
+    // distance, so does a projection on a unit axis
+    double T;
+    if (pca) {
+      T = __dadd_rn(ekey[a], __dmul_rn(alpha, 1.0 + 0x1p-30));
+      T = __dadd_rn(T, 0x1p-40 * (fabs(ekey[a]) + fabs(xi) + fabs(yi)));
+    } else {
+      const double r = __dadd_rn(__dsqrt_rn(ekey[a]), alpha);
+      T = __dmul_rn(__dmul_rn(r, r), 1.0 + 0x1p-30);
+    }
     if (tid == 0) { lab[a] = (int)a; is_start[a] = 1; }
     for (long long b = a + 1; b < n; b += nt) {
       if (tid == 0) s_stop = 0;
@@ -1525,19 +1546,19 @@ static float rup(double v) {
 
 void launch_merge(const jabba_group* groups, const double* item_X, const double* item_Y, const long long* n_groups,
                   long long group_capacity, const long long* dom_group_off, const double* sigma, double alpha,
-                  double scl, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,
+                  double scl, int key_mode, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,
                   long long dict_capacity, long long* k, Scratch& ws, unsigned* status, cudaStream_t st,
                   const Marks& mk) {
   const long long cap = group_capacity;
   const unsigned grid = (unsigned)(ws.num_sms * 8);
   MergeBufs& B = ws.mb;
   k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.bar_sub, B.flags, status, n_groups, cap);
-  k_mprep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, n_groups, cap, dom_group_off, sigma, scl, ws.m_k0, ws.m_v0,
-                                ws.m_rec, ws.m_X32, ws.m_Y32, B.bounds, B.flags);
+  k_mprep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, n_groups, cap, dom_group_off, sigma, scl, key_mode, ws.m_k0,
+                                ws.m_v0, ws.m_rec, ws.m_X32, ws.m_Y32, B.bounds, B.flags);
   unsigned long long* skey;
   int* sidx;
-  // keys are non-negative binary64: their bit patterns order as the values;
-  // the sort is stable and starts in compact-index order, so ties keep it
+  // the keys' order-preserving images (key_image) sort as the keys; the sort
+  // is stable and starts in compact-index order, so ties keep it
   radix_sort(ws.m_k0, ws.m_v0, ws.m_k1, ws.m_v1, n_groups, cap, 64, ws.m_hist, ws.num_sms, status, &skey, &sidx,
              B.flags, st);
   k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
@@ -1638,9 +1659,10 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   k_mlabel<<<grid, 256, 0, st>>>(V, cord, B.cX, B.cY, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab,
                                  B.is_start);
   // sequential fallback (only acts when flags[0] is set)
-  k_mexact_prep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, ws.m_rec, sidx, n_groups, cap, sigma, scl, B.flags,
-                                      B.eX, B.eY, B.ekey);
-  k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, B.flags, B.lab, B.is_start);
+  k_mexact_prep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, ws.m_rec, sidx, n_groups, cap, sigma, scl, key_mode,
+                                      B.flags, B.eX, B.eY, B.ekey);
+  k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, key_mode, B.flags, B.lab,
+                                      B.is_start);
   exclusive_scan<int>(B.is_start, cap, B.start_off, ws.scan_tiles, st);
   k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, n_groups, cap, dict_capacity, l2g, k, status, B.flags);
   k_dict_clear<<<grid, 256, 0, st>>>(k, dict_capacity, ws.d_acc);

@@ -19,7 +19,8 @@ def ctx():
 def params(cfg):
     import paper_2401_00109_gb300 as jb
     return jb.Params(tol=cfg["tol"], alpha=cfg["alpha"], scl=cfg["scl"], domain_mode=cfg["domain_mode"],
-                     domain_value=cfg["domain_value"], round_mode=cfg.get("round_mode", 0))
+                     domain_value=cfg["domain_value"], round_mode=cfg.get("round_mode", 0),
+                     key_mode=cfg.get("key_mode", 0))
 
 
 def run_gpu(c, x_np, off_np, cfg, recon=True):
@@ -63,7 +64,7 @@ def run_gpu(c, x_np, off_np, cfg, recon=True):
 def run_oracle(x_np, off_np, cfg, recon=True, threads=8):
     return oracle.pipeline(x_np, off_np, cfg["tol"], cfg["alpha"], cfg["scl"], cfg["domain_mode"],
                            cfg["domain_value"], threads=threads, with_reconstruct=recon,
-                           round_mode=cfg.get("round_mode", 0))
+                           round_mode=cfg.get("round_mode", 0), key="pca" if cfg.get("key_mode", 0) else "norm")
 
 
 def first_diff(a, b):
@@ -82,6 +83,8 @@ def assert_parity(g, r, recon=True):
         assert np.array_equal(g[k], r[k]), (k, first_diff(g[k], r[k]))
     assert np.array_equal(g["piece_inc"], r["piece_inc"]), ("piece_inc", first_diff(g["piece_inc"], r["piece_inc"]))
     assert g["sigma"][0] == r["sigma_len"] and g["sigma"][1] == r["sigma_inc"], (g["sigma"], r["sigma_len"], r["sigma_inc"])
+    if r.get("axis") is not None:                      # the PCA axis, bit for bit
+        assert (g["sigma"][2], g["sigma"][3]) == r["axis"], (g["sigma"], r["axis"])
     assert np.array_equal(g["local_label"], r["local_label"]), ("local_label", first_diff(g["local_label"], r["local_label"]))
     assert np.array_equal(g["dom_group_off"], r["dom_group_off"])
     assert np.array_equal(g["l2g"], r["l2g"]), ("l2g", first_diff(g["l2g"], r["l2g"]))

@@ -345,14 +345,16 @@ def test_scale_full_two_in_flight():
         assert np.array_equal(ln, h["piece_len"][s0:s0 + n]) and np.array_equal(inc, h["piece_inc"][s0:s0 + n]), d
 
 
-@pytest.mark.parametrize("name", ["multivar", "uneven"])
-def test_full_size_bit_exact(name):
+@pytest.mark.parametrize("name,key_mode", [("multivar", 0), ("uneven", 0), ("multivar", 1)])
+def test_full_size_bit_exact(name, key_mode):
     """The multivariate (64 x 2^20) and uneven (10,000 series) workloads at
     full size: every output of the path and the reconstruction equal the
     oracle's (pieces, sigma, local labels, map, dictionary, symbols, quantized
-    lengths bit for bit; reconstruction within 1e-9)."""
+    lengths bit for bit; reconstruction within 1e-9); the multivariate one
+    also with the PCA sort key (Sec. 5)."""
     from _gpu import assert_parity, check_flips, ctx, run_gpu, run_oracle
     x, off, cfg = synth.make(name)
+    cfg = dict(cfg, key_mode=key_mode)
     g, *_ = run_gpu(ctx(), x, off, cfg)
     r = run_oracle(x, off, cfg, threads=16)
     assert_parity(g, r)

@@ -28,6 +28,31 @@ def test_workload_parity(C, name, max_series):
                 g["dom_piece_off"], cfg["tol"])
 
 
+@pytest.mark.parametrize("name,max_series", [("small", None), ("uneven", 40), ("multivar", 2), ("diff", 48),
+                                             ("scale", 150)])
+def test_pca_key_parity(C, name, max_series):
+    """The PCA sort key (Sec. 5 "norm or PCA projection") in Stage I and II:
+    the axis, the signed projection order, the key-gap pruning and every
+    output equal the oracle's pipeline(key="pca") bit for bit."""
+    x, off, cfg = synth.make(name, max_series=max_series)
+    cfg = dict(cfg, key_mode=1)
+    g, *_ = run_gpu(C, x, off, cfg)
+    r = run_oracle(x, off, cfg)
+    assert r["axis"] is not None and r["axis"][1] != 0.0   # a tilted axis: negative keys occur
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("scl,alpha", [(0.5, 0.1), (2.0, 0.3), (0.0, 0.1)])
+def test_pca_key_parity_scl(C, scl, alpha):
+    """The PCA key with scl != 1 (an axis off the diagonal) and scl = 0
+    (lengths ignored: the axis is (0, 1))."""
+    x, off, cfg = synth.make("uneven", max_series=20)
+    cfg = dict(cfg, key_mode=1, scl=scl, alpha=alpha)
+    g, *_ = run_gpu(C, x, off, cfg, recon=False)
+    r = run_oracle(x, off, cfg, recon=False)
+    assert_parity(g, r, recon=False)
+
+
 @pytest.mark.parametrize("round_mode", [0, 1])
 def test_round_modes(C, round_mode):
     x, off, cfg = synth.make("small", max_series=5)
