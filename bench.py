@@ -343,13 +343,6 @@ def run_ours(args, ws, rank, local):
     # clocks sampled over both timed regions (one batch, two in flight)
     clocks = sampler.stop()
 
-    # ---- plain: the unbatched form (one compression launch and one Stage I
-    # launch per domain, eager, no graph) on a bounded sample of the same
-    # workload, next to the batched form on that sample
-    plain = None
-    if not args.no_plain:
-        plain = plain_form(jb, synth, args, local, ws)
-
     # ---- e2e: H2D of the series from pinned memory, the step, D2H of the
     # symbols and dictionary, all inside the timed region
     e2e = None
@@ -435,6 +428,13 @@ def run_ours(args, ws, rank, local):
         e2e = dict(value=ws * n / (ems * 1e-3) / 1e9, unit="Gpts/s", h2d_bytes_per_step=bi, d2h_bytes_per_step=bo,
                    ms_per_step=ems, batches_in_flight=2 if inflight is not None else 1)
         ctx.sync_status(where="e2e steps")
+
+    # ---- plain: the unbatched form (one compression launch and one Stage I
+    # launch per domain, eager, no graph) on a bounded sample of the same
+    # workload, next to the batched form on that sample
+    plain = None
+    if not args.no_plain:
+        plain = plain_form(jb, synth, args, local, ws)
 
     # ---- rooflines (HBM; nothing here is a dense contraction): the three
     # largest stages and the dominant one (roofline_table)

@@ -957,19 +957,37 @@ __global__ void __launch_bounds__(256) k_mrounds(RoundArgs R) {
 constexpr int kOwnSteps = 4;  // 128-item steps an evaluation tests in its own cell before it yields
 
 struct NbScratch {               // one per warp, shared memory
-  int sp[81];                    // decided starts of the 9 x 9 block: sorted position
-  float sx[81], sy[81];          // and FP32 coordinates
+  int sp[81];                    // decided starts of the 9 x 9 block (those of the 5 x 5 block first):
+  float sx[81], sy[81];          //   sorted position, FP32 coordinates,
+  signed char sdx[81], sdy[81];  //   cell offset from the evaluated cell
   int uq[24], ulo[24], uhi[24];  // undecided cells of the 5 x 5 block: cell, first item not known covered, end
   int ucd[24];                   // and the sorted position of that first item
+  signed char udx[24], udy[24];  // and its cell offset
 };
 
 // Item (sorted position r, FP32 x, y) covered by a gathered start that
-// precedes it.
+// precedes it, among the gathered starts [0, ns).
 __device__ __forceinline__ bool covered_by_starts(const MergeView& V, const NbScratch& W, int ns, int r, float x,
                                                   float y) {
   for (int i = 0; i < ns; ++i) {
     const int s = W.sp[i];
     if (s >= r) continue;
+    const int f = filter_c(W.sx[i], W.sy[i], x, y, V.a2lo, V.a2hi);
+    if (f == 1) return true;
+    if (f == 2 && exact_within_sorted(V, s, r)) return true;
+  }
+  return false;
+}
+
+// The same for an item of the cell at offset (qdx, qdy): only starts within
+// two cells of it can lie within alpha (the cell side exceeds alpha / 2, and
+// the grid check bounds the coordinates' error by 2^-8 of a cell), so the
+// others are skipped before the distance filter.
+__device__ __forceinline__ bool covered_by_starts_at(const MergeView& V, const NbScratch& W, int ns, int qdx,
+                                                     int qdy, int r, float x, float y) {
+  for (int i = 0; i < ns; ++i) {
+    const int s = W.sp[i];
+    if (s >= r || abs(W.sdx[i] - qdx) > 2 || abs(W.sdy[i] - qdy) > 2) continue;
     const int f = filter_c(W.sx[i], W.sy[i], x, y, V.a2lo, V.a2hi);
     if (f == 1) return true;
     if (f == 2 && exact_within_sorted(V, s, r)) return true;
@@ -1008,33 +1026,46 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
   unsigned long long sq[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) sq[i] = q[i] >= 0 ? ld_state(&R.state[q[i]]) : 0ull;
-  int ns = 0, nu = 0;
+  int ns = 0, nu = 0, ns5 = 0;
   bool und[3];  // undecided when gathered (a cell decided since is skipped when evaluated)
+  // two passes: the starts of the 5 x 5 block (the only ones that can cover
+  // the cell's own items) first, then the rest of the 9 x 9 block
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int k = i * 32 + lane;
-    const int dx = k % 9 - 4, dy = k / 9 - 4;
-    const unsigned sv = (unsigned)sq[i];
-    const bool is_s = q[i] >= 0 && sv < kNoStart;
-    und[i] = q[i] >= 0 && sv == kUndecided;
-    const bool is_u = und[i] && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2;
-    const unsigned ms = __ballot_sync(0xFFFFFFFFu, is_s), mu = __ballot_sync(0xFFFFFFFFu, is_u);
-    if (is_s) {
-      const int o = ns + __popc(ms & lt);
-      W.sp[o] = (int)sv;
-      W.sx[o] = R.V.sX[sv];
-      W.sy[o] = R.V.sY[sv];
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int k = i * 32 + lane;
+      const int dx = k % 9 - 4, dy = k / 9 - 4;
+      const bool inner = dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2;
+      const unsigned sv = (unsigned)sq[i];
+      const bool is_s = q[i] >= 0 && sv < kNoStart && inner == (pass == 0);
+      const unsigned ms = __ballot_sync(0xFFFFFFFFu, is_s);
+      if (is_s) {
+        const int o = ns + __popc(ms & lt);
+        W.sp[o] = (int)sv;
+        W.sx[o] = R.V.sX[sv];
+        W.sy[o] = R.V.sY[sv];
+        W.sdx[o] = (signed char)dx;
+        W.sdy[o] = (signed char)dy;
+      }
+      ns += __popc(ms);
+      if (pass == 1) continue;
+      und[i] = q[i] >= 0 && sv == kUndecided;
+      const bool is_u = und[i] && inner;
+      const unsigned mu = __ballot_sync(0xFFFFFFFFu, is_u);
+      if (is_u) {
+        const int o = nu + __popc(mu & lt);
+        const int lo = (int)(sq[i] >> 32);
+        W.uq[o] = q[i];
+        W.ulo[o] = lo;
+        W.uhi[o] = R.cell_end[q[i]];
+        W.ucd[o] = lo < R.item_cap ? R.cord[lo] : 0x7FFFFFFF;  // used only when lo < end
+        W.udx[o] = (signed char)dx;
+        W.udy[o] = (signed char)dy;
+      }
+      nu += __popc(mu);
     }
-    if (is_u) {
-      const int o = nu + __popc(mu & lt);
-      const int lo = (int)(sq[i] >> 32);
-      W.uq[o] = q[i];
-      W.ulo[o] = lo;
-      W.uhi[o] = R.cell_end[q[i]];
-      W.ucd[o] = lo < R.item_cap ? R.cord[lo] : 0x7FFFFFFF;  // used only when lo < end
-    }
-    ns += __popc(ms);
-    nu += __popc(mu);
+    if (pass == 0) ns5 = ns;
   }
   __syncwarp();
   // ---- own items: the first one not covered, 128 items per step (four per
@@ -1074,7 +1105,7 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       const int u = t + i * 32 + lane;
       bool unc = false;
       if (!h[i]) {  // also false past the end
-        if (covered_by_starts(R.V, W, ns, r[i], ux[i], uy[i])) R.cov[u] = 1;  // hint: covered by a decided start
+        if (covered_by_starts(R.V, W, ns5, r[i], ux[i], uy[i])) R.cov[u] = 1;  // hint: covered by a decided start
         else unc = true;
       }
       const unsigned b = __ballot_sync(0xFFFFFFFFu, unc);
@@ -1140,8 +1171,9 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       for (int i = 0; i < 4; ++i) {
         if (nl[i] < 0 || blocked) continue;
         const bool past = !v4[i] || r4[i] >= p;  // past the end of the cell counts as past
+        const int qn = nl[i] >= 0 ? nl[i] : 0;
         const bool hit = !past && !h4[i] && filter_c(x4[i], y4[i], px, py, R.V.a2lo, R.V.a2hi) != 0 &&
-                         !covered_by_starts(R.V, W, ns, r4[i], x4[i], y4[i]);
+                         !covered_by_starts_at(R.V, W, ns, W.udx[qn], W.udy[qn], r4[i], x4[i], y4[i]);
         if (__any_sync(0xFFFFFFFFu, hit)) blocked = true;
         else if (!__any_sync(0xFFFFFFFFu, past)) pend |= 1u << nl[i];
       }
@@ -1168,7 +1200,7 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
           const float ux = R.cX[u], uy = R.cY[u];
           past = r >= p;
           if (!past && !hint && filter_c(ux, uy, px, py, R.V.a2lo, R.V.a2hi) != 0 &&
-              !covered_by_starts(R.V, W, ns, r, ux, uy))
+              !covered_by_starts_at(R.V, W, ns, W.udx[l], W.udy[l], r, ux, uy))
             hit = true;
         }
         if (__any_sync(0xFFFFFFFFu, hit)) {

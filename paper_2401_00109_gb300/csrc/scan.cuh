@@ -49,19 +49,26 @@ static __global__ void k_scan_tile_sums(const T* in, long long n, long long* til
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-// One block scans the tile sums in place (exclusive), any number of tiles.
+// One block scans the tile sums in place (exclusive), any number of tiles:
+// thread t owns the contiguous range [t c, (t+1) c) of c = ceil(n / threads)
+// tiles, sums it, the block scans the per-thread sums once, and every thread
+// writes its range's prefixes (one block-wide scan instead of one per 256
+// tiles).
 static __global__ void k_scan_tile_offsets(long long* tile_sums, long long n_tiles, long long* grand_total) {
   __shared__ long long sw[kScanThreads / 32];
-  long long carry = 0;
-  for (long long base = 0; base < n_tiles; base += kScanThreads) {
-    const long long k = base + threadIdx.x;
-    const long long v = k < n_tiles ? tile_sums[k] : 0;
-    long long total;
-    const long long ex = block_exclusive_scan<long long>(v, sw, total);
-    if (k < n_tiles) tile_sums[k] = carry + ex;
-    carry += total;
+  const long long per = (n_tiles + kScanThreads - 1) / kScanThreads;
+  const long long lo = (long long)threadIdx.x * per;
+  const long long hi = lo + per < n_tiles ? lo + per : n_tiles;
+  long long v = 0;
+  for (long long k = lo; k < hi; ++k) v += tile_sums[k];
+  long long total;
+  long long run = block_exclusive_scan<long long>(v, sw, total);
+  for (long long k = lo; k < hi; ++k) {
+    const long long c = tile_sums[k];
+    tile_sums[k] = run;
+    run += c;
   }
-  if (threadIdx.x == 0 && grand_total) *grand_total = carry;
+  if (threadIdx.x == 0 && grand_total) *grand_total = total;
 }
 
 template <typename T>
