@@ -647,24 +647,33 @@ __device__ __forceinline__ unsigned zero_nibble(unsigned w) {
   return (m | (m >> 7) | (m >> 14) | (m >> 21)) & 0xFu;
 }
 
-// First index in [t, end) whose cov flag is 0, else end (whole warp; 16-byte
-// loads, 512 flags per step; the buffer is padded past its last item).
+// First index in [t, end) whose cov flag is 0, else end (whole warp; four
+// 16-byte loads per lane in flight together, 2,048 flags per step, so a long
+// run of covered items in a dense cell costs few dependent trips; the buffer
+// is padded past its last item).
 __device__ __forceinline__ int first_uncovered(const unsigned char* cov, int t, int end) {
   const int lane = threadIdx.x & 31;
-  for (int b = t & ~15; b < end; b += 512) {
-    const int o = b + lane * 16;
-    unsigned msk = 0;
-    if (o < end) {
-      const uint4 w = __ldcg((const uint4*)(cov + o));  // L2: flags written by other SMs
-      msk = zero_nibble(w.x) | (zero_nibble(w.y) << 4) | (zero_nibble(w.z) << 8) | (zero_nibble(w.w) << 12);
-      if (t > o) msk &= 0xFFFFu << (t - o < 16 ? t - o : 16);
-      if (end - o < 16) msk &= (1u << (end - o)) - 1u;
+  for (int b = t & ~15; b < end; b += 2048) {
+    unsigned msk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = b + k * 512 + lane * 16;
+      msk[k] = 0;
+      if (o < end) {
+        const uint4 w = __ldcg((const uint4*)(cov + o));  // L2: flags written by other SMs
+        msk[k] = zero_nibble(w.x) | (zero_nibble(w.y) << 4) | (zero_nibble(w.z) << 8) | (zero_nibble(w.w) << 12);
+        if (t > o) msk[k] &= 0xFFFFu << (t - o < 16 ? t - o : 16);
+        if (end - o < 16) msk[k] &= (1u << (end - o)) - 1u;
+      }
     }
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, msk != 0);
-    if (bal) {
-      const int l = __ffs(bal) - 1;
-      const unsigned mm = __shfl_sync(0xFFFFFFFFu, msk, l);
-      return b + l * 16 + __ffs(mm) - 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, msk[k] != 0);
+      if (bal) {
+        const int l = __ffs(bal) - 1;
+        const unsigned mm = __shfl_sync(0xFFFFFFFFu, msk[k], l);
+        return b + k * 512 + l * 16 + __ffs(mm) - 1;
+      }
     }
   }
   return end;
