@@ -641,6 +641,45 @@ __device__ bool grid_barrier(unsigned* bar, unsigned* sub, unsigned nblocks, uns
   return ok_s != 0;
 }
 
+// The same barrier for a caller that counts its barriers: the generation
+// starts at 0 for the launch (k_minit), so barrier b of the launch completes
+// when the generation reaches b + 1 and the waiters need not read it first
+// (one dependent trip fewer per barrier).
+__device__ bool grid_barrier_n(unsigned* bar, unsigned* sub, unsigned nblocks, unsigned* status, unsigned b) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    __threadfence();
+    int ok = 1;
+    const unsigned grp = blockIdx.x % kBarGroups;
+    const unsigned gsz = nblocks / kBarGroups + (grp < nblocks % kBarGroups ? 1u : 0u);
+    const unsigned ngrp = nblocks < kBarGroups ? nblocks : kBarGroups;
+    bool released = false;
+    if (atomicAdd(&sub[32 * grp], 1u) == gsz - 1) {
+      atomicExch(&sub[32 * grp], 0u);
+      if (atomicAdd(&sub[32 * kBarGroups], 1u) == ngrp - 1) {
+        atomicExch(&sub[32 * kBarGroups], 0u);
+        __threadfence();
+        atomicAdd(&bar[1], 1u);
+        released = true;
+      }
+    }
+    if (!released) {
+      unsigned spins = 0;
+      const unsigned lim = spin_limit(status);
+      while ((int)(*gen - (b + 1u)) < 0) {
+        if (++spins > lim) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
 // Bits 0..3 = bytes 0..3 of w are zero (flags hold 0 or 1).
 __device__ __forceinline__ unsigned zero_nibble(unsigned w) {
   const unsigned m = ~w & 0x01010101u;
@@ -1293,8 +1332,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
   const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
   const size_t stride = (size_t)(n_cells > 0 ? n_cells : 1);
+  // this round's list size, its coverage counter and this warp's first list
+  // entry: read together right after the previous round's barrier
+  unsigned n_eval = 0;
+  unsigned long long ctr = 0;
+  int j0 = 0;
   for (unsigned round = 0; round < R.max_rounds; ++round) {
-    const int cur = round % 3, nxt = (round + 1) % 3, old = (round + 2) % 3;
+    const int nxt = (round + 1) % 3, old = (round + 2) % 3;
     const int* lcur = R.chg_list + (size_t)(round & 1) * stride;
     int* lnxt = R.chg_list + (size_t)((round + 1) & 1) * stride;
     // the counters of slot `old` were last read in the previous round
@@ -1308,14 +1352,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
       for (long long j = warp_g; j < n_cells; j += n_warps)
         eval_cell1(R, g, (int)j, round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
     } else {
-      // the first entry of this warp is read beside the list size (past the
-      // size it is a stale entry of the buffer, not used)
-      const int j0 = warp_g < (long long)stride ? __ldcg(&lcur[warp_g]) : 0;
-      const unsigned n_eval = *((volatile unsigned*)&R.lcnt[cur]);
       for (long long i = warp_g; i < (long long)n_eval; i += n_warps)
         eval_cell1(R, g, i == warp_g ? j0 : __ldcg(&lcur[i]), round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
       // coverage hints of the previous round's starts (warps from the top)
-      const unsigned long long ctr = *((volatile unsigned long long*)&R.uctr[cur]);
       const unsigned n_new = (unsigned)(ctr >> 40);
       const unsigned total = (unsigned)(ctr & kUnitMask);
       const unsigned per = (unsigned)(((long long)total + n_warps - 1) / n_warps);
@@ -1324,8 +1363,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
         cover_units<false>(R, (long long)((round + 1) & 1) * R.slot_stride, u0, min(total, u0 + per), n_new, round,
                            nullptr, nullptr);
     }
-    if (!grid_barrier(R.bar, R.bar_sub, nblocks, R.status)) return;
-    if (*((volatile unsigned*)&R.lcnt[nxt]) == 0) {
+    if (!grid_barrier_n(R.bar, R.bar_sub, nblocks, R.status, round)) return;
+    // the next round's list entry is read beside its size (past the size it
+    // is a stale entry of the buffer, not used)
+    j0 = warp_g < (long long)stride ? __ldcg(&lnxt[warp_g]) : 0;
+    n_eval = *((volatile unsigned*)&R.lcnt[nxt]);
+    ctr = *((volatile unsigned long long*)&R.uctr[nxt]);
+    if (n_eval == 0) {
       if (warp_g == 0 && lane == 0) R.bar[2] = round + 1;  // diagnostics: rounds used
       return;
     }
