@@ -516,14 +516,27 @@ struct TileCfg {
   static constexpr int kGroupsPerPass = CAP / 4;
 };
 
-// Accumulator of one group during the sums: three 32-bit limbs of the
-// increments' 2^-64 fixed-point images, each summed as a signed 64-bit
-// integer (deferred carries), the length sum and the member count.
+// Accumulator of one group during the sums: the increments' 2^-64
+// fixed-point images (magnitudes below 2^96 under the range contract) in two
+// 48-bit limbs, each summed as a signed 64-bit integer (deferred carries: at
+// most 4,096 members, so below 2^60), and the member count and length sum
+// packed in one word (count << 40 | lensum: a domain of a series has fewer
+// than 2^31 intervals): three shared-memory atomics per piece.
 struct GroupAcc {
-  long long limb[3];
-  int lensum;
-  int count;
+  long long lo48, hi48;
+  unsigned long long cnt_len;
 };
+
+// 192-bit two's complement value of lo + hi 2^48 (both signed).
+__device__ __forceinline__ I192 from_limbs48(long long lo, long long hi) {
+  I192 r;
+  r.w0 = (u64)lo;
+  r.w1 = lo < 0 ? ~0ull : 0ull;
+  r.w2 = r.w1;
+  const u64 h0 = (u64)hi << 48, h1 = (u64)(hi >> 16), h2 = hi < 0 ? ~0ull : 0ull;  // hi 2^48, sign-extended
+  add192(r, h0, h1, h2);
+  return r;
+}
 
 // Synchronization of the W warps that own one domain.
 template <int W>
@@ -882,11 +895,9 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
       for (int g0 = 0; g0 < G; g0 += Cfg::kGroupsPerPass) {
         const int gn = min(G - g0, Cfg::kGroupsPerPass);
         for (int g = t; g < gn; g += T) {
-          acc[g].limb[0] = 0;
-          acc[g].limb[1] = 0;
-          acc[g].limb[2] = 0;
-          acc[g].lensum = 0;
-          acc[g].count = 0;
+          acc[g].lo48 = 0;
+          acc[g].hi48 = 0;
+          acc[g].cnt_len = 0;
         }
         tile_sync<W>();
         for (int i = t; i < n; i += T) {
@@ -894,26 +905,23 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
           if (g < 0 || g >= gn) continue;
           bool neg;
           const U128 m = fx_mag(pinc[i], neg);          // < 2^96 under the range contract
-          long long l0 = (long long)(m.lo & 0xFFFFFFFFull);
-          long long l1 = (long long)(m.lo >> 32);
-          long long l2 = (long long)(m.hi & 0xFFFFFFFFull);
-          if (neg) { l0 = -l0; l1 = -l1; l2 = -l2; }
-          atomicAdd((unsigned long long*)&acc[g].limb[0], (unsigned long long)l0);
-          atomicAdd((unsigned long long*)&acc[g].limb[1], (unsigned long long)l1);
-          atomicAdd((unsigned long long*)&acc[g].limb[2], (unsigned long long)l2);
-          atomicAdd(&acc[g].lensum, plen[i]);
-          atomicAdd(&acc[g].count, 1);
+          long long l0 = (long long)(m.lo & 0xFFFFFFFFFFFFull);
+          long long l1 = (long long)((m.lo >> 48) | (m.hi << 16));
+          if (neg) { l0 = -l0; l1 = -l1; }
+          atomicAdd((unsigned long long*)&acc[g].lo48, (unsigned long long)l0);
+          atomicAdd((unsigned long long*)&acc[g].hi48, (unsigned long long)l1);
+          atomicAdd(&acc[g].cnt_len, (1ull << 40) | (unsigned long long)(unsigned)plen[i]);
         }
         tile_sync<W>();
         for (int g = t; g < gn; g += T) {
-          const long long L[6] = {acc[g].limb[0], acc[g].limb[1], acc[g].limb[2], 0, 0, 0};
-          const I192 s = from_limbs6(L);
+          const I192 s = from_limbs48(acc[g].lo48, acc[g].hi48);
+          const unsigned long long cl = acc[g].cnt_len;
           jabba_group rec;
           rec.inc[0] = s.w0;
           rec.inc[1] = s.w1;
           rec.inc[2] = s.w2;
-          rec.lensum = acc[g].lensum;
-          rec.count = acc[g].count;
+          rec.lensum = (long long)(cl & ((1ull << 40) - 1));
+          rec.count = (int)(cl >> 40);
           rec.local_id = g0 + g;
           rec.domain = d;
           rec.pad = 0;
