@@ -530,11 +530,26 @@ __global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const lo
     const int cnt = dom_piece_cnt[d];
     const long long slot = dom_slot_off[d];
     double prev_end = x[dom_begin[d]];
-    for (int base = 0; base < cnt; base += 32) {
+    // four chunks of 32 pieces per group, their loads in flight together
+    // (the chunks of a group are then processed in order: each needs the end
+    // value of the one before)
+    for (int base0 = 0; base0 < cnt; base0 += 128) {
+    int lenq[4];
+    double endq[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = base0 + 32 * c + lane;
+      lenq[c] = j < cnt ? piece_len[slot + j] : 0;
+      endq[c] = j < cnt ? piece_inc[slot + j] : 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int base = base0 + 32 * c;
+      if (base >= cnt) break;
       const int j = base + lane;
       const bool valid = j < cnt;
-      const int len = valid ? piece_len[slot + j] : 0;
-      const double endv = valid ? piece_inc[slot + j] : 0.0;
+      const int len = lenq[c];
+      const double endv = endq[c];
       double startv = __shfl_up_sync(0xFFFFFFFFu, endv, 1);
       if (lane == 0) startv = prev_end;
       const double inc = __dsub_rn(endv, startv);
@@ -554,6 +569,7 @@ __global__ void __launch_bounds__(256) k_finish_pieces(const double* x, const lo
         add192(a2, q.lo, q.hi, 0);
         if (kProd) acc_signed(a3, fx_prod(inc, (unsigned)len), neg);
       }
+    }
     }
   }
   // warp reduction of limbs, then one set of atomics per warp

@@ -16,7 +16,17 @@ __global__ void __launch_bounds__(256) k_symbolize(const int* local_label, const
   for (long long d = w; d < n_domains; d += nw) {
     const int n = dom_piece_cnt[d];
     const long long slot = dom_slot_off[d], po = dom_piece_off[d], go = dom_group_off[d];
-    for (int j = lane; j < n; j += 32) symbol[po + j] = l2g[go + local_label[slot + j]];
+    // four labels per lane, then their four gathers, in flight together
+    for (int j0 = lane; j0 < n; j0 += 128) {
+      int lab[4], s[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) lab[c] = j0 + 32 * c < n ? local_label[slot + j0 + 32 * c] : 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s[c] = j0 + 32 * c < n ? l2g[go + lab[c]] : 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (j0 + 32 * c < n) symbol[po + j0 + 32 * c] = s[c];
+    }
   }
 }
 
