@@ -341,6 +341,18 @@ jabba_status jabba_profile_elapsed(jabba_ctx* ctx, int slot, int stage, float* m
  * last global merge.  n = entries wanted. */
 jabba_status jabba_diagnostics(jabba_ctx* ctx, int64_t* out, int n);
 
+/* Self-check of the binary64 division that jabba_merge_global evaluates on
+ * the integer units for the exact centres of Eq. 4 (no counterpart in the
+ * paper): for i < n, a[i] / b[i] by that path is compared bit for bit with
+ * the correctly rounded binary64 quotient.  a, b: device arrays of n
+ * doubles; counts: device int64[2], set to (quotients the path handled,
+ * quotients that differ); elements outside the path (non-normal operands or
+ * quotient, b <= 0) are skipped.  mode 0: b is any divisor; mode 1: b holds
+ * member counts 1..4096, divided through their tabulated reciprocals (other
+ * values are skipped).  Asynchronous on `stream`. */
+jabba_status jabba_check_division(jabba_ctx* ctx, const double* a, const double* b, int64_t n, int mode,
+                                  int64_t* counts, jabba_stream stream);
+
 /* Reconstruction error (Sec. 3.3): *out (device scalar) = (1/n) sum (x - xhat)^2,
  * summed in a fixed order (the same result on every call on a device). */
 jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int64_t n_points, double* out,

@@ -119,6 +119,7 @@ def load():
                 "jabba_reconstruct": (C.c_int, [V, V, I64, V, I64, V, V, V, V, V, C.POINTER(_Params), V, V, V]),
                 "jabba_reconstruct_backward": (C.c_int, [V, V, I64, V, I64, V, V, V, V, V, I64, V, V]),
                 "jabba_mse": (C.c_int, [V, V, V, I64, V, V]),
+                "jabba_check_division": (C.c_int, [V, V, V, I64, C.c_int, V, V]),
                 "jabba_profile_slot": (C.c_int, [V, C.c_int]),
                 "jabba_diagnostics": (C.c_int, [V, C.POINTER(C.c_int64), C.c_int]),
                 "jabba_reconstruct_noalloc": (C.c_int, [V, I64, V, I64, V, V, I64, V, V, V, C.c_int32, V, V, V]),
@@ -454,6 +455,17 @@ class Context:
         ms = C.c_float()
         _check(self.lib.jabba_profile_elapsed(self.h, int(slot), int(stage), C.byref(ms)), "jabba_profile_elapsed")
         return ms.value
+
+    def check_division(self, a, b, mode: int = 0, stream=None):
+        """Self-check of the merge's integer-unit binary64 division (device
+        float64 tensors a, b of one size): returns (quotients the path
+        handled, quotients that differ from the binary64 division)."""
+        torch = _torch()
+        counts = torch.zeros(2, dtype=torch.int64, device=a.device)
+        _check(self.lib.jabba_check_division(self.h, _ptr(a), _ptr(b), a.numel(), int(mode), _ptr(counts),
+                                             self._stream(stream)), "jabba_check_division")
+        c = counts.cpu().numpy()
+        return int(c[0]), int(c[1])
 
     def mse(self, x, xhat, stream=None):
         torch = _torch()

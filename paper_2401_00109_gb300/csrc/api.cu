@@ -111,6 +111,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
   w.m_v0 = (int*)take(4 * G);
   w.m_v1 = (int*)take(4 * G);
   w.m_rec = (int*)take(4 * G);
+  w.m_recip = (unsigned long long*)take(8 * (kRecipCnt + 1 + 8));
   w.m_hist = (unsigned*)take(4 * (size_t)rs_hist_words(G));
   w.m_X32 = (float*)take(4 * G);
   w.m_Y32 = (float*)take(4 * G);
@@ -866,6 +867,14 @@ jabba_status jabba_set_tuning(jabba_ctx* c, const jabba_tuning* in) {
   t.merge_form = in->merge_form;
   t.merge_warps = in->merge_warps;
   return JABBA_OK;
+}
+
+jabba_status jabba_check_division(jabba_ctx* c, const double* a, const double* b, int64_t n, int mode,
+                                  int64_t* counts, jabba_stream stream) {
+  if (!c || n < 0 || !counts || (mode != 0 && mode != 1) || (n > 0 && (!a || !b))) return JABBA_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  launch_check_div(a, b, n, mode, (long long*)counts, c->ws.num_sms, (cudaStream_t)stream);
+  return cuda_ok(cudaGetLastError());
 }
 
 jabba_status jabba_mse(jabba_ctx* c, const double* x, const double* xhat, int64_t n_points, double* out,

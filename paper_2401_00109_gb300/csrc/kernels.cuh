@@ -31,6 +31,9 @@ struct PerDevice {
 };
 
 // Buffers of the global merge (sizes: cap = group capacity, cells = grid cells).
+// Member counts up to this have tabulated reciprocals for the exact centres.
+constexpr int kRecipCnt = 4096;
+
 struct MergeBufs {
   int* bounds = nullptr;             // [4] ordered-int min/max of the FP32 coordinates
   unsigned* bar = nullptr;           // [16] grid barrier generation and round counters
@@ -126,6 +129,7 @@ struct Scratch {
   long long cap_cells = 0;        // grid cells of the merge
   MergeBufs mb;
   int* m_rec = nullptr;           // [cap_groups] record of each compact index
+  unsigned long long* m_recip = nullptr;  // [kRecipCnt + 1 + 8] reciprocal tables of the exact centres
   unsigned* m_hist = nullptr;     // radix histograms
   long long* d_acc = nullptr;     // [cap_groups * 8] dictionary accumulators
   // reconstruction
@@ -211,6 +215,9 @@ void launch_sse(const int* piece_len, const double* piece_inc, const long long* 
 
 // item_X / item_Y (nullable): binary64 points of the group records to merge
 // (the block form's starting points); null merges the records' centres.
+// Self-check of the integer-unit division of the exact centres (merge.cu).
+void launch_check_div(const double* a, const double* b, long long n, int mode, long long* counts, int num_sms,
+                      cudaStream_t st);
 void launch_merge(const jabba_group* groups, const double* item_X, const double* item_Y, const long long* n_groups,
                   long long group_capacity, const long long* dom_group_off, const double* sigma, double alpha,
                   double scl, int key_mode, int* l2g, double* dict_len, double* dict_inc, long long* dict_count,

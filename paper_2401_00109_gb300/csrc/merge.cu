@@ -90,6 +90,168 @@ struct MergeView {
 };
 
 // Binary64 point of record r: its centre, or the point given for it.
+// ------------------------------------------------------------------ binary64 division on the integer units
+// This GPU issues binary64 arithmetic at a small fraction of its integer
+// rate, and the exact centre of every item takes four correctly rounded
+// divisions, so k_mprep divides on the significands.  With a = ma 2^ea and
+// b = mb 2^eb (ma, mb in [2^52, 2^53)) and s = [ma < mb], the quotient's
+// 53-bit significand is Q = floor(ma 2^(52+s) / mb), rounded to nearest
+// (ties to even) by the remainder R = ma 2^(52+s) - Q mb: up when 2R > mb,
+// or 2R = mb and Q is odd; a carry out of 53 bits bumps the exponent.  Q is
+// estimated as floor(ma v / 2^(64-s)) from v = floor(2^116 / mb), which lies
+// below 2^116 / mb by less than 1, so the estimate errs by less than
+// ma 2^(52+s) / 2^116 < 1: it is Q or Q - 1, and R (below 2 mb < 2^54) is
+// exact in 64-bit arithmetic.  The result equals __ddiv_rn(a, b) wherever
+// this path applies (a normal or zero, b positive normal, the quotient
+// normal); elsewhere the caller divides in binary64.
+struct DivRecip {
+  u64 mb;  // the divisor's significand, [2^52, 2^53)
+  u64 v;   // floor(2^116 / mb) (2^64 - 1 for mb = 2^52)
+  int eb;  // the divisor is mb 2^eb
+  int ok;  // the divisor is a positive normal number
+};
+
+// v = floor(2^116 / mb) by restoring division, one quotient bit per step
+// (2^116 = 2^52 2^64 and 2^52 <= mb: the remainder starts at 2^52).
+__device__ __forceinline__ u64 recip116(u64 mb) {
+  u64 rem = 1ull << 52, v = 0;
+  for (int i = 0; i < 64; ++i) {
+    rem <<= 1;
+    const u64 bit = rem >= mb ? 1ull : 0ull;
+    rem -= bit ? mb : 0ull;
+    v = (v << 1) | bit;
+  }
+  return v;
+}
+
+__device__ __forceinline__ DivRecip make_recip(double b) {
+  const u64 bb = (u64)__double_as_longlong(b);
+  const int be = (int)((bb >> 52) & 0x7FF);
+  DivRecip r;
+  r.ok = (bb >> 63) == 0 && be != 0 && be != 0x7FF;
+  r.mb = (bb & ((1ull << 52) - 1)) | (1ull << 52);
+  r.eb = be - 1075;
+  r.v = recip116(r.mb);
+  return r;
+}
+
+// The divisor c = 1 .. kRecipCnt (a member count) from its table entry v.
+__device__ __forceinline__ DivRecip count_recip(int c, u64 v) {
+  const int top = 31 - __clz(c);
+  DivRecip r;
+  r.mb = (u64)c << (52 - top);
+  r.eb = top - 52;
+  r.v = v;
+  r.ok = 1;
+  return r;
+}
+
+// a / b rounded to nearest even; false where the path does not apply.
+__device__ __forceinline__ bool div_rn_int(double a, const DivRecip& r, double& q) {
+  const u64 ab = (u64)__double_as_longlong(a);
+  const u64 sign = ab & (1ull << 63);
+  const int ae = (int)((ab >> 52) & 0x7FF);
+  if (!r.ok || ae == 0x7FF) return false;
+  if (ae == 0) {
+    if ((ab << 1) != 0) return false;  // subnormal
+    q = __longlong_as_double((long long)sign);  // +-0 / b
+    return true;
+  }
+  const u64 ma = (ab & ((1ull << 52) - 1)) | (1ull << 52);
+  const int s = ma < r.mb ? 1 : 0;
+  const u64 hi = __umul64hi(ma, r.v), lo = ma * r.v;
+  u64 Q = s ? ((hi << 1) | (lo >> 63)) : hi;
+  long long R = (long long)((ma << (52 + s)) - Q * r.mb);
+  if (R < 0) {
+    Q -= 1;
+    R += (long long)r.mb;
+  } else if (R >= (long long)r.mb) {
+    Q += 1;
+    R -= (long long)r.mb;
+  }
+  const u64 R2 = (u64)R << 1;
+  if (R2 > r.mb || (R2 == r.mb && (Q & 1ull))) Q += 1;
+  int e = (ae - 1075) - r.eb - 52 - s;  // quotient = Q 2^e
+  if (Q == (1ull << 53)) {
+    Q >>= 1;
+    ++e;
+  }
+  const int be = e + 52 + 1023;
+  if (be <= 0 || be >= 0x7FF) return false;
+  q = __longlong_as_double((long long)(sign | ((u64)be << 52) | (Q & ((1ull << 52) - 1))));
+  return true;
+}
+
+// Reciprocals of the member counts 1 .. kRecipCnt (tab[c]) and of the two
+// normalisation divisors sigma[0], sigma[1] (sig[0..1]).
+__global__ void k_recip_tables(const double* sigma, u64* tab, DivRecip* sig, const int* flags) {
+  if (flags[1]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= 1 && c <= kRecipCnt) {
+    const int top = 31 - __clz(c);
+    tab[c] = recip116((u64)c << (52 - top));
+  }
+  if (c < 2) sig[c] = make_recip(sigma[c]);
+}
+
+// Self-check of div_rn_int against the binary64 division: counts[0] +=
+// quotients the path handled, counts[1] += those that differ in any bit.
+// mode 1: b[i] is a member count 1..kRecipCnt, divided through its table
+// form (as the exact centres do).
+__global__ void k_check_div(const double* a, const double* b, long long n, int mode, long long* counts) {
+  long long handled = 0, bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    DivRecip r;
+    if (mode == 1) {
+      const int c = (int)b[i];
+      if (!(b[i] >= 1.0 && b[i] <= (double)kRecipCnt) || (double)c != b[i]) continue;
+      const int top = 31 - __clz(c);
+      r = count_recip(c, recip116((u64)c << (52 - top)));
+    } else {
+      r = make_recip(b[i]);
+    }
+    double q;
+    if (!div_rn_int(a[i], r, q)) continue;
+    ++handled;
+    if (__double_as_longlong(q) != __double_as_longlong(__ddiv_rn(a[i], b[i]))) ++bad;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    handled += __shfl_xor_sync(0xFFFFFFFFu, handled, o);
+    bad += __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd((unsigned long long*)&counts[0], (unsigned long long)handled);
+    atomicAdd((unsigned long long*)&counts[1], (unsigned long long)bad);
+  }
+}
+
+void launch_check_div(const double* a, const double* b, long long n, int mode, long long* counts, int num_sms,
+                      cudaStream_t st) {
+  cudaMemsetAsync(counts, 0, 2 * sizeof(long long), st);
+  if (n > 0) k_check_div<<<(unsigned)(num_sms * 4), 256, 0, st>>>(a, b, n, mode, counts);
+}
+
+// exact_centre through div_rn_int: the same binary64 values (every division
+// correctly rounded either way); false where a division leaves the path.
+__device__ __forceinline__ bool exact_centre_int(const jabba_group& g, const u64* tab, const DivRecip& rsl,
+                                                 const DivRecip& rsi, double scl, ExactCentre& e) {
+  if (g.count < 1 || g.count > kRecipCnt || g.lensum < 1 || g.lensum >= (1ll << 53)) return false;
+  const DivRecip rc = count_recip(g.count, tab[g.count]);
+  const u64 L = (u64)g.lensum;  // exact in binary64
+  const int top = 63 - __clzll((long long)L);
+  const double len_d = __longlong_as_double((long long)(((u64)(top + 1023) << 52) | ((L << (52 - top)) & ((1ull << 52) - 1))));
+  I192 inc;
+  inc.w0 = g.inc[0];
+  inc.w1 = g.inc[1];
+  inc.w2 = g.inc[2];
+  double c_len, c_inc, X, Y;
+  if (!div_rn_int(len_d, rc, c_len) || !div_rn_int(i192_to_double(inc), rc, c_inc)) return false;
+  if (!div_rn_int(scl == 1.0 ? c_len : __dmul_rn(scl, c_len), rsl, X) || !div_rn_int(c_inc, rsi, Y)) return false;
+  e.X = X;
+  e.Y = Y;
+  return true;
+}
+
 __device__ __forceinline__ ExactCentre item_point(const jabba_group* groups, const double* iX, const double* iY,
                                                   long long r, const double* sigma, double scl) {
   if (iX) {
@@ -153,18 +315,20 @@ __device__ __forceinline__ float of_ord(int o) {
 __global__ void k_mprep(const jabba_group* groups, const double* iX, const double* iY, const long long* n_p,
                         long long cap, const long long* dom_group_off, const double* sigma, double scl, int pca,
                         unsigned long long* keys, int* vals, int* rec_of, float* X32, float* Y32, int* bounds,
-                        const int* flags) {
+                        const int* flags, const u64* rtab, const DivRecip* rsig) {
   if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
+  const DivRecip rsl = rsig[0], rsi = rsig[1];
   int mnx = 0x7FFFFFFF, mxx = -0x7FFFFFFF, mny = 0x7FFFFFFF, mxy = -0x7FFFFFFF;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < G; r += (long long)gridDim.x * blockDim.x) {
     const jabba_group g = groups[r];
     const long long c = dom_group_off[g.domain] + g.local_id;
     // the order needs the binary64 key itself (2e7 centres are denser than
     // any FP32 key interval), so every item computes its binary64 centre
-    // (4 divisions, once); the FP32 coordinates are that centre rounded to
-    // nearest (relative error 2^-24)
-    const ExactCentre e = item_point(groups, iX, iY, r, sigma, scl);
+    // (4 divisions, once, on the integer units where they apply); the FP32
+    // coordinates are that centre rounded to nearest (relative error 2^-24)
+    ExactCentre e;
+    if (iX || !exact_centre_int(g, rtab, rsl, rsi, scl, e)) e = item_point(groups, iX, iY, r, sigma, scl);
     const float x = __double2float_rn(e.X), y = __double2float_rn(e.Y);
     X32[c] = x;
     Y32[c] = y;
@@ -1638,8 +1802,12 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   const unsigned grid = (unsigned)(ws.num_sms * 8);
   MergeBufs& B = ws.mb;
   k_minit<<<1, 1, 0, st>>>(B.bounds, B.bar, B.bar_sub, B.flags, status, n_groups, cap);
+  const u64* rtab = (const u64*)ws.m_recip;
+  const DivRecip* rsig = (const DivRecip*)(ws.m_recip + kRecipCnt + 1);
+  if (!item_X)
+    k_recip_tables<<<(kRecipCnt + 256) / 256, 256, 0, st>>>(sigma, (u64*)ws.m_recip, (DivRecip*)rsig, B.flags);
   k_mprep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, n_groups, cap, dom_group_off, sigma, scl, key_mode, ws.m_k0,
-                                ws.m_v0, ws.m_rec, ws.m_X32, ws.m_Y32, B.bounds, B.flags);
+                                ws.m_v0, ws.m_rec, ws.m_X32, ws.m_Y32, B.bounds, B.flags, rtab, rsig);
   unsigned long long* skey;
   int* sidx;
   // the keys' order-preserving images (key_image) sort as the keys; the sort
