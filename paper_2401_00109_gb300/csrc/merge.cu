@@ -1660,8 +1660,9 @@ __global__ void __launch_bounds__(1024) k_mexact_greedy(const double* eX, const 
 }
 
 // ------------------------------------------------------------------ ids, map, dictionary
-__global__ void k_mids(const int* lab, const long long* start_off, const int* sidx, const long long* n_p, long long cap,
-                       long long dict_capacity, int* l2g, long long* k_out, unsigned* status, const int* flags) {
+__global__ void k_mids(const int* lab, const long long* start_off, const int* sidx, const int* rec_of,
+                       const long long* n_p, long long cap, long long dict_capacity, int* l2g, int2* gr,
+                       long long* k_out, unsigned* status, const int* flags) {
   if (flags[1]) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *k_out = 0;
     return;
@@ -1676,6 +1677,7 @@ __global__ void k_mids(const int* lab, const long long* start_off, const int* si
     const int gid = (int)start_off[la];
     const int c = sidx[a];
     l2g[c] = gid;
+    gr[a] = make_int2(gid, rec_of[c]);  // for the dictionary sums: global id and record by sorted position
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const long long K = start_off[n];
@@ -1696,12 +1698,10 @@ __global__ void k_dict_clear(const long long* k_p, long long dict_capacity, long
     acc[i] = 0;
 }
 
-__global__ void __launch_bounds__(256) k_dict_accumulate(const jabba_group* groups, const int* rec_of,
-                                                         const int* sidx, const int* cord, const int* lab,
-                                                         const long long* start_off, const long long* n_p,
-                                                         long long cap, const long long* k_p,
-                                                         long long dict_capacity, long long* acc,
-                                                         const int* flags) {
+__global__ void __launch_bounds__(256) k_dict_accumulate(const jabba_group* groups, const int* cord,
+                                                         const int2* gr, const long long* n_p, long long cap,
+                                                         const long long* k_p, long long dict_capacity,
+                                                         long long* acc, const int* flags) {
   if (flags[1]) return;
   const long long G = clamp_groups(n_p, cap);
   const long long K = *k_p;
@@ -1715,11 +1715,9 @@ __global__ void __launch_bounds__(256) k_dict_accumulate(const jabba_group* grou
     int gid = -1;
     long long v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid) {
-      const int a = cord[t];
-      int la = lab[a];
-      if (la < 0 || la >= G) la = 0;  // unresolved (status already set), as in k_mids
-      gid = (int)start_off[la];
-      const jabba_group g = groups[rec_of[sidx[a]]];
+      const int2 q = gr[cord[t]];
+      gid = q.x;
+      const jabba_group g = groups[q.y];
       v[0] = g.count;
       v[1] = g.lensum;
       I192 w;
@@ -1917,10 +1915,13 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   k_mexact_greedy<<<1, 1024, 0, st>>>(B.eX, B.eY, B.ekey, n_groups, cap, alpha, key_mode, B.flags, B.lab,
                                       B.is_start);
   exclusive_scan<int>(B.is_start, cap, B.start_off, ws.scan_tiles, st);
-  k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, n_groups, cap, dict_capacity, l2g, k, status, B.flags);
+  // (global id, record) by sorted position, in the cell keys' buffer (not
+  // read after the cells were filled)
+  int2* gr = (int2*)ckey;
+  k_mids<<<grid, 256, 0, st>>>(B.lab, B.start_off, sidx, ws.m_rec, n_groups, cap, dict_capacity, l2g, gr, k, status,
+                               B.flags);
   k_dict_clear<<<grid, 256, 0, st>>>(k, dict_capacity, ws.d_acc);
-  k_dict_accumulate<<<grid, 256, 0, st>>>(groups, ws.m_rec, sidx, cord, B.lab, B.start_off, n_groups, cap, k,
-                                          dict_capacity, ws.d_acc, B.flags);
+  k_dict_accumulate<<<grid, 256, 0, st>>>(groups, cord, gr, n_groups, cap, k, dict_capacity, ws.d_acc, B.flags);
   k_dict_finalize<<<grid, 256, 0, st>>>(ws.d_acc, k, dict_capacity, dict_len, dict_inc, dict_count);
 }
 

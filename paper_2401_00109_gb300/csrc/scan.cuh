@@ -35,15 +35,31 @@ __device__ __forceinline__ long long block_exclusive_scan(long long v, long long
   return before + x - v;
 }
 
+// A thread's kScanItems consecutive inputs from k: one or two 16-byte loads
+// when `vec` (both arrays 16-byte aligned) and all four are in range.
 template <typename T>
-static __global__ void k_scan_tile_sums(const T* in, long long n, long long* tile_sums) {
+__device__ __forceinline__ void scan_load4(const T* in, long long k, long long n, bool vec, long long (&v)[4]) {
+  static_assert(kScanItems == 4, "four items per thread");
+  if (vec && k + 3 < n) {
+    if constexpr (sizeof(T) == 4) {
+      const int4 w = *(const int4*)(in + k);
+      v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+    } else {
+      const longlong2 a = *(const longlong2*)(in + k), b = *(const longlong2*)(in + k + 2);
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    return;
+  }
+  for (int i = 0; i < 4; ++i) v[i] = k + i < n ? (long long)in[k + i] : 0;
+}
+
+template <typename T>
+static __global__ void k_scan_tile_sums(const T* in, long long n, long long* tile_sums, bool vec) {
   __shared__ long long sw[kScanThreads / 32];
   const long long base = (long long)blockIdx.x * kScanTile;
-  long long v = 0;
-  for (int i = 0; i < kScanItems; ++i) {
-    const long long k = base + (long long)threadIdx.x * kScanItems + i;
-    if (k < n) v += (long long)in[k];
-  }
+  long long vals[kScanItems];
+  scan_load4(in, base + (long long)threadIdx.x * kScanItems, n, vec, vals);
+  const long long v = vals[0] + vals[1] + vals[2] + vals[3];
   long long total;
   block_exclusive_scan<T>(v, sw, total);
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
@@ -72,22 +88,24 @@ static __global__ void k_scan_tile_offsets(long long* tile_sums, long long n_til
 }
 
 template <typename T>
-static __global__ void k_scan_apply(const T* in, long long n, const long long* tile_off, long long* out) {
+static __global__ void k_scan_apply(const T* in, long long n, const long long* tile_off, long long* out, bool vec) {
   __shared__ long long sw[kScanThreads / 32];
   const long long base = (long long)blockIdx.x * kScanTile;
+  const long long k0 = base + (long long)threadIdx.x * kScanItems;
   long long vals[kScanItems];
-  long long v = 0;
-  for (int i = 0; i < kScanItems; ++i) {
-    const long long k = base + (long long)threadIdx.x * kScanItems + i;
-    vals[i] = k < n ? (long long)in[k] : 0;
-    v += vals[i];
-  }
+  scan_load4(in, k0, n, vec, vals);
+  const long long v = vals[0] + vals[1] + vals[2] + vals[3];
   long long total;
-  long long ex = block_exclusive_scan<T>(v, sw, total) + tile_off[blockIdx.x];
-  for (int i = 0; i < kScanItems; ++i) {
-    const long long k = base + (long long)threadIdx.x * kScanItems + i;
-    if (k < n) out[k] = ex;
-    ex += vals[i];
+  const long long ex = block_exclusive_scan<T>(v, sw, total) + tile_off[blockIdx.x];
+  const long long o0 = ex, o1 = o0 + vals[0], o2 = o1 + vals[1], o3 = o2 + vals[2];
+  if (vec && k0 + 3 < n) {
+    *(longlong2*)(out + k0) = make_longlong2(o0, o1);
+    *(longlong2*)(out + k0 + 2) = make_longlong2(o2, o3);
+  } else {
+    if (k0 < n) out[k0] = o0;
+    if (k0 + 1 < n) out[k0 + 1] = o1;
+    if (k0 + 2 < n) out[k0 + 2] = o2;
+    if (k0 + 3 < n) out[k0 + 3] = o3;
   }
 }
 
@@ -98,9 +116,10 @@ static __global__ void k_store_total(const long long* total, long long* dst) { *
 template <typename T>
 inline void exclusive_scan(const T* in, long long n, long long* out, long long* tiles, cudaStream_t st) {
   const long long n_tiles = (n + kScanTile - 1) / kScanTile;
-  if (n_tiles > 0) k_scan_tile_sums<T><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(in, n, tiles);
+  const bool vec = ((size_t)in % 16) == 0 && ((size_t)out % 16) == 0;
+  if (n_tiles > 0) k_scan_tile_sums<T><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(in, n, tiles, vec);
   k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tiles, n_tiles, tiles + n_tiles);
-  if (n_tiles > 0) k_scan_apply<T><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(in, n, tiles, out);
+  if (n_tiles > 0) k_scan_apply<T><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(in, n, tiles, out, vec);
   k_store_total<<<1, 1, 0, st>>>(tiles + n_tiles, out + n);
 }
 
