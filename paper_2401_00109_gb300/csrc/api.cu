@@ -139,7 +139,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     const long long slots = (G < cells ? G : cells) + 1;
     B.cX = (float*)take(4 * G);
     B.cY = (float*)take(4 * G);
-    B.cov = (unsigned char*)take((G > 0 ? G : 1) + 64);  // 16-byte loads read past the last item
+    B.cov = (unsigned*)take(cov_bitmap_bytes(G));
     B.chg_list = (int*)take(8 * (G > 0 ? G : 1));
     // two buffers: the one-phase rounds mark a round's starts in the next round
     if (base) B.slots = slots;

@@ -34,6 +34,11 @@ struct PerDevice {
 // Member counts up to this have tabulated reciprocals for the exact centres.
 constexpr int kRecipCnt = 4096;
 
+// Bytes of the merge's coverage bitmap for cap items: whole 16-byte groups
+// of words (128 items each) plus one group of padding (a warp's 16-byte
+// loads may read past the last item).
+inline size_t cov_bitmap_bytes(long long cap) { return (size_t)(((cap > 0 ? cap : 1) + 127) / 128 + 1) * 16; }
+
 struct MergeBufs {
   int* bounds = nullptr;             // [4] ordered-int min/max of the FP32 coordinates
   unsigned* bar = nullptr;           // [16] grid barrier generation and round counters
@@ -53,7 +58,7 @@ struct MergeBufs {
   unsigned long long* state = nullptr;  // [cap]
   float* cX = nullptr;               // [cap] FP32 coordinates in cell order
   float* cY = nullptr;
-  unsigned char* cov = nullptr;      // [cap + 64] covered flags (cell order)
+  unsigned* cov = nullptr;           // covered flags (cell order), one bit per item
   int* chg_list = nullptr;           // [2 * cap] cells that changed (per round parity)
   long long slots = 0;               // slots of one buffer of s_* (two buffers)
   int* s_pos = nullptr;              // [2 * slots] new starts of a round: sorted position

@@ -730,7 +730,7 @@ struct RoundArgs {
   const int* cell_id;
   const int* cell_of_id;
   unsigned long long* state;
-  unsigned char* cov;       // [t] item covered by a start; maintained for undecided cells only
+  unsigned* cov;            // [t / 32] bit t: item covered by a start; maintained for undecided cells only
   // the starts created in the current round, in slot order (the order of the
   // packed counter, so s_base is non-decreasing)
   int* s_pos;               // [slots] sorted position of the start
@@ -844,39 +844,43 @@ __device__ bool grid_barrier_n(unsigned* bar, unsigned* sub, unsigned nblocks, u
   return ok_s != 0;
 }
 
-// Bits 0..3 = bytes 0..3 of w are zero (flags hold 0 or 1).
-__device__ __forceinline__ unsigned zero_nibble(unsigned w) {
-  const unsigned m = ~w & 0x01010101u;
-  return (m | (m >> 7) | (m >> 14) | (m >> 21)) & 0xFu;
+// Coverage flags: one bit per item (cell order), set with atomicOr (bits
+// only go from 0 to 1), read through L2 (other SMs set them).
+__device__ __forceinline__ bool cov_test(const unsigned* cov, int u) { return (__ldcg(&cov[u >> 5]) >> (u & 31)) & 1u; }
+__device__ __forceinline__ void cov_set(unsigned* cov, int u) { atomicOr(&cov[u >> 5], 1u << (u & 31)); }
+
+// Bits of the 32 items from `base` that lie in [lo, hi).
+__device__ __forceinline__ unsigned range_bits(int base, int lo, int hi) {
+  const int a = max(lo - base, 0), b = min(hi - base, 32);
+  if (b <= a) return 0u;
+  return (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) & (0xFFFFFFFFu << a);
 }
 
-// First index in [t, end) whose cov flag is 0, else end (whole warp; four
-// 16-byte loads per lane in flight together, 2,048 flags per step, so a long
-// run of covered items in a dense cell costs few dependent trips; the buffer
-// is padded past its last item).
-__device__ __forceinline__ int first_uncovered(const unsigned char* cov, int t, int end) {
+// First index in [t, end) whose coverage bit is 0, else end (whole warp;
+// four 16-byte loads per lane in flight together: 16,384 flags per
+// dependent step, so a long covered run in a dense cell costs few trips; the
+// bitmap is padded past its last item).
+__device__ __forceinline__ int first_uncovered(const unsigned* cov, int t, int end) {
   const int lane = threadIdx.x & 31;
-  for (int b = t & ~15; b < end; b += 2048) {
-    unsigned msk[4];
+  for (int b = t & ~127; b < end; b += 16384) {
+    int hit[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int o = b + k * 512 + lane * 16;
-      msk[k] = 0;
+      const int o = b + k * 4096 + lane * 128;
+      hit[k] = -1;
       if (o < end) {
-        const uint4 w = __ldcg((const uint4*)(cov + o));  // L2: flags written by other SMs
-        msk[k] = zero_nibble(w.x) | (zero_nibble(w.y) << 4) | (zero_nibble(w.z) << 8) | (zero_nibble(w.w) << 12);
-        if (t > o) msk[k] &= 0xFFFFu << (t - o < 16 ? t - o : 16);
-        if (end - o < 16) msk[k] &= (1u << (end - o)) - 1u;
+        const uint4 w = __ldcg((const uint4*)(cov + (o >> 5)));
+        const unsigned z[4] = {~w.x & range_bits(o, t, end), ~w.y & range_bits(o + 32, t, end),
+                               ~w.z & range_bits(o + 64, t, end), ~w.w & range_bits(o + 96, t, end)};
+#pragma unroll
+        for (int q = 3; q >= 0; --q)
+          if (z[q]) hit[k] = o + 32 * q + __ffs(z[q]) - 1;
       }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, msk[k] != 0);
-      if (bal) {
-        const int l = __ffs(bal) - 1;
-        const unsigned mm = __shfl_sync(0xFFFFFFFFu, msk[k], l);
-        return b + k * 512 + l * 16 + __ffs(mm) - 1;
-      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit[k] >= 0);
+      if (bal) return __shfl_sync(0xFFFFFFFFu, hit[k], __ffs(bal) - 1);
     }
   }
   return end;
@@ -955,7 +959,7 @@ __device__ __forceinline__ bool eval_cell(const RoundArgs& R, const GridGeom& g,
         if (u < qe) {
           const int r = R.cord[u];
           past = r >= p;
-          if (!past && !__ldcg(&R.cov[u]) &&
+          if (!past && !cov_test(R.cov, u) &&
               filter_c(R.cX[u], R.cY[u], px, py, R.V.a2lo, R.V.a2hi) != 0)
             hit = true;
         }
@@ -1044,12 +1048,12 @@ __device__ __forceinline__ void cover_units(const RoundArgs& R, long long soff, 
       const int t0 = __shfl_sync(0xFFFFFFFFu, lo_l, k) + (int)(u - pk) * kCoverUnit;
       const int t1 = min(t0 + kCoverUnit, R.cell_end[q]);
       int rr[kCoverUnit / 32];
-      unsigned char cv[kCoverUnit / 32];
+      bool cv[kCoverUnit / 32];
 #pragma unroll
       for (int i = 0; i < kCoverUnit / 32; ++i) {
         const int tt = t0 + i * 32 + lane;
         rr[i] = tt < t1 ? __ldg(&R.cord[tt]) : -1;
-        cv[i] = tt < t1 ? __ldcg(&R.cov[tt]) : (unsigned char)1;
+        cv[i] = tt < t1 ? cov_test(R.cov, tt) : true;
       }
       bool any = false;
 #pragma unroll
@@ -1059,7 +1063,7 @@ __device__ __forceinline__ void cover_units(const RoundArgs& R, long long soff, 
           int f = filter_c(spx, spy, __ldg(&R.cX[tt]), __ldg(&R.cY[tt]), R.V.a2lo, R.V.a2hi);
           if (f == 2) f = exact_within_sorted(R.V, sp, rr[i]) ? 1 : 0;
           if (f) {
-            R.cov[tt] = 1;
+            cov_set(R.cov, tt);
             any = true;
           }
         }
@@ -1294,17 +1298,17 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       yielded = true;
       break;
     }
-    unsigned char h[4];
+    bool h[4];
     int r[4];
     float ux[4], uy[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int u = t + i * 32 + lane;
-      h[i] = 1;
+      h[i] = true;
       r[i] = 0;
       ux[i] = uy[i] = 0.f;
       if (u < end) {
-        h[i] = __ldcg(&R.cov[u]);
+        h[i] = cov_test(R.cov, u);
         r[i] = R.cord[u];
         ux[i] = R.cX[u];
         uy[i] = R.cY[u];
@@ -1317,7 +1321,7 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       const int u = t + i * 32 + lane;
       bool unc = false;
       if (!h[i]) {  // also false past the end
-        if (covered_by_starts(R.V, W, ns5, r[i], ux[i], uy[i])) R.cov[u] = 1;  // hint: covered by a decided start
+        if (covered_by_starts(R.V, W, ns5, r[i], ux[i], uy[i])) cov_set(R.cov, u);  // hint: covered by a decided start
         else unc = true;
       }
       const unsigned b = __ballot_sync(0xFFFFFFFFu, unc);
@@ -1353,7 +1357,7 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
     unsigned pend = 0;  // neighbours (lane bits) still to scan from their second chunk
     {
       int nl[4], lo4[4], hi4[4], r4[4];
-      unsigned char h4[4];
+      bool h4[4];
       float x4[4], y4[4];
       bool v4[4];
       unsigned m = sm;
@@ -1369,11 +1373,11 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
         hi4[i] = __shfl_sync(0xFFFFFFFFu, hi, nl[i] >= 0 ? nl[i] : 0);
         const int u = lo4[i] + lane;
         v4[i] = nl[i] >= 0 && u < hi4[i];
-        h4[i] = 1;
+        h4[i] = true;
         r4[i] = 0x7FFFFFFF;
         x4[i] = y4[i] = 0.f;
         if (v4[i]) {
-          h4[i] = __ldcg(&R.cov[u]);
+          h4[i] = cov_test(R.cov, u);
           r4[i] = R.cord[u];
           x4[i] = R.cX[u];
           y4[i] = R.cY[u];
@@ -1407,7 +1411,7 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
         const int u = u0 + lane;
         bool past = true, hit = false;
         if (u < qe) {
-          const unsigned char hint = __ldcg(&R.cov[u]);
+          const bool hint = cov_test(R.cov, u);
           const int r = R.cord[u];
           const float ux = R.cX[u], uy = R.cY[u];
           past = r >= p;
@@ -1826,7 +1830,7 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
   k_clear_i32<<<grid, 256, 0, st>>>(B.cell_of_id, ws.cap_cells, -1);
-  cudaMemsetAsync(B.cov, 0, (size_t)(cap > 0 ? cap : 1) + 16, st);
+  cudaMemsetAsync(B.cov, 0, cov_bitmap_bytes(cap), st);
   cudaMemsetAsync(B.eval_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   cudaMemsetAsync(B.chg_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   k_mcell_fill<<<grid, 256, 0, st>>>(ckey, B.head, B.head_off, n_groups, cap, B.cell_beg, B.cell_end, B.cell_id,
