@@ -805,37 +805,34 @@ __device__ bool grid_barrier(unsigned* bar, unsigned* sub, unsigned nblocks, uns
   return ok_s != 0;
 }
 
-// The same barrier for a caller that counts its barriers: the generation
-// starts at 0 for the launch (k_minit), so barrier b of the launch completes
-// when the generation reaches b + 1 and the waiters need not read it first
-// (one dependent trip fewer per barrier).
+// The same barrier for a caller that counts its barriers (b = 0, 1, ...
+// within one launch), on counters that only grow (k_minit zeroes them before
+// the launch): barrier b is complete once the group counter of every group
+// has reached (b + 1) x its size, i.e. once the top counter, which the last
+// arrival of each group advances, reaches (b + 1) x the groups.  Every CTA
+// waits on the top counter itself: two dependent atomics and one poll per
+// barrier, with no resets.
 __device__ bool grid_barrier_n(unsigned* bar, unsigned* sub, unsigned nblocks, unsigned* status, unsigned b) {
   __shared__ int ok_s;
+  (void)bar;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
+    volatile unsigned* top = sub + 32 * kBarGroups;
     __threadfence();
     int ok = 1;
     const unsigned grp = blockIdx.x % kBarGroups;
     const unsigned gsz = nblocks / kBarGroups + (grp < nblocks % kBarGroups ? 1u : 0u);
     const unsigned ngrp = nblocks < kBarGroups ? nblocks : kBarGroups;
-    bool released = false;
-    if (atomicAdd(&sub[32 * grp], 1u) == gsz - 1) {
-      atomicExch(&sub[32 * grp], 0u);
-      if (atomicAdd(&sub[32 * kBarGroups], 1u) == ngrp - 1) {
-        atomicExch(&sub[32 * kBarGroups], 0u);
-        __threadfence();
-        atomicAdd(&bar[1], 1u);
-        released = true;
-      }
+    if (atomicAdd(&sub[32 * grp], 1u) == (b + 1u) * gsz - 1u) {
+      __threadfence();
+      atomicAdd(&sub[32 * kBarGroups], 1u);
     }
-    if (!released) {
-      unsigned spins = 0;
-      const unsigned lim = spin_limit(status);
-      while ((int)(*gen - (b + 1u)) < 0) {
-        if (++spins > lim) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
-        __nanosleep(32);
-      }
+    const unsigned target = (b + 1u) * ngrp;
+    unsigned spins = 0;
+    const unsigned lim = spin_limit(status);
+    while ((int)(*top - target) < 0) {
+      if (++spins > lim) { ok = 0; set_status(status, JABBA_ERR_TIMEOUT); break; }
+      __nanosleep(32);
     }
     __threadfence();
     ok_s = ok;
