@@ -59,6 +59,7 @@ struct MergeBufs {
   float* cX = nullptr;               // [cap] FP32 coordinates in cell order
   float* cY = nullptr;
   unsigned* cov = nullptr;           // covered flags (cell order), one bit per item
+  int4* cinfo = nullptr;             // [cap] per cell: start coordinates, first-item bound, end
   int* chg_list = nullptr;           // [2 * cap] cells that changed (per round parity)
   long long slots = 0;               // slots of one buffer of s_* (two buffers)
   int* s_pos = nullptr;              // [2 * slots] new starts of a round: sorted position

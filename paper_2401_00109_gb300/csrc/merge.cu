@@ -681,7 +681,7 @@ __global__ void k_mcell_heads(const unsigned long long* ckey_sorted, const int* 
 
 __global__ void k_mcell_fill(const unsigned long long* ckey_sorted, const int* head, const long long* head_off,
                              const long long* n_p, long long cap, int* cell_beg, int* cell_end, int* cell_id,
-                             int* cell_of_id, unsigned long long* state) {
+                             int* cell_of_id, unsigned long long* state, const int* cord, int4* cinfo) {
   const long long n = clamp_groups(n_p, cap);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     if (!head[t]) continue;
@@ -690,15 +690,21 @@ __global__ void k_mcell_fill(const unsigned long long* ckey_sorted, const int* h
     cell_id[j] = (int)ckey_sorted[t];
     cell_of_id[ckey_sorted[t]] = (int)j;
     state[j] = ((unsigned long long)(unsigned)t << 32) | 0xFFFFFFFFull;  // ptr = t, undecided
+    cinfo[j].x = 0x7FC00000;  // NaN: no start yet
+    cinfo[j].y = 0x7FC00000;
+    cinfo[j].z = cord[t];
   }
 }
 
 __global__ void k_mcell_end(const int* cell_beg, const long long* n_cells_p, const long long* n_p, long long cap,
-                            int* cell_end) {
+                            int* cell_end, int4* cinfo) {
   const long long nc = *n_cells_p;
   const long long n = clamp_groups(n_p, cap);
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += (long long)gridDim.x * blockDim.x)
-    cell_end[j] = j + 1 < nc ? cell_beg[j + 1] : (int)n;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += (long long)gridDim.x * blockDim.x) {
+    const int e = j + 1 < nc ? cell_beg[j + 1] : (int)n;
+    cell_end[j] = e;
+    cinfo[j].w = e;
+  }
 }
 
 // A bounded wait of the sort or of the rounds gave up: the kernels after it
@@ -731,6 +737,8 @@ struct RoundArgs {
   const int* cell_of_id;
   unsigned long long* state;
   unsigned* cov;            // [t / 32] bit t: item covered by a start; maintained for undecided cells only
+  int4* cinfo;              // [cell] FP32 start coordinates (bits; NaN until known), sorted position of the
+                            // first item not known covered (a lower bound), end (cell order)
   // the starts created in the current round, in slot order (the order of the
   // packed counter, so s_base is non-decreasing)
   int* s_pos;               // [slots] sorted position of the start
@@ -1237,8 +1245,12 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
     }
   }
   unsigned long long sq[3];
+  int4 ci[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) sq[i] = q[i] >= 0 ? ld_state(&R.state[q[i]]) : 0ull;
+  for (int i = 0; i < 3; ++i) {
+    sq[i] = q[i] >= 0 ? ld_state(&R.state[q[i]]) : 0ull;
+    ci[i] = q[i] >= 0 ? __ldcg(&R.cinfo[q[i]]) : make_int4(0, 0, 0, 0);
+  }
   int ns = 0, nu = 0, ns5 = 0;
   bool und[3];  // undecided when gathered (a cell decided since is skipped when evaluated)
   // two passes: the starts of the 5 x 5 block (the only ones that can cover
@@ -1255,9 +1267,14 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       const unsigned ms = __ballot_sync(0xFFFFFFFFu, is_s);
       if (is_s) {
         const int o = ns + __popc(ms & lt);
+        float sx = __int_as_float(ci[i].x), sy = __int_as_float(ci[i].y);
+        if (sx != sx || sy != sy) {  // the start's coordinates not visible yet: from the item
+          sx = R.V.sX[sv];
+          sy = R.V.sY[sv];
+        }
         W.sp[o] = (int)sv;
-        W.sx[o] = R.V.sX[sv];
-        W.sy[o] = R.V.sY[sv];
+        W.sx[o] = sx;
+        W.sy[o] = sy;
         W.sdx[o] = (signed char)dx;
         W.sdy[o] = (signed char)dy;
       }
@@ -1271,8 +1288,8 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
         const int lo = (int)(sq[i] >> 32);
         W.uq[o] = q[i];
         W.ulo[o] = lo;
-        W.uhi[o] = R.cell_end[q[i]];
-        W.ucd[o] = lo < R.item_cap ? R.cord[lo] : 0x7FFFFFFF;  // used only when lo < end
+        W.uhi[o] = ci[i].w;
+        W.ucd[o] = ci[i].z;  // at most the sorted position of item lo (used only when lo < end)
         W.udx[o] = (signed char)dx;
         W.udy[o] = (signed char)dy;
       }
@@ -1428,8 +1445,18 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
   const int tnew = yielded ? t : tp;
   const unsigned long long nsv = ((unsigned long long)(unsigned)tnew << 32) | result;
   if (nsv == st) return;
-  if (lane == 0) atomicExch(&R.state[j], nsv);
   const bool start = result < kNoStart;
+  if (lane == 0) {
+    // the cell's summary first (a reader that sees the new state with an
+    // older summary falls back to the items, or scans from an earlier item)
+    if (start) {
+      R.cinfo[j].x = __float_as_int(px);
+      R.cinfo[j].y = __float_as_int(py);
+    } else if (!yielded && tp < end) {
+      R.cinfo[j].z = p;
+    }
+    atomicExch(&R.state[j], nsv);
+  }
   // ---- coverage units of a new start (marked next round)
   if (start) {
     const unsigned cu = lane < nu ? (unsigned)((W.uhi[lane] - W.ulo[lane] + kCoverUnit - 1) / kCoverUnit) : 0u;
@@ -1831,8 +1858,8 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   cudaMemsetAsync(B.eval_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   cudaMemsetAsync(B.chg_stamp, 0, sizeof(unsigned) * (size_t)(cap > 0 ? cap : 1), st);
   k_mcell_fill<<<grid, 256, 0, st>>>(ckey, B.head, B.head_off, n_groups, cap, B.cell_beg, B.cell_end, B.cell_id,
-                                     B.cell_of_id, B.state);
-  k_mcell_end<<<grid, 256, 0, st>>>(B.cell_beg, B.head_off + cap, n_groups, cap, B.cell_end);
+                                     B.cell_of_id, B.state, cord, B.cinfo);
+  k_mcell_end<<<grid, 256, 0, st>>>(B.cell_beg, B.head_off + cap, n_groups, cap, B.cell_end, B.cinfo);
   MergeView V;
   V.groups = groups;
   V.rec = ws.m_rec;
@@ -1856,6 +1883,7 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   R.cell_of_id = B.cell_of_id;
   R.state = B.state;
   R.cov = B.cov;
+  R.cinfo = B.cinfo;
   R.s_pos = B.s_pos;
   R.s_base = B.s_base;
   R.s_pre = B.s_pre;
