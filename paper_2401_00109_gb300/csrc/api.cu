@@ -141,7 +141,7 @@ size_t layout(Scratch& w, long long S, long long D, long long slots, long long G
     B.cY = (float*)take(4 * G);
     B.cov = (unsigned*)take(cov_bitmap_bytes(G));
     B.cinfo = (int4*)take(16 * (G > 0 ? G : 1));
-    B.chg_list = (int*)take(8 * (G > 0 ? G : 1));
+    B.chg_list = (int*)take(16 * (G > 0 ? G : 1));
     // two buffers: the one-phase rounds mark a round's starts in the next round
     if (base) B.slots = slots;
     B.s_pos = (int*)take(4 * 2 * slots);

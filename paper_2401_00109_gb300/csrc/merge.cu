@@ -746,7 +746,8 @@ struct RoundArgs {
   unsigned* s_pre;          // [slots][26] first unit per neighbour k (entry 25: end)
   int* s_q;                 // [slots][25] neighbour cell to cover
   int* s_lo;                // [slots][25] first item (cell order) to test there
-  int* chg_list;            // [2][n_cells] cells whose state or coverage changed (by round parity)
+  int* chg_list;            // [2][n_cells] cells whose state or coverage changed (by round parity;
+                            // k_mrounds1: (cell, grid id) pairs, 2 ints each)
   unsigned* eval_stamp;     // [n_cells] last round + 1 in which the cell was evaluated
   unsigned* chg_stamp;      // [n_cells] last round + 1 in which the cell was listed as changed
   unsigned long long* nctr; // [2] packed new-start counters (by round parity)
@@ -1221,18 +1222,16 @@ __device__ __forceinline__ bool covered_by_starts_at(const MergeView& V, const N
 // neighbouring cell precedes p and may lie within alpha of it.  Loads that do
 // not depend on each other are issued together (the evaluations of a round
 // are latency bound).
-__device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigned round, NbScratch& W, int* lnxt,
-                           unsigned* lcnt_nxt, unsigned long long* uctr_nxt, long long soff) {
+__device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, int id, unsigned round, NbScratch& W,
+                           int2* lnxt, unsigned* lcnt_nxt, unsigned long long* uctr_nxt, long long soff) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   __syncwarp();  // the previous evaluation of this warp is done with W
   const unsigned long long st0 = ld_state(&R.state[j]);
-  const int id = R.cell_id[j];
   const int end = R.cell_end[j];
-  const unsigned long long st = __shfl_sync(0xFFFFFFFFu, st0, 0);
-  if ((unsigned)st != kUndecided) return;
   const int cx = id % g.ncx, cy = id / g.ncx;
-  // ---- gather: decided starts of the 9 x 9 block, undecided cells of the 5 x 5 block
+  // ---- gather: decided starts of the 9 x 9 block, undecided cells of the 5 x 5
+  // block (the neighbour indices are loaded beside the cell's own state)
   int q[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -1244,6 +1243,8 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
       if (xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy) q[i] = R.cell_of_id[yy * g.ncx + xx];
     }
   }
+  const unsigned long long st = __shfl_sync(0xFFFFFFFFu, st0, 0);
+  if ((unsigned)st != kUndecided) return;
   unsigned long long sq[3];
   int4 ci[3];
 #pragma unroll
@@ -1507,9 +1508,17 @@ __device__ void eval_cell1(const RoundArgs& R, const GridGeom& g, int j, unsigne
   unsigned lbase = 0;
   if (lane == 0) lbase = atomicAdd(lcnt_nxt, tot);
   lbase = __shfl_sync(0xFFFFFFFFu, lbase, 0);
-  if (c[0]) lnxt[lbase + __popc(m0 & lt)] = q[0];
-  if (c[1]) lnxt[lbase + n0 + __popc(m1 & lt)] = q[1];
-  if (c[2]) lnxt[lbase + n0 + n1 + __popc(m2 & lt)] = q[2];
+  // entries carry the cell's grid id beside its index (one dependent load
+  // fewer when the cell is evaluated)
+  int gid[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = i * 32 + lane;
+    gid[i] = k == 40 ? id : (cy + k / 9 - 4) * g.ncx + (cx + k % 9 - 4);
+  }
+  if (c[0]) lnxt[lbase + __popc(m0 & lt)] = make_int2(q[0], gid[0]);
+  if (c[1]) lnxt[lbase + n0 + __popc(m1 & lt)] = make_int2(q[1], gid[1]);
+  if (c[2]) lnxt[lbase + n0 + n1 + __popc(m2 & lt)] = make_int2(q[2], gid[2]);
 }
 
 template <int kWarps>
@@ -1528,11 +1537,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
   // entry: read together right after the previous round's barrier
   unsigned n_eval = 0;
   unsigned long long ctr = 0;
-  int j0 = 0;
+  int2 j0 = make_int2(0, 0);
   for (unsigned round = 0; round < R.max_rounds; ++round) {
     const int nxt = (round + 1) % 3, old = (round + 2) % 3;
-    const int* lcur = R.chg_list + (size_t)(round & 1) * stride;
-    int* lnxt = R.chg_list + (size_t)((round + 1) & 1) * stride;
+    const int2* lcur = (const int2*)R.chg_list + (size_t)(round & 1) * stride;
+    int2* lnxt = (int2*)R.chg_list + (size_t)((round + 1) & 1) * stride;
     // the counters of slot `old` were last read in the previous round
     if (warp_g == 0 && lane == 0) {
       R.lcnt[old] = 0;
@@ -1542,10 +1551,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
     const long long soff_new = (long long)(round & 1) * R.slot_stride;
     if (round == 0) {
       for (long long j = warp_g; j < n_cells; j += n_warps)
-        eval_cell1(R, g, (int)j, round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
+        eval_cell1(R, g, (int)j, R.cell_id[j], round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
     } else {
       for (long long i = warp_g; i < (long long)n_eval; i += n_warps)
-        eval_cell1(R, g, i == warp_g ? j0 : __ldcg(&lcur[i]), round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
+      {
+        const int2 e = i == warp_g ? j0 : __ldcg(&lcur[i]);
+        eval_cell1(R, g, e.x, e.y, round, w, lnxt, &R.lcnt[nxt], &R.uctr[nxt], soff_new);
+      }
       // coverage hints of the previous round's starts (warps from the top)
       const unsigned n_new = (unsigned)(ctr >> 40);
       const unsigned total = (unsigned)(ctr & kUnitMask);
@@ -1558,7 +1570,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mrounds1(RoundArgs R) {
     if (!grid_barrier_n(R.bar, R.bar_sub, nblocks, R.status, round)) return;
     // the next round's list entry is read beside its size (past the size it
     // is a stale entry of the buffer, not used)
-    j0 = warp_g < (long long)stride ? __ldcg(&lnxt[warp_g]) : 0;
+    j0 = warp_g < (long long)stride ? __ldcg(&lnxt[warp_g]) : make_int2(0, 0);
     n_eval = *((volatile unsigned*)&R.lcnt[nxt]);
     ctr = *((volatile unsigned long long*)&R.uctr[nxt]);
     if (n_eval == 0) {
