@@ -491,20 +491,33 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
       *(volatile unsigned long long*)mine = rs_word(tag, 2, run);
     } else {
       *(volatile unsigned long long*)mine = rs_word(tag, 1, run);
+      // walk back four tiles per dependent step (their words read together);
+      // a tile that has not published yet is polled until it has
       long long t = (long long)tile - 1;
       unsigned spins = 0;
       const unsigned lim = spin_limit(status_word);
-      while (t >= 0) {
-        const unsigned long long w = vs[t * 256 + d];
-        const unsigned wt = (unsigned)(w >> 33), st = (unsigned)(w >> 31) & 3u;
-        if (wt != tag || st == 0) {
+      bool done = false;
+      while (!done && t >= 0) {
+        unsigned long long w4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w4[k] = t - k >= 0 ? vs[(t - k) * 256 + d] : 0ull;
+        int k = 0;
+        for (; k < 4 && t - k >= 0; ++k) {
+          const unsigned long long w = w4[k];
+          const unsigned wt = (unsigned)(w >> 33), st = (unsigned)(w >> 31) & 3u;
+          if (wt != tag || st == 0) break;
+          excl += w & 0x7FFFFFFFull;
+          if (st == 2) {
+            done = true;
+            break;
+          }
+        }
+        if (done) break;
+        t -= k;
+        if (k < 4 && t >= 0) {  // tile t has not published: poll it again
           if (++spins > lim) { ok = 0; break; }
           if (spins > 64) __nanosleep(64);
-          continue;
         }
-        excl += w & 0x7FFFFFFFull;
-        if (st == 2) break;
-        --t;
       }
       __threadfence();
       *(volatile unsigned long long*)mine = rs_word(tag, 2, excl + run);
