@@ -196,19 +196,24 @@ def roofline_table(workload, n, N, G, D, comp_ms, loc_ms, rnd_ms, rounds_name, p
       local aggregation (tile kernels + routing + group offsets): 12 B per
         piece read (len, inc) + 4 B per piece written (label) + 48 B per group
         record + 12 B per domain (group count and offset);
-      merge rounds (k_mrounds1, or k_mrounds in the two-barrier form): 13 B per
-        local group (its FP32 centre, key-order position and coverage flag,
-        each read once).
+      merge rounds (k_mrounds1, or k_mrounds in the two-barrier form): 12.125 B
+        per local group (its FP32 centre and key-order position, 12 B, and its
+        coverage bit, each read once).
     DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is known for
-    the Stage I tiles of the scale workload from one ncu capture of its first
-    10,000 series (the five tile launches of a step: 223.2 MB read, 62.6 MB
-    written for 17,479,524 pieces), scaled to a launch by its pieces (the
-    traffic grows with them); null elsewhere."""
-    local_traffic = 285.827328e6 / 17479524 * N if workload == "scale" else None
-    cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N, None),
+    the scale workload from ncu captures of its first 10,000 series
+    (143,804,766 points, 17,479,524 pieces): k_compress 1,181.8 MB read and
+    216.4 MB written, scaled to a launch by its points; the five Stage I tile
+    launches of a step 222.5 MB read and 62.1 MB written, scaled by the
+    pieces (both stream their inputs once, so the traffic grows with them).
+    The rounds kernel's traffic is not scaled (the sample's working set fits
+    in L2, the full one does not): null there and for other workloads."""
+    scale = workload == "scale"
+    comp_traffic = 1398.107584e6 / 143804766 * n if scale else None
+    local_traffic = 284.588032e6 / 17479524 * N if scale else None
+    cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N, comp_traffic),
             ("local aggregation (k_local_tile x5, k_local_classify, k_local_warp, scan)", loc_ms,
              16.0 * N + 48.0 * G + 12.0 * D, local_traffic),
-            (rounds_name, rnd_ms, 13.0 * G, None)]
+            (rounds_name, rnd_ms, 12.125 * G, None)]
     by_kernel = []
     for name, ms_list, alg, traffic in cand:
         t = float(np.mean(ms_list))

@@ -26,13 +26,17 @@ def test_roofline_table_dominant_and_bytes(bench):
     assert r["ms_per_launch"] == 13.0
     ach = r["algorithmic_bytes_per_launch"] / 13e-3 / 1e9
     assert abs(r["achieved"] - ach) < 1e-9 * ach and abs(r["frac"] - ach / 6000.0) < 1e-12
-    # traffic: 16.35 B per piece of the capture, scaled by the pieces
-    assert abs(r["traffic"] - 285.827328e6 / 17479524 * N) < 1.0
+    # traffic: 16.28 B per piece of the capture, scaled by the pieces
+    assert abs(r["traffic"] - 284.588032e6 / 17479524 * N) < 1.0
     comp = r["by_kernel"][0]
-    assert comp["algorithmic_bytes_per_launch"] == 8.0 * n + 12.0 * N and comp["traffic"] is None
+    assert comp["algorithmic_bytes_per_launch"] == 8.0 * n + 12.0 * N
+    # compression: 9.72 B per point of the capture, scaled by the points
+    assert abs(comp["traffic"] - 1398.107584e6 / 143804766 * n) < 1.0
+    assert r["by_kernel"][2]["traffic"] is None
 
 
 def test_roofline_table_other_workload_has_no_traffic(bench):
     r = bench.roofline_table("multivar", 10, 5, 2, 1, [1.0], [1.0], [3.0], "k_mrounds", 100.0, "fallback")
     assert r["kernel"] == "k_mrounds" and r["traffic"] is None and r["peak_source"] == "fallback"
-    assert r["algorithmic_bytes_per_launch"] == 13.0 * 2
+    assert r["algorithmic_bytes_per_launch"] == 12.125 * 2
+    assert all(k["traffic"] is None for k in r["by_kernel"])
