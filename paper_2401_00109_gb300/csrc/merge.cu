@@ -1762,42 +1762,67 @@ __global__ void __launch_bounds__(256) k_dict_accumulate(const jabba_group* grou
   const int lane = threadIdx.x & 31;
   const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp_g * 32; base < G; base += n_warps * 32) {
-    const long long t = base + lane;
-    const bool valid = t < G;
-    int gid = -1;
-    long long v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (valid) {
-      const int2 q = gr[cord[t]];
-      gid = q.x;
-      const jabba_group g = groups[q.y];
-      v[0] = g.count;
-      v[1] = g.lensum;
-      I192 w;
-      w.w0 = g.inc[0];
-      w.w1 = g.inc[1];
-      w.w2 = g.inc[2];
-      limbs6(w, v + 2);
-    }
-    const int gprev = __shfl_up_sync(0xFFFFFFFFu, gid, 1);
-    const bool head = lane == 0 || gprev != gid;
-    bool f = head;
-    for (int o = 1; o < 32; o <<= 1) {
-      const bool fu = __shfl_up_sync(0xFFFFFFFFu, f, o);
+  // two chunks of 32 items per step, their gathers in flight together
+  for (long long base = warp_g * 64; base < G; base += n_warps * 64) {
+    int2 q[2];
+    jabba_group gg[2];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const long long vu = __shfl_up_sync(0xFFFFFFFFu, v[i], o);
-        if (lane >= o && !f) v[i] += vu;
+    for (int c = 0; c < 2; ++c) {
+      const long long t = base + 32 * c + lane;
+      q[c] = t < G ? gr[cord[t]] : make_int2(-1, -1);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (q[c].y >= 0) gg[c] = groups[q[c].y];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (base + 32 * c >= G) break;
+      const bool valid = q[c].y >= 0;
+      const int gid = valid ? q[c].x : -1;
+      // member count, length sum, and the increment sum in three limbs
+      // (bits 0-47 and 48-95 unsigned, bits 96-159 signed: the sums are far
+      // below 2^159 in magnitude, and 32 limbs of 48 bits fit a 64-bit
+      // word): five words per lane in the scan instead of eight
+      long long v[5] = {0, 0, 0, 0, 0};
+      if (valid) {
+        const jabba_group& g = gg[c];
+        v[0] = g.count;
+        v[1] = g.lensum;
+        v[2] = (long long)(g.inc[0] & 0xFFFFFFFFFFFFull);
+        v[3] = (long long)((g.inc[0] >> 48) | ((g.inc[1] & 0xFFFFFFFFull) << 16));
+        v[4] = (long long)((g.inc[1] >> 32) | (g.inc[2] << 32));
       }
-      if (lane >= o) f = f || fu;
-    }
-    const bool next_head = __shfl_down_sync(0xFFFFFFFFu, head, 1);
-    const bool tail = valid && (lane == 31 || next_head);
-    if (tail && gid >= 0 && gid < K) {
-      long long* e = acc + (long long)gid * 8;
+      const int gprev = __shfl_up_sync(0xFFFFFFFFu, gid, 1);
+      const bool head = lane == 0 || gprev != gid;
+      bool f = head;
+      for (int o = 1; o < 32; o <<= 1) {
+        const bool fu = __shfl_up_sync(0xFFFFFFFFu, f, o);
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (v[i]) atomicAdd((unsigned long long*)&e[i], (unsigned long long)v[i]);
+        for (int i = 0; i < 5; ++i) {
+          const long long vu = __shfl_up_sync(0xFFFFFFFFu, v[i], o);
+          if (lane >= o && !f) v[i] += vu;
+        }
+        if (lane >= o) f = f || fu;
+      }
+      const bool next_head = __shfl_down_sync(0xFFFFFFFFu, head, 1);
+      const bool tail = valid && (lane == 31 || next_head);
+      if (tail && gid >= 0 && gid < K) {
+        // back to the accumulators' layout: count, length sum, six 32-bit limbs
+        I192 w;
+        w.w0 = (u64)v[2];
+        w.w1 = 0;
+        w.w2 = 0;
+        add192(w, (u64)v[3] << 48, (u64)v[3] >> 16, 0);
+        add192(w, 0, (u64)v[4] << 32, (u64)(v[4] >> 32));
+        long long out[8];
+        out[0] = v[0];
+        out[1] = v[1];
+        limbs6(w, out + 2);
+        long long* e = acc + (long long)gid * 8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (out[i]) atomicAdd((unsigned long long*)&e[i], (unsigned long long)out[i]);
+      }
     }
   }
 }
