@@ -736,8 +736,8 @@ __global__ void k_clear_i32(int* p, long long n, int v) {
 // not known to be covered.
 constexpr unsigned kUndecided = 0xFFFFFFFFu;
 constexpr unsigned kNoStart = 0xFFFFFFFEu;
-constexpr int kCoverUnit = 256;    // items of one neighbour cell per phase-B work unit (8 per lane)
-constexpr int kScanChunks = 2;     // chunks of 32 a blocking scan reads before it waits instead
+constexpr int kCoverUnit = 128;    // items of one neighbour cell per phase-B work unit (4 per lane)
+constexpr int kScanChunks = 4;     // chunks of 32 a blocking scan reads before it waits instead
 constexpr unsigned long long kUnitMask = (1ull << 40) - 1;  // packed counter: starts << 40 | units
 
 struct RoundArgs {
