@@ -1609,28 +1609,45 @@ __global__ void k_mcheck(const unsigned long long* state, const long long* n_cel
 // share one cell and its 5 x 5 neighbourhood (broadcast loads).
 __global__ void __launch_bounds__(256) k_mlabel(MergeView V, const int* cord, const float* cX, const float* cY,
                                                const int* cell_of_id, const unsigned long long* state,
-                                               const GridGeom* geom, const int* flags, const long long* n_p,
-                                               long long cap, int* lab, int* is_start) {
+                                               const int4* cinfo, const GridGeom* geom, const int* flags,
+                                               const long long* n_p, long long cap, int* lab, int* is_start) {
   if (flags[0] || flags[1]) return;
   const long long n = clamp_groups(n_p, cap);
   const GridGeom g = *geom;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int a = cord[t];
-    const int id = cell_of(g, cX[t], cY[t]);
+    const float xa = cX[t], ya = cY[t];  // the item's FP32 coordinates (cell order)
+    const int id = cell_of(g, xa, ya);
     const int cx = id % g.ncx, cy = id / g.ncx;
+    // the 5 x 5 block's cells, then their states and summaries (start
+    // coordinates), each level's loads in flight together
+    int q[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) {
+      const int xx = cx + k % 5 - 2, yy = cy + k / 5 - 2;
+      q[k] = xx >= 0 && xx < g.ncx && yy >= 0 && yy < g.ncy ? cell_of_id[yy * g.ncx + xx] : -1;
+    }
+    unsigned sv[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) sv[k] = q[k] >= 0 ? (unsigned)state[q[k]] : kNoStart;
     int best = 0x7FFFFFFF;
-    for (int dy = -2; dy <= 2; ++dy) {
-      const int yy = cy + dy;
-      if (yy < 0 || yy >= g.ncy) continue;
-      for (int dx = -2; dx <= 2; ++dx) {
-        const int xx = cx + dx;
-        if (xx < 0 || xx >= g.ncx) continue;
-        const int q = cell_of_id[yy * g.ncx + xx];
-        if (q < 0) continue;
-        const unsigned s = (unsigned)state[q];
-        if (s >= kNoStart || (int)s > a || (int)s >= best) continue;
-        if ((int)s == a || within_sorted(V, (int)s, a)) best = (int)s;
+#pragma unroll
+    for (int k = 0; k < 25; ++k) {
+      const int sp = (int)sv[k];
+      if (sv[k] >= kNoStart || sp > a || sp >= best) continue;
+      if (sp == a) {
+        best = a;
+        continue;
       }
+      const int4 ci = cinfo[q[k]];
+      float sx = __int_as_float(ci.x), sy = __int_as_float(ci.y);
+      if (sx != sx || sy != sy) {  // (always written by the rounds; the item's copy otherwise)
+        sx = V.sX[sp];
+        sy = V.sY[sp];
+      }
+      int f = filter_c(sx, sy, xa, ya, V.a2lo, V.a2hi);
+      if (f == 2) f = exact_within_sorted(V, sp, a) ? 1 : 0;
+      if (f) best = sp;
     }
     lab[a] = best;
     is_start[a] = best == a ? 1 : 0;
@@ -1986,8 +2003,8 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
   k_mcheck<<<grid, 256, 0, st>>>(B.state, B.head_off + cap, B.flags, status);
   k_clear_i32<<<grid, 256, 0, st>>>(B.is_start, cap, 0);
-  k_mlabel<<<grid, 256, 0, st>>>(V, cord, B.cX, B.cY, B.cell_of_id, B.state, B.geom, B.flags, n_groups, cap, B.lab,
-                                 B.is_start);
+  k_mlabel<<<grid, 256, 0, st>>>(V, cord, B.cX, B.cY, B.cell_of_id, B.state, B.cinfo, B.geom, B.flags, n_groups,
+                                 cap, B.lab, B.is_start);
   // sequential fallback (only acts when flags[0] is set)
   k_mexact_prep<<<grid, 256, 0, st>>>(groups, item_X, item_Y, ws.m_rec, sidx, n_groups, cap, sigma, scl, key_mode,
                                       B.flags, B.eX, B.eY, B.ekey);
