@@ -900,17 +900,30 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
           acc[g].cnt_len = 0;
         }
         tile_sync<W>();
-        for (int i = t; i < n; i += T) {
-          const int g = plab[i] - g0;
-          if (g < 0 || g >= gn) continue;
-          bool neg;
-          const U128 m = fx_mag(pinc[i], neg);          // < 2^96 under the range contract
-          long long l0 = (long long)(m.lo & 0xFFFFFFFFFFFFull);
-          long long l1 = (long long)((m.lo >> 48) | (m.hi << 16));
-          if (neg) { l0 = -l0; l1 = -l1; }
-          atomicAdd((unsigned long long*)&acc[g].lo48, (unsigned long long)l0);
-          atomicAdd((unsigned long long*)&acc[g].hi48, (unsigned long long)l1);
-          atomicAdd(&acc[g].cnt_len, (1ull << 40) | (unsigned long long)(unsigned)plen[i]);
+        // four pieces' loads in flight together, then their atomics
+        for (int i0 = t; i0 < n; i0 += 4 * T) {
+          int L4[4], g4[4];
+          double I4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * T;
+            g4[u] = i < n ? plab[i] - g0 : -1;
+            L4[u] = i < n ? plen[i] : 0;
+            I4[u] = i < n ? pinc[i] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int g = g4[u];
+            if (g < 0 || g >= gn) continue;
+            bool neg;
+            const U128 m = fx_mag(I4[u], neg);          // < 2^96 under the range contract
+            long long l0 = (long long)(m.lo & 0xFFFFFFFFFFFFull);
+            long long l1 = (long long)((m.lo >> 48) | (m.hi << 16));
+            if (neg) { l0 = -l0; l1 = -l1; }
+            atomicAdd((unsigned long long*)&acc[g].lo48, (unsigned long long)l0);
+            atomicAdd((unsigned long long*)&acc[g].hi48, (unsigned long long)l1);
+            atomicAdd(&acc[g].cnt_len, (1ull << 40) | (unsigned long long)(unsigned)L4[u]);
+          }
         }
         tile_sync<W>();
         for (int g = t; g < gn; g += T) {
