@@ -97,10 +97,15 @@ void launch_build_domains(const long long* series_off, long long n_series, int m
 // Otherwise the whole warp evaluates the binary64 definition for that lane
 // (32 terms at a time, exact fixed-point sum): see warp_exact_admissible.
 constexpr unsigned kQuickPollLimit = 1024;  // run-time poll limits below this poll without suspending
-constexpr int kChunk = 16;                 // points per lane per stage
+// Stage size and CTA shape: one bulk copy stages kChunk points of a lane, so
+// larger chunks mean fewer copies per point; 48-point chunks in CTAs of 4
+// warps (two resident per SM by shared memory) were the fastest of the
+// shapes swept on the scale workload (16 to 64 points, 2 to 8 warps).
+constexpr int kChunk = 48;                 // points per lane per stage
 constexpr int kRow = kChunk + 2;           // doubles per staged row (16-byte multiple, alignment slack)
-constexpr int kWarpsPerCta = 8;
+constexpr int kWarpsPerCta = 4;
 constexpr int kStages = 2;
+constexpr size_t kStageBytes = sizeof(double) * kWarpsPerCta * kStages * 32 * kRow;  // dynamic shared memory
 
 struct CompressParams {
   const double* x;
@@ -317,7 +322,8 @@ __device__ __forceinline__ void step(const CompressParams& P, LaneState& L, cons
 }
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) k_compress(CompressParams P) {
-  __shared__ __align__(16) double stage[kWarpsPerCta][kStages][32][kRow];
+  extern __shared__ __align__(16) unsigned char stage_raw[];
+  double(*stage)[kStages][32][kRow] = reinterpret_cast<double(*)[kStages][32][kRow]>(stage_raw);
   __shared__ __align__(8) unsigned long long bars[kWarpsPerCta][kStages];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane < kStages) mbar_init(smem_u32(&bars[warp][lane]), 32);
@@ -723,7 +729,12 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
   const long long n_tasks = (n_domains + 31) / 32;
   int per_sm = ws.tune.compress_ctas_per_sm;
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 3) per_sm = 3;  // 2 are resident at the kernel's register count; a third CTA per SM waits for a slot
+  if (per_sm > 3) per_sm = 3;  // 2 are resident (shared memory); a third CTA per SM waits for a slot
+  static PerDevice attr;
+  attr.get([] {
+    cudaFuncSetAttribute(k_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+    return 1;
+  });
   long long ctas = (long long)ws.num_sms * per_sm;
   const long long need = (n_tasks + kWarpsPerCta - 1) / kWarpsPerCta;
   if (ctas > need) ctas = need;
@@ -739,7 +750,7 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
     for (long long d = 0; d < n_domains; ++d) {
       Q.dom_order = ws.dom_order + d;
       Q.task_counter = ws.plain_ctr + d;
-      k_compress<<<1, kWarpsPerCta * 32, 0, st>>>(Q);
+      k_compress<<<1, kWarpsPerCta * 32, kStageBytes, st>>>(Q);
     }
   } else {
     if (ws.tune.compress_pack) {
@@ -747,7 +758,7 @@ void launch_compress(const double* x, long long n_points, const long long* dom_b
     } else if (n_domains > 0) {
       k_dom_iota<<<(unsigned)(ws.num_sms * 4), 256, 0, st>>>(n_domains, ws.dom_order);
     }
-    if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, 0, st>>>(P);
+    if (ctas > 0) k_compress<<<(unsigned)ctas, kWarpsPerCta * 32, kStageBytes, st>>>(P);
   }
   mark(mk.a1, st);
   mark(mk.b0, st);
