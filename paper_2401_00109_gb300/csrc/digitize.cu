@@ -496,20 +496,20 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
 // starts follow one another; each start's window is scanned 32 W pieces per
 // step, one ballot per warp and one barrier per step).  Domains are routed to
 // the smallest tile that holds them (k_local_classify), so small domains run
-// many warps per SM.  After the sort, the W * 1024 histogram bytes serve as
+// many warps per SM.  After the sort, the W * 512 histogram bytes serve as
 // scratch: the binary64 keys of an overlapping-key run, then the greedy's
 // per-warp next-start candidates.
 //
-// Per-tile shared memory: W * 1024 histogram bytes, then per piece 4 B key
+// Per-tile shared memory: W * 512 histogram bytes, then per piece 4 B key
 // (later sY), 4 B sort temp (later sX), 2 B position, 2 B sort temp (later
 // labels by position), 2 B label by sorted index, and 128 misc bytes.  The
 // FP32 key of a piece is recomputed from (sX, sY) by the same expression that
 // produced the sorted key, so it is not kept; after the greedy the 8 CAP bytes
-// of sX/sY hold the group accumulators (32 B per group, CAP / 4 per pass).
+// of sX/sY hold the group accumulators (24 B per group, CAP / 4 per pass).
 template <int W, int CAP>
 struct TileCfg {
   static constexpr int kThreads = 32 * W;
-  static constexpr size_t kBytes = (size_t)W * 1024 + (size_t)CAP * 14 + 128;
+  static constexpr size_t kBytes = (size_t)W * 512 + (size_t)CAP * 14 + 128;
   // W = 1: independent warps per CTA, as many as fit in ~56 KB (at most 8)
   static constexpr int kTilesPerCta = W > 1 ? 1 : (57344 / (int)kBytes < 1 ? 1 : (57344 / (int)kBytes > 8 ? 8 : 57344 / (int)kBytes));
   static constexpr int kBlock = kThreads * kTilesPerCta;
@@ -557,11 +557,13 @@ __device__ __forceinline__ bool tile_sync_or(bool p) {
 // warps of a tile: warp w ranks the contiguous segment [w seg, (w+1) seg) of
 // the input into digit-major, warp-minor positions, so equal digits keep
 // their input order.  Thread t owns the 256 / (32 W) consecutive digits
-// starting at t * 256 / (32 W) for the offset scan.  hist: W x 256 counters;
-// wsum: W words.  The result is back in (key, val) after four passes.
+// starting at t * 256 / (32 W) for the offset scan.  hist: W x 256 16-bit
+// counters (a tile holds at most 4,096 pieces; counts are added through the
+// 32-bit word that holds two counters); wsum: W words.  The result is back in
+// (key, val) after four passes.
 template <int W>
 __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* tk, unsigned short* tv, int n,
-                                  unsigned* hist, unsigned* wsum) {
+                                  unsigned short* hist, unsigned* wsum) {
   constexpr int T = 32 * W;
   constexpr int PER = 256 / T;
   static_assert(PER * T == 256, "W must divide 8");
@@ -571,15 +573,19 @@ __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
   const int seg = (((n + W - 1) / W) + 31) & ~31;
   const int lo = w * seg;
   const int hi = min(n, lo + seg);
-  unsigned* h = hist + w * 256;
+  unsigned short* h = hist + w * 256;
+  unsigned* hw = (unsigned*)h;  // the same counters, two per word
   unsigned* kin = key;
   unsigned short* vin = val;
   unsigned* kout = tk;
   unsigned short* vout = tv;
   for (int shift = 0; shift < 32; shift += 8) {
-    for (int i = lane; i < 256; i += 32) h[i] = 0;
+    for (int i = lane; i < 128; i += 32) hw[i] = 0;
     __syncwarp();
-    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&h[(kin[i] >> shift) & 255u], 1u);
+    for (int i = lo + lane; i < hi; i += 32) {
+      const unsigned d = (kin[i] >> shift) & 255u;
+      atomicAdd(&hw[d >> 1], 1u << (16 * (d & 1u)));
+    }
     tile_sync<W>();
     {
       const int d0 = t * PER;
@@ -590,7 +596,7 @@ __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
         unsigned run = 0;
         for (int v = 0; v < W; ++v) {
           const unsigned c = hist[v * 256 + d0 + k];
-          hist[v * 256 + d0 + k] = run;
+          hist[v * 256 + d0 + k] = (unsigned short)run;
           run += c;
         }
         tot[k] = run;
@@ -610,7 +616,7 @@ __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
       unsigned ex = before + incl - sum;
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
-        for (int v = 0; v < W; ++v) hist[v * 256 + d0 + k] += ex;
+        for (int v = 0; v < W; ++v) hist[v * 256 + d0 + k] = (unsigned short)(hist[v * 256 + d0 + k] + ex);
         ex += tot[k];
       }
     }
@@ -629,7 +635,7 @@ __device__ void tile_radix_sort16(unsigned* key, unsigned short* val, unsigned* 
         vout[pos] = vv;
       }
       __syncwarp();
-      if (v && r == 0) h[d] += __popc(peers);
+      if (v && r == 0) h[d] = (unsigned short)(h[d] + __popc(peers));
       __syncwarp();
     }
     tile_sync<W>();
@@ -649,8 +655,8 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
   const int tile = threadIdx.x / T;          // W == 1: one tile per warp
   const int t = threadIdx.x % T;
   unsigned char* base = smem_raw + (size_t)tile * Cfg::kBytes;
-  unsigned* hist = (unsigned*)base;                                  // W * 256 words
-  unsigned* key = (unsigned*)(base + W * 1024);                      // [CAP] sorted keys, then sY
+  unsigned short* hist = (unsigned short*)base;                      // W * 256 16-bit counters
+  unsigned* key = (unsigned*)(base + W * 512);                       // [CAP] sorted keys, then sY
   unsigned* tk = key + CAP;                                          // [CAP] sort temp, then sX
   unsigned short* idx = (unsigned short*)(tk + CAP);                 // [CAP] sorted index -> position
   unsigned short* tv = idx + CAP;                                    // [CAP] sort temp, then labels by position
