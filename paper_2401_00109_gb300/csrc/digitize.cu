@@ -502,14 +502,16 @@ __global__ void __launch_bounds__(kLocWarps * 32) k_local_warp(LocalParams P) {
 //
 // Per-tile shared memory: W * 512 histogram bytes, then per piece 4 B key
 // (later sY), 4 B sort temp (later sX), 2 B position, 2 B sort temp (later
-// labels by position), 2 B label by sorted index, and 128 misc bytes.  The
-// FP32 key of a piece is recomputed from (sX, sY) by the same expression that
-// produced the sorted key, so it is not kept; after the greedy the 8 CAP bytes
-// of sX/sY hold the group accumulators (24 B per group, CAP / 4 per pass).
+// the label by sorted index), and 128 misc bytes: 12 B per piece, so the
+// 2,048-piece tile of 4 warps fits 8 CTAs per SM.  The FP32 key of a piece is
+// recomputed from (sX, sY) by the same expression that produced the sorted
+// key, so it is not kept; after the greedy the 8 CAP bytes of sX/sY hold the
+// group accumulators (24 B per group, CAP / 4 per pass: 6 CAP bytes) and the
+// labels by position (the last 2 CAP bytes).
 template <int W, int CAP>
 struct TileCfg {
   static constexpr int kThreads = 32 * W;
-  static constexpr size_t kBytes = (size_t)W * 512 + (size_t)CAP * 14 + 128;
+  static constexpr size_t kBytes = (size_t)W * 512 + (size_t)CAP * 12 + 128;
   // W = 1: independent warps per CTA, as many as fit in ~56 KB (at most 8)
   static constexpr int kTilesPerCta = W > 1 ? 1 : (57344 / (int)kBytes < 1 ? 1 : (57344 / (int)kBytes > 8 ? 8 : 57344 / (int)kBytes));
   static constexpr int kBlock = kThreads * kTilesPerCta;
@@ -659,13 +661,13 @@ __global__ void __launch_bounds__(TileCfg<W, CAP>::kBlock) k_local_tile(LocalPar
   unsigned* key = (unsigned*)(base + W * 512);                       // [CAP] sorted keys, then sY
   unsigned* tk = key + CAP;                                          // [CAP] sort temp, then sX
   unsigned short* idx = (unsigned short*)(tk + CAP);                 // [CAP] sorted index -> position
-  unsigned short* tv = idx + CAP;                                    // [CAP] sort temp, then labels by position
-  short* lab = (short*)(tv + CAP);                                   // [CAP] label by sorted index
-  int* misc = (int*)(lab + CAP);                                     // 32 words
+  unsigned short* tv = idx + CAP;                                    // [CAP] sort temp, then labels by sorted index
+  int* misc = (int*)(tv + CAP);                                      // 32 words
+  short* lab = (short*)tv;
   float* sX = (float*)tk;
   float* sY = (float*)key;
-  short* plab = (short*)tv;
-  GroupAcc* acc = (GroupAcc*)key;                                    // after the greedy: CAP / 4 groups
+  GroupAcc* acc = (GroupAcc*)key;                                    // after the greedy: CAP / 4 groups (6 CAP bytes)
+  short* plab = (short*)((unsigned char*)key + 6 * CAP);             // after the greedy: labels by position
   unsigned* wsum = (unsigned*)(misc + 4);                            // [W] sort scan
   long long* gbase_s = (long long*)(misc + 16);                      // group record base
   const double a2 = __dmul_rn(P.alpha, P.alpha);
