@@ -785,7 +785,7 @@ def tune_inflight(pipelines, base: dict, steps: int = 4, finalists: int = 4, fin
     m_opts = [(1, 8), (2, 8), (1, 4), (2, 4)] if base.get("merge_form", 1) == 1 else [(1, 8), (2, 8)]
     first = []
     for c_sm in (1, 2):
-        for cap in (2, 3, 4):
+        for cap in (2, 3, 4, 6):
             for m_sm, m_w in m_opts:
                 cfg = dict(base, compress_ctas_per_sm=c_sm, local_ctas_cap=cap, merge_ctas_per_sm=m_sm,
                            merge_warps=m_w)
