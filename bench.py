@@ -201,15 +201,15 @@ def roofline_table(workload, n, N, G, D, comp_ms, loc_ms, rnd_ms, rounds_name, p
         coverage bit, each read once).
     DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) is known for
     the scale workload from ncu captures of its first 10,000 series
-    (143,804,766 points, 17,479,524 pieces): k_compress 1,181.8 MB read and
-    216.4 MB written, scaled to a launch by its points; the five Stage I tile
-    launches of a step 222.5 MB read and 62.1 MB written, scaled by the
+    (143,804,766 points, 17,479,524 pieces): k_compress 1,184.6 MB read and
+    212.7 MB written, scaled to a launch by its points; the five Stage I tile
+    launches of a step 222.6 MB read and 60.7 MB written, scaled by the
     pieces (both stream their inputs once, so the traffic grows with them).
     The rounds kernel's traffic is not scaled (the sample's working set fits
     in L2, the full one does not): null there and for other workloads."""
     scale = workload == "scale"
-    comp_traffic = 1398.107584e6 / 143804766 * n if scale else None
-    local_traffic = 284.588032e6 / 17479524 * N if scale else None
+    comp_traffic = 1397.301728e6 / 143804766 * n if scale else None
+    local_traffic = 283.246592e6 / 17479524 * N if scale else None
     cand = [("k_compress", comp_ms, 8.0 * n + 12.0 * N, comp_traffic),
             ("local aggregation (k_local_tile x5, k_local_classify, k_local_warp, scan)", loc_ms,
              16.0 * N + 48.0 * G + 12.0 * D, local_traffic),

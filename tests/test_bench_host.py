@@ -26,12 +26,12 @@ def test_roofline_table_dominant_and_bytes(bench):
     assert r["ms_per_launch"] == 13.0
     ach = r["algorithmic_bytes_per_launch"] / 13e-3 / 1e9
     assert abs(r["achieved"] - ach) < 1e-9 * ach and abs(r["frac"] - ach / 6000.0) < 1e-12
-    # traffic: 16.28 B per piece of the capture, scaled by the pieces
-    assert abs(r["traffic"] - 284.588032e6 / 17479524 * N) < 1.0
+    # traffic: 16.20 B per piece of the capture, scaled by the pieces
+    assert abs(r["traffic"] - 283.246592e6 / 17479524 * N) < 1.0
     comp = r["by_kernel"][0]
     assert comp["algorithmic_bytes_per_launch"] == 8.0 * n + 12.0 * N
     # compression: 9.72 B per point of the capture, scaled by the points
-    assert abs(comp["traffic"] - 1398.107584e6 / 143804766 * n) < 1.0
+    assert abs(comp["traffic"] - 1397.301728e6 / 143804766 * n) < 1.0
     assert r["by_kernel"][2]["traffic"] is None
 
 
