@@ -366,13 +366,21 @@ def run_ours(args, ws, rank, local):
             di_host[:k].copy_(pl.b["dict_inc"][:k], non_blocking=True)
             dc_host[:k].copy_(pl.b["dict_count"][:k], non_blocking=True)
 
+        e2e_tuning = tuning
         if inflight is not None:
             # the same two pipelines: the host->device copies run back to back
             # on a copy stream of their own (the copy of a step waits only
             # until the front half of the step two before it, on the same
             # pipeline, has read its input), each step waits for its copy,
             # runs, and copies its symbols and dictionary out on its stream,
-            # so the link stays busy while the kernels of the steps overlap
+            # so the link stays busy while the kernels of the steps overlap.
+            # The steps run in the single-batch configuration: the link sets
+            # the pace, and the copies, not the other batch's kernels, fill
+            # the time beside each step, so each step's own latency counts
+            # (the in-flight caps lengthen it).
+            for q in (pl, pl2):
+                q.ctx.set_tuning(tuning)
+            fl = jb.InFlight([pl, pl2])
             syms = [sym_host, torch.empty_like(sym_host).pin_memory()]
             dicts = [(dl_host, di_host, dc_host),
                      tuple(torch.empty_like(t).pin_memory() for t in (dl_host, di_host, dc_host))]
@@ -431,7 +439,7 @@ def run_ours(args, ws, rank, local):
         bi = 8 * n + 8 * (S + 1)
         bo = 4 * N + 24 * k
         e2e = dict(value=ws * n / (ems * 1e-3) / 1e9, unit="Gpts/s", h2d_bytes_per_step=bi, d2h_bytes_per_step=bo,
-                   ms_per_step=ems, batches_in_flight=2 if inflight is not None else 1)
+                   ms_per_step=ems, batches_in_flight=2 if inflight is not None else 1, tuning=e2e_tuning)
         ctx.sync_status(where="e2e steps")
 
     # ---- plain: the unbatched form (one compression launch and one Stage I

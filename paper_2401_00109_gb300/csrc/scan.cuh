@@ -65,20 +65,47 @@ static __global__ void k_scan_tile_sums(const T* in, long long n, long long* til
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-// One block scans the tile sums in place (exclusive), any number of tiles:
-// thread t owns the contiguous range [t c, (t+1) c) of c = ceil(n / threads)
-// tiles, sums it, the block scans the per-thread sums once, and every thread
-// writes its range's prefixes (one block-wide scan instead of one per 256
-// tiles).
-static __global__ void k_scan_tile_offsets(long long* tile_sums, long long n_tiles, long long* grand_total) {
-  __shared__ long long sw[kScanThreads / 32];
-  const long long per = (n_tiles + kScanThreads - 1) / kScanThreads;
+// One block of kOffThreads scans the tile sums in place (exclusive), any
+// number of tiles: thread t owns the contiguous range [t c, (t+1) c) of
+// c = ceil(n / threads) tiles, sums it, the block scans the per-thread sums
+// once, and every thread writes its range's prefixes (one block-wide scan
+// instead of one per 256 tiles).
+constexpr int kOffThreads = 1024;
+
+__device__ __forceinline__ long long block_exclusive_scan_1024(long long v, long long* smem_warp, long long& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = smem_warp[lane];  // 32 warps
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    smem_warp[lane] = w;
+  }
+  __syncthreads();
+  total = smem_warp[31];
+  const long long before = warp ? smem_warp[warp - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+static __global__ void __launch_bounds__(kOffThreads) k_scan_tile_offsets(long long* tile_sums, long long n_tiles,
+                                                                         long long* grand_total) {
+  __shared__ long long sw[kOffThreads / 32];
+  const long long per = (n_tiles + kOffThreads - 1) / kOffThreads;
   const long long lo = (long long)threadIdx.x * per;
   const long long hi = lo + per < n_tiles ? lo + per : n_tiles;
   long long v = 0;
   for (long long k = lo; k < hi; ++k) v += tile_sums[k];
   long long total;
-  long long run = block_exclusive_scan<long long>(v, sw, total);
+  long long run = block_exclusive_scan_1024(v, sw, total);
   for (long long k = lo; k < hi; ++k) {
     const long long c = tile_sums[k];
     tile_sums[k] = run;
@@ -118,7 +145,7 @@ inline void exclusive_scan(const T* in, long long n, long long* out, long long* 
   const long long n_tiles = (n + kScanTile - 1) / kScanTile;
   const bool vec = ((size_t)in % 16) == 0 && ((size_t)out % 16) == 0;
   if (n_tiles > 0) k_scan_tile_sums<T><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(in, n, tiles, vec);
-  k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tiles, n_tiles, tiles + n_tiles);
+  k_scan_tile_offsets<<<1, kOffThreads, 0, st>>>(tiles, n_tiles, tiles + n_tiles);
   if (n_tiles > 0) k_scan_apply<T><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(in, n, tiles, out, vec);
   k_store_total<<<1, 1, 0, st>>>(tiles + n_tiles, out + n);
 }
