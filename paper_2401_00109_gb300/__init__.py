@@ -751,7 +751,7 @@ class InFlight:
             s.wait_stream(cur)
 
 
-def tune_inflight(pipelines, base: dict, steps: int = 4, finalists: int = 4, final_steps: int = 10):
+def tune_inflight(pipelines, base: dict, steps: int = 4, finalists: int = 4, final_steps: int = 20):
     """Pick the launch configuration of two batches in flight: the front
     half's kernels must leave room on every SM for the other batch's
     cooperative merge, so the resident CTAs per SM of compression, of the
