@@ -414,7 +414,10 @@ def run_ours(args, ws, rank, local):
                     fl.step(wait_copy, d2h)
 
             cs.wait_stream(st)
-            e2e_steps(2)
+            # two untimed steps per pipeline (a trace of this leg showed the
+            # copies right after the first step of each pipeline running at
+            # half the link rate once, then at full rate)
+            e2e_steps(4)
             fl.join()
             torch.cuda.synchronize()
             barrier(ws)

@@ -389,7 +389,8 @@ struct RsScratch {
   unsigned* epoch;             // [1]
 };
 
-__global__ void __launch_bounds__(256) k_rs_global_hist(const unsigned long long* keys, const long long* n_p,
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_rs_global_hist(const KeyT* keys, const long long* n_p,
                                                        long long cap, int passes, unsigned* ghist,
                                                        const int* flags) {
   __shared__ unsigned h[kRsPasses][256];
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(256) k_rs_global_hist(const unsigned long long
   for (int i = threadIdx.x; i < kRsPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long k = keys[i];
+    const KeyT k = keys[i];
     for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
   }
   __syncthreads();
@@ -427,8 +428,9 @@ __global__ void k_rs_bases(const unsigned* ghist, int passes, unsigned* gbase, u
   if (threadIdx.x == 0) *epoch += 1;
 }
 
+template <typename KeyT>
 struct RsSmem {
-  unsigned long long key[kRsTile];
+  KeyT key[kRsTile];
   int val[kRsTile];
   unsigned wh[kRsWarps][256];
   unsigned lstart[256];      // first local position of each digit
@@ -442,12 +444,13 @@ __device__ __forceinline__ unsigned long long rs_word(unsigned tag, unsigned sta
   return ((unsigned long long)tag << 33) | ((unsigned long long)state << 31) | v;
 }
 
-__global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long long* kin, const int* vin,
-                                                          unsigned long long* kout, int* vout, const long long* n_p,
+template <typename KeyT>
+__global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const KeyT* kin, const int* vin,
+                                                          KeyT* kout, int* vout, const long long* n_p,
                                                           long long cap, int pass, RsScratch R, long long n_tiles,
                                                           const int* flags, unsigned* status_word) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  RsSmem& S = *(RsSmem*)smem_raw;
+  RsSmem<KeyT>& S = *(RsSmem<KeyT>*)smem_raw;
   // after an error (a look-back of an earlier pass gave up, so the keys no
   // longer match the digit histograms) the remaining passes do nothing
   const long long n = (flags[1] || *(volatile unsigned*)status_word) ? 0 : clamp_groups(n_p, cap);
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
   if (base >= n) return;  // tiles are taken in order: every later tile is empty too
   const unsigned tag = ((*R.epoch) * kRsPasses + (unsigned)pass) & 0x7FFFFFFFu;
   const long long wbase = base + (long long)warp * kRsPerWarp;
-  unsigned long long kr[kRsPerLane];
+  KeyT kr[kRsPerLane];
   int vr[kRsPerLane];
   for (int i = lane; i < 256; i += 32) S.wh[warp][i] = 0;
   __syncwarp();
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
   for (int j = 0; j < kRsPerLane; ++j) {
     const long long k = wbase + j * 32 + lane;
     const bool valid = k < n;
-    kr[j] = valid ? kin[k] : 0ull;
+    kr[j] = valid ? kin[k] : (KeyT)0;
     vr[j] = valid ? vin[k] : 0;
     if (valid) atomicAdd(&S.wh[warp][(unsigned)(kr[j] >> shift) & 255u], 1u);
   }
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_pass(const unsigned long l
   __syncthreads();
   const int in_tile = (int)(n - base < kRsTile ? n - base : kRsTile);
   for (int i = threadIdx.x; i < in_tile; i += kRsThreads) {
-    const unsigned long long key = S.key[i];
+    const KeyT key = S.key[i];
     const unsigned dgt = (unsigned)(key >> shift) & 255u;
     const long long pos = S.gpos[dgt] + (i - (long long)S.lstart[dgt]);
     kout[pos] = key;
@@ -581,15 +584,17 @@ long long rs_hist_words(long long cap) {
   return 2 * kRsPasses * 256 + 64 + 2 * 256 * n_tiles;
 }
 
-// Stable sort of (keys, vals) by the low `bits` bits of the keys; the result
-// ends in the buffers returned through kres/vres.
-static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, const long long* n_p,
+// Stable sort of (keys, vals) by the low `bits` bits of the keys (64-bit
+// keys, or 32-bit ones when bits <= 32: fewer bytes moved per pass); the
+// result ends in the buffers returned through kres/vres.
+template <typename KeyT>
+static void radix_sort(KeyT* k0, int* v0, KeyT* k1, int* v1, const long long* n_p,
                        long long cap, int bits, unsigned* hist_words, int num_sms, unsigned* status_word,
-                       unsigned long long** kres, int** vres, const int* flags, cudaStream_t st) {
+                       KeyT** kres, int** vres, const int* flags, cudaStream_t st) {
   const long long n_tiles = (cap + kRsTile - 1) / kRsTile;
   static PerDevice attr;
   attr.get([] {
-    cudaFuncSetAttribute(k_rs_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem));
+    cudaFuncSetAttribute(k_rs_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RsSmem<KeyT>));
     return 1;
   });
   // Fixed header (histograms, tile counters, epoch) first, status words after
@@ -602,19 +607,19 @@ static void radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1, 
   R.epoch = R.tile_ctr + 16;
   R.status = (unsigned long long*)(hist_words + 2 * kRsPasses * 256 + 64);
   const int passes = (bits + 7) / 8;
-  unsigned long long* kin = k0;
-  unsigned long long* kout = k1;
+  KeyT* kin = k0;
+  KeyT* kout = k1;
   int* vin = v0;
   int* vout = v1;
   if (n_tiles > 0) {
     cudaMemsetAsync(R.ghist, 0, sizeof(unsigned) * kRsPasses * 256, st);
-    k_rs_global_hist<<<(unsigned)(num_sms * 4), 256, 0, st>>>(k0, n_p, cap, passes, R.ghist, flags);
+    k_rs_global_hist<KeyT><<<(unsigned)(num_sms * 4), 256, 0, st>>>(k0, n_p, cap, passes, R.ghist, flags);
     k_rs_bases<<<1, 32 * kRsPasses, 0, st>>>(R.ghist, passes, R.gbase, R.tile_ctr, R.epoch);
   }
   for (int pass = 0; pass < passes && n_tiles > 0; ++pass) {
-    k_rs_pass<<<(unsigned)n_tiles, kRsThreads, sizeof(RsSmem), st>>>(kin, vin, kout, vout, n_p, cap, pass, R,
-                                                                     n_tiles, flags, status_word);
-    unsigned long long* tk = kin; kin = kout; kout = tk;
+    k_rs_pass<KeyT><<<(unsigned)n_tiles, kRsThreads, sizeof(RsSmem<KeyT>), st>>>(kin, vin, kout, vout, n_p, cap,
+                                                                                 pass, R, n_tiles, flags, status_word);
+    KeyT* tk = kin; kin = kout; kout = tk;
     int* tv = vin; vin = vout; vout = tv;
   }
   *kres = kin;
@@ -660,7 +665,7 @@ __device__ __forceinline__ int cell_of(const GridGeom& g, float x, float y) {
 
 __global__ void k_msorted(const int* sidx, const float* X32, const float* Y32, const long long* n_p, long long cap,
                           const GridGeom* geom, const int* flags, float* sX, float* sY,
-                          unsigned long long* ckey, int* cval) {
+                          unsigned* ckey, int* cval) {
   if (flags[1]) return;
   const long long n = clamp_groups(n_p, cap);
   const GridGeom g = *geom;
@@ -670,14 +675,14 @@ __global__ void k_msorted(const int* sidx, const float* X32, const float* Y32, c
     const float x = X32[c], y = Y32[c];
     sX[a] = x;
     sY[a] = y;
-    ckey[a] = fb ? 0ull : (unsigned long long)cell_of(g, x, y);
+    ckey[a] = fb ? 0u : (unsigned)cell_of(g, x, y);
     cval[a] = (int)a;
   }
 }
 
 // Cell table: cells in id order; cell_of_id[id] = cell index or -1.  Also
 // the FP32 coordinates in cell order.
-__global__ void k_mcell_heads(const unsigned long long* ckey_sorted, const int* cord, const float* sX,
+__global__ void k_mcell_heads(const unsigned* ckey_sorted, const int* cord, const float* sX,
                               const float* sY, const long long* n_p, long long cap, const int* flags, int* head,
                               float* cX, float* cY) {
   const long long n = clamp_groups(n_p, cap);
@@ -692,7 +697,7 @@ __global__ void k_mcell_heads(const unsigned long long* ckey_sorted, const int* 
   }
 }
 
-__global__ void k_mcell_fill(const unsigned long long* ckey_sorted, const int* head, const long long* head_off,
+__global__ void k_mcell_fill(const unsigned* ckey_sorted, const int* head, const long long* head_off,
                              const long long* n_p, long long cap, int* cell_beg, int* cell_end, int* cell_id,
                              int* cell_of_id, unsigned long long* state, const int* cord, int4* cinfo) {
   const long long n = clamp_groups(n_p, cap);
@@ -1910,13 +1915,16 @@ void launch_merge(const jabba_group* groups, const double* item_X, const double*
   k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
   k_mgeom<<<1, 1, 0, st>>>(B.bounds, alpha, ws.cap_cells, B.geom, B.flags, n_groups, cap);
   // the cell sort ping-pongs in the buffers the key sort left free
-  unsigned long long* ck0 = skey == ws.m_k0 ? ws.m_k1 : ws.m_k0;
+  // (32-bit cell keys in the 64-bit buffers; each buffer still holds the
+  // 8 bytes per item that the (global id, record) pairs need later)
+  unsigned* ck0 = (unsigned*)(skey == ws.m_k0 ? ws.m_k1 : ws.m_k0);
   int* cv0 = sidx == ws.m_v0 ? ws.m_v1 : ws.m_v0;
   k_msorted<<<grid, 256, 0, st>>>(sidx, ws.m_X32, ws.m_Y32, n_groups, cap, B.geom, B.flags, B.sX, B.sY, ck0, cv0);
-  unsigned long long* ckey;
+  unsigned* ckey;
   int* cord;
-  // cell ids are below cap_cells = 2^23: three 8-bit passes order them
-  radix_sort(ck0, cv0, B.ck1, B.cv1, n_groups, cap, 24, ws.m_hist, ws.num_sms, status, &ckey, &cord, B.flags, st);
+  // cell ids are below cap_cells = 2^23: three 8-bit passes over 32-bit keys order them
+  radix_sort<unsigned>(ck0, cv0, (unsigned*)B.ck1, B.cv1, n_groups, cap, 24, ws.m_hist, ws.num_sms, status, &ckey,
+                       &cord, B.flags, st);
   k_mflag_status<<<1, 1, 0, st>>>(B.flags, status);
   k_mcell_heads<<<grid, 256, 0, st>>>(ckey, cord, B.sX, B.sY, n_groups, cap, B.flags, B.head, B.cX, B.cY);
   exclusive_scan<int>(B.head, cap, B.head_off, ws.scan_tiles, st);  // head_off[cap] = number of cells
