@@ -365,7 +365,8 @@ jabba_status jabba_mse(jabba_ctx* ctx, const double* x, const double* xhat, int6
  * each; larger domains by the number of warps chosen here.
  * Defaults: {2, 1, 4, 4, 4, 0, 1, 0, 1, 8}. */
 typedef struct {
-  int32_t compress_ctas_per_sm; /* resident CTAs per SM of the persistent compression kernel: 1..3            */
+  int32_t compress_ctas_per_sm; /* CTAs (of 4 warps) per SM of the persistent compression kernel: 1..3; two
+                                   are resident at once (shared memory), a third waits for a slot         */
   int32_t compress_pack;        /* 1 = domains handed to warps longest first (length packing), 0 = in order    */
   int32_t local_mid_warps;      /* warps that aggregate one domain of 1025..2048 pieces together: 1, 2, 4, 8   */
   int32_t local_big_warps;      /* warps that aggregate one domain of 2049..4096 pieces together: 4 or 8       */
